@@ -1,0 +1,118 @@
+"""Seeded synthetic inputs shared by the tests, the bench and the oracle runs.
+
+This module only builds inputs: Hermitian test matrices with a prescribed
+spectrum, the correlated perturbations of a problem sequence and random start
+blocks.  It contains none of the eigensolver's arithmetic.  Every generator
+takes an integer seed and a torch device; the same seed on the same device
+type gives the same tensor.
+
+Workload shapes follow the paper's DFT workloads (Sec. 4.1.4, Sec. 6.1):
+a dense low band of eigenvalues below a sparse tail, and sequences whose
+consecutive problems differ by a small Hermitian perturbation.
+"""
+
+from __future__ import annotations
+
+import math
+
+import torch
+
+__all__ = [
+    "generator",
+    "gaussian_block",
+    "unitary_qr",
+    "unitary_dft",
+    "spectrum_clustered",
+    "spectrum_dft",
+    "spectrum_uniform",
+    "hermitian_from",
+    "hermitian_noise",
+]
+
+
+def generator(seed: int, device="cpu") -> torch.Generator:
+    g = torch.Generator(device=torch.device(device))
+    g.manual_seed(int(seed))
+    return g
+
+
+def gaussian_block(n: int, b: int, seed: int, device="cpu") -> torch.Tensor:
+    """i.i.d. complex Gaussian block (n x b, complex128, column-major storage)."""
+    g = generator(seed, device)
+    re = torch.randn(b, n, dtype=torch.float64, device=device, generator=g)
+    im = torch.randn(b, n, dtype=torch.float64, device=device, generator=g)
+    # store as the transpose of a contiguous (b, n) tensor: columns are contiguous
+    return torch.complex(re, im).mul_(1.0 / math.sqrt(2.0)).t()
+
+
+def unitary_qr(n: int, seed: int, device="cpu") -> torch.Tensor:
+    """Random unitary: QR of an i.i.d. complex Gaussian, phases fixed so that
+    R has a positive real diagonal (Haar distributed)."""
+    g = generator(seed, device)
+    re = torch.randn(n, n, dtype=torch.float64, device=device, generator=g)
+    im = torch.randn(n, n, dtype=torch.float64, device=device, generator=g)
+    z = torch.complex(re, im)
+    q, r = torch.linalg.qr(z)
+    d = torch.diagonal(r)
+    ph = d / d.abs()
+    return q * ph[None, :]
+
+
+def unitary_dft(n: int, seed: int, device="cpu") -> torch.Tensor:
+    """Dense structured unitary ``D1 F D2 F D3`` (F the unitary DFT, D_i
+    random phase diagonals).  O(n^2 log n) to form, unitary to rounding."""
+    g = generator(seed, device)
+    ph = torch.rand(3, n, dtype=torch.float64, device=device, generator=g) * (2.0 * math.pi)
+    d = torch.polar(torch.ones_like(ph), ph)
+    x = torch.diag(d[2])
+    x = torch.fft.fft(x, dim=0, norm="ortho")
+    x = x * d[1][:, None]
+    x = torch.fft.fft(x, dim=0, norm="ortho")
+    return x * d[0][:, None]
+
+
+def spectrum_clustered(n: int, seed: int, n_cluster: int = 60, device="cpu") -> torch.Tensor:
+    """``n_cluster`` values U[-1, -0.9] and the rest U(-0.9, 1]; ascending."""
+    g = generator(seed, device)
+    lo = -1.0 + 0.1 * torch.rand(n_cluster, dtype=torch.float64, device=device, generator=g)
+    hi = -0.9 + 1.9 * (1.0 - torch.rand(n - n_cluster, dtype=torch.float64, device=device,
+                                       generator=g))
+    return torch.sort(torch.cat([lo, hi])).values
+
+
+def spectrum_dft(n: int, seed: int, device="cpu") -> torch.Tensor:
+    """DFT-like density: n/4 values U[-2, 0] (dense low band) and 3n/4 values
+    ``50 u^2``, u ~ U(0, 1] (sparse tail up to 50, no gap); ascending."""
+    g = generator(seed, device)
+    nb = n // 4
+    band = -2.0 + 2.0 * torch.rand(nb, dtype=torch.float64, device=device, generator=g)
+    u = 1.0 - torch.rand(n - nb, dtype=torch.float64, device=device, generator=g)
+    return torch.sort(torch.cat([band, 50.0 * u * u])).values
+
+
+def spectrum_uniform(n: int, seed: int, device="cpu") -> torch.Tensor:
+    g = generator(seed, device)
+    return torch.sort(-1.0 + 2.0 * torch.rand(n, dtype=torch.float64, device=device,
+                                              generator=g)).values
+
+
+def hermitian_from(q: torch.Tensor, lam: torch.Tensor) -> torch.Tensor:
+    """``H = Q diag(lam) Q^H`` as a full (both triangles) Hermitian matrix,
+    stored column-major (the returned tensor is the transpose view of a
+    contiguous row-major array, so its columns are contiguous)."""
+    h = (q * lam.to(q.dtype)[None, :]) @ q.conj().t()
+    h = 0.5 * (h + h.conj().t())
+    # column-major storage: element (i, j) at j*n + i
+    return h.t().contiguous().t()
+
+
+def hermitian_noise(n: int, seed: int, device="cpu") -> torch.Tensor:
+    """``E = (G + G^H) / (2 sqrt(2n))`` with G i.i.d. complex Gaussian of unit
+    entry variance: off-diagonal variance 1/(4n), so the semicircle edge, and
+    ``||E||_2``, is close to 1."""
+    g = generator(seed, device)
+    re = torch.randn(n, n, dtype=torch.float64, device=device, generator=g)
+    im = torch.randn(n, n, dtype=torch.float64, device=device, generator=g)
+    z = torch.complex(re, im).mul_(1.0 / math.sqrt(2.0))
+    e = (z + z.conj().t()) * (1.0 / (2.0 * math.sqrt(2.0 * n)))
+    return e.t().contiguous().t()
