@@ -1,0 +1,230 @@
+/*
+ * chase.h -- C ABI of libchase: Chebyshev Accelerated Subspace iteration
+ * Eigensolver (ChASE, Winkelmann, Springer, Di Napoli, arXiv 1805.10121)
+ * for dense complex Hermitian matrices on one NVIDIA GB300 GPU (sm_103a).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Matrices are column-major complex128 with interleaved (re, im) doubles,
+ *   the layout of C99 `double complex` and `std::complex<double>` (the
+ *   paper's element type, Listing 1).  Element (i, j) of a matrix with
+ *   leading dimension ld sits at index j*ld + i.
+ * - H is Hermitian and stored in full (both triangles are read).  It is
+ *   never modified: the shift (A - cI) of Alg. 4 is applied inside the
+ *   product instead of on A (the paper's Shift() kernel, Listing 1).
+ * - Array arguments marked "host or device" may point to host memory or to
+ *   device memory of the current CUDA device; the library detects which
+ *   (cudaPointerGetAttributes).  Host arrays are staged through device
+ *   buffers that the library allocates and frees within the call.  All
+ *   arrays of one call must be of the same kind.
+ * - The caller owns every array it passes (the paper's ChaseBLAS takes
+ *   caller-owned buffers, Listing 2).  Device workspace needed beyond the
+ *   caller's arrays is allocated stream-ordered (cudaMallocAsync) on
+ *   `stream` and released before the call returns.
+ * - `stream` is a cudaStream_t (NULL = the legacy default stream).  Every
+ *   call returns after its work on `stream` has completed.
+ * - Every entry point returns a CHASE_* status; none aborts or throws.  On a
+ *   status other than CHASE_OK or CHASE_NOT_CONVERGED, chase_last_error()
+ *   returns a message for the calling thread.
+ */
+#ifndef CHASE_H_
+#define CHASE_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* complex128, interleaved */
+typedef struct {
+  double re, im;
+} chase_c64;
+
+/* ---- status codes ---- */
+#define CHASE_OK 0
+#define CHASE_INVALID_ARG 1       /* a size, pointer, degree or option is invalid */
+#define CHASE_NOT_CONVERGED 2     /* max_iter reached; outputs hold the current subspace (Sec. 5.3) */
+#define CHASE_QR_BREAKDOWN 3      /* orthogonalisation failed even with the shifted retry */
+#define CHASE_BOUND_VIOLATION 4   /* a Ritz value exceeded b_sup (Sec. 4.2: the bound must hold) */
+#define CHASE_CUDA_ERROR 5        /* a CUDA runtime call failed */
+#define CHASE_OUT_OF_MEMORY 6     /* device workspace could not be allocated */
+#define CHASE_TIMEOUT 7           /* a bounded wait inside a kernel gave up */
+#define CHASE_EIGENSOLVER_ERROR 8 /* the projected eigensolve (Alg. 2 line 3) failed */
+
+/* ---- arithmetic of the filter products ---- */
+#define CHASE_FP64 0 /* complex128 products on the FP64 tensor pipe (DMMA) */
+
+/* ---- residual test used for locking (Alg. 3 line 4) ---- */
+#define CHASE_CONV_ABS 0 /* Res <= tol (the paper's absolute criterion, Sec. 6.1) */
+#define CHASE_CONV_REL 1 /* Res <= tol * h, h = largest |Ritz value| seen (<= ||H||_2) */
+
+/* Configuration: the fields of Table 1 (ChaseConfig) plus build options. */
+typedef struct {
+  int deg;          /* initial / constant degree (Table 1: 20); rounded up to even */
+  int optim;        /* 1: per-column optimised degrees (Alg. 5); 0: constant deg (Table 1: false) */
+  int deg_extra;    /* DEGEXTRA of Alg. 5 line 5 (Table 1: 2) */
+  int deg_max;      /* DEGMAX of Alg. 5 line 5 (Table 1: 36) */
+  int max_iter;     /* cap on the while loop of Alg. 1 (Table 1: 25) */
+  int lanczos_iter; /* k, steps of each Lanczos run (Table 1: 25) */
+  int num_lanczos;  /* n_vec, density runs of Alg. 6 (Table 1: 4) */
+  int approx;       /* 1: V and Lambda hold an approximate solution (Sec. 3.3) */
+  double dos_sigma; /* Gaussian width of Eq. 10 in the variable mapped to [-1, 1] (Sec. 4.2: 0.25) */
+  int conv_mode;    /* CHASE_CONV_ABS or CHASE_CONV_REL */
+  int precision;    /* CHASE_FP64 */
+} chase_opts;
+
+/* Counters and per-phase times of one chase_solve call. */
+typedef struct {
+  int iterations;          /* while-loop iterations of Alg. 1 */
+  int nconv;               /* locked pairs */
+  long long matvecs;       /* column products with H: filter + RR + Lanczos (Sec. 6.1, footnote 6) */
+  long long filter_matvecs;/* column products inside the filter (= sum of the degrees) */
+  double b_sup, mu1, mu_nevnex; /* final spectral estimates (Sec. 4.2) */
+  double tol_eff;          /* the absolute residual threshold used for locking */
+  double flops_filter;     /* 8 N^2 * filter_matvecs + 8 N * (columns touched) */
+  double flops_total;      /* all algorithmic FLOPs of the solve */
+  double t_total, t_lanczos, t_filter, t_qr, t_rr, t_eigh, t_resid, t_host; /* seconds */
+} chase_stats;
+
+/* Fill `opts` with the defaults of Table 1 (double precision column):
+ * deg 20, optim 1 (the paper's default is false; this library's default is
+ * the optimised filter of Sec. 4.1), deg_extra 2, deg_max 36, max_iter 25,
+ * lanczos_iter 25, num_lanczos 4, approx 0, dos_sigma 0.25,
+ * conv_mode CHASE_CONV_REL, precision CHASE_FP64.
+ * Returns CHASE_INVALID_ARG if opts is NULL. */
+int chase_opts_default(chase_opts* opts);
+
+/* Message describing the last failure on the calling thread ("" if none).
+ * The string stays valid until the thread's next call into the library. */
+const char* chase_last_error(void);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (all entry points, all threads).  Instrumentation; never fails. */
+long long chase_kernel_launches(void);
+
+/* Chebyshev filter with per-column degrees: Alg. 4 with the three-term
+ * recurrence of Eq. 7, c = (b_sup + mu_nevnex)/2, e = (b_sup - mu_nevnex)/2,
+ * sigma_1 = e / (mu1 - c).  Column a of V is replaced by p_{m_a}(H) v_a with
+ * p_m the normalised Chebyshev polynomial of Eq. 5 (p_m(mu1) = 1).
+ *
+ * H        N x N, leading dimension ldh >= N (host or device)
+ * V        N x b, leading dimension ldv >= N, in/out (host or device);
+ *          columns keep the caller's order
+ * degrees  b ints, each even and in [2, 1024], any order (host or device).
+ *          Even degrees are required because the recurrence double-buffers
+ *          (Sec. 4.1.3, Alg. 5 line 6).  Internally the columns are sorted by
+ *          degree so that every product acts on a contiguous suffix; a column
+ *          leaves the products once it reaches its degree (Alg. 4 lines 12-14).
+ * work     N x b device workspace with leading dimension N, or NULL (the
+ *          library allocates it); ignored for host V.
+ * Requires mu1 < mu_nevnex < b_sup.  b == 0 or N == 0 is a no-op.
+ * Errors: CHASE_INVALID_ARG (sizes, bounds, odd or out-of-range degree,
+ * misaligned pointer), CHASE_OUT_OF_MEMORY, CHASE_CUDA_ERROR, CHASE_TIMEOUT. */
+int chase_filter(const chase_c64* H, int64_t N, int64_t ldh, chase_c64* V, int64_t ldv, int b,
+                 const int* degrees, double b_sup, double mu1, double mu_nevnex, chase_c64* work,
+                 void* stream);
+
+/* Spectral estimates by Lanczos (Alg. 6, Sec. 4.2).
+ * starts   N x (1 + nvec) start vectors, leading dimension N (host or device);
+ *          column 0 drives the bound run of Alg. 6 line 2, columns 1..nvec
+ *          the density runs of line 8.  They need not be normalised.
+ * k        Lanczos steps per run (1 <= k <= N).
+ * approx   1: only b_sup is computed (Alg. 6 lines 4-6); 0: also mu1,
+ *          mu_nevnex from the density of states of Eq. 10 (integral equal to
+ *          (nev+nex)/N, Gaussian width dos_sigma in the variable mapping
+ *          [mu1, b_sup] to [-1, 1]), and, if V is not NULL, the Ritz vectors
+ *          of the first density run whose Ritz value lies below mu_nevnex
+ *          overwrite the leading columns of V (Alg. 6 line 13).
+ * V        N x (nev + nex), leading dimension ldv, in/out, or NULL.
+ * b_sup    out: max over the runs of ||f_k|| + max Ritz value (Alg. 6 line 3).
+ * mu1, mu_nevnex, theta_absmax  out (host doubles; mu values untouched when approx).
+ * Errors: CHASE_INVALID_ARG, CHASE_OUT_OF_MEMORY, CHASE_CUDA_ERROR. */
+int chase_lanczos(const chase_c64* H, int64_t N, int64_t ldh, int k, int nvec, int approx, int nev,
+                  int nex, double dos_sigma, const chase_c64* starts, chase_c64* V, int64_t ldv,
+                  double* b_sup, double* mu1, double* mu_nevnex, double* theta_absmax,
+                  void* stream);
+
+/* Optimised degrees (Alg. 5, Eq. 8), host arrays only:
+ * t = (ritz_a - c)/e, |rho| = max|t -+ sqrt(t^2 - 1)|,
+ * deg = ceil(|log(resid_a / tol) / log|rho||), deg = min(deg + deg_extra, deg_max),
+ * degrees_out[a] = deg + mod(deg, 2); lowered by 2 if that exceeds an odd deg_max.
+ * When |rho| <= 1 (Ritz value inside the damped interval) or the quotient is
+ * not finite the degree is deg_max before the even rounding.
+ * Errors: CHASE_INVALID_ARG (NULL array with b > 0, e <= 0, tol <= 0, deg_max < 2). */
+int chase_degrees(int b, const double* resid, const double* ritz, double c, double e, double tol,
+                  int deg_extra, int deg_max, int* degrees_out);
+
+/* Deflation and locking rule (Alg. 3), host arrays only: writes in order_out
+ * the stable permutation that sorts ritz ascending (line 2) and in *n_lock
+ * the length of the leading run of that order whose residual is <= tol
+ * (line 4 stops at the first residual above tol).
+ * Errors: CHASE_INVALID_ARG. */
+int chase_lock(int b, const double* ritz, const double* resid, double tol, int* order_out,
+               int* n_lock);
+
+/* Eigen-decomposition of a real symmetric tridiagonal matrix, host arrays
+ * only: the Lanczos matrix T_k of Alg. 6 (diag[k] on the diagonal, off[k-1]
+ * beside it).  Writes the eigenvalues ascending in w[k] and the normalised
+ * eigenvectors column-major in z[k*k] (column j belongs to w[j]); the
+ * Eq. 10 weights are the squared first components z[j*k]^2.  Implicit QR
+ * sweeps with Wilkinson shifts.
+ * Errors: CHASE_INVALID_ARG, CHASE_EIGENSOLVER_ERROR (no convergence). */
+int chase_tridiag_eigh(int k, const double* diag, const double* off, double* w, double* z);
+
+/* Orthonormalise V against the locked block Y and within itself (Alg. 1
+ * line 5, QR of [Y V], keeping Y): block Gram-Schmidt against Y followed by
+ * Cholesky QR, twice; if a Cholesky pivot is not safely positive the first
+ * pass is replaced by shifted Cholesky QR.  On return span(V_out) equals the
+ * part of span([Y V_in]) orthogonal to Y and V_out^H V_out = I.
+ * Y        N x nconv, leading dimension ldy (nconv may be 0; Y may then be NULL)
+ * V        N x b, leading dimension ldv, in/out; b <= N - nconv.
+ * Both arrays device, or both host.
+ * Errors: CHASE_INVALID_ARG, CHASE_QR_BREAKDOWN, CHASE_OUT_OF_MEMORY, CHASE_CUDA_ERROR. */
+int chase_orthonormalize(const chase_c64* Y, int64_t N, int64_t ldy, int nconv, chase_c64* V,
+                         int64_t ldv, int b, void* stream);
+
+/* Rayleigh-Ritz (Alg. 2): G = Q^H H Q, (W, ritz) = eigh(G) with ritz
+ * ascending, Q <- Q W.  Q must have orthonormal columns.  If resid is not
+ * NULL it receives ||H q_a - ritz_a q_a||_2 for the new columns (Alg. 1
+ * line 8).
+ * H        N x N, ldh (host or device)
+ * Q        N x b, ldq, in/out (same kind as H)
+ * ritz     b doubles out; resid b doubles out or NULL (host arrays)
+ * Errors: CHASE_INVALID_ARG, CHASE_EIGENSOLVER_ERROR, CHASE_OUT_OF_MEMORY, CHASE_CUDA_ERROR. */
+int chase_rayleigh_ritz(const chase_c64* H, int64_t N, int64_t ldh, chase_c64* Q, int64_t ldq,
+                        int b, double* ritz, double* resid, void* stream);
+
+/* Residuals (Alg. 1 line 8): resid[a] = ||H v_a - lambda_a v_a||_2.
+ * H N x N (ldh), V N x b (ldv), lambda b doubles (host), resid b doubles out (host).
+ * H and V both host or both device.
+ * Errors: CHASE_INVALID_ARG, CHASE_OUT_OF_MEMORY, CHASE_CUDA_ERROR. */
+int chase_residuals(const chase_c64* H, int64_t N, int64_t ldh, const chase_c64* V, int64_t ldv,
+                    int b, const double* lambda, double* resid, void* stream);
+
+/* The ChASE eigensolver (Alg. 1) for the nev smallest eigenpairs of H.
+ * H        N x N Hermitian, ldh (host or device)
+ * V        N x (nev + nex), ldv, in/out (same kind as H).  In: random
+ *          start vectors when opts->approx == 0, approximate eigenvectors
+ *          when approx == 1 (Sec. 3.3).  Out: Ritz vectors, ascending.
+ * Lambda   nev + nex doubles, in/out (host).  In (approx == 1): approximate
+ *          eigenvalues; their min and max give mu1 and mu_nevnex.  Out: Ritz
+ *          values ascending; the first nev are converged on CHASE_OK.
+ * resid    nev + nex doubles out (host): ||H v_a - lambda_a v_a||_2.
+ * lanczos_starts  N x (1 + num_lanczos), leading dimension N (same kind as
+ *          H): start vectors of the Lanczos runs (random numbers are inputs).
+ * opts     NULL for chase_opts_default().
+ * stats    out, or NULL.
+ * Requires 1 <= nev, 0 <= nex, nev + nex <= N, tol > 0.
+ * Returns CHASE_OK, or CHASE_NOT_CONVERGED after max_iter iterations with
+ * the current subspace in V, Lambda, resid (Sec. 5.3), or an error status. */
+int chase_solve(const chase_c64* H, int64_t N, int64_t ldh, int nev, int nex, double tol,
+                chase_c64* V, int64_t ldv, double* Lambda, double* resid,
+                const chase_c64* lanczos_starts, const chase_opts* opts, chase_stats* stats,
+                void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHASE_H_ */

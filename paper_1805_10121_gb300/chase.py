@@ -1,0 +1,325 @@
+"""Thin ctypes binding to libchase.so (the C ABI declared in include/chase.h).
+
+Argument marshalling only: every function passes the data pointers of torch
+tensors (device or host) and the sizes to the C entry point of the same
+name; all arithmetic runs in the library's kernels.  Importing this module
+does not load the library; the first call does, and fails loudly if the
+library has not been built.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from typing import Optional
+
+import numpy as np
+import torch
+
+__all__ = [
+    "ChaseError", "ChaseOpts", "ChaseStats", "lib", "lib_path", "declared_symbols",
+    "chase_opts_default", "chase_last_error", "chase_kernel_launches", "chase_filter", "chase_lanczos",
+    "chase_degrees", "chase_lock", "chase_tridiag_eigh", "chase_orthonormalize",
+    "chase_rayleigh_ritz", "chase_residuals", "chase_solve",
+    "CHASE_OK", "CHASE_INVALID_ARG", "CHASE_NOT_CONVERGED", "CHASE_QR_BREAKDOWN",
+    "CHASE_BOUND_VIOLATION", "CHASE_CUDA_ERROR", "CHASE_OUT_OF_MEMORY", "CHASE_TIMEOUT",
+    "CHASE_EIGENSOLVER_ERROR", "CHASE_CONV_ABS", "CHASE_CONV_REL", "CHASE_FP64",
+]
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_HEADER = os.path.join(os.path.dirname(_PKG), "include", "chase.h")
+
+CHASE_OK = 0
+CHASE_INVALID_ARG = 1
+CHASE_NOT_CONVERGED = 2
+CHASE_QR_BREAKDOWN = 3
+CHASE_BOUND_VIOLATION = 4
+CHASE_CUDA_ERROR = 5
+CHASE_OUT_OF_MEMORY = 6
+CHASE_TIMEOUT = 7
+CHASE_EIGENSOLVER_ERROR = 8
+CHASE_FP64 = 0
+CHASE_CONV_ABS = 0
+CHASE_CONV_REL = 1
+
+
+class ChaseError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: status {status}: {message}")
+        self.status = status
+
+
+class ChaseOpts(ctypes.Structure):
+    _fields_ = [
+        ("deg", ctypes.c_int), ("optim", ctypes.c_int), ("deg_extra", ctypes.c_int),
+        ("deg_max", ctypes.c_int), ("max_iter", ctypes.c_int), ("lanczos_iter", ctypes.c_int),
+        ("num_lanczos", ctypes.c_int), ("approx", ctypes.c_int), ("dos_sigma", ctypes.c_double),
+        ("conv_mode", ctypes.c_int), ("precision", ctypes.c_int),
+    ]
+
+
+class ChaseStats(ctypes.Structure):
+    _fields_ = [
+        ("iterations", ctypes.c_int), ("nconv", ctypes.c_int),
+        ("matvecs", ctypes.c_longlong), ("filter_matvecs", ctypes.c_longlong),
+        ("b_sup", ctypes.c_double), ("mu1", ctypes.c_double), ("mu_nevnex", ctypes.c_double),
+        ("tol_eff", ctypes.c_double), ("flops_filter", ctypes.c_double),
+        ("flops_total", ctypes.c_double), ("t_total", ctypes.c_double),
+        ("t_lanczos", ctypes.c_double), ("t_filter", ctypes.c_double), ("t_qr", ctypes.c_double),
+        ("t_rr", ctypes.c_double), ("t_eigh", ctypes.c_double), ("t_resid", ctypes.c_double),
+        ("t_host", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_c_p = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+_dbl = ctypes.c_double
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+_SIGNATURES = {
+    "chase_opts_default": (_int, [ctypes.POINTER(ChaseOpts)]),
+    "chase_last_error": (ctypes.c_char_p, []),
+    "chase_kernel_launches": (ctypes.c_longlong, []),
+    "chase_filter": (_int, [_c_p, _i64, _i64, _c_p, _i64, _int, _c_p, _dbl, _dbl, _dbl, _c_p, _c_p]),
+    "chase_lanczos": (_int, [_c_p, _i64, _i64, _int, _int, _int, _int, _int, _dbl, _c_p, _c_p,
+                             _i64, _dp, _dp, _dp, _dp, _c_p]),
+    "chase_degrees": (_int, [_int, _dp, _dp, _dbl, _dbl, _dbl, _int, _int, _ip]),
+    "chase_lock": (_int, [_int, _dp, _dp, _dbl, _ip, _ip]),
+    "chase_tridiag_eigh": (_int, [_int, _dp, _dp, _dp, _dp]),
+    "chase_orthonormalize": (_int, [_c_p, _i64, _i64, _int, _c_p, _i64, _int, _c_p]),
+    "chase_rayleigh_ritz": (_int, [_c_p, _i64, _i64, _c_p, _i64, _int, _dp, _dp, _c_p]),
+    "chase_residuals": (_int, [_c_p, _i64, _i64, _c_p, _i64, _int, _dp, _dp, _c_p]),
+    "chase_solve": (_int, [_c_p, _i64, _i64, _int, _int, _dbl, _c_p, _i64, _dp, _dp, _c_p,
+                           ctypes.POINTER(ChaseOpts), ctypes.POINTER(ChaseStats), _c_p]),
+}
+
+_lib = None
+
+
+def lib_path() -> str:
+    return os.path.join(_PKG, "libchase.so")
+
+
+def lib() -> ctypes.CDLL:
+    """Load libchase.so (built in-tree by ``paper_1805_10121_gb300.build``)."""
+    global _lib
+    if _lib is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build()")
+        handle = ctypes.CDLL(path)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = handle
+    return _lib
+
+
+def declared_symbols(header: str = _HEADER) -> list[str]:
+    """Names of the functions declared in include/chase.h."""
+    text = open(header).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(chase_[a-z_0-9]+)\s*\(", text)))
+
+
+def chase_kernel_launches() -> int:
+    return int(lib().chase_kernel_launches())
+
+
+def chase_last_error() -> str:
+    return (lib().chase_last_error() or b"").decode()
+
+
+def _check(status: int, where: str, allow=(CHASE_OK,)):
+    if status not in allow:
+        raise ChaseError(status, where, chase_last_error())
+    return status
+
+
+def _mat(t: torch.Tensor, rows: int, name: str):
+    """Pointer and leading dimension of a column-major complex128 matrix."""
+    if t.dtype != torch.complex128:
+        raise TypeError(f"{name} must be complex128")
+    if t.dim() != 2 or t.shape[0] != rows:
+        raise ValueError(f"{name} must have {rows} rows")
+    if t.shape[1] > 1 and t.stride(0) != 1:
+        raise ValueError(f"{name} must be column-major (stride(0) == 1)")
+    ld = t.stride(1) if t.shape[1] > 1 else max(rows, 1)
+    if t.shape[1] == 1 and t.stride(0) != 1:
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr()), ld
+
+
+def _stream(t: torch.Tensor, stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    if t.is_cuda:
+        return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+def _f64(a, n: Optional[int] = None) -> np.ndarray:
+    x = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if n is not None and x.shape != (n,):
+        raise ValueError(f"expected {n} values")
+    return x
+
+
+def _dptr(x: np.ndarray):
+    return x.ctypes.data_as(_dp)
+
+
+def _iptr(x: np.ndarray):
+    return x.ctypes.data_as(_ip)
+
+
+def chase_opts_default(**overrides) -> ChaseOpts:
+    o = ChaseOpts()
+    _check(lib().chase_opts_default(ctypes.byref(o)), "chase_opts_default")
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+def chase_filter(H, V, degrees, b_sup, mu1, mu_nevnex, work=None, stream=None):
+    """Filter the columns of V in place (Alg. 4).  ``degrees``: int32 tensor
+    (host or device) or a sequence of ints."""
+    n = H.shape[0]
+    hp, ldh = _mat(H, n, "H")
+    vp, ldv = _mat(V, n, "V")
+    b = V.shape[1]
+    if isinstance(degrees, torch.Tensor):
+        if degrees.dtype != torch.int32 or not degrees.is_contiguous():
+            raise TypeError("degrees must be a contiguous int32 tensor")
+        deg_keep = degrees
+        dptr = ctypes.c_void_p(degrees.data_ptr())
+    else:
+        deg_keep = np.ascontiguousarray(np.asarray(degrees, dtype=np.int32))
+        dptr = ctypes.c_void_p(deg_keep.ctypes.data)
+    if len(deg_keep) != b:
+        raise ValueError("one degree per column")
+    wp = ctypes.c_void_p(work.data_ptr()) if work is not None else None
+    st = lib().chase_filter(hp, n, ldh, vp, ldv, b, dptr, float(b_sup), float(mu1),
+                            float(mu_nevnex), wp, _stream(V, stream))
+    _check(st, "chase_filter")
+    return V
+
+
+def chase_lanczos(H, k, nvec, approx, nev, nex, starts, V=None, dos_sigma=0.25, stream=None):
+    n = H.shape[0]
+    hp, ldh = _mat(H, n, "H")
+    sp, lds = _mat(starts, n, "starts")
+    if lds != max(n, 1) and starts.shape[1] > 1:
+        raise ValueError("starts must have leading dimension N")
+    vp, ldv = (None, n) if V is None else _mat(V, n, "V")
+    out = np.zeros(4)
+    st = lib().chase_lanczos(hp, n, ldh, int(k), int(nvec), int(approx), int(nev), int(nex),
+                             float(dos_sigma), sp, vp, ldv, _dptr(out[0:]), _dptr(out[1:]),
+                             _dptr(out[2:]), _dptr(out[3:]), _stream(H, stream))
+    _check(st, "chase_lanczos")
+    res = {"b_sup": out[0], "theta_absmax": out[3]}
+    if not approx:
+        res.update(mu1=out[1], mu_nevnex=out[2])
+    return res
+
+
+def chase_degrees(resid, ritz, c, e, tol, deg_extra=2, deg_max=36):
+    r = _f64(resid)
+    lam = _f64(ritz, len(r))
+    out = np.zeros(len(r), dtype=np.int32)
+    _check(lib().chase_degrees(len(r), _dptr(r), _dptr(lam), float(c), float(e), float(tol),
+                               int(deg_extra), int(deg_max), _iptr(out)), "chase_degrees")
+    return out
+
+
+def chase_lock(ritz, resid, tol):
+    lam = _f64(ritz)
+    r = _f64(resid, len(lam))
+    order = np.zeros(len(lam), dtype=np.int32)
+    n = ctypes.c_int(0)
+    _check(lib().chase_lock(len(lam), _dptr(lam), _dptr(r), float(tol), _iptr(order),
+                            ctypes.byref(n)), "chase_lock")
+    return order, n.value
+
+
+def chase_tridiag_eigh(diag, off):
+    dg = _f64(diag)
+    k = len(dg)
+    of = _f64(off, max(k - 1, 0)) if k > 1 else np.zeros(1)
+    w = np.zeros(k)
+    z = np.zeros(k * k)
+    _check(lib().chase_tridiag_eigh(k, _dptr(dg), _dptr(of), _dptr(w), _dptr(z)),
+           "chase_tridiag_eigh")
+    return w, z.reshape(k, k).T.copy()
+
+
+def chase_orthonormalize(Y, V, stream=None):
+    n = V.shape[0]
+    vp, ldv = _mat(V, n, "V")
+    if Y is None or Y.shape[1] == 0:
+        yp, ldy, nconv = None, n, 0
+    else:
+        yp, ldy = _mat(Y, n, "Y")
+        nconv = Y.shape[1]
+    _check(lib().chase_orthonormalize(yp, n, ldy, nconv, vp, ldv, V.shape[1],
+                                      _stream(V, stream)), "chase_orthonormalize")
+    return V
+
+
+def chase_rayleigh_ritz(H, Q, want_resid=True, stream=None):
+    n = H.shape[0]
+    hp, ldh = _mat(H, n, "H")
+    qp, ldq = _mat(Q, n, "Q")
+    b = Q.shape[1]
+    ritz = np.zeros(b)
+    resid = np.zeros(b) if want_resid else None
+    _check(lib().chase_rayleigh_ritz(hp, n, ldh, qp, ldq, b, _dptr(ritz),
+                                     _dptr(resid) if want_resid else None, _stream(Q, stream)),
+           "chase_rayleigh_ritz")
+    return ritz, resid
+
+
+def chase_residuals(H, V, lam, stream=None):
+    n = H.shape[0]
+    hp, ldh = _mat(H, n, "H")
+    vp, ldv = _mat(V, n, "V")
+    b = V.shape[1]
+    lam = _f64(lam, b)
+    out = np.zeros(b)
+    _check(lib().chase_residuals(hp, n, ldh, vp, ldv, b, _dptr(lam), _dptr(out),
+                                 _stream(V, stream)), "chase_residuals")
+    return out
+
+
+def chase_solve(H, nev, nex, tol, V, lanczos_starts, Lambda=None, opts=None, stream=None,
+                raise_not_converged=False):
+    """Alg. 1.  V (N x (nev+nex)) is overwritten with the Ritz vectors.
+    Returns ``(status, Lambda, resid, stats_dict)``."""
+    n = H.shape[0]
+    nx = nev + nex
+    hp, ldh = _mat(H, n, "H")
+    vp, ldv = _mat(V, n, "V")
+    sp, lds = _mat(lanczos_starts, n, "lanczos_starts")
+    if lanczos_starts.shape[1] > 1 and lds != n:
+        raise ValueError("lanczos_starts must have leading dimension N")
+    lam = np.zeros(nx) if Lambda is None else np.array(Lambda, dtype=np.float64, copy=True)
+    if lam.shape != (nx,):
+        raise ValueError("Lambda must have nev + nex values")
+    resid = np.zeros(nx)
+    o = opts if opts is not None else chase_opts_default()
+    stats = ChaseStats()
+    st = lib().chase_solve(hp, n, ldh, int(nev), int(nex), float(tol), vp, ldv, _dptr(lam),
+                           _dptr(resid), sp, ctypes.byref(o), ctypes.byref(stats),
+                           _stream(H, stream))
+    allow = (CHASE_OK,) if raise_not_converged else (CHASE_OK, CHASE_NOT_CONVERGED)
+    _check(st, "chase_solve", allow)
+    return st, lam, resid, stats.as_dict()

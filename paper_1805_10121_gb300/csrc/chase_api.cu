@@ -1,0 +1,744 @@
+// Entry points of libchase and the ChASE driver (Alg. 1) on one GPU.
+//
+// The driver keeps H, the search block V (locked prefix + active suffix,
+// the buffer layout of Sec. 5.1.1) and all workspace in device memory.  Per
+// iteration only nev+nex Ritz values and residuals come back to the host,
+// where the locking rule (Alg. 3), the spectral updates (Alg. 1 lines
+// 10-11) and the degree rule (Alg. 5) run; the resulting column permutation
+// goes back to the device as one gather.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "chase.h"
+#include "common.cuh"
+#include "context.hpp"
+
+namespace chase {
+
+namespace {
+
+constexpr int kMaxDegAllowed = 1024;
+
+// Events bracketing the phases of one call, accumulated into seconds.
+struct PhaseTimer {
+  cudaStream_t st;
+  cudaEvent_t a = nullptr, b = nullptr;
+  double* acc = nullptr;
+  explicit PhaseTimer(cudaStream_t s) : st(s) {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+  }
+  ~PhaseTimer() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+  void begin(double* target) {
+    acc = target;
+    cudaEventRecord(a, st);
+  }
+  void end() {
+    cudaEventRecord(b, st);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    if (acc) *acc += 1e-3 * ms;
+  }
+};
+
+// Alg. 4 on a block whose columns are sorted by ascending degree.
+// X (N x b, ldx) holds the input and receives the output; Wk (N x b, ldw)
+// is the second buffer of the double buffering.  start[i] = number of
+// columns with degree < i for i = 0 .. maxdeg + 1 (columns with degree < i
+// have retired before step i).  Returns the column-product count.
+int filter_sorted(Dev& d, const chase_c64* H, int64_t N, int64_t ldh, chase_c64* X, int64_t ldx,
+                  chase_c64* Wk, int64_t ldw, int b, const int* start, int maxdeg, double b_sup,
+                  double mu1, double mu_nn, long long* matvecs) {
+  const double c = 0.5 * (b_sup + mu_nn);  // Alg. 4 line 2
+  const double e = 0.5 * (b_sup - mu_nn);
+  const double sigma1 = e / (mu1 - c);     // line 3
+  // line 4: W = (sigma_1 / e) (H - c I) V
+  CHASE_TRY(zgemm(d, N, N, H, ldh, X, ldx, b, Wk, ldw, 0, b, sigma1 / e, 0.0, c));
+  long long mv = b;
+  double sigma = sigma1;  // line 5
+  chase_c64* Vb = X;
+  chase_c64* Wb = Wk;
+  int64_t ldV = ldx, ldW = ldw;
+  for (int i = 2; i <= maxdeg; ++i) {  // line 7
+    const double tau = 1.0 / (2.0 / sigma1 - sigma);  // line 8
+    const int s = start[i];  // lines 12-14: columns with degree < i are done
+    // line 9: V[:, s:] = 2 (tau / e) (H - c I) W[:, s:] - tau sigma V[:, s:]
+    CHASE_TRY(zgemm(d, N, N, H, ldh, Wb, ldW, b, Vb, ldV, s, b, 2.0 * tau / e, -tau * sigma, c));
+    mv += b - s;
+    std::swap(Vb, Wb);  // line 10
+    std::swap(ldV, ldW);
+    sigma = tau;  // line 11
+  }
+  // With even degrees the last product of every column lands in X (Sec. 4.1.3).
+  if (Wb != X) {
+    set_error("filter: odd maximum degree");
+    return CHASE_INVALID_ARG;
+  }
+  if (matvecs) *matvecs += mv;
+  return CHASE_OK;
+}
+
+void starts_from_sorted(const int* m, int b, int maxdeg, std::vector<int>& start) {
+  start.assign(maxdeg + 2, 0);
+  int s = 0;
+  for (int i = 0; i <= maxdeg + 1; ++i) {
+    while (s < b && m[s] < i) ++s;
+    start[i] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Orthogonalisation (Alg. 1 line 5): block Gram-Schmidt against the locked
+// block Y and Cholesky QR, twice; shifted Cholesky QR first when a pivot is
+// not safely positive.
+// ---------------------------------------------------------------------------
+struct OrthWork {
+  chase_c64* T = nullptr;     // N x b
+  chase_c64* P = nullptr;     // nconv x b
+  chase_c64* G = nullptr;     // b x b
+  chase_c64* Rinv = nullptr;  // b x b
+  double* nrm = nullptr;      // b
+};
+
+int orth_alloc(Dev& d, int64_t N, int nconv, int b, OrthWork& w) {
+  CHASE_TRY(d.alloc(&w.T, static_cast<size_t>(N) * b));
+  CHASE_TRY(d.alloc(&w.P, static_cast<size_t>(std::max(nconv, 1)) * b));
+  CHASE_TRY(d.alloc(&w.G, static_cast<size_t>(b) * b));
+  CHASE_TRY(d.alloc(&w.Rinv, static_cast<size_t>(b) * b));
+  CHASE_TRY(d.alloc(&w.nrm, static_cast<size_t>(b)));
+  return CHASE_OK;
+}
+
+int cholqr_pass(Dev& d, int64_t N, const chase_c64* Y, int64_t ldy, int nconv, chase_c64* V,
+                int64_t ldv, int b, OrthWork& w, double shift, double* flops) {
+  if (nconv > 0) {  // V <- V - Y (Y^H V)
+    CHASE_TRY(zgram(d, N, Y, ldy, nconv, V, ldv, b, w.P, nconv));
+    CHASE_TRY(zgemm(d, N, nconv, Y, ldy, w.P, nconv, b, V, ldv, 0, b, -1.0, 1.0, 0.0));
+    *flops += 16.0 * N * nconv * b;
+  }
+  CHASE_TRY(zgram(d, N, V, ldv, b, V, ldv, b, w.G, b));
+  CHASE_TRY(launch_cholesky(d, w.G, b, b, 1e-12, shift));
+  int st = d.sync_check("cholesky");
+  if (st != CHASE_OK) {
+    cudaMemsetAsync(d.err, 0, sizeof(int), d.st);
+    return st;
+  }
+  CHASE_TRY(launch_tri_inv_upper(d, w.G, b, b, w.Rinv, b));
+  CHASE_TRY(zgemm(d, N, b, V, ldv, w.Rinv, b, b, w.T, N, 0, b, 1.0, 0.0, 0.0));
+  CHASE_TRY(copy_block(d, V, ldv, w.T, N, N, b, cudaMemcpyDeviceToDevice));
+  *flops += 16.0 * N * b * b + 8.0 * b * b * b / 3.0;
+  return CHASE_OK;
+}
+
+int orth_core(Dev& d, int64_t N, const chase_c64* Y, int64_t ldy, int nconv, chase_c64* V,
+              int64_t ldv, int b, OrthWork& w, double* flops) {
+  if (b == 0) return CHASE_OK;
+  // QR of V D equals QR of V for any positive diagonal D: normalise columns.
+  CHASE_TRY(launch_col_norms(d, V, ldv, N, b, w.nrm));
+  CHASE_TRY(launch_col_inv_scale(d, V, ldv, N, b, w.nrm));
+  int st = cholqr_pass(d, N, Y, ldy, nconv, V, ldv, b, w, 0.0, flops);
+  if (st == CHASE_QR_BREAKDOWN) {
+    // Shifted Cholesky QR: ||G||_2 <= trace(G) <= b for columns of norm <= 1.
+    const double u = 1.1102230246251565e-16;
+    const double shift = 11.0 * (static_cast<double>(N) * b + static_cast<double>(b) * (b + 1)) * u * b;
+    CHASE_TRY(launch_col_norms(d, V, ldv, N, b, w.nrm));
+    CHASE_TRY(launch_col_inv_scale(d, V, ldv, N, b, w.nrm));
+    st = cholqr_pass(d, N, Y, ldy, nconv, V, ldv, b, w, shift, flops);
+    if (st == CHASE_QR_BREAKDOWN) {
+      set_error("orthonormalisation: shifted Cholesky QR broke down");
+      return CHASE_QR_BREAKDOWN;
+    }
+    CHASE_TRY(st);
+    st = cholqr_pass(d, N, Y, ldy, nconv, V, ldv, b, w, 0.0, flops);
+  }
+  CHASE_TRY(st);
+  st = cholqr_pass(d, N, Y, ldy, nconv, V, ldv, b, w, 0.0, flops);
+  if (st == CHASE_QR_BREAKDOWN) set_error("orthonormalisation: Cholesky QR broke down");
+  return st;
+}
+
+// ---------------------------------------------------------------------------
+// Rayleigh-Ritz (Alg. 2) with residuals (Alg. 1 line 8)
+// ---------------------------------------------------------------------------
+struct RRWork {
+  chase_c64* HQ = nullptr;  // N x b
+  chase_c64* T2 = nullptr;  // N x b
+  chase_c64* T3 = nullptr;  // N x b
+  chase_c64* G = nullptr;   // b x b
+};
+
+int rr_alloc(Dev& d, int64_t N, int b, RRWork& w) {
+  CHASE_TRY(d.alloc(&w.HQ, static_cast<size_t>(N) * b));
+  CHASE_TRY(d.alloc(&w.T2, static_cast<size_t>(N) * b));
+  CHASE_TRY(d.alloc(&w.T3, static_cast<size_t>(N) * b));
+  CHASE_TRY(d.alloc(&w.G, static_cast<size_t>(b) * b));
+  return CHASE_OK;
+}
+
+int rr_core(Dev& d, const chase_c64* H, int64_t N, int64_t ldh, chase_c64* Q, int64_t ldq, int b,
+            double* w_dev, double* res_dev, RRWork& w, double* t_eigh, double* flops) {
+  if (b == 0) return CHASE_OK;
+  CHASE_TRY(zgemm(d, N, N, H, ldh, Q, ldq, b, w.HQ, N, 0, b, 1.0, 0.0, 0.0));  // H Q
+  CHASE_TRY(zgram(d, N, Q, ldq, b, w.HQ, N, b, w.G, b));                       // G = Q^H H Q
+  CHASE_TRY(launch_hermitize(d, w.G, b, b));
+  PhaseTimer tm(d.st);
+  tm.begin(t_eigh);
+  CHASE_TRY(eigh_device(d, w.G, b, b, w_dev));  // (W, Lambda) = TSOLVE(G)
+  tm.end();
+  CHASE_TRY(zgemm(d, N, b, Q, ldq, w.G, b, b, w.T2, N, 0, b, 1.0, 0.0, 0.0));  // Q W
+  if (res_dev) {
+    // H (Q W) = (H Q) W: the residual reuses the product with H
+    CHASE_TRY(zgemm(d, N, b, w.HQ, N, w.G, b, b, w.T3, N, 0, b, 1.0, 0.0, 0.0));
+    CHASE_TRY(launch_resid_norms(d, w.T3, N, w.T2, N, N, b, w_dev, res_dev));
+  }
+  CHASE_TRY(copy_block(d, Q, ldq, w.T2, N, N, b, cudaMemcpyDeviceToDevice));
+  *flops += 8.0 * N * N * b + 8.0 * N * b * b * (res_dev ? 3.0 : 2.0);
+  return CHASE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Lanczos (Alg. 6)
+// ---------------------------------------------------------------------------
+struct LanczosOut {
+  double b_sup = 0, mu1 = 0, mu_nn = 0, theta_absmax = 0;
+  long long matvecs = 0;
+};
+
+double normal_cdf(double x) { return 0.5 * (1.0 + std::erf(x / std::sqrt(2.0))); }
+
+// starts: N x r device (ld N), r = 1 (approx) or 1 + nvec.  V: N x ncolv
+// device or NULL.
+int lanczos_core(Dev& d, const chase_c64* H, int64_t N, int64_t ldh, int k, int nvec, bool approx,
+                 int nev, int nex, double dos_sigma, const chase_c64* starts, chase_c64* V,
+                 int64_t ldv, int ncolv, LanczosOut& out) {
+  const int r = approx ? 1 : 1 + nvec;
+  chase_c64* U = nullptr;   // N x (k r): vector j of run c is column j r + c
+  chase_c64* Wt = nullptr;  // N x r
+  double *alpha = nullptr, *beta = nullptr;
+  CHASE_TRY(d.alloc(&U, static_cast<size_t>(N) * k * r));
+  CHASE_TRY(d.alloc(&Wt, static_cast<size_t>(N) * r));
+  CHASE_TRY(d.alloc(&alpha, static_cast<size_t>(k) * r));
+  CHASE_TRY(d.alloc(&beta, static_cast<size_t>(k) * r));
+  CHASE_TRY(copy_block(d, U, N, starts, N, N, r, cudaMemcpyDeviceToDevice));
+  CHASE_TRY(launch_normalize_cols(d, U, N, N, r));
+  for (int j = 0; j < k; ++j) {
+    chase_c64* Vj = U + static_cast<size_t>(j) * r * N;
+    const chase_c64* Vp = j > 0 ? U + static_cast<size_t>(j - 1) * r * N : nullptr;
+    chase_c64* Vn = j + 1 < k ? U + static_cast<size_t>(j + 1) * r * N : nullptr;
+    CHASE_TRY(zgemm(d, N, N, H, ldh, Vj, N, r, Wt, N, 0, r, 1.0, 0.0, 0.0));  // A v_j
+    CHASE_TRY(launch_lanczos_step(d, N, r, j, Vj, Vp, Wt, Vn, alpha, beta));
+  }
+  std::vector<double> ha(static_cast<size_t>(k) * r), hb(static_cast<size_t>(k) * r);
+  CHASE_CUDA(cudaMemcpyAsync(ha.data(), alpha, ha.size() * sizeof(double), cudaMemcpyDeviceToHost, d.st));
+  CHASE_CUDA(cudaMemcpyAsync(hb.data(), beta, hb.size() * sizeof(double), cudaMemcpyDeviceToHost, d.st));
+  CHASE_TRY(d.sync_check("lanczos"));
+  out.matvecs = static_cast<long long>(k) * r;
+
+  // per run: truncate at the first step whose beta is rounding noise
+  std::vector<std::vector<double>> theta(r), Z(r);
+  std::vector<int> steps(r);
+  std::vector<double> fnorm(r);
+  for (int c = 0; c < r; ++c) {
+    int st = k;
+    double scale = 0.0;
+    for (int j = 0; j < k; ++j) {
+      const double a = ha[static_cast<size_t>(j) * r + c], bj = hb[static_cast<size_t>(j) * r + c];
+      scale = std::max(scale, std::max(std::fabs(a), bj));
+      if (!(bj > 1e-13 * scale)) {
+        st = j + 1;
+        break;
+      }
+    }
+    steps[c] = st;
+    std::vector<double> dg(st), of(std::max(st - 1, 0));
+    for (int j = 0; j < st; ++j) dg[j] = ha[static_cast<size_t>(j) * r + c];
+    for (int j = 0; j + 1 < st; ++j) of[j] = hb[static_cast<size_t>(j) * r + c];
+    fnorm[c] = hb[static_cast<size_t>(st - 1) * r + c];
+    theta[c].resize(st);
+    Z[c].resize(static_cast<size_t>(st) * st);
+    if (!tridiag_eigh(st, dg.data(), of.data(), theta[c].data(), Z[c].data())) {
+      set_error("lanczos: tridiagonal eigensolve did not converge");
+      return CHASE_EIGENSOLVER_ERROR;
+    }
+  }
+  double bsup = fnorm[0] + theta[0].back();  // Alg. 6 line 3
+  double absmax = 0.0;
+  for (int c = 0; c < r; ++c) {
+    bsup = std::max(bsup, fnorm[c] + theta[c].back());
+    for (double t : theta[c]) absmax = std::max(absmax, std::fabs(t));
+  }
+  out.b_sup = bsup;
+  out.theta_absmax = absmax;
+  if (approx) return CHASE_OK;
+
+  // density runs are c = 1 .. nvec
+  double mu1 = theta[1][0];
+  for (int c = 2; c < r; ++c) mu1 = std::min(mu1, theta[c][0]);  // Alg. 6 line 12
+  const double half = 0.5 * (bsup - mu1);
+  const double sig = half > 1e-12 * std::max(1.0, std::max(std::fabs(bsup), std::fabs(mu1)))
+                         ? dos_sigma * half
+                         : dos_sigma;
+  auto cdf = [&](double t) {  // integral of Eq. 10 up to t
+    double total = 0.0;
+    for (int c = 1; c < r; ++c)
+      for (int i = 0; i < steps[c]; ++i) {
+        const double z0 = Z[c][static_cast<size_t>(i) * steps[c]];
+        total += z0 * z0 * normal_cdf((t - theta[c][i]) / sig);
+      }
+    return total / nvec;
+  };
+  const double target = static_cast<double>(nev + nex) / static_cast<double>(N);  // line 11
+  double lo = mu1 - 10.0 * sig, hi = bsup + 10.0 * sig;
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (cdf(mid) < target)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  out.mu1 = mu1;
+  out.mu_nn = 0.5 * (lo + hi);
+
+  if (V && ncolv > 0) {  // line 13: Ritz vectors of the first density run
+    const int st = steps[1];
+    std::vector<int> sel;
+    for (int i = 0; i < st && static_cast<int>(sel.size()) < ncolv; ++i)
+      if (theta[1][i] < out.mu_nn) sel.push_back(i);
+    if (!sel.empty()) {
+      const int ns = static_cast<int>(sel.size());
+      std::vector<chase_c64> zs(static_cast<size_t>(st) * ns);
+      for (int a = 0; a < ns; ++a)
+        for (int i = 0; i < st; ++i)
+          zs[static_cast<size_t>(a) * st + i] = {Z[1][static_cast<size_t>(sel[a]) * st + i], 0.0};
+      chase_c64* dz = nullptr;
+      CHASE_TRY(d.alloc(&dz, zs.size()));
+      CHASE_CUDA(cudaMemcpyAsync(dz, zs.data(), zs.size() * sizeof(chase_c64),
+                                 cudaMemcpyHostToDevice, d.st));
+      // U_1 Z_sel: basis of run 1 is columns j r + 1, i.e. leading dimension r N
+      CHASE_TRY(zgemm(d, N, st, U + N, static_cast<int64_t>(r) * N, dz, st, ns, V, ldv, 0, ns,
+                      1.0, 0.0, 0.0));
+      CHASE_TRY(d.sync_check("lanczos ritz vectors"));
+    }
+  }
+  return CHASE_OK;
+}
+
+// Stage an array that may live on the host into device memory.
+int stage_in(Dev& d, bool on_dev, const chase_c64* src, int64_t ld, int64_t rows, int64_t cols,
+             chase_c64** dst, int64_t* ldd) {
+  if (on_dev) {
+    *dst = const_cast<chase_c64*>(src);
+    *ldd = ld;
+    return CHASE_OK;
+  }
+  CHASE_TRY(d.alloc(dst, static_cast<size_t>(rows) * std::max<int64_t>(cols, 1)));
+  *ldd = rows;
+  return copy_block(d, *dst, rows, src, ld, rows, cols, cudaMemcpyHostToDevice);
+}
+
+bool ld_ok(int64_t ld, int64_t n) { return ld >= std::max<int64_t>(1, n); }
+
+}  // namespace
+}  // namespace chase
+
+using namespace chase;
+
+extern "C" int chase_opts_default(chase_opts* o) {
+  if (!o) {
+    set_error("chase_opts_default: NULL");
+    return CHASE_INVALID_ARG;
+  }
+  o->deg = 20;
+  o->optim = 1;
+  o->deg_extra = 2;
+  o->deg_max = 36;
+  o->max_iter = 25;
+  o->lanczos_iter = 25;
+  o->num_lanczos = 4;
+  o->approx = 0;
+  o->dos_sigma = 0.25;
+  o->conv_mode = CHASE_CONV_REL;
+  o->precision = CHASE_FP64;
+  return CHASE_OK;
+}
+
+extern "C" int chase_filter(const chase_c64* H, int64_t N, int64_t ldh, chase_c64* V, int64_t ldv,
+                            int b, const int* degrees, double b_sup, double mu1, double mu_nevnex,
+                            chase_c64* work, void* stream) {
+  if (N < 0 || b < 0 || !ld_ok(ldh, N) || !ld_ok(ldv, N) || N > (1LL << 30)) {
+    set_error("chase_filter: invalid size or leading dimension");
+    return CHASE_INVALID_ARG;
+  }
+  if (N == 0 || b == 0) return CHASE_OK;
+  if (!H || !V || !degrees) {
+    set_error("chase_filter: NULL array");
+    return CHASE_INVALID_ARG;
+  }
+  if (!(mu1 < mu_nevnex && mu_nevnex < b_sup) || !std::isfinite(b_sup) || !std::isfinite(mu1)) {
+    set_error("chase_filter: need mu1 < mu_nevnex < b_sup");
+    return CHASE_INVALID_ARG;
+  }
+  Dev d(stream);
+  CHASE_TRY(d.init());
+  const bool dev = is_device_ptr(H);
+  if (is_device_ptr(V) != dev) {
+    set_error("chase_filter: H and V must both be host or both be device arrays");
+    return CHASE_INVALID_ARG;
+  }
+  chase_c64 *dH = nullptr, *dV = nullptr;
+  int64_t lh = 0, lv = 0;
+  CHASE_TRY(stage_in(d, dev, H, ldh, N, N, &dH, &lh));
+  CHASE_TRY(stage_in(d, dev, V, ldv, N, b, &dV, &lv));
+  chase_c64* wk = dev ? work : nullptr;
+  if (!wk) CHASE_TRY(d.alloc(&wk, static_cast<size_t>(N) * b));
+  // degrees -> device, plan on the device (stable sort by degree)
+  int *ddeg = nullptr, *dperm = nullptr, *dstart = nullptr, *dinfo = nullptr;
+  if (is_device_ptr(degrees)) {
+    ddeg = const_cast<int*>(degrees);
+  } else {
+    CHASE_TRY(d.alloc(&ddeg, b));
+    CHASE_CUDA(cudaMemcpyAsync(ddeg, degrees, sizeof(int) * b, cudaMemcpyHostToDevice, d.st));
+  }
+  CHASE_TRY(d.alloc(&dperm, b));
+  CHASE_TRY(d.alloc(&dstart, kMaxDegAllowed + 2));
+  CHASE_TRY(d.alloc(&dinfo, 1));
+  CHASE_TRY(launch_filter_plan(d, ddeg, b, kMaxDegAllowed, dperm, dstart, dinfo));
+  std::vector<int> start(kMaxDegAllowed + 2);
+  int maxdeg = 0;
+  CHASE_CUDA(cudaMemcpyAsync(start.data(), dstart, sizeof(int) * start.size(), cudaMemcpyDeviceToHost, d.st));
+  CHASE_CUDA(cudaMemcpyAsync(&maxdeg, dinfo, sizeof(int), cudaMemcpyDeviceToHost, d.st));
+  CHASE_TRY(d.sync_check("chase_filter plan"));
+  // sorted copy into the workspace; V becomes the second buffer
+  CHASE_TRY(launch_permute_cols(d, dV, lv, wk, N, N, b, dperm, false));
+  CHASE_TRY(filter_sorted(d, dH, N, lh, wk, N, dV, lv, b, start.data(), maxdeg, b_sup, mu1,
+                          mu_nevnex, nullptr));
+  CHASE_TRY(launch_permute_cols(d, wk, N, dV, lv, N, b, dperm, true));
+  if (!dev) CHASE_TRY(copy_block(d, V, ldv, dV, lv, N, b, cudaMemcpyDeviceToHost));
+  return d.sync_check("chase_filter");
+}
+
+extern "C" int chase_lanczos(const chase_c64* H, int64_t N, int64_t ldh, int k, int nvec, int approx,
+                             int nev, int nex, double dos_sigma, const chase_c64* starts,
+                             chase_c64* V, int64_t ldv, double* b_sup, double* mu1,
+                             double* mu_nevnex, double* theta_absmax, void* stream) {
+  if (N < 1 || !ld_ok(ldh, N) || k < 1 || k > N || !H || !starts || !b_sup ||
+      (!approx && (nvec < 1 || nev < 1 || nex < 0 || nev + nex > N || !mu1 || !mu_nevnex)) ||
+      (V && !ld_ok(ldv, N))) {
+    set_error("chase_lanczos: invalid argument");
+    return CHASE_INVALID_ARG;
+  }
+  Dev d(stream);
+  CHASE_TRY(d.init());
+  const bool dev = is_device_ptr(H);
+  if (is_device_ptr(starts) != dev || (V && is_device_ptr(V) != dev)) {
+    set_error("chase_lanczos: arrays must all be host or all be device");
+    return CHASE_INVALID_ARG;
+  }
+  const int r = approx ? 1 : 1 + nvec;
+  chase_c64 *dH, *dS, *dV = nullptr;
+  int64_t lh, ls, lv = ldv;
+  CHASE_TRY(stage_in(d, dev, H, ldh, N, N, &dH, &lh));
+  CHASE_TRY(stage_in(d, dev, starts, N, N, r, &dS, &ls));
+  const int ncolv = V && !approx ? nev + nex : 0;
+  if (ncolv) CHASE_TRY(stage_in(d, dev, V, ldv, N, ncolv, &dV, &lv));
+  LanczosOut out;
+  CHASE_TRY(lanczos_core(d, dH, N, lh, k, nvec, approx != 0, nev, nex, dos_sigma, dS, dV, lv,
+                         ncolv, out));
+  if (ncolv && !dev) CHASE_TRY(copy_block(d, V, ldv, dV, lv, N, ncolv, cudaMemcpyDeviceToHost));
+  CHASE_TRY(d.sync_check("chase_lanczos"));
+  *b_sup = out.b_sup;
+  if (theta_absmax) *theta_absmax = out.theta_absmax;
+  if (!approx) {
+    *mu1 = out.mu1;
+    *mu_nevnex = out.mu_nn;
+  }
+  return CHASE_OK;
+}
+
+extern "C" int chase_orthonormalize(const chase_c64* Y, int64_t N, int64_t ldy, int nconv,
+                                    chase_c64* V, int64_t ldv, int b, void* stream) {
+  if (N < 0 || nconv < 0 || b < 0 || nconv + b > N || !ld_ok(ldv, N) ||
+      (nconv > 0 && (!Y || !ld_ok(ldy, N))) || (b > 0 && !V)) {
+    set_error("chase_orthonormalize: invalid argument");
+    return CHASE_INVALID_ARG;
+  }
+  if (b == 0) return CHASE_OK;
+  Dev d(stream);
+  CHASE_TRY(d.init());
+  const bool dev = is_device_ptr(V);
+  if (nconv > 0 && is_device_ptr(Y) != dev) {
+    set_error("chase_orthonormalize: Y and V must be of the same kind");
+    return CHASE_INVALID_ARG;
+  }
+  chase_c64 *dY = nullptr, *dV = nullptr;
+  int64_t ly = N, lv = 0;
+  if (nconv > 0) CHASE_TRY(stage_in(d, dev, Y, ldy, N, nconv, &dY, &ly));
+  CHASE_TRY(stage_in(d, dev, V, ldv, N, b, &dV, &lv));
+  OrthWork w;
+  CHASE_TRY(orth_alloc(d, N, nconv, b, w));
+  double fl = 0.0;
+  CHASE_TRY(orth_core(d, N, dY, ly, nconv, dV, lv, b, w, &fl));
+  if (!dev) CHASE_TRY(copy_block(d, V, ldv, dV, lv, N, b, cudaMemcpyDeviceToHost));
+  return d.sync_check("chase_orthonormalize");
+}
+
+extern "C" int chase_rayleigh_ritz(const chase_c64* H, int64_t N, int64_t ldh, chase_c64* Q,
+                                   int64_t ldq, int b, double* ritz, double* resid, void* stream) {
+  if (N < 0 || b < 0 || b > N || !ld_ok(ldh, N) || !ld_ok(ldq, N) ||
+      (b > 0 && (!H || !Q || !ritz))) {
+    set_error("chase_rayleigh_ritz: invalid argument");
+    return CHASE_INVALID_ARG;
+  }
+  if (b == 0) return CHASE_OK;
+  Dev d(stream);
+  CHASE_TRY(d.init());
+  const bool dev = is_device_ptr(H);
+  if (is_device_ptr(Q) != dev) {
+    set_error("chase_rayleigh_ritz: H and Q must be of the same kind");
+    return CHASE_INVALID_ARG;
+  }
+  chase_c64 *dH, *dQ;
+  int64_t lh, lq;
+  CHASE_TRY(stage_in(d, dev, H, ldh, N, N, &dH, &lh));
+  CHASE_TRY(stage_in(d, dev, Q, ldq, N, b, &dQ, &lq));
+  RRWork w;
+  CHASE_TRY(rr_alloc(d, N, b, w));
+  double *dw = nullptr, *dr = nullptr;
+  CHASE_TRY(d.alloc(&dw, b));
+  if (resid) CHASE_TRY(d.alloc(&dr, b));
+  double te = 0.0, fl = 0.0;
+  CHASE_TRY(rr_core(d, dH, N, lh, dQ, lq, b, dw, dr, w, &te, &fl));
+  if (!dev) CHASE_TRY(copy_block(d, Q, ldq, dQ, lq, N, b, cudaMemcpyDeviceToHost));
+  CHASE_CUDA(cudaMemcpyAsync(ritz, dw, sizeof(double) * b, cudaMemcpyDeviceToHost, d.st));
+  if (resid) CHASE_CUDA(cudaMemcpyAsync(resid, dr, sizeof(double) * b, cudaMemcpyDeviceToHost, d.st));
+  return d.sync_check("chase_rayleigh_ritz");
+}
+
+extern "C" int chase_residuals(const chase_c64* H, int64_t N, int64_t ldh, const chase_c64* V,
+                               int64_t ldv, int b, const double* lambda, double* resid,
+                               void* stream) {
+  if (N < 0 || b < 0 || !ld_ok(ldh, N) || !ld_ok(ldv, N) ||
+      (b > 0 && (!H || !V || !lambda || !resid))) {
+    set_error("chase_residuals: invalid argument");
+    return CHASE_INVALID_ARG;
+  }
+  if (b == 0 || N == 0) return CHASE_OK;
+  Dev d(stream);
+  CHASE_TRY(d.init());
+  const bool dev = is_device_ptr(H);
+  if (is_device_ptr(V) != dev) {
+    set_error("chase_residuals: H and V must be of the same kind");
+    return CHASE_INVALID_ARG;
+  }
+  chase_c64 *dH, *dV, *HV = nullptr;
+  int64_t lh, lv;
+  CHASE_TRY(stage_in(d, dev, H, ldh, N, N, &dH, &lh));
+  CHASE_TRY(stage_in(d, dev, V, ldv, N, b, &dV, &lv));
+  double *dl = nullptr, *dr = nullptr;
+  CHASE_TRY(d.alloc(&HV, static_cast<size_t>(N) * b));
+  CHASE_TRY(d.alloc(&dl, b));
+  CHASE_TRY(d.alloc(&dr, b));
+  CHASE_CUDA(cudaMemcpyAsync(dl, lambda, sizeof(double) * b, cudaMemcpyHostToDevice, d.st));
+  CHASE_TRY(zgemm(d, N, N, dH, lh, dV, lv, b, HV, N, 0, b, 1.0, 0.0, 0.0));
+  CHASE_TRY(launch_resid_norms(d, HV, N, dV, lv, N, b, dl, dr));
+  CHASE_CUDA(cudaMemcpyAsync(resid, dr, sizeof(double) * b, cudaMemcpyDeviceToHost, d.st));
+  return d.sync_check("chase_residuals");
+}
+
+extern "C" int chase_solve(const chase_c64* H, int64_t N, int64_t ldh, int nev, int nex, double tol,
+                           chase_c64* V, int64_t ldv, double* Lambda, double* resid,
+                           const chase_c64* lanczos_starts, const chase_opts* opts_in,
+                           chase_stats* stats, void* stream) {
+  chase_opts o;
+  if (opts_in)
+    o = *opts_in;
+  else
+    chase_opts_default(&o);
+  const int nx = nev + nex;
+  if (N < 1 || nev < 1 || nex < 0 || nx > N || !ld_ok(ldh, N) || !ld_ok(ldv, N) || !(tol > 0.0) ||
+      !H || !V || !Lambda || !resid || !lanczos_starts || o.deg < 1 ||
+      o.deg > kMaxDegAllowed - 1 || o.deg_max < 2 || o.deg_max > kMaxDegAllowed ||
+      o.deg_extra < 0 || o.max_iter < 0 || o.lanczos_iter < 1 || o.lanczos_iter > N ||
+      (!o.approx && o.num_lanczos < 1) || o.precision != CHASE_FP64 ||
+      (o.conv_mode != CHASE_CONV_ABS && o.conv_mode != CHASE_CONV_REL)) {
+    set_error("chase_solve: invalid argument");
+    return CHASE_INVALID_ARG;
+  }
+  chase_stats S;
+  std::memset(&S, 0, sizeof(S));
+  Dev d(stream);
+  CHASE_TRY(d.init());
+  PhaseTimer total(d.st), tm(d.st);
+  total.begin(&S.t_total);
+  const bool dev = is_device_ptr(H);
+  if (is_device_ptr(V) != dev || is_device_ptr(lanczos_starts) != dev) {
+    set_error("chase_solve: H, V and lanczos_starts must all be host or all be device");
+    return CHASE_INVALID_ARG;
+  }
+  const int r = o.approx ? 1 : 1 + o.num_lanczos;
+  chase_c64 *dH, *dV, *dS;
+  int64_t lh, lv, ls;
+  CHASE_TRY(stage_in(d, dev, H, ldh, N, N, &dH, &lh));
+  CHASE_TRY(stage_in(d, dev, V, ldv, N, nx, &dV, &lv));
+  CHASE_TRY(stage_in(d, dev, lanczos_starts, N, N, r, &dS, &ls));
+
+  chase_c64* Wk = nullptr;  // filter double buffer / permutation scratch
+  CHASE_TRY(d.alloc(&Wk, static_cast<size_t>(N) * nx));
+  OrthWork ow;
+  CHASE_TRY(orth_alloc(d, N, nx, nx, ow));
+  RRWork rw;
+  CHASE_TRY(rr_alloc(d, N, nx, rw));
+  double *dw = nullptr, *dres = nullptr;
+  int* dperm = nullptr;
+  CHASE_TRY(d.alloc(&dw, nx));
+  CHASE_TRY(d.alloc(&dres, nx));
+  CHASE_TRY(d.alloc(&dperm, nx));
+
+  const double N2 = static_cast<double>(N) * static_cast<double>(N);
+  // Alg. 1 line 1: constant initial degree, rounded up to even
+  const int d0 = std::min(o.deg + o.deg % 2, kMaxDegAllowed);
+  std::vector<int> m(nx, d0);
+  // line 2: bounds (and start vectors when approx == 0)
+  LanczosOut lz;
+  tm.begin(&S.t_lanczos);
+  CHASE_TRY(lanczos_core(d, dH, N, lh, o.lanczos_iter, o.num_lanczos, o.approx != 0, nev, nex,
+                         o.dos_sigma, dS, o.approx ? nullptr : dV, lv, o.approx ? 0 : nx, lz));
+  tm.end();
+  S.matvecs += lz.matvecs;
+  S.flops_total += 8.0 * N2 * lz.matvecs;
+  const double b_sup = lz.b_sup;
+  double mu1, mu_nn;
+  if (o.approx) {
+    mu1 = *std::min_element(Lambda, Lambda + nx);
+    mu_nn = *std::max_element(Lambda, Lambda + nx);
+  } else {
+    mu1 = lz.mu1;
+    mu_nn = lz.mu_nn;
+  }
+  double h = lz.theta_absmax;
+  std::vector<double> ritz(nx, 0.0), res(nx, HUGE_VAL), ra(nx), rr(nx);
+  std::vector<int> order(nx), perm(nx), start;
+  int nconv = 0, iter = 0, status = CHASE_OK;
+  double tol_eff = o.conv_mode == CHASE_CONV_REL ? tol * h : tol;
+
+  while (nconv < nev && iter < o.max_iter) {  // line 3
+    ++iter;
+    const int b = nx - nconv;
+    chase_c64* Va = dV + static_cast<size_t>(nconv) * lv;
+    // line 4: filter; the active columns are sorted by degree (line 15)
+    if (!(mu1 < mu_nn && mu_nn < b_sup)) {
+      set_error("chase_solve: spectral estimates out of order (mu1=%g, mu_nevnex=%g, b_sup=%g)",
+                mu1, mu_nn, b_sup);
+      status = CHASE_BOUND_VIOLATION;
+      break;
+    }
+    const int maxdeg = m[nx - 1];
+    starts_from_sorted(m.data() + nconv, b, maxdeg, start);
+    long long fm = 0;
+    tm.begin(&S.t_filter);
+    CHASE_TRY(filter_sorted(d, dH, N, lh, Va, lv, Wk, N, b, start.data(), maxdeg, b_sup, mu1, mu_nn,
+                            &fm));
+    tm.end();
+    S.filter_matvecs += fm;
+    S.matvecs += fm;
+    S.flops_filter += 8.0 * N2 * fm;
+    S.flops_total += 8.0 * N2 * fm;
+    // lines 5-6: orthonormalise the active block against the locked one
+    tm.begin(&S.t_qr);
+    CHASE_TRY(orth_core(d, N, dV, lv, nconv, Va, lv, b, ow, &S.flops_total));
+    tm.end();
+    // lines 7-8: Rayleigh-Ritz on the active block, residuals
+    tm.begin(&S.t_rr);
+    CHASE_TRY(rr_core(d, dH, N, lh, Va, lv, b, dw, dres, rw, &S.t_eigh, &S.flops_total));
+    CHASE_CUDA(cudaMemcpyAsync(ra.data(), dw, sizeof(double) * b, cudaMemcpyDeviceToHost, d.st));
+    CHASE_CUDA(cudaMemcpyAsync(rr.data(), dres, sizeof(double) * b, cudaMemcpyDeviceToHost, d.st));
+    tm.end();
+    CHASE_TRY(d.sync_check("chase_solve iteration"));
+    S.matvecs += b;
+    // host decisions
+    const auto t_host0 = std::chrono::steady_clock::now();
+    for (int a = 0; a < b; ++a) h = std::max(h, std::fabs(ra[a]));
+    tol_eff = o.conv_mode == CHASE_CONV_REL ? tol * h : tol;
+    if (ra[b - 1] > b_sup + 1e-10 * std::max(1.0, std::fabs(b_sup))) {
+      set_error("chase_solve: Ritz value %g above b_sup %g", ra[b - 1], b_sup);
+      status = CHASE_BOUND_VIOLATION;
+    }
+    int n_new = 0;
+    chase_lock(b, ra.data(), rr.data(), tol_eff, order.data(), &n_new);  // line 9 (Alg. 3)
+    for (int a = 0; a < b; ++a) {
+      ritz[nconv + a] = ra[order[a]];
+      res[nconv + a] = rr[order[a]];
+    }
+    const int nconv_new = nconv + n_new;
+    mu1 = *std::min_element(ritz.begin(), ritz.end());  // line 10
+    mu_nn = *std::max_element(ritz.begin(), ritz.end());
+    const double c = 0.5 * (b_sup + mu_nn);  // line 11
+    const double e = 0.5 * (b_sup - mu_nn);
+    const int nrest = nx - nconv_new;
+    std::vector<int> ord2(nrest);
+    if (nrest > 0) {
+      if (o.optim && e > 0.0)  // lines 12-14
+        chase_degrees(nrest, res.data() + nconv_new, ritz.data() + nconv_new, c, e, tol_eff,
+                      o.deg_extra, std::min(o.deg_max, kMaxDegAllowed), m.data() + nconv_new);
+      else
+        std::fill(m.begin() + nconv_new, m.end(), d0);
+      std::iota(ord2.begin(), ord2.end(), 0);  // line 15: stable sort by degree
+      std::stable_sort(ord2.begin(), ord2.end(), [&](int x, int y) {
+        return m[nconv_new + x] < m[nconv_new + y];
+      });
+    }
+    // one gather over the active block: locked first (Ritz order), then the
+    // rest by degree
+    for (int a = 0; a < n_new; ++a) perm[a] = order[a];
+    for (int a = 0; a < nrest; ++a) perm[n_new + a] = order[n_new + ord2[a]];
+    std::vector<double> r2(nrest), s2(nrest);
+    std::vector<int> m2(nrest);
+    for (int a = 0; a < nrest; ++a) {
+      r2[a] = ritz[nconv_new + ord2[a]];
+      s2[a] = res[nconv_new + ord2[a]];
+      m2[a] = m[nconv_new + ord2[a]];
+    }
+    for (int a = 0; a < nrest; ++a) {
+      ritz[nconv_new + a] = r2[a];
+      res[nconv_new + a] = s2[a];
+      m[nconv_new + a] = m2[a];
+    }
+    S.t_host += std::chrono::duration<double>(std::chrono::steady_clock::now() - t_host0).count();
+    CHASE_CUDA(cudaMemcpyAsync(dperm, perm.data(), sizeof(int) * b, cudaMemcpyHostToDevice, d.st));
+    CHASE_TRY(launch_permute_cols(d, Va, lv, Wk, N, N, b, dperm, false));
+    CHASE_TRY(copy_block(d, Va, lv, Wk, N, N, b, cudaMemcpyDeviceToDevice));
+    nconv = nconv_new;
+    if (status != CHASE_OK) break;
+  }
+  // output: all pairs ascending by Ritz value
+  std::vector<int> fin(nx);
+  std::iota(fin.begin(), fin.end(), 0);
+  std::stable_sort(fin.begin(), fin.end(), [&](int x, int y) { return ritz[x] < ritz[y]; });
+  CHASE_CUDA(cudaMemcpyAsync(dperm, fin.data(), sizeof(int) * nx, cudaMemcpyHostToDevice, d.st));
+  CHASE_TRY(launch_permute_cols(d, dV, lv, Wk, N, N, nx, dperm, false));
+  CHASE_TRY(copy_block(d, dV, lv, Wk, N, N, nx, cudaMemcpyDeviceToDevice));
+  if (!dev) CHASE_TRY(copy_block(d, V, ldv, dV, lv, N, nx, cudaMemcpyDeviceToHost));
+  CHASE_TRY(d.sync_check("chase_solve output"));
+  for (int a = 0; a < nx; ++a) {
+    Lambda[a] = ritz[fin[a]];
+    resid[a] = res[fin[a]];
+  }
+  total.end();
+  S.iterations = iter;
+  S.nconv = nconv;
+  S.b_sup = b_sup;
+  S.mu1 = mu1;
+  S.mu_nevnex = mu_nn;
+  S.tol_eff = tol_eff;
+  if (stats) *stats = S;
+  if (status != CHASE_OK) return status;
+  return nconv >= nev ? CHASE_OK : CHASE_NOT_CONVERGED;
+}

@@ -1,0 +1,85 @@
+// Per-call device context and the internal launch interface of libchase.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace chase {
+
+// Device context of one ABI call: the stream, a device error flag and the
+// stream-ordered workspace allocations, released when the context ends.
+struct Dev {
+  cudaStream_t st = nullptr;
+  int* err = nullptr;  // device int, bit field of KERR_* codes
+  std::vector<void*> bufs;
+
+  explicit Dev(void* stream) : st(static_cast<cudaStream_t>(stream)) {}
+  Dev(const Dev&) = delete;
+  Dev& operator=(const Dev&) = delete;
+  ~Dev();
+
+  int init();
+  int alloc_bytes(void** p, size_t bytes);
+  template <class T>
+  int alloc(T** p, size_t count) {
+    return alloc_bytes(reinterpret_cast<void**>(p), count * sizeof(T));
+  }
+  // Synchronise the stream and turn the device error flag into a status.
+  int sync_check(const char* where);
+};
+
+bool is_device_ptr(const void* p);
+
+// 2-D copies of column-major complex128 blocks (rows x cols).
+int copy_block(Dev& d, chase_c64* dst, int64_t ldd, const chase_c64* src, int64_t lds, int64_t rows,
+               int64_t cols, cudaMemcpyKind kind);
+
+// ---- kernels.cu ------------------------------------------------------------
+// Stable counting sort of the degrees (warp-level match/popc scans):
+// perm[pos] = original column at sorted position pos; start[i] = number of
+// columns with degree < i (i = 0 .. max_deg + 1); info[0] = max degree.
+int launch_filter_plan(Dev& d, const int* deg, int b, int max_allowed, int* perm, int* start,
+                       int* info);
+// Y[:, j] = X[:, perm[j]]  (gather) or Y[:, perm[j]] = X[:, j] (scatter)
+int launch_permute_cols(Dev& d, const chase_c64* X, int64_t ldx, chase_c64* Y, int64_t ldy,
+                        int64_t N, int b, const int* perm, bool scatter);
+// out[j] = ||X[:, j]||_2
+int launch_col_norms(Dev& d, const chase_c64* X, int64_t ldx, int64_t N, int b, double* out);
+// X[:, j] *= 1 / s[j]   (s[j] == 0 leaves the column)
+int launch_col_inv_scale(Dev& d, chase_c64* X, int64_t ldx, int64_t N, int b, const double* s);
+// res[j] = ||HV[:, j] - lam[j] V[:, j]||_2
+int launch_resid_norms(Dev& d, const chase_c64* HV, int64_t ldhv, const chase_c64* V, int64_t ldv,
+                       int64_t N, int b, const double* lam, double* res);
+// G <- (G + G^H) / 2 for a p x p matrix
+int launch_hermitize(Dev& d, chase_c64* G, int64_t ldg, int p);
+// In-place lower Cholesky G = L L^H (one CTA); sets KERR_CHOL_BREAKDOWN when a
+// pivot is not above rel_tol * G_jj.  `shift` is added to the diagonal first.
+int launch_cholesky(Dev& d, chase_c64* G, int64_t ldg, int p, double rel_tol, double shift);
+// Rinv = (L^{-1})^H, upper triangular, from the lower factor L.
+int launch_tri_inv_upper(Dev& d, const chase_c64* L, int64_t ldl, int p, chase_c64* Rinv,
+                         int64_t ldr);
+// One Lanczos three-term step on r independent runs (one CTA per run):
+// alpha = Re(v^H w); w -= alpha v + beta_prev v_prev; beta = ||w||;
+// v_next = w / beta (zero when beta is rounding noise).  alpha/beta arrays
+// are indexed [step * r + run].
+int launch_lanczos_step(Dev& d, int64_t N, int r, int step, const chase_c64* Vj, const chase_c64* Vprev,
+                        chase_c64* W, chase_c64* Vnext, double* alpha, double* beta);
+// Normalise r columns in place (Lanczos start vectors).
+int launch_normalize_cols(Dev& d, chase_c64* X, int64_t ldx, int64_t N, int r);
+// Fill the strict lower (lower=true) or upper part of a p x p matrix with zero.
+int launch_zero_triangle(Dev& d, chase_c64* A, int64_t lda, int p, bool lower);
+
+// ---- eigh (cuSOLVER, the small projected eigensolve of Alg. 2 line 3) -----
+int eigh_device(Dev& d, chase_c64* G, int64_t ldg, int p, double* w_dev);
+
+// ---- host_alg.cpp ----------------------------------------------------------
+// Symmetric tridiagonal eigenproblem (implicit QL with Wilkinson shifts):
+// diag[k], off[k-1] -> eigenvalues ascending in w, eigenvectors (k x k,
+// column-major) in z.  Returns false if it fails to converge.
+bool tridiag_eigh(int k, const double* diag, const double* off, double* w, double* z);
+
+}  // namespace chase

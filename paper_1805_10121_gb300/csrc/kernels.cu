@@ -1,0 +1,629 @@
+// Supporting kernels of the ChASE iteration on sm_103a: Gram products for
+// the orthogonalisation and the Rayleigh quotient, the degree plan of the
+// filter, column permutations, norms, residuals, the small Cholesky and
+// triangular inverse of Cholesky QR, and the Lanczos three-term step.
+#include <cusolverDn.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "common.cuh"
+#include "context.hpp"
+
+namespace chase {
+
+namespace {
+
+constexpr int kRed = 256;  // threads of the reduction kernels
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the block; result valid in every thread.
+__device__ double block_sum(double v, double* scratch /* >= 33 doubles */) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) scratch[warp] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  double s = 0.0;
+  if (warp == 0) {
+    s = lane < nw ? scratch[lane] : 0.0;
+    s = warp_sum(s);
+    if (lane == 0) scratch[32] = s;
+  }
+  __syncthreads();
+  return scratch[32];
+}
+
+// ---------------------------------------------------------------------------
+// Gram product C = X^H Y on the FP64 tensor pipe, split over K
+// ---------------------------------------------------------------------------
+constexpr int GT = 32;  // output tile (p and q)
+constexpr int GK = 16;  // K per shared-memory tile
+
+__global__ void __launch_bounds__(128)
+    gram_kernel(const double2* __restrict__ X, long long ldx, int p, const double2* __restrict__ Y,
+                long long ldy, int q, long long N, long long kchunk, double2* __restrict__ P,
+                long long ldp, long long pstride) {
+  __shared__ double2 sX[GT][GK];
+  __shared__ double2 sY[GT][GK];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int wm = warp & 1, wn = warp >> 1;  // 2 x 2 warps, 16 x 16 each
+  const int p0 = blockIdx.x * GT, q0 = blockIdx.y * GT;
+  const long long kbeg = blockIdx.z * kchunk;
+  const long long kend = min(N, kbeg + kchunk);
+
+  double acr[2][2][2] = {}, aci[2][2][2] = {};
+  for (long long k0 = kbeg; k0 < kend; k0 += GK) {
+    // load: 32 columns x 16 rows of X and of Y (column-contiguous in k)
+    for (int e = threadIdx.x; e < GT * GK; e += 128) {
+      const int col = e / GK, kk = e % GK;
+      const long long k = k0 + kk;
+      double2 xv = make_double2(0.0, 0.0), yv = make_double2(0.0, 0.0);
+      if (k < kend) {
+        if (p0 + col < p) xv = X[(long long)(p0 + col) * ldx + k];
+        if (q0 + col < q) yv = Y[(long long)(q0 + col) * ldy + k];
+      }
+      sX[col][kk] = xv;
+      sY[col][kk] = yv;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; kk += 4) {
+      double2 a[2], b[2];
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi) a[mi] = sX[wm * 16 + mi * 8 + g][kk + t];
+#pragma unroll
+      for (int ni = 0; ni < 2; ++ni) b[ni] = sY[wn * 16 + ni * 8 + g][kk + t];
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 2; ++ni) {
+          // conj(x) y = (xr yr + xi yi) + i (xr yi - xi yr)
+          dmma_8x8x4(acr[mi][ni][0], acr[mi][ni][1], a[mi].x, b[ni].x);
+          dmma_8x8x4(acr[mi][ni][0], acr[mi][ni][1], a[mi].y, b[ni].y);
+          dmma_8x8x4(aci[mi][ni][0], aci[mi][ni][1], a[mi].x, b[ni].y);
+          dmma_8x8x4(aci[mi][ni][0], aci[mi][ni][1], -a[mi].y, b[ni].x);
+        }
+    }
+    __syncthreads();
+  }
+  double2* Pz = P + blockIdx.z * pstride;
+#pragma unroll
+  for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int r = p0 + wm * 16 + mi * 8 + g;
+        const int c = q0 + wn * 16 + ni * 8 + 2 * t + h;
+        if (r < p && c < q) Pz[(long long)c * ldp + r] = make_double2(acr[mi][ni][h], aci[mi][ni][h]);
+      }
+}
+
+__global__ void sum_partials_kernel(const double2* __restrict__ P, int p, int q, int nsplit,
+                                    long long pstride, double2* __restrict__ C, long long ldc) {
+  const long long n = (long long)p * q;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    double sr = 0.0, si = 0.0;
+    for (int z = 0; z < nsplit; ++z) {
+      const double2 v = P[z * pstride + e];
+      sr += v.x;
+      si += v.y;
+    }
+    const long long r = e % p, c = e / p;
+    C[c * ldc + r] = make_double2(sr, si);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Degree plan: stable counting sort by degree with warp match / popc scans
+// ---------------------------------------------------------------------------
+constexpr int kMaxDeg = 1024;
+
+__global__ void filter_plan_kernel(const int* __restrict__ deg, int b, int max_allowed,
+                                   int* __restrict__ perm, int* __restrict__ start,
+                                   int* __restrict__ info, int* __restrict__ err) {
+  __shared__ int off[kMaxDeg + 2];
+  const int lane = threadIdx.x;  // one warp
+  for (int i = lane; i < max_allowed + 2; i += 32) off[i] = 0;
+  __syncwarp();
+  int mx = 0;
+  for (int j = lane; j < b; j += 32) {
+    int m = deg[j];
+    if (m < 2 || m > max_allowed || (m & 1)) {
+      atomicOr(err, KERR_BAD_DEGREE);
+      m = 2;
+    }
+    atomicAdd(&off[m], 1);
+    mx = max(mx, m);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __syncwarp();
+  // exclusive scan of the histogram, 32 degree values per round
+  int carry = 0;
+  for (int base = 0; base < max_allowed + 2; base += 32) {
+    const int i = base + lane;
+    const int v = i < max_allowed + 2 ? off[i] : 0;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    if (i < max_allowed + 2) {
+      off[i] = carry + incl - v;
+      start[i] = carry + incl - v;  // columns with degree < i
+    }
+    carry += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  __syncwarp();
+  if (lane == 0) info[0] = mx;
+  // stable placement: ranks among equal degrees inside each 32-column chunk
+  const unsigned lt_mask = (1u << lane) - 1u;
+  for (int base = 0; base < b; base += 32) {
+    const int j = base + lane;
+    int m = -1;
+    if (j < b) {
+      m = deg[j];
+      if (m < 2 || m > max_allowed || (m & 1)) m = 2;
+    }
+    const unsigned grp = __match_any_sync(0xffffffffu, m);
+    const int rank = __popc(grp & lt_mask);
+    if (j < b) perm[off[m] + rank] = j;
+    __syncwarp();
+    if (j < b && rank == 0) off[m] += __popc(grp);
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Column permutations, norms, scaling, residuals
+// ---------------------------------------------------------------------------
+__global__ void permute_cols_kernel(const double2* __restrict__ X, long long ldx,
+                                    double2* __restrict__ Y, long long ldy, long long N,
+                                    const int* __restrict__ perm, int scatter) {
+  const int j = blockIdx.y;
+  const int src = scatter ? j : perm[j];
+  const int dst = scatter ? perm[j] : j;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x)
+    Y[(long long)dst * ldy + i] = X[(long long)src * ldx + i];
+}
+
+__global__ void __launch_bounds__(kRed) col_norms_kernel(const double2* __restrict__ X, long long ldx,
+                                                         long long N, double* __restrict__ out) {
+  __shared__ double scratch[33];
+  const double2* x = X + (long long)blockIdx.x * ldx;
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < N; i += blockDim.x) {
+    const double2 v = x[i];
+    s += v.x * v.x + v.y * v.y;
+  }
+  s = block_sum(s, scratch);
+  if (threadIdx.x == 0) out[blockIdx.x] = sqrt(s);
+}
+
+__global__ void col_inv_scale_kernel(double2* __restrict__ X, long long ldx, long long N,
+                                     const double* __restrict__ s) {
+  const int j = blockIdx.y;
+  const double sj = s[j];
+  if (sj == 0.0) return;
+  const double f = 1.0 / sj;
+  double2* x = X + (long long)j * ldx;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = x[i];
+    x[i] = make_double2(v.x * f, v.y * f);
+  }
+}
+
+__global__ void __launch_bounds__(kRed)
+    resid_norms_kernel(const double2* __restrict__ HV, long long ldhv, const double2* __restrict__ V,
+                       long long ldv, long long N, const double* __restrict__ lam,
+                       double* __restrict__ res) {
+  __shared__ double scratch[33];
+  const int j = blockIdx.x;
+  const double l = lam[j];
+  const double2* hv = HV + (long long)j * ldhv;
+  const double2* v = V + (long long)j * ldv;
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < N; i += blockDim.x) {
+    const double2 a = hv[i], b = v[i];
+    const double dr = a.x - l * b.x, di = a.y - l * b.y;
+    s += dr * dr + di * di;
+  }
+  s = block_sum(s, scratch);
+  if (threadIdx.x == 0) res[j] = sqrt(s);
+}
+
+__global__ void hermitize_kernel(double2* __restrict__ G, long long ldg, int p) {
+  const long long n = (long long)p * p;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e % p), c = (int)(e / p);
+    if (r > c) continue;
+    double2* a = G + (long long)c * ldg + r;  // (r, c), upper
+    double2* b = G + (long long)r * ldg + c;  // (c, r), lower
+    if (r == c) {
+      a->y = 0.0;
+      continue;
+    }
+    const double2 x = *a, y = *b;
+    const double re = 0.5 * (x.x + y.x), im = 0.5 * (x.y - y.y);
+    *a = make_double2(re, im);
+    *b = make_double2(re, -im);
+  }
+}
+
+__global__ void zero_triangle_kernel(double2* __restrict__ A, long long lda, int p, int lower) {
+  const long long n = (long long)p * p;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e % p), c = (int)(e / p);
+    if (lower ? (r > c) : (r < c)) A[(long long)c * lda + r] = make_double2(0.0, 0.0);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Cholesky (left-looking, one CTA) and triangular inverse
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024)
+    cholesky_kernel(double2* __restrict__ G, long long ld, int p, double rel_tol, double shift,
+                    int* __restrict__ err) {
+  __shared__ double scratch[33];
+  __shared__ double s_ljj;
+  __shared__ int s_fail;
+  if (threadIdx.x == 0) s_fail = 0;
+  if (shift != 0.0)
+    for (int j = threadIdx.x; j < p; j += blockDim.x) G[(long long)j * ld + j].x += shift;
+  __syncthreads();
+  for (int j = 0; j < p; ++j) {
+    // pivot: d = G_jj - sum_k |L_jk|^2
+    double part = 0.0;
+    for (int k = threadIdx.x; k < j; k += blockDim.x) {
+      const double2 l = G[(long long)k * ld + j];
+      part += l.x * l.x + l.y * l.y;
+    }
+    part = block_sum(part, scratch);
+    if (threadIdx.x == 0) {
+      const double gjj = G[(long long)j * ld + j].x;
+      const double dj = gjj - part;
+      const bool bad = !(dj > rel_tol * fabs(gjj)) || !isfinite(dj);
+      if (bad) {
+        s_fail = 1;
+        atomicOr(err, KERR_CHOL_BREAKDOWN);
+      }
+      s_ljj = bad ? 1.0 : sqrt(dj);
+      G[(long long)j * ld + j] = make_double2(s_ljj, 0.0);
+    }
+    __syncthreads();
+    if (s_fail) return;
+    const double inv = 1.0 / s_ljj;
+    for (int i = j + 1 + threadIdx.x; i < p; i += blockDim.x) {
+      double2 acc = G[(long long)j * ld + i];
+      for (int k = 0; k < j; ++k) {
+        const double2 lik = G[(long long)k * ld + i];
+        const double2 ljk = G[(long long)k * ld + j];
+        // acc -= lik * conj(ljk)
+        acc.x -= lik.x * ljk.x + lik.y * ljk.y;
+        acc.y -= lik.y * ljk.x - lik.x * ljk.y;
+      }
+      G[(long long)j * ld + i] = make_double2(acc.x * inv, acc.y * inv);
+    }
+    __syncthreads();
+  }
+}
+
+// Column j of L^{-1} by forward substitution (thread per column), written
+// conjugated into row j of Rinv = (L^{-1})^H.
+__global__ void tri_inv_upper_kernel(const double2* __restrict__ L, long long ldl, int p,
+                                     double2* __restrict__ R, long long ldr) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < p; j += gridDim.x * blockDim.x) {
+    // x_j = 1 / L_jj
+    const double2 ljj = L[(long long)j * ldl + j];
+    double2 xj = make_double2(1.0 / ljj.x, 0.0);  // L_jj is real and positive
+    R[(long long)j * ldr + j] = make_double2(xj.x, -xj.y);
+    for (int i = j + 1; i < p; ++i) {
+      double sr = 0.0, si = 0.0;
+      for (int k = j; k < i; ++k) {
+        const double2 lik = L[(long long)k * ldl + i];
+        const double2 rk = R[(long long)k * ldr + j];  // conj(x_k)
+        const double xr = rk.x, xi = -rk.y;
+        sr += lik.x * xr - lik.y * xi;
+        si += lik.x * xi + lik.y * xr;
+      }
+      const double lii = L[(long long)i * ldl + i].x;
+      const double xr = -sr / lii, xi = -si / lii;
+      R[(long long)i * ldr + j] = make_double2(xr, -xi);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Lanczos
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kRed)
+    lanczos_step_kernel(long long N, int r, int step, const double2* __restrict__ Vj,
+                        const double2* __restrict__ Vprev, double2* __restrict__ W,
+                        double2* __restrict__ Vnext, double* __restrict__ alpha,
+                        double* __restrict__ beta) {
+  __shared__ double scratch[33];
+  const int c = blockIdx.x;
+  const double2* v = Vj + (long long)c * N;
+  double2* w = W + (long long)c * N;
+  // alpha = Re(v^H w)
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < N; i += blockDim.x) {
+    const double2 a = v[i], b = w[i];
+    s += a.x * b.x + a.y * b.y;
+  }
+  const double al = block_sum(s, scratch);
+  const double bprev = step > 0 ? beta[(step - 1) * r + c] : 0.0;
+  const double2* vp = step > 0 ? Vprev + (long long)c * N : nullptr;
+  double nrm = 0.0;
+  for (long long i = threadIdx.x; i < N; i += blockDim.x) {
+    const double2 a = v[i];
+    double2 b = w[i];
+    b.x -= al * a.x;
+    b.y -= al * a.y;
+    if (vp) {
+      const double2 pv = vp[i];
+      b.x -= bprev * pv.x;
+      b.y -= bprev * pv.y;
+    }
+    w[i] = b;
+    nrm += b.x * b.x + b.y * b.y;
+  }
+  const double be = sqrt(block_sum(nrm, scratch));
+  // beta is rounding noise once the Krylov space is invariant: stop the run
+  double scale = fabs(al);
+  for (int k = 0; k < step; ++k) scale = fmax(scale, fmax(fabs(alpha[k * r + c]), beta[k * r + c]));
+  const bool stop = !(be > 1e-13 * fmax(scale, be));
+  if (threadIdx.x == 0) {
+    alpha[step * r + c] = al;
+    beta[step * r + c] = be;
+  }
+  if (Vnext) {
+    double2* vn = Vnext + (long long)c * N;
+    const double f = stop ? 0.0 : 1.0 / be;
+    for (long long i = threadIdx.x; i < N; i += blockDim.x) {
+      const double2 b = w[i];
+      vn[i] = make_double2(b.x * f, b.y * f);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kRed) normalize_cols_kernel(double2* __restrict__ X, long long ldx,
+                                                              long long N) {
+  __shared__ double scratch[33];
+  double2* x = X + (long long)blockIdx.x * ldx;
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < N; i += blockDim.x) {
+    const double2 v = x[i];
+    s += v.x * v.x + v.y * v.y;
+  }
+  s = block_sum(s, scratch);
+  const double f = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+  for (long long i = threadIdx.x; i < N; i += blockDim.x) {
+    const double2 v = x[i];
+    x[i] = make_double2(v.x * f, v.y * f);
+  }
+}
+
+unsigned grid_for(long long n, int threads, unsigned cap = 65535u) {
+  long long g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  return static_cast<unsigned>(std::min<long long>(g, cap));
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+int zgram(Dev& d, int64_t N, const chase_c64* X, int64_t ldx, int p, const chase_c64* Y,
+          int64_t ldy, int q, chase_c64* C, int64_t ldc) {
+  if (p == 0 || q == 0) return CHASE_OK;
+  const int tp = (p + GT - 1) / GT, tq = (q + GT - 1) / GT;
+  // split K so that the grid covers the 152 SMs about four times
+  long long nsplit = std::max<long long>(1, (4 * 152) / std::max(1, tp * tq));
+  nsplit = std::min<long long>(nsplit, std::max<long long>(1, N / 256));
+  long long kchunk = (N + nsplit - 1) / nsplit;
+  kchunk = ((kchunk + GK - 1) / GK) * GK;
+  nsplit = (N + kchunk - 1) / kchunk;
+  if (nsplit < 1) nsplit = 1;
+  dim3 grid(tp, tq, static_cast<unsigned>(nsplit));
+  if (nsplit == 1) {
+    gram_kernel<<<grid, 128, 0, d.st>>>(reinterpret_cast<const double2*>(X), ldx, p,
+                                        reinterpret_cast<const double2*>(Y), ldy, q, N, kchunk,
+                                        reinterpret_cast<double2*>(C), ldc, 0);
+    note_launch();
+  CHASE_CUDA(cudaGetLastError());
+    return CHASE_OK;
+  }
+  double2* P = nullptr;
+  const long long pstride = (long long)p * q;
+  CHASE_TRY(d.alloc(&P, static_cast<size_t>(pstride * nsplit)));
+  gram_kernel<<<grid, 128, 0, d.st>>>(reinterpret_cast<const double2*>(X), ldx, p,
+                                      reinterpret_cast<const double2*>(Y), ldy, q, N, kchunk, P, p,
+                                      pstride);
+  note_launch();
+  CHASE_CUDA(cudaGetLastError());
+  sum_partials_kernel<<<grid_for(pstride, 256, 4096), 256, 0, d.st>>>(
+      P, p, q, static_cast<int>(nsplit), pstride, reinterpret_cast<double2*>(C), ldc);
+  note_launch();
+  CHASE_CUDA(cudaGetLastError());
+  return CHASE_OK;
+}
+
+int launch_filter_plan(Dev& d, const int* deg, int b, int max_allowed, int* perm, int* start,
+                       int* info) {
+  if (max_allowed > kMaxDeg) max_allowed = kMaxDeg;
+  filter_plan_kernel<<<1, 32, 0, d.st>>>(deg, b, max_allowed, perm, start, info, d.err);
+  note_launch();
+  CHASE_CUDA(cudaGetLastError());
+  return CHASE_OK;
+}
+
+int launch_permute_cols(Dev& d, const chase_c64* X, int64_t ldx, chase_c64* Y, int64_t ldy,
+                        int64_t N, int b, const int* perm, bool scatter) {
+  if (b == 0 || N == 0) return CHASE_OK;
+  if (b > 65535) {
+    set_error("permute: too many columns");
+    return CHASE_INVALID_ARG;
+  }
+  dim3 grid(grid_for(N, 256, 64), b);
+  permute_cols_kernel<<<grid, 256, 0, d.st>>>(reinterpret_cast<const double2*>(X), ldx,
+                                              reinterpret_cast<double2*>(Y), ldy, N, perm,
+                                              scatter ? 1 : 0);
+  note_launch();
+  CHASE_CUDA(cudaGetLastError());
+  return CHASE_OK;
+}
+
+int launch_col_norms(Dev& d, const chase_c64* X, int64_t ldx, int64_t N, int b, double* out) {
+  if (b == 0) return CHASE_OK;
+  col_norms_kernel<<<b, kRed, 0, d.st>>>(reinterpret_cast<const double2*>(X), ldx, N, out);
+  note_launch();
+  CHASE_CUDA(cudaGetLastError());
+  return CHASE_OK;
+}
+
+int launch_col_inv_scale(Dev& d, chase_c64* X, int64_t ldx, int64_t N, int b, const double* s) {
+  if (b == 0 || N == 0) return CHASE_OK;
+  if (b > 65535) {
+    set_error("column scaling: too many columns");
+    return CHASE_INVALID_ARG;
+  }
+  dim3 grid(grid_for(N, 256, 64), b);
+  col_inv_scale_kernel<<<grid, 256, 0, d.st>>>(reinterpret_cast<double2*>(X), ldx, N, s);
+  note_launch();
+  CHASE_CUDA(cudaGetLastError());
+  return CHASE_OK;
+}
+
+int launch_resid_norms(Dev& d, const chase_c64* HV, int64_t ldhv, const chase_c64* V, int64_t ldv,
+                       int64_t N, int b, const double* lam, double* res) {
+  if (b == 0) return CHASE_OK;
+  resid_norms_kernel<<<b, kRed, 0, d.st>>>(reinterpret_cast<const double2*>(HV), ldhv,
+                                           reinterpret_cast<const double2*>(V), ldv, N, lam, res);
+  note_launch();
+  CHASE_CUDA(cudaGetLastError());
+  return CHASE_OK;
+}
+
+int launch_hermitize(Dev& d, chase_c64* G, int64_t ldg, int p) {
+  if (p == 0) return CHASE_OK;
+  hermitize_kernel<<<grid_for((long long)p * p, 256, 4096), 256, 0, d.st>>>(
+      reinterpret_cast<double2*>(G), ldg, p);
+  note_launch();
+  CHASE_CUDA(cudaGetLastError());
+  return CHASE_OK;
+}
+
+int launch_zero_triangle(Dev& d, chase_c64* A, int64_t lda, int p, bool lower) {
+  if (p == 0) return CHASE_OK;
+  zero_triangle_kernel<<<grid_for((long long)p * p, 256, 4096), 256, 0, d.st>>>(
+      reinterpret_cast<double2*>(A), lda, p, lower ? 1 : 0);
+  note_launch();
+  CHASE_CUDA(cudaGetLastError());
+  return CHASE_OK;
+}
+
+int launch_cholesky(Dev& d, chase_c64* G, int64_t ldg, int p, double rel_tol, double shift) {
+  if (p == 0) return CHASE_OK;
+  cholesky_kernel<<<1, 1024, 0, d.st>>>(reinterpret_cast<double2*>(G), ldg, p, rel_tol, shift,
+                                        d.err);
+  note_launch();
+  CHASE_CUDA(cudaGetLastError());
+  return CHASE_OK;
+}
+
+int launch_tri_inv_upper(Dev& d, const chase_c64* L, int64_t ldl, int p, chase_c64* Rinv,
+                         int64_t ldr) {
+  if (p == 0) return CHASE_OK;
+  CHASE_TRY(launch_zero_triangle(d, Rinv, ldr, p, true));
+  tri_inv_upper_kernel<<<grid_for(p, 64, 1024), 64, 0, d.st>>>(
+      reinterpret_cast<const double2*>(L), ldl, p, reinterpret_cast<double2*>(Rinv), ldr);
+  note_launch();
+  CHASE_CUDA(cudaGetLastError());
+  return CHASE_OK;
+}
+
+int launch_lanczos_step(Dev& d, int64_t N, int r, int step, const chase_c64* Vj,
+                        const chase_c64* Vprev, chase_c64* W, chase_c64* Vnext, double* alpha,
+                        double* beta) {
+  lanczos_step_kernel<<<r, kRed, 0, d.st>>>(N, r, step, reinterpret_cast<const double2*>(Vj),
+                                            reinterpret_cast<const double2*>(Vprev),
+                                            reinterpret_cast<double2*>(W),
+                                            reinterpret_cast<double2*>(Vnext), alpha, beta);
+  note_launch();
+  CHASE_CUDA(cudaGetLastError());
+  return CHASE_OK;
+}
+
+int launch_normalize_cols(Dev& d, chase_c64* X, int64_t ldx, int64_t N, int r) {
+  if (r == 0) return CHASE_OK;
+  normalize_cols_kernel<<<r, kRed, 0, d.st>>>(reinterpret_cast<double2*>(X), ldx, N);
+  note_launch();
+  CHASE_CUDA(cudaGetLastError());
+  return CHASE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Projected eigensolve (Alg. 2 line 3): cuSOLVER zheevd, eigenvalues ascending
+// ---------------------------------------------------------------------------
+namespace {
+thread_local cusolverDnHandle_t t_solver = nullptr;
+}
+
+int eigh_device(Dev& d, chase_c64* G, int64_t ldg, int p, double* w_dev) {
+  if (p == 0) return CHASE_OK;
+  if (!t_solver) {
+    if (cusolverDnCreate(&t_solver) != CUSOLVER_STATUS_SUCCESS) {
+      t_solver = nullptr;
+      set_error("cusolverDnCreate failed");
+      return CHASE_EIGENSOLVER_ERROR;
+    }
+  }
+  if (cusolverDnSetStream(t_solver, d.st) != CUSOLVER_STATUS_SUCCESS) {
+    set_error("cusolverDnSetStream failed");
+    return CHASE_EIGENSOLVER_ERROR;
+  }
+  int lwork = 0;
+  if (cusolverDnZheevd_bufferSize(t_solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, p,
+                                  reinterpret_cast<cuDoubleComplex*>(G), static_cast<int>(ldg),
+                                  w_dev, &lwork) != CUSOLVER_STATUS_SUCCESS) {
+    set_error("cusolverDnZheevd_bufferSize failed");
+    return CHASE_EIGENSOLVER_ERROR;
+  }
+  cuDoubleComplex* work = nullptr;
+  int* info = nullptr;
+  CHASE_TRY(d.alloc(&work, static_cast<size_t>(std::max(lwork, 1))));
+  CHASE_TRY(d.alloc(&info, 1));
+  if (cusolverDnZheevd(t_solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, p,
+                       reinterpret_cast<cuDoubleComplex*>(G), static_cast<int>(ldg), w_dev, work,
+                       lwork, info) != CUSOLVER_STATUS_SUCCESS) {
+    set_error("cusolverDnZheevd failed to launch");
+    return CHASE_EIGENSOLVER_ERROR;
+  }
+  int h_info = 0;
+  CHASE_CUDA(cudaMemcpyAsync(&h_info, info, sizeof(int), cudaMemcpyDeviceToHost, d.st));
+  CHASE_CUDA(cudaStreamSynchronize(d.st));
+  if (h_info != 0) {
+    set_error("zheevd returned info = %d", h_info);
+    return CHASE_EIGENSOLVER_ERROR;
+  }
+  return CHASE_OK;
+}
+
+}  // namespace chase

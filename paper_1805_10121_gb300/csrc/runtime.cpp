@@ -1,0 +1,162 @@
+// Host runtime of libchase: error strings, tensor maps, device context,
+// pointer kinds and block copies.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "common.cuh"
+#include "context.hpp"
+
+namespace chase {
+
+namespace {
+thread_local char g_err[512] = "";
+std::atomic<long long> g_launches{0};
+}
+
+void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+int cuda_status(cudaError_t e, const char* what) {
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  if (e == cudaErrorMemoryAllocation) return CHASE_OUT_OF_MEMORY;
+  return CHASE_CUDA_ERROR;
+}
+
+// ---------------------------------------------------------------------------
+// Tensor maps (driver entry point fetched through the runtime, so the library
+// needs no link-time dependency on libcuda)
+// ---------------------------------------------------------------------------
+namespace {
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn g_encode = nullptr;
+std::once_flag g_encode_once;
+}  // namespace
+
+int make_tmap_c64(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld,
+                  int box_rows, int box_cols) {
+  std::call_once(g_encode_once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = reinterpret_cast<EncodeTiledFn>(fn);
+  });
+  if (!g_encode) {
+    set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return CHASE_CUDA_ERROR;
+  }
+  if ((reinterpret_cast<uintptr_t>(base) & 15) != 0) {
+    set_error("TMA operand base address is not 16-byte aligned");
+    return CHASE_INVALID_ARG;
+  }
+  cuuint64_t gdim[2] = {static_cast<cuuint64_t>(2 * rows), static_cast<cuuint64_t>(cols)};
+  cuuint64_t gstride[1] = {static_cast<cuuint64_t>(ld) * 16u};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(2 * box_rows), static_cast<cuuint32_t>(box_cols)};
+  cuuint32_t estride[2] = {1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<void*>(base), gdim,
+                        gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d) rows=%lld cols=%lld ld=%lld box=%dx%d", (int)r,
+              (long long)rows, (long long)cols, (long long)ld, box_rows, box_cols);
+    return CHASE_INVALID_ARG;
+  }
+  return CHASE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Device context
+// ---------------------------------------------------------------------------
+Dev::~Dev() {
+  for (void* p : bufs) cudaFreeAsync(p, st);
+  if (err) cudaFreeAsync(err, st);
+  cudaStreamSynchronize(st);
+}
+
+int Dev::init() {
+  void* p = nullptr;
+  CHASE_CUDA(cudaMallocAsync(&p, sizeof(int), st));
+  err = static_cast<int*>(p);
+  CHASE_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+  return CHASE_OK;
+}
+
+int Dev::alloc_bytes(void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return CHASE_OK;
+  cudaError_t e = cudaMallocAsync(p, bytes, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("device workspace allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    *p = nullptr;
+    return CHASE_OUT_OF_MEMORY;
+  }
+  bufs.push_back(*p);
+  return CHASE_OK;
+}
+
+int Dev::sync_check(const char* where) {
+  int h = 0;
+  CHASE_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e, where);
+  if (h & (KERR_TIMEOUT_FULL | KERR_TIMEOUT_EMPTY)) {
+    set_error("%s: a bounded wait in a kernel gave up (flags 0x%x)", where, h);
+    return CHASE_TIMEOUT;
+  }
+  if (h & KERR_BAD_DEGREE) {
+    set_error("%s: degrees must be even and in [2, 1024]", where);
+    return CHASE_INVALID_ARG;
+  }
+  if (h & KERR_CHOL_BREAKDOWN) {
+    set_error("%s: Cholesky breakdown", where);
+    return CHASE_QR_BREAKDOWN;
+  }
+  return CHASE_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int copy_block(Dev& d, chase_c64* dst, int64_t ldd, const chase_c64* src, int64_t lds, int64_t rows,
+               int64_t cols, cudaMemcpyKind kind) {
+  if (rows == 0 || cols == 0) return CHASE_OK;
+  CHASE_CUDA(cudaMemcpy2DAsync(dst, static_cast<size_t>(ldd) * sizeof(chase_c64), src,
+                               static_cast<size_t>(lds) * sizeof(chase_c64),
+                               static_cast<size_t>(rows) * sizeof(chase_c64),
+                               static_cast<size_t>(cols), kind, d.st));
+  return CHASE_OK;
+}
+
+}  // namespace chase
+
+extern "C" const char* chase_last_error(void) { return chase::g_err; }
+
+extern "C" long long chase_kernel_launches(void) {
+  return chase::g_launches.load(std::memory_order_relaxed);
+}

@@ -1,0 +1,241 @@
+// Complex FP64 GEMM with the Chebyshev-recurrence epilogue fused in:
+//
+//   C[:, j] = alpha * (A * B[:, j] - shift * B[0:M, j]) + beta * C[:, j],  j in [j0, j1)
+//
+// With A = H, B = the current filter block, shift = c, alpha = 2 tau / e and
+// beta = -tau sigma this is one step of the three-term recurrence (Eq. 7,
+// Alg. 4 line 9); the first step (Alg. 4 line 4) is alpha = sigma_1 / e,
+// beta = 0.  Restricting j to the active suffix [j0, j1) is the column
+// retirement of Alg. 4 lines 12-14.  The same kernel with shift = 0 forms H Q
+// for Rayleigh-Ritz and the block products of the orthogonalisation.
+//
+// GB300 mapping.  Every FP64 product runs on the FP64 tensor pipe through
+// mma.sync.m8n8k4.f64 (there is no f64 kind of tcgen05.mma).  On GB300 that
+// pipe delivers about 1 TFLOP/s, roughly 0.15 FLOP per byte of HBM
+// bandwidth, so every tile shape used here is compute bound by a wide margin;
+// the design goal is to keep the DMMA pipe of all 152 SMs busy:
+//  * operand tiles are streamed by TMA (cp.async.bulk.tensor) into a ring
+//    of shared-memory stages guarded by mbarriers; one producer warp issues
+//    the copies, four consumer warps issue DMMAs, so address generation and
+//    copies never occupy the math warps;
+//  * a complex product is four real DMMAs on the interleaved (re, im)
+//    operands read as 16-byte pairs from shared memory;
+//  * the shift, scale and axpby of the recurrence are applied while the
+//    accumulators are still in registers, so the filter makes one pass over
+//    its output per degree step;
+//  * every mbarrier wait is bounded; a wait that gives up records an error
+//    flag that the host turns into CHASE_TIMEOUT, and the producer drains
+//    its own copies in flight before the CTA exits.
+#include "common.cuh"
+#include "context.hpp"
+
+namespace chase {
+
+namespace {
+
+template <int BM_, int BN_, int BK_, int STAGES_, int WARPS_M_>
+struct Cfg {
+  static constexpr int BM = BM_, BN = BN_, BK = BK_, STAGES = STAGES_;
+  static constexpr int WARPS_M = WARPS_M_;
+  static constexpr int WARPS_N = 4 / WARPS_M_;
+  static constexpr int kConsumerWarps = 4;
+  static constexpr int kThreads = (kConsumerWarps + 1) * 32;
+  static constexpr int WTM = BM / WARPS_M;
+  static constexpr int WTN = BN / WARPS_N;
+  static constexpr int MI = WTM / 8;
+  static constexpr int NI = WTN / 8;
+  static constexpr int A_BYTES = BM * BK * 16;
+  static constexpr int B_BYTES = BK * BN * 16;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 2 * STAGES * 8 + 128;
+  static_assert(MI >= 1 && NI >= 1, "warp tile too small");
+  static_assert(WTM % 8 == 0 && WTN % 8 == 0, "warp tile must be a multiple of 8");
+  static_assert(BK % 4 == 0, "BK must be a multiple of 4");
+  static_assert(2 * BM <= 256 && 2 * BK <= 256 && BN <= 256, "TMA box limit");
+};
+
+template <class C>
+__global__ void __launch_bounds__(C::kThreads)
+    zgemm_tma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                     int M, int K, int j0, int j1, const double2* __restrict__ Bsh, long long ldb,
+                     double2* __restrict__ Cout, long long ldc, double alpha, double beta,
+                     double shift, int* __restrict__ err) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+  double2* sA = reinterpret_cast<double2*>(smem);                         // [STAGES][BK][BM]
+  double2* sB = reinterpret_cast<double2*>(smem + C::STAGES * C::A_BYTES);  // [STAGES][BN][BK]
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE_BYTES);
+  uint64_t* empty = full + C::STAGES;
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int row0 = blockIdx.x * C::BM;
+  const int col0 = j0 + blockIdx.y * C::BN;
+  const int nk = (K + C::BK - 1) / C::BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], C::kConsumerWarps);
+    }
+    fence_barrier_init();
+  }
+  __syncthreads();
+
+  if (warp == C::kConsumerWarps) {
+    // ---------------- producer: one thread issues every TMA copy ----------
+    if (lane == 0) {
+      prefetch_tmap(&tmA);
+      prefetch_tmap(&tmB);
+      int issued = 0;
+      for (int kt = 0; kt < nk; ++kt) {
+        const int s = kt % C::STAGES;
+        if (kt >= C::STAGES) {
+          if (!mbar_wait_bounded(&empty[s], ((kt / C::STAGES) & 1) ^ 1)) {
+            atomicOr(err, KERR_TIMEOUT_EMPTY);
+            break;
+          }
+        }
+        mbar_arrive_expect_tx(&full[s], C::STAGE_BYTES);
+        tma_load_2d(sA + s * C::BK * C::BM, &tmA, 2 * row0, kt * C::BK, &full[s]);
+        tma_load_2d(sB + s * C::BN * C::BK, &tmB, 2 * kt * C::BK, col0, &full[s]);
+        ++issued;
+      }
+      // Drain: no copy of this CTA may still be landing when it exits.
+      for (int kt = (issued > C::STAGES ? issued - C::STAGES : 0); kt < issued; ++kt) {
+        if (!mbar_wait_bounded(&full[kt % C::STAGES], (kt / C::STAGES) & 1))
+          atomicOr(err, KERR_TIMEOUT_FULL);
+      }
+    }
+    return;
+  }
+
+  // ---------------- consumers: DMMA on the staged tiles ---------------------
+  const int wm = warp % C::WARPS_M;
+  const int wn = warp / C::WARPS_M;
+  const int g = lane >> 2;  // fragment row (A, C) / column (B)
+  const int t = lane & 3;   // fragment k index (A, B) / column pair (C)
+
+  double acr[C::MI][C::NI][2];
+  double aci[C::MI][C::NI][2];
+#pragma unroll
+  for (int mi = 0; mi < C::MI; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < C::NI; ++ni) {
+      acr[mi][ni][0] = acr[mi][ni][1] = 0.0;
+      aci[mi][ni][0] = aci[mi][ni][1] = 0.0;
+    }
+
+  for (int kt = 0; kt < nk; ++kt) {
+    const int s = kt % C::STAGES;
+    if (!mbar_wait_bounded(&full[s], (kt / C::STAGES) & 1)) {
+      if (lane == 0) atomicOr(err, KERR_TIMEOUT_FULL);
+      return;
+    }
+    const double2* a_s = sA + s * C::BK * C::BM;
+    const double2* b_s = sB + s * C::BN * C::BK;
+#pragma unroll
+    for (int kk = 0; kk < C::BK; kk += 4) {
+      double2 af[C::MI], bf[C::NI];
+#pragma unroll
+      for (int mi = 0; mi < C::MI; ++mi)
+        af[mi] = a_s[(kk + t) * C::BM + wm * C::WTM + mi * 8 + g];
+#pragma unroll
+      for (int ni = 0; ni < C::NI; ++ni)
+        bf[ni] = b_s[(wn * C::WTN + ni * 8 + g) * C::BK + kk + t];
+#pragma unroll
+      for (int mi = 0; mi < C::MI; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < C::NI; ++ni) {
+          // (ar + i ai)(br + i bi) = (ar br - ai bi) + i (ar bi + ai br)
+          dmma_8x8x4(acr[mi][ni][0], acr[mi][ni][1], af[mi].x, bf[ni].x);
+          dmma_8x8x4(acr[mi][ni][0], acr[mi][ni][1], af[mi].y, -bf[ni].y);
+          dmma_8x8x4(aci[mi][ni][0], aci[mi][ni][1], af[mi].x, bf[ni].y);
+          dmma_8x8x4(aci[mi][ni][0], aci[mi][ni][1], af[mi].y, bf[ni].x);
+        }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+  }
+
+  // ---------------- fused epilogue: shift, scale, axpby ---------------------
+#pragma unroll
+  for (int mi = 0; mi < C::MI; ++mi) {
+    const int r = row0 + wm * C::WTM + mi * 8 + g;
+    if (r >= M) continue;
+#pragma unroll
+    for (int ni = 0; ni < C::NI; ++ni) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = col0 + wn * C::WTN + ni * 8 + 2 * t + h;
+        if (c >= j1) continue;
+        double vr = acr[mi][ni][h], vi = aci[mi][ni][h];
+        if (shift != 0.0) {
+          const double2 bv = Bsh[static_cast<long long>(c) * ldb + r];
+          vr -= shift * bv.x;
+          vi -= shift * bv.y;
+        }
+        vr *= alpha;
+        vi *= alpha;
+        double2* cp = Cout + static_cast<long long>(c) * ldc + r;
+        if (beta != 0.0) {
+          const double2 cv = *cp;
+          vr += beta * cv.x;
+          vi += beta * cv.y;
+        }
+        *cp = make_double2(vr, vi);
+      }
+    }
+  }
+}
+
+template <class C>
+int launch_cfg(Dev& d, int64_t M, int64_t K, const chase_c64* A, int64_t lda, const chase_c64* B,
+               int64_t ldb, int64_t ncols_b, chase_c64* Cm, int64_t ldc, int j0, int j1,
+               double alpha, double beta, double shift) {
+  CUtensorMap tmA, tmB;
+  CHASE_TRY(make_tmap_c64(&tmA, A, M, K, lda, C::BM, C::BK));
+  CHASE_TRY(make_tmap_c64(&tmB, B, K, ncols_b, ldb, C::BK, C::BN));
+  static bool attr_done = false;  // per instantiation
+  if (!attr_done) {
+    CHASE_CUDA(cudaFuncSetAttribute(zgemm_tma_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    C::SMEM));
+    attr_done = true;
+  }
+  dim3 grid(static_cast<unsigned>((M + C::BM - 1) / C::BM),
+            static_cast<unsigned>((j1 - j0 + C::BN - 1) / C::BN));
+  zgemm_tma_kernel<C><<<grid, C::kThreads, C::SMEM, d.st>>>(
+      tmA, tmB, static_cast<int>(M), static_cast<int>(K), j0, j1,
+      reinterpret_cast<const double2*>(B), ldb, reinterpret_cast<double2*>(Cm), ldc, alpha, beta,
+      shift, d.err);
+  note_launch();
+  CHASE_CUDA(cudaGetLastError());
+  return CHASE_OK;
+}
+
+using CfgWide = Cfg<64, 32, 16, 2, 2>;    // 64 x 32 tile, warps 2 x 2 (32 x 16 each)
+using CfgMid = Cfg<64, 16, 16, 2, 4>;     // 64 x 16 tile, warps 4 x 1 (16 x 16 each)
+using CfgNarrow = Cfg<64, 8, 16, 2, 4>;   // 64 x 8 tile, warps 4 x 1 (16 x 8 each)
+
+}  // namespace
+
+int zgemm(Dev& d, int64_t M, int64_t K, const chase_c64* A, int64_t lda, const chase_c64* B,
+          int64_t ldb, int64_t ncols_b, chase_c64* Cm, int64_t ldc, int j0, int j1, double alpha,
+          double beta, double shift) {
+  if (j1 <= j0 || M == 0) return CHASE_OK;
+  if (K == 0) {
+    set_error("zgemm: K == 0 is not supported");
+    return CHASE_INVALID_ARG;
+  }
+  if (shift != 0.0 && M != K) {
+    set_error("zgemm: the shifted product needs a square A");
+    return CHASE_INVALID_ARG;
+  }
+  const int w = j1 - j0;
+  if (w <= 8) return launch_cfg<CfgNarrow>(d, M, K, A, lda, B, ldb, ncols_b, Cm, ldc, j0, j1, alpha, beta, shift);
+  if (w <= 16) return launch_cfg<CfgMid>(d, M, K, A, lda, B, ldb, ncols_b, Cm, ldc, j0, j1, alpha, beta, shift);
+  return launch_cfg<CfgWide>(d, M, K, A, lda, B, ldb, ncols_b, Cm, ldc, j0, j1, alpha, beta, shift);
+}
+
+}  // namespace chase
