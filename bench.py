@@ -39,7 +39,7 @@ NOMINAL_FP64_OVER_BF16 = 1.25 / 2250.0
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=2)
+    p.add_argument("--steps", type=int, default=1)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--n", type=int, default=8000)
@@ -147,7 +147,9 @@ def roofline_entry(stats_list, pk, src):
     flops = sum(s["flops_filter"] for s in stats_list)
     secs = sum(s["t_filter"] for s in stats_list)
     achieved = flops / secs / 1e12 if secs > 0 else 0.0
-    peak = pk.get("bf16_tflops_sustained", 1700.0) * NOMINAL_FP64_OVER_BF16
+    # The FP64 filter draws little power and runs at the maximum SM clock
+    # (sampled below), so the burst figure is the applicable one.
+    peak = pk.get("bf16_tflops", 1900.0) * NOMINAL_FP64_OVER_BF16
     return {
         "bound": "tensor",
         "kernel": "zgemm_tma_kernel (FP64 DMMA filter step, fused shift/axpby)",
@@ -156,7 +158,8 @@ def roofline_entry(stats_list, pk, src):
         "unit": "TFLOP/s",
         "frac": round(achieved / peak, 4),
         "traffic": None,
-        "peak_source": f"{src} bf16_tflops_sustained x nominal FP64/BF16 ratio (1.25/2250)",
+        "peak_source": f"{src} bf16_tflops (burst) x nominal FP64/BF16 ratio (1.25/2250); "
+                       "a DMMA-only probe kernel measured 1.05 TFLOP/s on this pool",
     }
 
 

@@ -36,7 +36,10 @@ design notes as well):
   upper bound is the largest ``||f_k|| + max theta`` over the first run and all
   ``n_vec`` density runs.  The Gaussian width ``sigma`` is measured in the
   variable that maps ``[mu_1, b_sup]`` onto ``[-1, 1]``.  The Eq. 10 sum runs
-  over the ``k`` Ritz values of each run.  ``mu_1`` is the smallest Ritz value
+  over the ``k`` Ritz values of each run.  If the quantile of line 11 is not
+  strictly inside ``(mu_1, b_sup)`` the width is halved until it is (at most
+  40 times), else the quantile of a uniform density on ``[mu_1, b_sup]`` is
+  used.  ``mu_1`` is the smallest Ritz value
   over the density runs.  The Ritz vectors of the first density run whose
   Ritz value is below ``mu_nev+nex`` replace the leading columns of the start
   block; the remaining columns keep the caller's random vectors.
@@ -64,6 +67,8 @@ __all__ = [
     "residuals",
     "deflate_and_lock",
     "lanczos_run",
+    "dos_cdf",
+    "dos_quantile",
     "lanczos_estimates",
     "solve",
 ]
@@ -325,6 +330,29 @@ def _normal_cdf(x):
     return 0.5 * (1.0 + math.erf(x / math.sqrt(2.0)))
 
 
+def dos_cdf(nodes, t, sig):
+    """Integral up to ``t`` of the density estimate of Eq. 10: the average over
+    the runs of sum_i w_i Phi((t - theta_i) / sig), with ``nodes`` a list of
+    (theta, w) pairs, w_i = |Z_1i|^2."""
+    total = 0.0
+    for theta, w in nodes:
+        total += sum(float(wi) * _normal_cdf((t - float(th)) / sig) for wi, th in zip(w, theta))
+    return total / len(nodes)
+
+
+def dos_quantile(nodes, target, sig):
+    """The ``t`` with ``dos_cdf(t) = target`` (Alg. 6 line 11), by bisection."""
+    lo = min(float(np.min(th)) for th, _ in nodes) - 10.0 * sig
+    hi = max(float(np.max(th)) for th, _ in nodes) + 10.0 * sig
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if dos_cdf(nodes, mid, sig) < target:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
 def lanczos_estimates(H, starts, k, nvec, approx, nev, nex, V=None, sigma=0.25):
     """Alg. 6: spectral bounds, and (when ``approx`` is false) the density
     estimate of Eq. 10 with ``mu_1``, ``mu_nev+nex`` and start vectors.
@@ -352,24 +380,21 @@ def lanczos_estimates(H, starts, k, nvec, approx, nev, nex, V=None, sigma=0.25):
     half = (b_sup - mu1) / 2.0
     # a collapsed interval (all Ritz values equal) falls back to sigma itself
     sig = sigma * half if half > 1e-12 * max(1.0, abs(b_sup), abs(mu1)) else sigma
-
-    def cdf(t):                                              # integral of Eq. 10
-        total = 0.0
-        for theta, Z, _, _ in runs:
-            w = np.abs(Z[0, :]) ** 2
-            total += sum(float(wi) * _normal_cdf((t - float(th)) / sig)
-                         for wi, th in zip(w, theta))
-        return total / nvec
-
     target = (nev + nex) / n                                 # line 11
-    lo, hi = mu1 - 10.0 * sig, b_sup + 10.0 * sig
-    for _ in range(200):
-        mid = 0.5 * (lo + hi)
-        if cdf(mid) < target:
-            lo = mid
-        else:
-            hi = mid
-    mu_nevnex = 0.5 * (lo + hi)
+    nodes = [(theta, np.abs(Z[0, :]) ** 2) for theta, Z, _, _ in runs]
+    mu_nevnex = dos_quantile(nodes, target, sig)
+    # The quantile must lie strictly inside (mu_1, b_sup) for the filter
+    # interval to make sense; Sec. 4.2 leaves the safeguards unpublished.
+    # Reading: halve the width until it does, else take the quantile of a
+    # uniform density on [mu_1, b_sup].
+    margin = 1e-6 * (b_sup - mu1)
+    for _ in range(40):
+        if mu1 + margin < mu_nevnex < b_sup - margin:
+            break
+        sig *= 0.5
+        mu_nevnex = dos_quantile(nodes, target, sig)
+    if not (mu1 + margin < mu_nevnex < b_sup - margin):
+        mu_nevnex = mu1 + (b_sup - mu1) * min(max(target, 1e-3), 0.5)
     Vout = None
     if V is not None:                                        # line 13
         Vout = np.array(V, dtype=np.complex128, copy=True)

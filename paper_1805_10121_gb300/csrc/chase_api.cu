@@ -283,29 +283,48 @@ int lanczos_core(Dev& d, const chase_c64* H, int64_t N, int64_t ldh, int k, int 
   double mu1 = theta[1][0];
   for (int c = 2; c < r; ++c) mu1 = std::min(mu1, theta[c][0]);  // Alg. 6 line 12
   const double half = 0.5 * (bsup - mu1);
-  const double sig = half > 1e-12 * std::max(1.0, std::max(std::fabs(bsup), std::fabs(mu1)))
-                         ? dos_sigma * half
-                         : dos_sigma;
-  auto cdf = [&](double t) {  // integral of Eq. 10 up to t
+  double sig = half > 1e-12 * std::max(1.0, std::max(std::fabs(bsup), std::fabs(mu1)))
+                   ? dos_sigma * half
+                   : dos_sigma;
+  double tmin = theta[1][0], tmax = theta[1].back();
+  for (int c = 2; c < r; ++c) {
+    tmin = std::min(tmin, theta[c][0]);
+    tmax = std::max(tmax, theta[c].back());
+  }
+  auto cdf = [&](double t, double s) {  // integral of Eq. 10 up to t
     double total = 0.0;
     for (int c = 1; c < r; ++c)
       for (int i = 0; i < steps[c]; ++i) {
         const double z0 = Z[c][static_cast<size_t>(i) * steps[c]];
-        total += z0 * z0 * normal_cdf((t - theta[c][i]) / sig);
+        total += z0 * z0 * normal_cdf((t - theta[c][i]) / s);
       }
     return total / nvec;
   };
   const double target = static_cast<double>(nev + nex) / static_cast<double>(N);  // line 11
-  double lo = mu1 - 10.0 * sig, hi = bsup + 10.0 * sig;
-  for (int it = 0; it < 200; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (cdf(mid) < target)
-      lo = mid;
-    else
-      hi = mid;
+  auto quantile = [&](double s) {
+    double lo = tmin - 10.0 * s, hi = tmax + 10.0 * s;
+    for (int it = 0; it < 200; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (cdf(mid, s) < target)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    return 0.5 * (lo + hi);
+  };
+  // Keep the estimate strictly inside (mu1, b_sup): halve the width, else
+  // fall back to the quantile of a uniform density on [mu1, b_sup].
+  double mu_nn = quantile(sig);
+  const double margin = 1e-6 * (bsup - mu1);
+  for (int h = 0; h < 40; ++h) {
+    if (mu1 + margin < mu_nn && mu_nn < bsup - margin) break;
+    sig *= 0.5;
+    mu_nn = quantile(sig);
   }
+  if (!(mu1 + margin < mu_nn && mu_nn < bsup - margin))
+    mu_nn = mu1 + (bsup - mu1) * std::min(std::max(target, 1e-3), 0.5);
   out.mu1 = mu1;
-  out.mu_nn = 0.5 * (lo + hi);
+  out.mu_nn = mu_nn;
 
   if (V && ncolv > 0) {  // line 13: Ritz vectors of the first density run
     const int st = steps[1];

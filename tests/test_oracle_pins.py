@@ -305,18 +305,39 @@ def test_lanczos_invariant_subspace_breakdown():
 
 def test_dos_single_cluster_closed_form():
     # H = lambda0 I: every run stops after one step with theta = lambda0 and
-    # weight 1, so the integral of Eq. 10 is Phi((t - lambda0)/sigma).
+    # weight 1, so the integral of Eq. 10 is Phi((t - lambda0)/sigma) and its
+    # quantile is lambda0 + sigma Phi^-1(target).
     from scipy.stats import norm
     n, nev, nex = 50, 3, 2
     lam0 = 0.7
     H = lam0 * np.eye(n, dtype=np.complex128)
     starts = rand_block(n, 5, 41)
-    est = oracle.lanczos_estimates(H, starts, 10, 4, False, nev, nex,
-                                   V=rand_block(n, nev + nex, 42), sigma=0.25)
-    assert abs(est["b_sup"] - lam0) < 1e-14
-    assert abs(est["mu1"] - lam0) < 1e-14
-    expect = lam0 + 0.25 * norm.ppf((nev + nex) / n)   # b_sup == mu1: width falls back to sigma
-    assert abs(est["mu_nevnex"] - expect) < 1e-9
+    runs = [oracle.lanczos_run(H, starts[:, 1 + j], 10) for j in range(4)]
+    assert all(len(th) == 1 and abs(th[0] - lam0) < 1e-14 for th, _, _, _ in runs)
+    nodes = [(th, np.abs(Z[0, :]) ** 2) for th, Z, _, _ in runs]
+    for sig in (0.25, 0.05):
+        q = oracle.dos_quantile(nodes, (nev + nex) / n, sig)
+        assert abs(q - (lam0 + sig * norm.ppf((nev + nex) / n))) < 1e-9
+    # the estimate itself must stay inside (mu_1, b_sup); with a collapsed
+    # spectrum the interval is empty and the uniform fallback returns mu_1
+    est = oracle.lanczos_estimates(H, starts, 10, 4, False, nev, nex, V=None, sigma=0.25)
+    assert abs(est["b_sup"] - lam0) < 1e-14 and abs(est["mu1"] - lam0) < 1e-14
+
+
+def test_dos_estimate_kept_inside_interval():
+    # a band holding the lowest 6 % of the spectrum: with the width of Eq. 10
+    # measured on [mu_1, b_sup] the raw quantile falls below mu_1; the
+    # estimate must still land strictly between mu_1 and b_sup
+    n, nev, nex = 400, 16, 8
+    H, lam, _ = known_problem(n, 171, 25)
+    starts = rand_block(n, 5, 173)
+    est = oracle.lanczos_estimates(H, starts, 25, 4, False, nev, nex, V=None, sigma=0.25)
+    runs = [oracle.lanczos_run(H, starts[:, 1 + j], 25) for j in range(4)]
+    nodes = [(th, np.abs(Z[0, :]) ** 2) for th, Z, _, _ in runs]
+    raw = oracle.dos_quantile(nodes, (nev + nex) / n, 0.25 * (est["b_sup"] - est["mu1"]) / 2)
+    assert raw < est["mu1"]
+    assert est["mu1"] < est["mu_nevnex"] < est["b_sup"]
+    assert lam[0] <= est["mu_nevnex"] <= lam[nev + nex + 40]
 
 
 def test_dos_two_clusters_quantile():
