@@ -202,6 +202,27 @@ int chase_rayleigh_ritz(const chase_c64* H, int64_t N, int64_t ldh, chase_c64* Q
 int chase_residuals(const chase_c64* H, int64_t N, int64_t ldh, const chase_c64* V, int64_t ldv,
                     int b, const double* lambda, double* resid, void* stream);
 
+/* Residual norms with no device allocation (the paper has no counterpart:
+ * it exists for callers that cannot let a library allocate device memory,
+ * e.g. a host framework that owns all device memory through its own budgeted
+ * pool, or a latency-critical caller that cannot afford the device-wide
+ * synchronisation cudaMalloc/cudaFree may cause).  Same result as
+ * chase_residuals: resid[a] = ||H v_a - lambda_a v_a||_2.
+ * H        N x N (ldh), device
+ * V        N x b (ldv), device
+ * lambda   b doubles, device;  resid  b doubles out, device
+ * Scratch is a fixed static device array inside the library of 2^21
+ * complex128 entries (32 MiB), held by every GPU that loads the library
+ * until the process exits: requires N * b <= 2097152, else
+ * CHASE_INVALID_ARG.  Calls no cudaMalloc / cudaFree.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  All calls share the array:
+ * calls whose work overlaps on the GPU race.
+ * Errors: CHASE_INVALID_ARG (sizes, non-device arrays), CHASE_CUDA_ERROR,
+ * CHASE_TIMEOUT. */
+int chase_residuals_noalloc(const chase_c64* H, int64_t N, int64_t ldh, const chase_c64* V,
+                            int64_t ldv, int b, const double* lambda, double* resid, void* stream);
+
 /* The ChASE eigensolver (Alg. 1) for the nev smallest eigenpairs of H.
  * H        N x N Hermitian, ldh (host or device)
  * V        N x (nev + nex), ldv, in/out (same kind as H).  In: random

@@ -21,7 +21,7 @@ __all__ = [
     "ChaseError", "ChaseOpts", "ChaseStats", "lib", "lib_path", "declared_symbols",
     "chase_opts_default", "chase_last_error", "chase_kernel_launches", "chase_filter", "chase_lanczos",
     "chase_degrees", "chase_lock", "chase_tridiag_eigh", "chase_orthonormalize",
-    "chase_rayleigh_ritz", "chase_residuals", "chase_solve",
+    "chase_rayleigh_ritz", "chase_residuals", "chase_residuals_noalloc", "chase_solve",
     "CHASE_OK", "CHASE_INVALID_ARG", "CHASE_NOT_CONVERGED", "CHASE_QR_BREAKDOWN",
     "CHASE_BOUND_VIOLATION", "CHASE_CUDA_ERROR", "CHASE_OUT_OF_MEMORY", "CHASE_TIMEOUT",
     "CHASE_EIGENSOLVER_ERROR", "CHASE_CONV_ABS", "CHASE_CONV_REL", "CHASE_FP64",
@@ -95,6 +95,7 @@ _SIGNATURES = {
     "chase_orthonormalize": (_int, [_c_p, _i64, _i64, _int, _c_p, _i64, _int, _c_p]),
     "chase_rayleigh_ritz": (_int, [_c_p, _i64, _i64, _c_p, _i64, _int, _dp, _dp, _c_p]),
     "chase_residuals": (_int, [_c_p, _i64, _i64, _c_p, _i64, _int, _dp, _dp, _c_p]),
+    "chase_residuals_noalloc": (_int, [_c_p, _i64, _i64, _c_p, _i64, _int, _c_p, _c_p, _c_p]),
     "chase_solve": (_int, [_c_p, _i64, _i64, _int, _int, _dbl, _c_p, _i64, _dp, _dp, _c_p,
                            ctypes.POINTER(ChaseOpts), ctypes.POINTER(ChaseStats), _c_p]),
 }
@@ -298,6 +299,22 @@ def chase_residuals(H, V, lam, stream=None):
     _check(lib().chase_residuals(hp, n, ldh, vp, ldv, b, _dptr(lam), _dptr(out),
                                  _stream(V, stream)), "chase_residuals")
     return out
+
+
+def chase_residuals_noalloc(H, V, lam, resid, stream=None):
+    """Residual norms into the device tensor ``resid`` (float64, b) from the
+    device tensor ``lam``; the library allocates nothing for this call."""
+    n = H.shape[0]
+    hp, ldh = _mat(H, n, "H")
+    vp, ldv = _mat(V, n, "V")
+    b = V.shape[1]
+    for t, name in ((lam, "lam"), (resid, "resid")):
+        if t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != b:
+            raise ValueError(f"{name} must be a contiguous float64 tensor of {b} values")
+    _check(lib().chase_residuals_noalloc(hp, n, ldh, vp, ldv, b, ctypes.c_void_p(lam.data_ptr()),
+                                         ctypes.c_void_p(resid.data_ptr()), _stream(V, stream)),
+           "chase_residuals_noalloc")
+    return resid
 
 
 def chase_solve(H, nev, nex, tol, V, lanczos_starts, Lambda=None, opts=None, stream=None,
