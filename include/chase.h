@@ -52,8 +52,17 @@ typedef struct {
 #define CHASE_TIMEOUT 7           /* a bounded wait inside a kernel gave up */
 #define CHASE_EIGENSOLVER_ERROR 8 /* the projected eigensolve (Alg. 2 line 3) failed */
 
-/* ---- arithmetic of the filter products ---- */
-#define CHASE_FP64 0 /* complex128 products on the FP64 tensor pipe (DMMA) */
+/* ---- arithmetic of the filter products (Alg. 4) ---- */
+#define CHASE_FP64 0 /* complex128 products on the FP64 tensor pipe (mma.sync f64, ~1 TFLOP/s) */
+/* Split-BF16: both operands cut into seven 7-bit integer slices (one power-
+ * of-two scale per row of H without its diagonal and per column of the
+ * block), slice products on the BF16 tensor cores (tcgen05) with exactly
+ * accumulated leading levels; the diagonal of H and the recurrence's
+ * shift/scale/axpby are applied in FP64.  Each entry of a product is
+ * accurate to about 2^-49 max|off-diagonal row of H| max|column| per term.
+ * Reads H through its Hermitian symmetry; needs N <= 22000.  QR,
+ * Rayleigh-Ritz, residuals and Lanczos stay FP64. */
+#define CHASE_SPLIT_BF16 1
 
 /* ---- residual test used for locking (Alg. 3 line 4) ---- */
 #define CHASE_CONV_ABS 0 /* Res <= tol (the paper's absolute criterion, Sec. 6.1) */
@@ -71,7 +80,7 @@ typedef struct {
   int approx;       /* 1: V and Lambda hold an approximate solution (Sec. 3.3) */
   double dos_sigma; /* Gaussian width of Eq. 10 in the variable mapped to [-1, 1] (Sec. 4.2: 0.25) */
   int conv_mode;    /* CHASE_CONV_ABS or CHASE_CONV_REL */
-  int precision;    /* CHASE_FP64 */
+  int precision;    /* filter arithmetic: CHASE_FP64 or CHASE_SPLIT_BF16 */
 } chase_opts;
 
 /* Counters and per-phase times of one chase_solve call. */
@@ -116,14 +125,15 @@ long long chase_kernel_launches(void);
  *          (Sec. 4.1.3, Alg. 5 line 6).  Internally the columns are sorted by
  *          degree so that every product acts on a contiguous suffix; a column
  *          leaves the products once it reaches its degree (Alg. 4 lines 12-14).
+ * precision  CHASE_FP64 or CHASE_SPLIT_BF16.
  * work     N x b device workspace with leading dimension N, or NULL (the
  *          library allocates it); ignored for host V.
  * Requires mu1 < mu_nevnex < b_sup.  b == 0 or N == 0 is a no-op.
  * Errors: CHASE_INVALID_ARG (sizes, bounds, odd or out-of-range degree,
  * misaligned pointer), CHASE_OUT_OF_MEMORY, CHASE_CUDA_ERROR, CHASE_TIMEOUT. */
 int chase_filter(const chase_c64* H, int64_t N, int64_t ldh, chase_c64* V, int64_t ldv, int b,
-                 const int* degrees, double b_sup, double mu1, double mu_nevnex, chase_c64* work,
-                 void* stream);
+                 const int* degrees, double b_sup, double mu1, double mu_nevnex, int precision,
+                 chase_c64* work, void* stream);
 
 /* Spectral estimates by Lanczos (Alg. 6, Sec. 4.2).
  * starts   N x (1 + nvec) start vectors, leading dimension N (host or device);

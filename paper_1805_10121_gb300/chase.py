@@ -25,6 +25,7 @@ __all__ = [
     "CHASE_OK", "CHASE_INVALID_ARG", "CHASE_NOT_CONVERGED", "CHASE_QR_BREAKDOWN",
     "CHASE_BOUND_VIOLATION", "CHASE_CUDA_ERROR", "CHASE_OUT_OF_MEMORY", "CHASE_TIMEOUT",
     "CHASE_EIGENSOLVER_ERROR", "CHASE_CONV_ABS", "CHASE_CONV_REL", "CHASE_FP64",
+    "CHASE_SPLIT_BF16",
 ]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -40,6 +41,7 @@ CHASE_OUT_OF_MEMORY = 6
 CHASE_TIMEOUT = 7
 CHASE_EIGENSOLVER_ERROR = 8
 CHASE_FP64 = 0
+CHASE_SPLIT_BF16 = 1
 CHASE_CONV_ABS = 0
 CHASE_CONV_REL = 1
 
@@ -86,7 +88,8 @@ _SIGNATURES = {
     "chase_opts_default": (_int, [ctypes.POINTER(ChaseOpts)]),
     "chase_last_error": (ctypes.c_char_p, []),
     "chase_kernel_launches": (ctypes.c_longlong, []),
-    "chase_filter": (_int, [_c_p, _i64, _i64, _c_p, _i64, _int, _c_p, _dbl, _dbl, _dbl, _c_p, _c_p]),
+    "chase_filter": (_int, [_c_p, _i64, _i64, _c_p, _i64, _int, _c_p, _dbl, _dbl, _dbl, _int, _c_p,
+                            _c_p]),
     "chase_lanczos": (_int, [_c_p, _i64, _i64, _int, _int, _int, _int, _int, _dbl, _c_p, _c_p,
                              _i64, _dp, _dp, _dp, _dp, _c_p]),
     "chase_degrees": (_int, [_int, _dp, _dp, _dbl, _dbl, _dbl, _int, _int, _ip]),
@@ -191,7 +194,8 @@ def chase_opts_default(**overrides) -> ChaseOpts:
     return o
 
 
-def chase_filter(H, V, degrees, b_sup, mu1, mu_nevnex, work=None, stream=None):
+def chase_filter(H, V, degrees, b_sup, mu1, mu_nevnex, work=None, stream=None,
+                 precision=CHASE_FP64):
     """Filter the columns of V in place (Alg. 4).  ``degrees``: int32 tensor
     (host or device) or a sequence of ints."""
     n = H.shape[0]
@@ -210,7 +214,7 @@ def chase_filter(H, V, degrees, b_sup, mu1, mu_nevnex, work=None, stream=None):
         raise ValueError("one degree per column")
     wp = ctypes.c_void_p(work.data_ptr()) if work is not None else None
     st = lib().chase_filter(hp, n, ldh, vp, ldv, b, dptr, float(b_sup), float(mu1),
-                            float(mu_nevnex), wp, _stream(V, stream))
+                            float(mu_nevnex), int(precision), wp, _stream(V, stream))
     _check(st, "chase_filter")
     return V
 

@@ -22,6 +22,7 @@ namespace chase {
 namespace {
 
 constexpr int kMaxDegAllowed = 1024;
+constexpr int64_t kSplitMaxN = 22000;  // exact int32 level sums of the split-BF16 product
 
 // Events bracketing the phases of one call, accumulated into seconds.
 struct PhaseTimer {
@@ -54,14 +55,24 @@ struct PhaseTimer {
 // is the second buffer of the double buffering.  start[i] = number of
 // columns with degree < i for i = 0 .. maxdeg + 1 (columns with degree < i
 // have retired before step i).  Returns the column-product count.
+// One filter product: the FP64 DMMA kernel, or the split-BF16 tensor-core
+// kernel when slices of H are given.
+int filter_product(Dev& d, const chase_c64* H, int64_t N, int64_t ldh, const SplitH* sh, SplitX* sx,
+                   const chase_c64* X, int64_t ldx, int b, chase_c64* Y, int64_t ldy, int j0,
+                   double alpha, double beta, double shift) {
+  if (sh) return zgemm_split(d, *sh, *sx, X, ldx, j0, b, Y, ldy, alpha, beta, shift);
+  return zgemm(d, N, N, H, ldh, X, ldx, b, Y, ldy, j0, b, alpha, beta, shift);
+}
+
 int filter_sorted(Dev& d, const chase_c64* H, int64_t N, int64_t ldh, chase_c64* X, int64_t ldx,
                   chase_c64* Wk, int64_t ldw, int b, const int* start, int maxdeg, double b_sup,
-                  double mu1, double mu_nn, long long* matvecs) {
+                  double mu1, double mu_nn, long long* matvecs, const SplitH* sh = nullptr,
+                  SplitX* sx = nullptr) {
   const double c = 0.5 * (b_sup + mu_nn);  // Alg. 4 line 2
   const double e = 0.5 * (b_sup - mu_nn);
   const double sigma1 = e / (mu1 - c);     // line 3
   // line 4: W = (sigma_1 / e) (H - c I) V
-  CHASE_TRY(zgemm(d, N, N, H, ldh, X, ldx, b, Wk, ldw, 0, b, sigma1 / e, 0.0, c));
+  CHASE_TRY(filter_product(d, H, N, ldh, sh, sx, X, ldx, b, Wk, ldw, 0, sigma1 / e, 0.0, c));
   long long mv = b;
   double sigma = sigma1;  // line 5
   chase_c64* Vb = X;
@@ -71,7 +82,8 @@ int filter_sorted(Dev& d, const chase_c64* H, int64_t N, int64_t ldh, chase_c64*
     const double tau = 1.0 / (2.0 / sigma1 - sigma);  // line 8
     const int s = start[i];  // lines 12-14: columns with degree < i are done
     // line 9: V[:, s:] = 2 (tau / e) (H - c I) W[:, s:] - tau sigma V[:, s:]
-    CHASE_TRY(zgemm(d, N, N, H, ldh, Wb, ldW, b, Vb, ldV, s, b, 2.0 * tau / e, -tau * sigma, c));
+    CHASE_TRY(filter_product(d, H, N, ldh, sh, sx, Wb, ldW, b, Vb, ldV, s, 2.0 * tau / e,
+                             -tau * sigma, c));
     mv += b - s;
     std::swap(Vb, Wb);  // line 10
     std::swap(ldV, ldW);
@@ -391,7 +403,15 @@ extern "C" int chase_opts_default(chase_opts* o) {
 
 extern "C" int chase_filter(const chase_c64* H, int64_t N, int64_t ldh, chase_c64* V, int64_t ldv,
                             int b, const int* degrees, double b_sup, double mu1, double mu_nevnex,
-                            chase_c64* work, void* stream) {
+                            int precision, chase_c64* work, void* stream) {
+  if (precision != CHASE_FP64 && precision != CHASE_SPLIT_BF16) {
+    set_error("chase_filter: unknown precision %d", precision);
+    return CHASE_INVALID_ARG;
+  }
+  if (precision == CHASE_SPLIT_BF16 && N > kSplitMaxN) {
+    set_error("chase_filter: split-BF16 needs N <= %d", kSplitMaxN);
+    return CHASE_INVALID_ARG;
+  }
   if (N < 0 || b < 0 || !ld_ok(ldh, N) || !ld_ok(ldv, N) || N > (1LL << 30)) {
     set_error("chase_filter: invalid size or leading dimension");
     return CHASE_INVALID_ARG;
@@ -435,10 +455,16 @@ extern "C" int chase_filter(const chase_c64* H, int64_t N, int64_t ldh, chase_c6
   CHASE_CUDA(cudaMemcpyAsync(start.data(), dstart, sizeof(int) * start.size(), cudaMemcpyDeviceToHost, d.st));
   CHASE_CUDA(cudaMemcpyAsync(&maxdeg, dinfo, sizeof(int), cudaMemcpyDeviceToHost, d.st));
   CHASE_TRY(d.sync_check("chase_filter plan"));
+  SplitH sh;
+  SplitX sx;
+  if (precision == CHASE_SPLIT_BF16) {
+    CHASE_TRY(split_prepare_h(d, dH, N, lh, sh));
+    CHASE_TRY(split_alloc_x(d, N, b, sx));
+  }
   // sorted copy into the workspace; V becomes the second buffer
   CHASE_TRY(launch_permute_cols(d, dV, lv, wk, N, N, b, dperm, false));
   CHASE_TRY(filter_sorted(d, dH, N, lh, wk, N, dV, lv, b, start.data(), maxdeg, b_sup, mu1,
-                          mu_nevnex, nullptr));
+                          mu_nevnex, nullptr, precision == CHASE_SPLIT_BF16 ? &sh : nullptr, &sx));
   CHASE_TRY(launch_permute_cols(d, wk, N, dV, lv, N, b, dperm, true));
   if (!dev) CHASE_TRY(copy_block(d, V, ldv, dV, lv, N, b, cudaMemcpyDeviceToHost));
   return d.sync_check("chase_filter");
@@ -586,7 +612,9 @@ extern "C" int chase_solve(const chase_c64* H, int64_t N, int64_t ldh, int nev, 
       !H || !V || !Lambda || !resid || !lanczos_starts || o.deg < 1 ||
       o.deg > kMaxDegAllowed - 1 || o.deg_max < 2 || o.deg_max > kMaxDegAllowed ||
       o.deg_extra < 0 || o.max_iter < 0 || o.lanczos_iter < 1 || o.lanczos_iter > N ||
-      (!o.approx && o.num_lanczos < 1) || o.precision != CHASE_FP64 ||
+      (!o.approx && o.num_lanczos < 1) ||
+      (o.precision != CHASE_FP64 && o.precision != CHASE_SPLIT_BF16) ||
+      (o.precision == CHASE_SPLIT_BF16 && N > kSplitMaxN) ||
       (o.conv_mode != CHASE_CONV_ABS && o.conv_mode != CHASE_CONV_REL)) {
     set_error("chase_solve: invalid argument");
     return CHASE_INVALID_ARG;
@@ -615,6 +643,13 @@ extern "C" int chase_solve(const chase_c64* H, int64_t N, int64_t ldh, int nev, 
   CHASE_TRY(orth_alloc(d, N, nx, nx, ow));
   RRWork rw;
   CHASE_TRY(rr_alloc(d, N, nx, rw));
+  SplitH sh;
+  SplitX sx;
+  const bool split = o.precision == CHASE_SPLIT_BF16;
+  if (split) {  // slices of H once per solve, slice workspace for the block
+    CHASE_TRY(split_prepare_h(d, dH, N, lh, sh));
+    CHASE_TRY(split_alloc_x(d, N, nx, sx));
+  }
   double *dw = nullptr, *dres = nullptr;
   int* dperm = nullptr;
   CHASE_TRY(d.alloc(&dw, nx));
@@ -664,7 +699,7 @@ extern "C" int chase_solve(const chase_c64* H, int64_t N, int64_t ldh, int nev, 
     long long fm = 0;
     tm.begin(&S.t_filter);
     CHASE_TRY(filter_sorted(d, dH, N, lh, Va, lv, Wk, N, b, start.data(), maxdeg, b_sup, mu1, mu_nn,
-                            &fm));
+                            &fm, split ? &sh : nullptr, &sx));
     tm.end();
     S.filter_matvecs += fm;
     S.matvecs += fm;

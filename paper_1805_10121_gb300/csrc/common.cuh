@@ -124,6 +124,10 @@ __device__ __forceinline__ void dmma_8x8x4(double& d0, double& d1, double a, dou
 // as a 2-D float64 tensor {2*rows, cols}; box {2*box_rows, box_cols}.
 int make_tmap_c64(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld,
                   int box_rows, int box_cols);
+// A 3-D bf16 tensor {d0, d1, d2} with byte strides s1 (dim 1) and s2 (dim 2),
+// box {b0, b1, b2}, 32-byte swizzle (b0 * 2 must be 32).
+int make_tmap_bf16_3d(CUtensorMap* map, const void* base, int64_t d0, int64_t d1, int64_t d2,
+                      int64_t s1, int64_t s2, int b0, int b1, int b2);
 
 // ----------------------------------------------------------------------------
 // Host: launch wrappers implemented in the .cu files

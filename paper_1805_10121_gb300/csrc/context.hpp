@@ -73,6 +73,26 @@ int launch_normalize_cols(Dev& d, chase_c64* X, int64_t ldx, int64_t N, int r);
 // Fill the strict lower (lower=true) or upper part of a p x p matrix with zero.
 int launch_zero_triangle(Dev& d, chase_c64* A, int64_t lda, int p, bool lower);
 
+// ---- zgemm_split.cu: split-BF16 filter product on the tensor cores --------
+// Slices of Ht = [Re H | Im H] (S planes of N x Kp bf16) and row exponents.
+struct SplitH {
+  void* A = nullptr;
+  int* E = nullptr;
+  double* Dg = nullptr;  // real diagonal of H, applied in FP64 by the epilogue
+  int64_t N = 0, Kp = 0;
+};
+// Slice workspace for up to max_cols complex columns of the filter block.
+struct SplitX {
+  void* B = nullptr;
+  int* F = nullptr;
+  int cap_cols = 0;
+};
+int split_prepare_h(Dev& d, const chase_c64* H, int64_t N, int64_t ldh, SplitH& out);
+int split_alloc_x(Dev& d, int64_t N, int max_cols, SplitX& out);
+// C[:, j0:j1] = alpha (H X[:, j0:j1] - shift X[:, j0:j1]) + beta C[:, j0:j1]
+int zgemm_split(Dev& d, const SplitH& h, SplitX& x, const chase_c64* X, int64_t ldx, int j0, int j1,
+                chase_c64* C, int64_t ldc, double alpha, double beta, double shift);
+
 // ---- eigh (cuSOLVER, the small projected eigensolve of Alg. 2 line 3) -----
 int eigh_device(Dev& d, chase_c64* G, int64_t ldg, int p, double* w_dev);
 

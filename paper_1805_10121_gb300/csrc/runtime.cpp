@@ -81,6 +81,42 @@ int make_tmap_c64(CUtensorMap* map, const void* base, int64_t rows, int64_t cols
   return CHASE_OK;
 }
 
+int make_tmap_bf16_3d(CUtensorMap* map, const void* base, int64_t d0, int64_t d1, int64_t d2,
+                      int64_t s1, int64_t s2, int b0, int b1, int b2) {
+  EncodeTiledFn enc = nullptr;
+  std::call_once(g_encode_once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = reinterpret_cast<EncodeTiledFn>(fn);
+  });
+  enc = g_encode;
+  if (!enc) {
+    set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return CHASE_CUDA_ERROR;
+  }
+  if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (s1 & 15) != 0 || (s2 & 15) != 0 || b0 * 2 != 32) {
+    set_error("bf16 tensor map: misaligned base/stride or box");
+    return CHASE_INVALID_ARG;
+  }
+  cuuint64_t gdim[3] = {static_cast<cuuint64_t>(d0), static_cast<cuuint64_t>(d1),
+                        static_cast<cuuint64_t>(d2)};
+  cuuint64_t gstride[2] = {static_cast<cuuint64_t>(s1), static_cast<cuuint64_t>(s2)};
+  cuuint32_t box[3] = {static_cast<cuuint32_t>(b0), static_cast<cuuint32_t>(b1),
+                       static_cast<cuuint32_t>(b2)};
+  cuuint32_t estride[3] = {1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), gdim, gstride,
+                   box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled (bf16 3-D) failed (%d)", (int)r);
+    return CHASE_INVALID_ARG;
+  }
+  return CHASE_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Device context
 // ---------------------------------------------------------------------------

@@ -1,0 +1,489 @@
+// Complex GEMM with the Chebyshev-recurrence epilogue on the BF16 tensor cores
+// (tcgen05), accurate to about 1e-11 relative: the "split-BF16" filter product.
+//
+//   C[:, j] = alpha * (H X[:, j] - shift * X[:, j]) + beta * C[:, j],  j in [j0, j1)
+//
+// Why.  GB300 runs FP64 at about 1 TFLOP/s and BF16 at about 2 PFLOP/s.  The
+// filter product is exact integer arithmetic once both operands are cut into
+// 7-bit integer slices with one power-of-two scale per row of H and per column
+// of X, so it can run on the BF16 tensor pipe without giving up accuracy:
+//
+//   Ht[r, :] = [Re H[r, :], Im H[r, :]] = 2^E_r  sum_s a_s[r, :] 2^-7(s+1)
+//   Xt[:, 2c] = [Re X[:, c]; -Im X[:, c]],  Xt[:, 2c+1] = [Im X[:, c]; Re X[:, c]]
+//             = 2^F_c sum_t b_t[:, .] 2^-7(t+1)
+//   (H X)(r, c) = 2^(E_r + F_c - 14) sum_d 2^-7d L_d,   L_d = sum_{s+t=d} a_s b_t
+//
+// with a_s, b_t integers in [-127, 127] (exact in BF16).  S = 7 slices per
+// operand keep the 28 pairs with s + t <= 6; truncation and the dropped pairs
+// leave a relative error near 2^-49 of max|row| max|column| per entry.
+//
+// Diagonal.  The slices carry H without its (real) diagonal: the diagonal of
+// a Hermitian matrix is often far larger than its other entries (it holds
+// the mean eigenvalue), and a row scale set by it would waste the slices'
+// bits on every other entry.  The epilogue adds (H_rr - shift) X[r, c] in
+// FP64, next to the recurrence's own shift.
+//
+// Exactness.  Products of slices are integers below 2^14, so a level-d sum is
+// exact in an FP32 accumulator while it stays below 2^24: levels 0-2 are
+// flushed from TMEM into exact int32 sums in shared memory every 256 K
+// (3 * 256 * 127^2 < 2^24); levels 3-6, already scaled by 2^-21 or less,
+// accumulate in FP32 over the whole K.  The int32 sums bound K = 2N below
+// 44380 (N <= 22000).
+//
+// Structure (one CTA = 128 rows of H x 32 complex columns, 192 threads):
+//  * warp 0: TMA producer, one 3-D box per operand per stage loads all S
+//    slices of a 16-wide K block (SWIZZLE_32B), 3-stage mbarrier ring;
+//  * warp 1: allocates 512 TMEM columns (7 levels x 64 FP32 columns) and one
+//    thread issues the 28 tcgen05.mma (M=128, N=64, K=16) per K block,
+//    committing stages back to the producer and chunks to the flush warps;
+//  * warps 2-5: flush the exact levels every chunk, then combine all levels in
+//    FP64 and apply the recurrence's shift, scale and axpby (Eq. 7) while
+//    writing the FP64 output.
+// Every wait is bounded; a wait that gives up sets the error flag.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "context.hpp"
+
+namespace chase {
+namespace split {
+constexpr int S = 7;                 // 7-bit slices per operand
+constexpr int BM = 128;              // rows per CTA (TMEM lanes)
+constexpr int BN = 64;               // real columns of the product per CTA (32 complex)
+constexpr int BK = 16;               // K per stage (one 32-byte swizzle row)
+constexpr int NSTAGE = 3;
+constexpr int CHUNK = 16;            // k-blocks per exact chunk (256 K)
+constexpr int NEXACT = 3;            // levels accumulated exactly
+constexpr int A_TILE = BM * BK * 2;  // 4096 B per slice
+constexpr int B_TILE = BN * BK * 2;  // 2048 B per slice
+constexpr int STAGE_A = S * A_TILE;
+constexpr int STAGE_B = S * B_TILE;
+constexpr int STAGE_BYTES = STAGE_A + STAGE_B;
+constexpr int SUM_BYTES = NEXACT * BM * BN * 4;
+constexpr int TMEM_COLS = 512;
+constexpr int kThreads = 192;
+constexpr int SMEM = 1024 + NSTAGE * STAGE_BYTES + SUM_BYTES + 256;
+
+__device__ __forceinline__ uint64_t desc_sw32(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;                 // LBO (unused for swizzled K-major)
+  d |= (uint64_t)(256 >> 4) << 32;        // SBO: 8 rows x 32 B
+  d |= (uint64_t)1 << 46;                 // version
+  d |= (uint64_t)6 << 61;                 // SWIZZLE_32B
+  return d;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
+                                          uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(da), "l"(db), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+               : "memory");
+}
+
+#define TMEM_LD32(taddr, r)                                                                          \
+  asm volatile(                                                                                      \
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15," \
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"                   \
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),         \
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),      \
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),   \
+        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),   \
+        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])                                           \
+      : "r"(taddr))
+
+__global__ void __launch_bounds__(kThreads, 1)
+    zgemm_split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                    const int* __restrict__ Erow, const int* __restrict__ Fcol,
+                    const double* __restrict__ Dg, int M, int nkb,
+                    int ncols, int j0, const double2* __restrict__ Xsh, long long ldx,
+                    double2* __restrict__ Y, long long ldy, double alpha, double beta, double shift,
+                    int* __restrict__ err) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  unsigned char* sA = sm;
+  unsigned char* sB = sm + NSTAGE * STAGE_A;
+  int* sums = reinterpret_cast<int*>(sm + NSTAGE * STAGE_BYTES);  // [NEXACT][BN][BM]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + NSTAGE * STAGE_BYTES + SUM_BYTES);
+  uint64_t* full = bars;                 // [NSTAGE]
+  uint64_t* empty = bars + NSTAGE;       // [NSTAGE]
+  uint64_t* chunk_full = bars + 2 * NSTAGE;
+  uint64_t* chunk_empty = chunk_full + 1;
+  uint64_t* done = chunk_full + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(chunk_full + 3);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row0 = blockIdx.y * BM;
+  const int colr0 = blockIdx.x * BN;  // first real column (relative to the active block)
+  const int nchunks = (nkb + CHUNK - 1) / CHUNK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NSTAGE; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(chunk_full, 1);
+    mbar_init(chunk_empty, 4);
+    mbar_init(done, 1);
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {  // ---------------- TMA producer
+      prefetch_tmap(&tmA);
+      prefetch_tmap(&tmB);
+      int issued = 0;
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int st = kb % NSTAGE;
+        if (kb >= NSTAGE && !mbar_wait_bounded(&empty[st], ((kb / NSTAGE) & 1) ^ 1)) {
+          atomicOr(err, KERR_TIMEOUT_EMPTY);
+          break;
+        }
+        mbar_arrive_expect_tx(&full[st], STAGE_BYTES);
+        tma_load_3d(smem_u32(sA + st * STAGE_A), &tmA, kb * BK, row0, 0, smem_u32(&full[st]));
+        tma_load_3d(smem_u32(sB + st * STAGE_B), &tmB, kb * BK, colr0, 0, smem_u32(&full[st]));
+        ++issued;
+      }
+      for (int kb = (issued > NSTAGE ? issued - NSTAGE : 0); kb < issued; ++kb)
+        if (!mbar_wait_bounded(&full[kb % NSTAGE], (kb / NSTAGE) & 1)) atomicOr(err, KERR_TIMEOUT_FULL);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // ---------------- MMA issuer
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                             ((uint32_t)(BM >> 4) << 24);
+      bool ok = true;
+      for (int kb = 0; kb < nkb && ok; ++kb) {
+        const int st = kb % NSTAGE;
+        const int ch = kb / CHUNK, kin = kb % CHUNK;
+        if (kin == 0 && ch > 0 && !mbar_wait_bounded(chunk_empty, (ch - 1) & 1)) {
+          atomicOr(err, KERR_TIMEOUT_FULL);
+          ok = false;
+          break;
+        }
+        if (!mbar_wait_bounded(&full[st], (kb / NSTAGE) & 1)) {
+          atomicOr(err, KERR_TIMEOUT_FULL);
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const uint32_t a0 = smem_u32(sA + st * STAGE_A);
+        const uint32_t b0 = smem_u32(sB + st * STAGE_B);
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+#pragma unroll
+          for (int t = 0; t + s < S; ++t) {
+            const int d = s + t;
+            // first contribution to level d in this accumulation window?
+            const bool first = (s == 0) && (d < NEXACT ? kin == 0 : kb == 0);
+            umma_bf16(tmem + d * BN, desc_sw32(a0 + s * A_TILE), desc_sw32(b0 + t * B_TILE), idesc,
+                      first ? 0u : 1u);
+          }
+        }
+        umma_commit(smem_u32(&empty[st]));
+        if (kin == CHUNK - 1 || kb == nkb - 1) umma_commit(smem_u32(chunk_full));
+      }
+      umma_commit(smem_u32(done));  // every MMA of this CTA has completed when this fires
+      if (!mbar_wait_bounded(done, 0)) atomicOr(err, KERR_TIMEOUT_FULL);
+    }
+  } else {
+    // ---------------- flush and epilogue (warps 2..5)
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    const uint32_t tbase = tmem + (static_cast<uint32_t>(q * 32) << 16);
+    bool ok = true;
+    for (int ch = 0; ch < nchunks; ++ch) {
+      if (!mbar_wait_bounded(chunk_full, ch & 1)) {
+        if (lane == 0) atomicOr(err, KERR_TIMEOUT_FULL);
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+#pragma unroll 1
+      for (int d = 0; d < NEXACT; ++d) {
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+          uint32_t r[32];
+          TMEM_LD32(tbase + d * BN + c0, r);
+          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+          int* dst = sums + (d * BN + c0) * BM + row;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int v = __float2int_rn(__uint_as_float(r[j]));
+            dst[j * BM] = (ch == 0) ? v : dst[j * BM] + v;
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(chunk_empty);
+    }
+    if (ok) {
+      // last chunk_full covers every MMA, tail levels included
+      const int grow = row0 + row;
+      const int er = grow < M ? Erow[grow] : 0;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        double acc[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[j] = 0.0;
+        // exact levels, highest scale first
+#pragma unroll 1
+        for (int d = 0; d < NEXACT; ++d) {
+          const int* src = sums + (d * BN + c0) * BM + row;
+          const double f = ldexp(1.0, -7 * d);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) acc[j] += f * static_cast<double>(src[j * BM]);
+        }
+#pragma unroll 1
+        for (int d = NEXACT; d < S; ++d) {
+          uint32_t r[32];
+          TMEM_LD32(tbase + d * BN + c0, r);
+          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+          const double f = ldexp(1.0, -7 * d);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) acc[j] += f * static_cast<double>(__uint_as_float(r[j]));
+        }
+        if (grow < M) {
+#pragma unroll
+          for (int j = 0; j < 32; j += 2) {
+            const int cc = (colr0 + c0 + j) >> 1;  // complex column relative to the block
+            if (cc >= ncols) continue;
+            const int ex = er + Fcol[cc] - 14;
+            double vr = ldexp(acc[j], ex), vi = ldexp(acc[j + 1], ex);
+            const long long jc = j0 + cc;
+            const double dshift = (Dg ? Dg[grow] : 0.0) - shift;
+            if (dshift != 0.0) {
+              const double2 xv = Xsh[jc * ldx + grow];
+              vr += dshift * xv.x;
+              vi += dshift * xv.y;
+            }
+            vr *= alpha;
+            vi *= alpha;
+            double2* yp = Y + jc * ldy + grow;
+            if (beta != 0.0) {
+              const double2 yv = *yp;
+              vr += beta * yv.x;
+              vi += beta * yv.y;
+            }
+            *yp = make_double2(vr, vi);
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
+
+// ---------------------------------------------------------------------------
+// Slicing.  For |y| < 1: a = trunc(128 y), y <- 128 y - a, S times; every step
+// is exact in FP64 and every a is an integer in [-127, 127].
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int exponent_above(double m) {
+  // smallest E with m < 2^E (0 for m == 0)
+  if (!(m > 0.0)) return 0;
+  int e;
+  frexp(m, &e);
+  return e;
+}
+
+__device__ __forceinline__ void slice7(double y, float* a) {
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const double t = y * 128.0;
+    const double q = trunc(t);
+    a[s] = static_cast<float>(q);
+    y = t - q;
+  }
+}
+
+__device__ double block_max(double v, double* scratch) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) scratch[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    double w = lane < static_cast<int>((blockDim.x + 31) >> 5) ? scratch[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) w = fmax(w, __shfl_xor_sync(0xffffffffu, w, o));
+    if (lane == 0) scratch[32] = w;
+  }
+  __syncthreads();
+  return scratch[32];
+}
+
+// Row r of Ht from column r of the Hermitian H: Re H[r, k] = Re H[k, r],
+// Im H[r, k] = -Im H[k, r].  A: [S][N][Kp] bf16, E: [N].
+__global__ void __launch_bounds__(256) slice_h_kernel(const double2* __restrict__ H, long long ldh,
+                                                      int N, __nv_bfloat16* __restrict__ A,
+                                                      long long Kp, int* __restrict__ E,
+                                                      double* __restrict__ Dg) {
+  __shared__ double scratch[33];
+  const int r = blockIdx.x;
+  const double2* col = H + static_cast<long long>(r) * ldh;
+  double m = 0.0;
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    if (k == r) continue;  // the diagonal is applied in FP64 by the epilogue
+    const double2 v = col[k];
+    m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+  }
+  m = block_max(m, scratch);
+  const int er = exponent_above(m);
+  if (threadIdx.x == 0) {
+    E[r] = er;
+    Dg[r] = col[r].x;
+  }
+  const long long plane = static_cast<long long>(N) * Kp;
+  __nv_bfloat16* row = A + static_cast<long long>(r) * Kp;
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    const double2 v = k == r ? make_double2(0.0, 0.0) : col[k];
+    float ar[S], ai[S];
+    slice7(ldexp(v.x, -er), ar);
+    slice7(ldexp(-v.y, -er), ai);
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      row[s * plane + k] = __float2bfloat16_rn(ar[s]);
+      row[s * plane + N + k] = __float2bfloat16_rn(ai[s]);
+    }
+  }
+}
+
+// Rows 2c and 2c+1 of Xt^T for the columns c of X in [j0, j0 + ncols):
+// B: [S][rows_cap][Kp] bf16, F: [ncols].
+__global__ void __launch_bounds__(256) slice_x_kernel(const double2* __restrict__ X, long long ldx,
+                                                      int N, int j0, __nv_bfloat16* __restrict__ B,
+                                                      long long Kp, long long rows_cap,
+                                                      int* __restrict__ F) {
+  __shared__ double scratch[33];
+  const int c = blockIdx.x;
+  const double2* col = X + static_cast<long long>(j0 + c) * ldx;
+  double m = 0.0;
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    const double2 v = col[k];
+    m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+  }
+  m = block_max(m, scratch);
+  const int fc = exponent_above(m);
+  if (threadIdx.x == 0) F[c] = fc;
+  const long long plane = rows_cap * Kp;
+  __nv_bfloat16* r0 = B + static_cast<long long>(2 * c) * Kp;
+  __nv_bfloat16* r1 = r0 + Kp;
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    const double2 v = col[k];
+    float sr[S], si[S];
+    slice7(ldexp(v.x, -fc), sr);
+    slice7(ldexp(v.y, -fc), si);
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      r0[s * plane + k] = __float2bfloat16_rn(sr[s]);
+      r0[s * plane + N + k] = __float2bfloat16_rn(-si[s]);
+      r1[s * plane + k] = __float2bfloat16_rn(si[s]);
+      r1[s * plane + N + k] = __float2bfloat16_rn(sr[s]);
+    }
+  }
+}
+
+}  // namespace split
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+namespace {
+int64_t k_padded(int64_t N) { return ((2 * N + split::BK - 1) / split::BK) * split::BK; }
+}  // namespace
+
+int split_prepare_h(Dev& d, const chase_c64* H, int64_t N, int64_t ldh, SplitH& out) {
+  if (2 * N > 44000) {
+    set_error("split-BF16 filter: N = %lld above the exact-accumulation limit 22000",
+              static_cast<long long>(N));
+    return CHASE_INVALID_ARG;
+  }
+  out.N = N;
+  out.Kp = k_padded(N);
+  CHASE_TRY(d.alloc_bytes(&out.A, static_cast<size_t>(split::S) * N * out.Kp * 2));
+  CHASE_TRY(d.alloc(&out.E, static_cast<size_t>(N)));
+  CHASE_TRY(d.alloc(&out.Dg, static_cast<size_t>(N)));
+  split::slice_h_kernel<<<static_cast<unsigned>(N), 256, 0, d.st>>>(
+      reinterpret_cast<const double2*>(H), ldh, static_cast<int>(N),
+      static_cast<__nv_bfloat16*>(out.A), out.Kp, out.E, out.Dg);
+  note_launch();
+  CHASE_CUDA(cudaGetLastError());
+  return CHASE_OK;
+}
+
+int split_alloc_x(Dev& d, int64_t N, int max_cols, SplitX& out) {
+  out.cap_cols = max_cols;
+  const int64_t Kp = k_padded(N);
+  CHASE_TRY(d.alloc_bytes(&out.B, static_cast<size_t>(split::S) * 2 * max_cols * Kp * 2));
+  CHASE_TRY(d.alloc(&out.F, static_cast<size_t>(max_cols)));
+  return CHASE_OK;
+}
+
+int zgemm_split(Dev& d, const SplitH& h, SplitX& x, const chase_c64* X, int64_t ldx, int j0, int j1,
+                chase_c64* C, int64_t ldc, double alpha, double beta, double shift) {
+  const int ncols = j1 - j0;
+  if (ncols <= 0) return CHASE_OK;
+  if (ncols > x.cap_cols) {
+    set_error("zgemm_split: %d columns exceed the slice workspace (%d)", ncols, x.cap_cols);
+    return CHASE_INVALID_ARG;
+  }
+  const int64_t N = h.N, Kp = h.Kp;
+  const int64_t rows_cap = 2LL * x.cap_cols;
+  split::slice_x_kernel<<<static_cast<unsigned>(ncols), 256, 0, d.st>>>(
+      reinterpret_cast<const double2*>(X), ldx, static_cast<int>(N), j0,
+      static_cast<__nv_bfloat16*>(x.B), Kp, rows_cap, x.F);
+  note_launch();
+  CHASE_CUDA(cudaGetLastError());
+  CUtensorMap tmA, tmB;
+  CHASE_TRY(make_tmap_bf16_3d(&tmA, h.A, 2 * N, N, split::S, Kp * 2, Kp * 2 * N, split::BK,
+                              split::BM, split::S));
+  CHASE_TRY(make_tmap_bf16_3d(&tmB, x.B, 2 * N, 2LL * ncols, split::S, Kp * 2, Kp * 2 * rows_cap,
+                              split::BK, split::BN, split::S));
+  static bool attr_done = false;
+  if (!attr_done) {
+    CHASE_CUDA(cudaFuncSetAttribute(split::zgemm_split_kernel,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, split::SMEM));
+    attr_done = true;
+  }
+  dim3 grid(static_cast<unsigned>((2 * ncols + split::BN - 1) / split::BN),
+            static_cast<unsigned>((N + split::BM - 1) / split::BM));
+  split::zgemm_split_kernel<<<grid, split::kThreads, split::SMEM, d.st>>>(
+      tmA, tmB, h.E, x.F, h.Dg, static_cast<int>(N), static_cast<int>(Kp / split::BK), ncols, j0,
+      reinterpret_cast<const double2*>(X), ldx, reinterpret_cast<double2*>(C), ldc, alpha, beta,
+      shift, d.err);
+  note_launch();
+  CHASE_CUDA(cudaGetLastError());
+  return CHASE_OK;
+}
+
+}  // namespace chase

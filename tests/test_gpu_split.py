@@ -1,0 +1,148 @@
+"""GPU parity of the split-BF16 (tensor-core) filter and of full solves that
+use it, against the CPU oracle and known spectra.
+
+Tolerance of the filter: each split-BF16 product carries an error of about
+2^-49 max|off-diagonal row of H| max|column| per term (7 slices of 7 bits);
+six slices measured 1.1e-11 to 1.4e-11 of a column's norm on Gaussian
+operands, seven are 128 times finer.  The diagonal of H and the shift are
+applied exactly in FP64.  A degree-m filter chains m such products whose
+errors add, so m <= 36 stays far below the 1e-9 per column used here.  Full solves
+must meet the same eigenvalue (1e-10 ||H||) and residual (tol ||H||) bars as
+the FP64 path, because Rayleigh-Ritz, QR and residuals stay FP64."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1805_10121_gb300 import chase, synth
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+SPLIT_FILTER_RTOL = 1e-9
+EIG_RTOL = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1805_10121_gb300 import build
+    build.build()
+    chase.lib()
+
+
+def dcol(t):
+    return t.to(DEV).t().contiguous().t()
+
+
+def known_h(n, seed, n_cluster=None):
+    q = synth.unitary_qr(n, seed)
+    lam = synth.spectrum_clustered(n, seed + 1, n_cluster=n_cluster or max(2, n // 16))
+    return synth.hermitian_from(q, lam), lam
+
+
+def oracle_filter_any_order(H, V, deg, b_sup, mu1, mu_nn):
+    order = np.argsort(deg, kind="stable")
+    out = np.empty_like(V)
+    out[:, order] = oracle.cheb_filter(H, V[:, order], np.asarray(deg)[order], b_sup, mu1, mu_nn)
+    return out
+
+
+def col_rel_err(a, b):
+    return np.max(np.linalg.norm(a - b, axis=0) / np.linalg.norm(b, axis=0))
+
+
+@pytest.mark.parametrize("n,b", [(300, 37), (517, 70), (129, 1), (64, 64), (1000, 33)])
+def test_split_filter_matches_oracle(n, b):
+    H, lam = known_h(n, 211 + n)
+    V = synth.gaussian_block(n, b, 212 + b)
+    rng = np.random.default_rng(n + 3 * b)
+    deg = (2 * rng.integers(1, 19, size=b)).astype(np.int32)
+    l = lam.numpy()
+    b_sup, mu1, mu_nn = 1.02, float(l[0]), float(l[min(n - 1, max(1, n // 8))])
+    ref = oracle_filter_any_order(H.numpy(), V.numpy(), deg, b_sup, mu1, mu_nn)
+    Vd = dcol(V)
+    chase.chase_filter(dcol(H), Vd, deg, b_sup, mu1, mu_nn, precision=chase.CHASE_SPLIT_BF16)
+    assert col_rel_err(Vd.cpu().numpy(), ref) <= SPLIT_FILTER_RTOL
+
+
+def test_split_filter_full_size_sampled_columns():
+    n, b = 8000, 480
+    lam = synth.spectrum_dft(n, 221, device=DEV)
+    q = synth.unitary_dft(n, 222, device=DEV)
+    H = synth.hermitian_from(q, lam)
+    del q
+    V = synth.gaussian_block(n, b, 223, device=DEV)
+    rng = np.random.default_rng(224)
+    deg = (2 * rng.integers(1, 19, size=b)).astype(np.int32)
+    l = lam.cpu().numpy()
+    b_sup, mu1, mu_nn = 50.5, float(l[0]), float(l[b])
+    Vin = V.clone()
+    chase.chase_filter(H, V, deg, b_sup, mu1, mu_nn, precision=chase.CHASE_SPLIT_BF16)
+    cols = [0, 7, 200, 333, 478, 479]
+    ref = oracle_filter_any_order(H.cpu().numpy(), Vin[:, cols].cpu().numpy(), deg[cols], b_sup,
+                                  mu1, mu_nn)
+    assert col_rel_err(V[:, cols].cpu().numpy(), ref) <= SPLIT_FILTER_RTOL
+
+
+def test_split_filter_rejects_too_large_n():
+    # rejected while validating the arguments, before any GPU work
+    n = 22001
+    H = torch.empty(n, n, dtype=torch.complex128, device=DEV).t()
+    V = torch.empty(1, n, dtype=torch.complex128, device=DEV).t()
+    with pytest.raises(chase.ChaseError) as ei:
+        chase.chase_filter(H, V, [2], 1.0, -1.0, 0.0, precision=chase.CHASE_SPLIT_BF16)
+    assert ei.value.status == chase.CHASE_INVALID_ARG
+    del H, V
+    torch.cuda.empty_cache()
+
+
+def check_solution(H, lam_true, ritz, resid, V, nev, tol):
+    hn = float(np.abs(lam_true).max())
+    assert np.max(np.abs(ritz[:nev] - lam_true[:nev])) <= EIG_RTOL * hn
+    assert np.all(resid[:nev] <= tol * hn)
+    nx = V.shape[1]
+    assert np.linalg.norm(V.conj().T @ V - np.eye(nx)) < 1e-12
+    r = oracle.residuals(H, V[:, :nev], ritz[:nev])
+    assert np.all(r <= tol * hn * 1.05)
+
+
+def test_split_solve_single_problem_1000():
+    n, nev, nex, tol = 1000, 50, 20, 1e-10
+    H, lam = known_h(n, 231, n_cluster=60)
+    V0 = synth.gaussian_block(n, nev + nex, 232)
+    S = synth.gaussian_block(n, 5, 233)
+    Vd = dcol(V0)
+    o = chase.chase_opts_default(precision=chase.CHASE_SPLIT_BF16)
+    st, ritz, resid, stats = chase.chase_solve(dcol(H), nev, nex, tol, Vd, dcol(S), opts=o)
+    assert st == chase.CHASE_OK
+    check_solution(H.numpy(), lam.numpy(), ritz, resid, Vd.cpu().numpy(), nev, tol)
+    ref = oracle.solve(H.numpy(), nev, nex, V0.numpy(), S.numpy(), tol=tol)
+    assert np.max(np.abs(ritz[:nev] - ref["ritz"][:nev])) <= EIG_RTOL
+
+
+def test_split_solve_sequence_matches_fp64():
+    n, nev, nex, tol = 600, 24, 8, 1e-10
+    lam = synth.spectrum_dft(n, 241)
+    q = synth.unitary_qr(n, 242)
+    H = synth.hermitian_from(q, lam)
+    V0 = synth.gaussian_block(n, nev + nex, 243)
+    S = synth.gaussian_block(n, 5, 244)
+    out = {}
+    for prec in (chase.CHASE_FP64, chase.CHASE_SPLIT_BF16):
+        Vd = dcol(V0)
+        o = chase.chase_opts_default(precision=prec)
+        st, r1, _, _ = chase.chase_solve(dcol(H), nev, nex, tol, Vd, dcol(S), opts=o)
+        assert st == chase.CHASE_OK
+        E = synth.hermitian_noise(n, 245)
+        H2 = (H + 1e-3 * float(lam.abs().max()) * E).t().contiguous().t()
+        o2 = chase.chase_opts_default(precision=prec, approx=1)
+        st, r2, res2, s2 = chase.chase_solve(dcol(H2), nev, nex, tol, Vd,
+                                             dcol(S[:, :1].contiguous()), Lambda=r1, opts=o2)
+        assert st == chase.CHASE_OK
+        w2 = np.linalg.eigvalsh(H2.numpy())
+        check_solution(H2.numpy(), w2, r2, res2, Vd.cpu().numpy(), nev, tol)
+        out[prec] = r2
+    hn = float(lam.abs().max())
+    assert np.max(np.abs(out[chase.CHASE_FP64][:nev] - out[chase.CHASE_SPLIT_BF16][:nev])) \
+        <= EIG_RTOL * hn
