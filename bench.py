@@ -188,57 +188,95 @@ def roofline_entry(stats_list, pk, src, precision):
     }
 
 
+def workload_config(args, world):
+    n, nev, nex, tol = args.n, args.nev, args.nex, args.tol
+    return {
+        "workload": f"sequence of correlated problems, N={n} complex128, nev={nev}, "
+                    f"nex={nex}, tol={tol} x ||H||, warm start; step = one solve",
+        "n": n, "nev": nev, "nex": nex, "tol": tol, "precision": args.precision,
+        "l2": f"inputs larger than L2 (H = {n * n * 16 / 1e9:.2f} GB per problem)",
+        "parallelism": "replicas" if world > 1 else "single GPU",
+    }
+
+
+class OracleSample:
+    """A bounded sample of the workload for the CPU oracle: one degree-2
+    filter of the full N x (nev+nex) block of problem 1, its Householder QR
+    and the Rayleigh quotient (the dense products that dominate a solve).
+    Inputs come from the same seeded generators on the host (the host and
+    device random streams differ, the shapes and distributions do not)."""
+
+    def __init__(self, n, nev, nex, seed):
+        import oracle
+        from paper_1805_10121_gb300 import synth
+        self.oracle = oracle
+        nx = nev + nex
+        lam = synth.spectrum_dft(n, seed)
+        q = synth.unitary_dft(n, seed + 1)
+        self.H = synth.hermitian_from(q, lam).numpy()
+        del q
+        self.V = synth.gaussian_block(n, nx, seed + 7).numpy()
+        self.l = lam.numpy()
+        self.n, self.nx = n, nx
+        self.flops = 2 * 8.0 * n * n * nx + 8.0 * n * n * nx + 8.0 * n * nx * nx + 16.0 * n * nx * nx
+
+    def step(self):
+        o = self.oracle
+        W = o.cheb_filter(self.H, self.V, [2] * self.nx, 50.5, float(self.l[0]),
+                          float(self.l[self.nx]))
+        Q, _ = o.householder_qr(W)
+        G = Q.conj().T @ (self.H @ Q)
+        return G
+
+    def describe(self, reps):
+        return (f"{reps} x [degree-2 filter + Householder QR + Rayleigh quotient] on the "
+                f"N={self.n} x {self.nx} block of problem 1, NumPy (BLAS threads = all host cores)")
+
+
 def cpu_baseline_sample(n, nev, nex, seed, budget_s):
-    """Time the oracle on a bounded sample of the workload: degree-2 filter,
-    Householder QR and the Rayleigh quotient of the full N x (nev+nex) block
-    of problem 1 (the dense products dominate a solve)."""
-    import oracle
-    from paper_1805_10121_gb300 import synth
-    nx = nev + nex
-    lam = synth.spectrum_dft(n, seed)
-    q = synth.unitary_dft(n, seed + 1)
-    H = synth.hermitian_from(q, lam).numpy()
-    del q
-    V = synth.gaussian_block(n, nx, seed + 7).numpy()
-    l = lam.numpy()
+    smp = OracleSample(n, nev, nex, seed)
     t0 = time.perf_counter()
-    flops = 0.0
     reps = 0
     while True:
-        W = oracle.cheb_filter(H, V, [2] * nx, 50.5, float(l[0]), float(l[nx]))
-        Q, _ = oracle.householder_qr(W)
-        G = Q.conj().T @ (H @ Q)
-        flops += 2 * 8.0 * n * n * nx + 8.0 * n * n * nx + 8.0 * n * nx * nx + 16.0 * n * nx * nx
+        smp.step()
         reps += 1
         if time.perf_counter() - t0 > budget_s or reps >= 3:
             break
     dt = time.perf_counter() - t0
-    del G
     return {
-        "value": round(flops / dt / 1e12, 6),
+        "value": round(smp.flops * reps / dt / 1e12, 6),
         "unit": "TFLOP/s",
         "cores": os.cpu_count(),
         "kind": "oracle",
-        "sample": (f"{reps} x [degree-2 filter + Householder QR + Rayleigh quotient] on the "
-                   f"N={n} x {nx} block of problem 1, NumPy (BLAS threads = all host cores)"),
+        "sample": smp.describe(reps),
         "seconds": round(dt, 2),
     }
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the CPU oracle as it stands, W untimed and K timed
+    bounded samples of the workload (rank 0 only)."""
     if rank != 0:
         return
-    cb = cpu_baseline_sample(args.n, args.nev, args.nex, args.seed, args.cpu_sample_seconds)
-    steps = args.steps
+    smp = OracleSample(args.n, args.nev, args.nex, args.seed)
+    for _ in range(args.warmup):
+        smp.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        smp.step()
+    dt = time.perf_counter() - t0
+    value = smp.flops * args.steps / dt / 1e12
+    cfg = workload_config(args, world)
+    cfg["precision"] = "fp64 (CPU oracle)"
     line = {
-        "impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "TFLOP/s",
-        "n_gpus": world, "steps": steps, "warmup": args.warmup, "ms_per_step": None,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": f"sequence N={args.n} nev={args.nev} nex={args.nex} "
-                               f"tol={args.tol} (CPU oracle sample)"},
-        "cpu_baseline": cb,
-        "e2e": {"value": cb["value"], "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "TFLOP/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * dt / args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": cfg,
+        "cpu_baseline": {"value": round(value, 6), "unit": "TFLOP/s", "cores": os.cpu_count(),
+                         "kind": "oracle", "sample": smp.describe(args.steps)},
+        "e2e": {"value": round(value, 6), "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -389,13 +427,7 @@ def main():
         "vs_baseline": None,
         "dtype": "bf16-split+f64" if args.precision == "split" else "f64",
         "data": "synthetic",
-        "config": {
-            "workload": f"sequence of correlated problems, N={n} complex128, nev={nev}, "
-                        f"nex={nex}, tol={tol} x ||H||, warm start; step = one solve",
-            "n": n, "nev": nev, "nex": nex, "tol": tol, "precision": args.precision,
-            "l2": f"inputs larger than L2 (H = {n * n * 16 / 1e9:.2f} GB per problem)",
-            "parallelism": "replicas" if world > 1 else "single GPU",
-        },
+        "config": workload_config(args, world),
         "s_per_solve": round(t_max / K, 3),
         "filter_tflops": round(filt_fl / filt_t / 1e12, 4) if filt_t > 0 else None,
         "filter_share_of_time": round(filt_t / max(elapsed, 1e-12), 4),

@@ -60,8 +60,8 @@ typedef struct {
  * accumulated leading levels; the diagonal of H and the recurrence's
  * shift/scale/axpby are applied in FP64.  Each entry of a product is
  * accurate to about 2^-49 max|off-diagonal row of H| max|column| per term.
- * Reads H through its Hermitian symmetry; needs N <= 22000.  QR,
- * Rayleigh-Ritz, residuals and Lanczos stay FP64. */
+ * Reads H through its Hermitian symmetry.  QR, Rayleigh-Ritz, residuals
+ * and Lanczos stay FP64. */
 #define CHASE_SPLIT_BF16 1
 
 /* ---- residual test used for locking (Alg. 3 line 4) ---- */

@@ -22,7 +22,6 @@ namespace chase {
 namespace {
 
 constexpr int kMaxDegAllowed = 1024;
-constexpr int64_t kSplitMaxN = 22000;  // exact int32 level sums of the split-BF16 product
 
 // Events bracketing the phases of one call, accumulated into seconds.
 struct PhaseTimer {
@@ -116,7 +115,7 @@ struct OrthWork {
   chase_c64* T = nullptr;     // N x b
   chase_c64* P = nullptr;     // nconv x b
   chase_c64* G = nullptr;     // b x b
-  chase_c64* Rinv = nullptr;  // b x b
+  chase_c64* Rinv = nullptr;  // panel workspace of the blocked Cholesky / solve, >= 32 b
   double* nrm = nullptr;      // b
 };
 
@@ -124,7 +123,7 @@ int orth_alloc(Dev& d, int64_t N, int nconv, int b, OrthWork& w) {
   CHASE_TRY(d.alloc(&w.T, static_cast<size_t>(N) * b));
   CHASE_TRY(d.alloc(&w.P, static_cast<size_t>(std::max(nconv, 1)) * b));
   CHASE_TRY(d.alloc(&w.G, static_cast<size_t>(b) * b));
-  CHASE_TRY(d.alloc(&w.Rinv, static_cast<size_t>(b) * b));
+  CHASE_TRY(d.alloc(&w.Rinv, static_cast<size_t>(std::max(b, 32)) * b));
   CHASE_TRY(d.alloc(&w.nrm, static_cast<size_t>(b)));
   return CHASE_OK;
 }
@@ -137,16 +136,15 @@ int cholqr_pass(Dev& d, int64_t N, const chase_c64* Y, int64_t ldy, int nconv, c
     *flops += 16.0 * N * nconv * b;
   }
   CHASE_TRY(zgram(d, N, V, ldv, b, V, ldv, b, w.G, b));
-  CHASE_TRY(launch_cholesky(d, w.G, b, b, 1e-12, shift));
+  CHASE_TRY(cholesky_blocked(d, w.G, b, b, 1e-12, shift, w.nrm, w.Rinv));
   int st = d.sync_check("cholesky");
   if (st != CHASE_OK) {
     cudaMemsetAsync(d.err, 0, sizeof(int), d.st);
     return st;
   }
-  CHASE_TRY(launch_tri_inv_upper(d, w.G, b, b, w.Rinv, b));
-  CHASE_TRY(zgemm(d, N, b, V, ldv, w.Rinv, b, b, w.T, N, 0, b, 1.0, 0.0, 0.0));
-  CHASE_TRY(copy_block(d, V, ldv, w.T, N, N, b, cudaMemcpyDeviceToDevice));
-  *flops += 16.0 * N * b * b + 8.0 * b * b * b / 3.0;
+  // V <- V L^-H (= V R^-1 with R = L^H), in place
+  CHASE_TRY(trsm_right_lh(d, V, ldv, N, w.G, b, b, w.Rinv));
+  *flops += 8.0 * N * b * b + 4.0 * N * b * b + 8.0 * b * b * b / 3.0;
   return CHASE_OK;
 }
 
@@ -408,10 +406,6 @@ extern "C" int chase_filter(const chase_c64* H, int64_t N, int64_t ldh, chase_c6
     set_error("chase_filter: unknown precision %d", precision);
     return CHASE_INVALID_ARG;
   }
-  if (precision == CHASE_SPLIT_BF16 && N > kSplitMaxN) {
-    set_error("chase_filter: split-BF16 needs N <= %d", kSplitMaxN);
-    return CHASE_INVALID_ARG;
-  }
   if (N < 0 || b < 0 || !ld_ok(ldh, N) || !ld_ok(ldv, N) || N > (1LL << 30)) {
     set_error("chase_filter: invalid size or leading dimension");
     return CHASE_INVALID_ARG;
@@ -614,7 +608,6 @@ extern "C" int chase_solve(const chase_c64* H, int64_t N, int64_t ldh, int nev, 
       o.deg_extra < 0 || o.max_iter < 0 || o.lanczos_iter < 1 || o.lanczos_iter > N ||
       (!o.approx && o.num_lanczos < 1) ||
       (o.precision != CHASE_FP64 && o.precision != CHASE_SPLIT_BF16) ||
-      (o.precision == CHASE_SPLIT_BF16 && N > kSplitMaxN) ||
       (o.conv_mode != CHASE_CONV_ABS && o.conv_mode != CHASE_CONV_REL)) {
     set_error("chase_solve: invalid argument");
     return CHASE_INVALID_ARG;

@@ -59,9 +59,14 @@ int launch_hermitize(Dev& d, chase_c64* G, int64_t ldg, int p);
 // In-place lower Cholesky G = L L^H (one CTA); sets KERR_CHOL_BREAKDOWN when a
 // pivot is not above rel_tol * G_jj.  `shift` is added to the diagonal first.
 int launch_cholesky(Dev& d, chase_c64* G, int64_t ldg, int p, double rel_tol, double shift);
-// Rinv = (L^{-1})^H, upper triangular, from the lower factor L.
-int launch_tri_inv_upper(Dev& d, const chase_c64* L, int64_t ldl, int p, chase_c64* Rinv,
-                         int64_t ldr);
+// Blocked Cholesky (32-wide panels, trailing updates on the FP64 GEMM); the
+// pivot test uses the diagonal of G + shift before any update (diag_ref, p
+// doubles of workspace); work holds >= 32 p entries.
+int cholesky_blocked(Dev& d, chase_c64* G, int64_t ldg, int p, double rel_tol, double shift,
+                     double* diag_ref, chase_c64* work);
+// X (N x p) <- X L^-H (blocked right-side triangular solve); work >= 32 p entries.
+int trsm_right_lh(Dev& d, chase_c64* X, int64_t ldx, int64_t N, const chase_c64* L, int64_t ldl,
+                  int p, chase_c64* work);
 // One Lanczos three-term step on r independent runs (one CTA per run):
 // alpha = Re(v^H w); w -= alpha v + beta_prev v_prev; beta = ||w||;
 // v_next = w / beta (zero when beta is rounding noise).  alpha/beta arrays
@@ -86,6 +91,8 @@ struct SplitX {
   void* B = nullptr;
   int* F = nullptr;
   int cap_cols = 0;
+  void* P = nullptr;  // FP64 partial products of K segments (grow-only)
+  size_t P_cap = 0;   // in complex entries
 };
 int split_prepare_h(Dev& d, const chase_c64* H, int64_t N, int64_t ldh, SplitH& out);
 int split_alloc_x(Dev& d, int64_t N, int max_cols, SplitX& out);

@@ -278,7 +278,7 @@ __global__ void zero_triangle_kernel(double2* __restrict__ A, long long lda, int
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024)
     cholesky_kernel(double2* __restrict__ G, long long ld, int p, double rel_tol, double shift,
-                    int* __restrict__ err) {
+                    const double* __restrict__ diag_ref, int* __restrict__ err) {
   __shared__ double scratch[33];
   __shared__ double s_ljj;
   __shared__ int s_fail;
@@ -297,7 +297,8 @@ __global__ void __launch_bounds__(1024)
     if (threadIdx.x == 0) {
       const double gjj = G[(long long)j * ld + j].x;
       const double dj = gjj - part;
-      const bool bad = !(dj > rel_tol * fabs(gjj)) || !isfinite(dj);
+      const double ref = diag_ref ? diag_ref[j] : gjj;
+      const bool bad = !(dj > rel_tol * fabs(ref)) || !isfinite(dj);
       if (bad) {
         s_fail = 1;
         atomicOr(err, KERR_CHOL_BREAKDOWN);
@@ -323,29 +324,59 @@ __global__ void __launch_bounds__(1024)
   }
 }
 
-// Column j of L^{-1} by forward substitution (thread per column), written
-// conjugated into row j of Rinv = (L^{-1})^H.
-__global__ void tri_inv_upper_kernel(const double2* __restrict__ L, long long ldl, int p,
-                                     double2* __restrict__ R, long long ldr) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < p; j += gridDim.x * blockDim.x) {
-    // x_j = 1 / L_jj
-    const double2 ljj = L[(long long)j * ldl + j];
-    double2 xj = make_double2(1.0 / ljj.x, 0.0);  // L_jj is real and positive
-    R[(long long)j * ldr + j] = make_double2(xj.x, -xj.y);
-    for (int i = j + 1; i < p; ++i) {
-      double sr = 0.0, si = 0.0;
-      for (int k = j; k < i; ++k) {
-        const double2 lik = L[(long long)k * ldl + i];
-        const double2 rk = R[(long long)k * ldr + j];  // conj(x_k)
-        const double xr = rk.x, xi = -rk.y;
-        sr += lik.x * xr - lik.y * xi;
-        si += lik.x * xi + lik.y * xr;
+// Rows of X (nrows x kb, leading dimension ldx) are replaced by the solution y
+// of y L^H = x, with L the kb x kb lower factor at (Lp, ldl): thread per row,
+// y_j = (x_j - sum_{m<j} y_m conj(L_jm)) / L_jj.  kb <= 32.
+__global__ void __launch_bounds__(128)
+    row_trsm_lh_kernel(double2* __restrict__ X, long long ldx, long long nrows,
+                       const double2* __restrict__ Lp, long long ldl, int kb) {
+  __shared__ double2 sL[32][33];
+  for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+    const int r = e % kb, c = e / kb;
+    sL[r][c] = r >= c ? Lp[(long long)c * ldl + r] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nrows;
+       i += (long long)gridDim.x * blockDim.x) {
+    double2 y[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      if (j >= kb) break;
+      double2 a = X[(long long)j * ldx + i];
+      for (int m = 0; m < j; ++m) {
+        const double2 l = sL[j][m];
+        // a -= y_m * conj(l)
+        a.x -= y[m].x * l.x + y[m].y * l.y;
+        a.y -= y[m].y * l.x - y[m].x * l.y;
       }
-      const double lii = L[(long long)i * ldl + i].x;
-      const double xr = -sr / lii, xi = -si / lii;
-      R[(long long)i * ldr + j] = make_double2(xr, -xi);
+      const double inv = 1.0 / sL[j][j].x;
+      y[j] = make_double2(a.x * inv, a.y * inv);
+      X[(long long)j * ldx + i] = y[j];
     }
   }
+}
+
+// dst (cols x rows, leading dimension ldd) = conj(src)^T, src rows x cols (lds)
+__global__ void conj_transpose_kernel(const double2* __restrict__ src, long long lds, int rows,
+                                      int cols, double2* __restrict__ dst, long long ldd) {
+  const long long n = (long long)rows * cols;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e % rows), c = (int)(e / rows);
+    const double2 v = src[(long long)c * lds + r];
+    dst[(long long)r * ldd + c] = make_double2(v.x, -v.y);
+  }
+}
+
+__global__ void copy_diag_kernel(const double2* __restrict__ G, long long ld, int p,
+                                 double* __restrict__ out, double shift) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < p; j += gridDim.x * blockDim.x)
+    out[j] = G[(long long)j * ld + j].x + shift;
+}
+
+__global__ void add_diag_kernel(double2* __restrict__ G, long long ld, int p, double shift) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < p; j += gridDim.x * blockDim.x)
+    G[(long long)j * ld + j].x += shift;
 }
 
 // ---------------------------------------------------------------------------
@@ -542,20 +573,88 @@ int launch_zero_triangle(Dev& d, chase_c64* A, int64_t lda, int p, bool lower) {
 int launch_cholesky(Dev& d, chase_c64* G, int64_t ldg, int p, double rel_tol, double shift) {
   if (p == 0) return CHASE_OK;
   cholesky_kernel<<<1, 1024, 0, d.st>>>(reinterpret_cast<double2*>(G), ldg, p, rel_tol, shift,
-                                        d.err);
+                                        nullptr, d.err);
   note_launch();
   CHASE_CUDA(cudaGetLastError());
   return CHASE_OK;
 }
 
-int launch_tri_inv_upper(Dev& d, const chase_c64* L, int64_t ldl, int p, chase_c64* Rinv,
-                         int64_t ldr) {
-  if (p == 0) return CHASE_OK;
-  CHASE_TRY(launch_zero_triangle(d, Rinv, ldr, p, true));
-  tri_inv_upper_kernel<<<grid_for(p, 64, 1024), 64, 0, d.st>>>(
-      reinterpret_cast<const double2*>(L), ldl, p, reinterpret_cast<double2*>(Rinv), ldr);
+int launch_row_trsm_lh(Dev& d, chase_c64* X, int64_t ldx, int64_t nrows, const chase_c64* L,
+                       int64_t ldl, int kb) {
+  if (nrows <= 0 || kb <= 0) return CHASE_OK;
+  if (kb > 32) {
+    set_error("row_trsm: block wider than 32");
+    return CHASE_INVALID_ARG;
+  }
+  row_trsm_lh_kernel<<<grid_for(nrows, 128, 152 * 8), 128, 0, d.st>>>(
+      reinterpret_cast<double2*>(X), ldx, nrows, reinterpret_cast<const double2*>(L), ldl, kb);
   note_launch();
   CHASE_CUDA(cudaGetLastError());
+  return CHASE_OK;
+}
+
+int launch_conj_transpose(Dev& d, const chase_c64* src, int64_t lds, int rows, int cols,
+                          chase_c64* dst, int64_t ldd) {
+  if (rows <= 0 || cols <= 0) return CHASE_OK;
+  conj_transpose_kernel<<<grid_for((long long)rows * cols, 256, 4096), 256, 0, d.st>>>(
+      reinterpret_cast<const double2*>(src), lds, rows, cols, reinterpret_cast<double2*>(dst),
+      ldd);
+  note_launch();
+  CHASE_CUDA(cudaGetLastError());
+  return CHASE_OK;
+}
+
+// Blocked right-looking Cholesky G = L L^H (lower, in place), 32-wide panels:
+// the diagonal block by the one-CTA kernel, the panel below it by row
+// triangular solves, the trailing matrix by the FP64 tensor-pipe GEMM.  The
+// pivot test compares against the diagonal of G + shift before any update.
+int cholesky_blocked(Dev& d, chase_c64* G, int64_t ldg, int p, double rel_tol, double shift,
+                     double* diag_ref, chase_c64* work /* >= 32 * p */) {
+  if (p == 0) return CHASE_OK;
+  constexpr int nb = 32;
+  copy_diag_kernel<<<grid_for(p, 256, 64), 256, 0, d.st>>>(reinterpret_cast<double2*>(G), ldg, p,
+                                                           diag_ref, shift);
+  note_launch();
+  if (shift != 0.0) {
+    add_diag_kernel<<<grid_for(p, 256, 64), 256, 0, d.st>>>(reinterpret_cast<double2*>(G), ldg, p,
+                                                            shift);
+    note_launch();
+  }
+  CHASE_CUDA(cudaGetLastError());
+  for (int k0 = 0; k0 < p; k0 += nb) {
+    const int kb = std::min(nb, p - k0);
+    chase_c64* Akk = G + static_cast<size_t>(k0) * ldg + k0;
+    cholesky_kernel<<<1, 1024, 0, d.st>>>(reinterpret_cast<double2*>(Akk), ldg, kb, rel_tol, 0.0,
+                                          diag_ref + k0, d.err);
+    note_launch();
+    CHASE_CUDA(cudaGetLastError());
+    const int m = p - k0 - kb;
+    if (m <= 0) break;
+    chase_c64* Pn = Akk + kb;  // panel rows k0+kb .. p-1, columns k0 .. k0+kb-1
+    CHASE_TRY(launch_row_trsm_lh(d, Pn, ldg, m, Akk, ldg, kb));
+    // trailing A22 -= Pn Pn^H
+    CHASE_TRY(launch_conj_transpose(d, Pn, ldg, m, kb, work, kb));
+    chase_c64* A22 = Akk + static_cast<size_t>(kb) * ldg + kb;
+    CHASE_TRY(zgemm(d, m, kb, Pn, ldg, work, kb, m, A22, ldg, 0, m, -1.0, 1.0, 0.0));
+  }
+  return CHASE_OK;
+}
+
+// X (N x p) <- X L^-H with L the lower Cholesky factor (p x p): blocked
+// right-side triangular solve, column blocks of 32.
+int trsm_right_lh(Dev& d, chase_c64* X, int64_t ldx, int64_t N, const chase_c64* L, int64_t ldl,
+                  int p, chase_c64* work /* >= 32 * p */) {
+  constexpr int nb = 32;
+  for (int k0 = 0; k0 < p; k0 += nb) {
+    const int kb = std::min(nb, p - k0);
+    chase_c64* Xk = X + static_cast<size_t>(k0) * ldx;
+    if (k0 > 0) {
+      // X[:, k0:k0+kb] -= X[:, 0:k0] R[0:k0, k0:k0+kb],  R = L^H
+      CHASE_TRY(launch_conj_transpose(d, L + k0, ldl, kb, k0, work, k0));
+      CHASE_TRY(zgemm(d, N, k0, X, ldx, work, k0, kb, Xk, ldx, 0, kb, -1.0, 1.0, 0.0));
+    }
+    CHASE_TRY(launch_row_trsm_lh(d, Xk, ldx, N, L + static_cast<size_t>(k0) * ldl + k0, ldl, kb));
+  }
   return CHASE_OK;
 }
 

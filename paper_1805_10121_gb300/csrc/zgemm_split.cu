@@ -27,8 +27,10 @@
 // exact in an FP32 accumulator while it stays below 2^24: levels 0-2 are
 // flushed from TMEM into exact int32 sums in shared memory every 256 K
 // (3 * 256 * 127^2 < 2^24); levels 3-6, already scaled by 2^-21 or less,
-// accumulate in FP32 over the whole K.  The int32 sums bound K = 2N below
-// 44380 (N <= 22000).
+// accumulate in FP32 over the whole K.  The int32 sums bound one launch's K
+// below 44380; longer K (N > 22000), and narrow blocks that would leave SMs
+// idle, are split into K segments whose FP64 partial products a combine
+// kernel sums before the epilogue.
 //
 // Structure (one CTA = 128 rows of H x 32 complex columns, 192 threads):
 //  * warp 0: TMA producer, one 3-D box per operand per stage loads all S
@@ -41,6 +43,8 @@
 //    writing the FP64 output.
 // Every wait is bounded; a wait that gives up sets the error flag.
 #include <cuda_bf16.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 #include "context.hpp"
@@ -111,10 +115,10 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
 __global__ void __launch_bounds__(kThreads, 1)
     zgemm_split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     const int* __restrict__ Erow, const int* __restrict__ Fcol,
-                    const double* __restrict__ Dg, int M, int nkb,
+                    const double* __restrict__ Dg, int M, int kb0, int nkb,
                     int ncols, int j0, const double2* __restrict__ Xsh, long long ldx,
                     double2* __restrict__ Y, long long ldy, double alpha, double beta, double shift,
-                    int* __restrict__ err) {
+                    double2* __restrict__ P, long long ldp, int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -167,8 +171,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         mbar_arrive_expect_tx(&full[st], STAGE_BYTES);
-        tma_load_3d(smem_u32(sA + st * STAGE_A), &tmA, kb * BK, row0, 0, smem_u32(&full[st]));
-        tma_load_3d(smem_u32(sB + st * STAGE_B), &tmB, kb * BK, colr0, 0, smem_u32(&full[st]));
+        tma_load_3d(smem_u32(sA + st * STAGE_A), &tmA, (kb0 + kb) * BK, row0, 0, smem_u32(&full[st]));
+        tma_load_3d(smem_u32(sB + st * STAGE_B), &tmB, (kb0 + kb) * BK, colr0, 0, smem_u32(&full[st]));
         ++issued;
       }
       for (int kb = (issued > NSTAGE ? issued - NSTAGE : 0); kb < issued; ++kb)
@@ -277,6 +281,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (cc >= ncols) continue;
             const int ex = er + Fcol[cc] - 14;
             double vr = ldexp(acc[j], ex), vi = ldexp(acc[j + 1], ex);
+            if (P) {  // one K segment: raw product, the combine kernel finishes
+              P[static_cast<long long>(cc) * ldp + grow] = make_double2(vr, vi);
+              continue;
+            }
             const long long jc = j0 + cc;
             const double dshift = (Dg ? Dg[grow] : 0.0) - shift;
             if (dshift != 0.0) {
@@ -413,6 +421,39 @@ __global__ void __launch_bounds__(256) slice_x_kernel(const double2* __restrict_
   }
 }
 
+// Sum of the K segments' products plus the FP64 epilogue:
+// C[r, j0+c] = alpha (sum_g P_g[r, c] + (H_rr - shift) X[r, j0+c]) + beta C[r, j0+c].
+__global__ void split_combine_kernel(const double2* __restrict__ P, int nseg, long long pstride,
+                                     long long ldp, const double* __restrict__ Dg,
+                                     const double2* __restrict__ X, long long ldx, int j0, int ncols,
+                                     int N, double2* __restrict__ C, long long ldc, double alpha,
+                                     double beta, double shift) {
+  const long long total = static_cast<long long>(N) * ncols;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int r = static_cast<int>(e % N);
+    const int c = static_cast<int>(e / N);
+    double vr = 0.0, vi = 0.0;
+    for (int g = 0; g < nseg; ++g) {
+      const double2 p = P[g * pstride + c * ldp + r];
+      vr += p.x;
+      vi += p.y;
+    }
+    const long long jc = j0 + c;
+    const double ds = Dg[r] - shift;
+    const double2 xv = X[jc * ldx + r];
+    vr = alpha * (vr + ds * xv.x);
+    vi = alpha * (vi + ds * xv.y);
+    double2* cp = C + jc * ldc + r;
+    if (beta != 0.0) {
+      const double2 cv = *cp;
+      vr += beta * cv.x;
+      vi += beta * cv.y;
+    }
+    *cp = make_double2(vr, vi);
+  }
+}
+
 }  // namespace split
 
 // ---------------------------------------------------------------------------
@@ -423,11 +464,6 @@ int64_t k_padded(int64_t N) { return ((2 * N + split::BK - 1) / split::BK) * spl
 }  // namespace
 
 int split_prepare_h(Dev& d, const chase_c64* H, int64_t N, int64_t ldh, SplitH& out) {
-  if (2 * N > 44000) {
-    set_error("split-BF16 filter: N = %lld above the exact-accumulation limit 22000",
-              static_cast<long long>(N));
-    return CHASE_INVALID_ARG;
-  }
   out.N = N;
   out.Kp = k_padded(N);
   CHASE_TRY(d.alloc_bytes(&out.A, static_cast<size_t>(split::S) * N * out.Kp * 2));
@@ -447,6 +483,22 @@ int split_alloc_x(Dev& d, int64_t N, int max_cols, SplitX& out) {
   CHASE_TRY(d.alloc_bytes(&out.B, static_cast<size_t>(split::S) * 2 * max_cols * Kp * 2));
   CHASE_TRY(d.alloc(&out.F, static_cast<size_t>(max_cols)));
   return CHASE_OK;
+}
+
+namespace {
+// K blocks one launch may cover with exact int32 level sums: level 2 holds
+// 3 pairs, 3 * K * 127^2 < 2^31 gives K < 44380.
+constexpr int kMaxKBlocksPerSegment = 44000 / split::BK;
+}  // namespace
+
+int split_segments(int64_t N, int ncols) {
+  const int64_t nkb = k_padded(N) / split::BK;
+  int nseg = static_cast<int>((nkb + kMaxKBlocksPerSegment - 1) / kMaxKBlocksPerSegment);
+  // Narrow blocks leave SMs idle: split K until the grid covers the SMs,
+  // keeping every segment at least 64 K blocks long.
+  const int64_t tiles = ((2LL * ncols + split::BN - 1) / split::BN) * ((N + split::BM - 1) / split::BM);
+  while (tiles * nseg < 152 && nkb / (nseg + 1) >= 64 && nseg < 8) ++nseg;
+  return nseg;
 }
 
 int zgemm_split(Dev& d, const SplitH& h, SplitX& x, const chase_c64* X, int64_t ldx, int j0, int j1,
@@ -477,10 +529,45 @@ int zgemm_split(Dev& d, const SplitH& h, SplitX& x, const chase_c64* X, int64_t 
   }
   dim3 grid(static_cast<unsigned>((2 * ncols + split::BN - 1) / split::BN),
             static_cast<unsigned>((N + split::BM - 1) / split::BM));
-  split::zgemm_split_kernel<<<grid, split::kThreads, split::SMEM, d.st>>>(
-      tmA, tmB, h.E, x.F, h.Dg, static_cast<int>(N), static_cast<int>(Kp / split::BK), ncols, j0,
-      reinterpret_cast<const double2*>(X), ldx, reinterpret_cast<double2*>(C), ldc, alpha, beta,
-      shift, d.err);
+  const int nkb = static_cast<int>(Kp / split::BK);
+  const int nseg = split_segments(N, ncols);
+  if (nseg == 1) {
+    split::zgemm_split_kernel<<<grid, split::kThreads, split::SMEM, d.st>>>(
+        tmA, tmB, h.E, x.F, h.Dg, static_cast<int>(N), 0, nkb, ncols, j0,
+        reinterpret_cast<const double2*>(X), ldx, reinterpret_cast<double2*>(C), ldc, alpha, beta,
+        shift, nullptr, 0, d.err);
+    note_launch();
+    CHASE_CUDA(cudaGetLastError());
+    return CHASE_OK;
+  }
+  // K segments write raw partial products; the combine kernel sums them and
+  // applies the diagonal, the shift and the axpby in FP64.
+  const long long pstride = static_cast<long long>(N) * ncols;
+  const size_t need = static_cast<size_t>(pstride) * nseg;
+  if (need > x.P_cap) {  // grow-only: released with the call's other workspace
+    void* np = nullptr;
+    CHASE_TRY(d.alloc_bytes(&np, std::max(need, 2 * x.P_cap) * sizeof(double2)));
+    x.P = np;
+    x.P_cap = std::max(need, 2 * x.P_cap);
+  }
+  double2* P = static_cast<double2*>(x.P);
+  const int per = (nkb + nseg - 1) / nseg;
+  for (int g = 0; g < nseg; ++g) {
+    const int kb0 = g * per;
+    const int cnt = std::min(per, nkb - kb0);
+    if (cnt <= 0) break;
+    split::zgemm_split_kernel<<<grid, split::kThreads, split::SMEM, d.st>>>(
+        tmA, tmB, h.E, x.F, h.Dg, static_cast<int>(N), kb0, cnt, ncols, j0,
+        reinterpret_cast<const double2*>(X), ldx, reinterpret_cast<double2*>(C), ldc, alpha, beta,
+        shift, P + g * pstride, N, d.err);
+    note_launch();
+    CHASE_CUDA(cudaGetLastError());
+  }
+  const long long total = pstride;
+  const unsigned blocks = static_cast<unsigned>(std::min<long long>((total + 255) / 256, 152 * 16));
+  split::split_combine_kernel<<<blocks, 256, 0, d.st>>>(
+      P, nseg, pstride, N, h.Dg, reinterpret_cast<const double2*>(X), ldx, j0, ncols,
+      static_cast<int>(N), reinterpret_cast<double2*>(C), ldc, alpha, beta, shift);
   note_launch();
   CHASE_CUDA(cudaGetLastError());
   return CHASE_OK;

@@ -212,6 +212,25 @@ def test_orthonormalize_against_locked_matches_householder():
     assert np.linalg.norm(M - np.diag(np.diag(M))) < 1e-10
 
 
+@pytest.mark.parametrize("n,nconv,b", [(700, 0, 100), (900, 33, 97), (300, 5, 32)])
+def test_orthonormalize_blocked_panels(n, nconv, b):
+    # several 32-wide panels of the blocked Cholesky and triangular solve
+    Y = None
+    if nconv:
+        Y = torch.from_numpy(oracle.householder_qr(synth.gaussian_block(n, nconv, 105).numpy())[0])
+        Y = Y.t().contiguous().t()
+    scales = torch.logspace(-3, 3, b, dtype=torch.float64).to(torch.complex128)
+    V = synth.gaussian_block(n, b, 106) * scales[None, :]
+    Vd = dcol(V)
+    chase.chase_orthonormalize(dcol(Y) if Y is not None else None, Vd)
+    Q = Vd.cpu().numpy()
+    assert np.linalg.norm(Q.conj().T @ Q - np.eye(b)) < 1e-13
+    full = V.numpy() if Y is None else np.hstack([Y.numpy(), V.numpy()])
+    Qr = oracle.householder_qr(full)[0][:, nconv:]
+    M = Q.conj().T @ Qr
+    assert np.allclose(np.abs(np.diag(M)), 1.0, atol=1e-10)
+
+
 def test_orthonormalize_ill_conditioned_block():
     # nearly dependent columns force the shifted Cholesky QR path
     n, b = 400, 24

@@ -85,16 +85,23 @@ def test_split_filter_full_size_sampled_columns():
     assert col_rel_err(V[:, cols].cpu().numpy(), ref) <= SPLIT_FILTER_RTOL
 
 
-def test_split_filter_rejects_too_large_n():
-    # rejected while validating the arguments, before any GPU work
-    n = 22001
-    H = torch.empty(n, n, dtype=torch.complex128, device=DEV).t()
-    V = torch.empty(1, n, dtype=torch.complex128, device=DEV).t()
-    with pytest.raises(chase.ChaseError) as ei:
-        chase.chase_filter(H, V, [2], 1.0, -1.0, 0.0, precision=chase.CHASE_SPLIT_BF16)
-    assert ei.value.status == chase.CHASE_INVALID_ARG
-    del H, V
-    torch.cuda.empty_cache()
+def test_split_filter_narrow_block_uses_k_segments():
+    # 8 columns at N = 4000 give 32 output tiles, so the product is split into
+    # K segments whose partial sums are combined in FP64; degrees up to 36
+    n, b = 4000, 8
+    lam = synth.spectrum_dft(n, 251, device=DEV)
+    q = synth.unitary_dft(n, 252, device=DEV)
+    H = synth.hermitian_from(q, lam)
+    del q
+    V = synth.gaussian_block(n, b, 253, device=DEV)
+    deg = np.array([36, 2, 20, 36, 8, 12, 36, 4], dtype=np.int32)
+    l = lam.cpu().numpy()
+    Vin = V.clone()
+    chase.chase_filter(H, V, deg, 50.5, float(l[0]), float(l[240]),
+                       precision=chase.CHASE_SPLIT_BF16)
+    ref = oracle_filter_any_order(H.cpu().numpy(), Vin.cpu().numpy(), deg, 50.5, float(l[0]),
+                                  float(l[240]))
+    assert col_rel_err(V.cpu().numpy(), ref) <= SPLIT_FILTER_RTOL
 
 
 def check_solution(H, lam_true, ritz, resid, V, nev, tol):
