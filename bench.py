@@ -48,6 +48,10 @@ def parse():
     p.add_argument("--tol", type=float, default=1e-10)
     p.add_argument("--seed", type=int, default=2024)
     p.add_argument("--precision", default="split", choices=["split", "fp64"])
+    p.add_argument("--workload", default="sequence", choices=["sequence", "filter"],
+                   help="sequence: timed solves of the correlated sequence (default); "
+                        "filter: timed degree-m filter calls on one problem, split vs FP64")
+    p.add_argument("--filter-degree", type=int, default=20)
     p.add_argument("--no-fp64-compare", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -282,11 +286,82 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_filter_workload(args, rank, world, local):
+    """One problem (N, nev + nex columns, same spectrum law): time the filter
+    of constant degree m on the whole block with the split-BF16 product, and
+    one FP64 degree-2 filter for comparison (FP64 is ~30x slower per column
+    product, so a full FP64 filter at this size is extrapolated by FLOPs)."""
+    from paper_1805_10121_gb300 import build, chase, synth
+    build.build()
+    chase.lib()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n, nx, m = args.n, args.nev + args.nex, args.filter_degree
+    seed = args.seed + 1000 * rank
+    lam = synth.spectrum_dft(n, seed, device=dev)
+    H = synth.hermitian_dft(lam, seed + 1)
+    V0 = synth.gaussian_block(n, nx, seed + 7, device=dev)
+    l = lam.cpu().numpy()
+    b_sup, mu1, mu_nn = float(l[-1]) * 1.01, float(l[0]), float(l[nx])
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(prec, deg, reps):
+        V = V0.clone()
+        for _ in range(args.warmup if reps > 1 else 1):
+            chase.chase_filter(H, V, [deg] * nx, b_sup, mu1, mu_nn, precision=prec)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        clocks = ClockSampler(local)
+        clocks.start()
+        a.record(stream)
+        for _ in range(reps):
+            chase.chase_filter(H, V, [deg] * nx, b_sup, mu1, mu_nn, precision=prec)
+        b.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        return a.elapsed_time(b) / 1e3 / reps, clk
+
+    launches0 = chase.chase_kernel_launches()
+    t_split, clk = timed(chase.CHASE_SPLIT_BF16, m, args.steps)
+    launches = chase.chase_kernel_launches() - launches0
+    fl = 8.0 * n * n * nx * m
+    t_fp64, _ = timed(chase.CHASE_FP64, 2, 1)
+    fl64 = 8.0 * n * n * nx * 2
+    pk, src = peaks()
+    split_tf = fl / t_split / 1e12
+    fp64_tf = fl64 / t_fp64 / 1e12
+    cfg = workload_config(args, world)
+    cfg["workload"] = (f"filter of degree {m} on N={n} x {nx} (nev={args.nev}, nex={args.nex}), "
+                       f"spectrum of the sequence workload; step = one filter call")
+    line = {
+        "metric": METRIC, "value": round(split_tf, 3), "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t_split, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16-split+f64", "data": "synthetic", "config": cfg,
+        "fp64": {"filter_tflops": round(fp64_tf, 4), "seconds_degree2": round(t_fp64, 3),
+                 "seconds_same_filter_extrapolated": round(t_fp64 * m / 2.0, 1)},
+        "speedup_split_vs_fp64_filter": round(split_tf / fp64_tf, 1),
+        "roofline": {"bound": "tensor", "kernel": "zgemm_split_kernel",
+                     "achieved": round(SPLIT_PAIRS * split_tf, 2),
+                     "peak": pk.get("bf16_tflops_sustained", 1700.0), "unit": "TFLOP/s",
+                     "frac": round(SPLIT_PAIRS * split_tf / pk.get("bf16_tflops_sustained", 1700.0), 4),
+                     "traffic": None, "peak_source": f"{src} bf16_tflops_sustained",
+                     "fp64_equivalent_tflops": round(split_tf, 3)},
+        "gpu_launches": int(launches), "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "filter":
+        run_filter_workload(args, rank, world, local)
         return
     from paper_1805_10121_gb300 import build, chase, synth
     build.build()

@@ -26,6 +26,7 @@ __all__ = [
     "spectrum_dft",
     "spectrum_uniform",
     "hermitian_from",
+    "hermitian_dft",
     "hermitian_noise",
 ]
 
@@ -103,6 +104,31 @@ def hermitian_from(q: torch.Tensor, lam: torch.Tensor) -> torch.Tensor:
     h = (q * lam.to(q.dtype)[None, :]) @ q.conj().t()
     h = 0.5 * (h + h.conj().t())
     # column-major storage: element (i, j) at j*n + i
+    return h.t().contiguous().t()
+
+
+def hermitian_dft(lam: torch.Tensor, seed: int) -> torch.Tensor:
+    """``Q diag(lam) Q^H`` for the unitary ``Q = D1 F D2 F D3`` of
+    ``unitary_dft(n, seed)`` without forming Q: ``D3 diag(lam) D3^H`` is
+    ``diag(lam)``, ``F diag(lam) F^H`` is circulant with first column
+    ``fft(lam) / n``, and the remaining factors are FFTs along the two axes
+    and phase scalings.  O(n^2 log n); column-major full storage."""
+    n = lam.numel()
+    device = lam.device
+    g = generator(seed, device)
+    ph = torch.rand(3, n, dtype=torch.float64, device=device, generator=g) * (2.0 * math.pi)
+    d = torch.polar(torch.ones_like(ph), ph)
+    c = torch.fft.fft(lam.to(torch.complex128)) / n           # circulant column
+    idx = (torch.arange(n, device=device)[:, None] - torch.arange(n, device=device)[None, :]) % n
+    t = c[idx]                                                 # F diag(lam) F^H
+    del idx
+    t.mul_(d[1][:, None]).mul_(d[1].conj()[None, :])           # D2 . D2^H
+    t = torch.fft.fft(t, dim=0, norm="ortho")                  # F .
+    t = torch.fft.ifft(t, dim=1, norm="ortho")                 # . F^H
+    t.mul_(d[0][:, None]).mul_(d[0].conj()[None, :])           # D1 . D1^H
+    h = t.t().conj()
+    h = 0.5 * (t + h)
+    del t
     return h.t().contiguous().t()
 
 

@@ -104,6 +104,26 @@ def test_split_filter_narrow_block_uses_k_segments():
     assert col_rel_err(V.cpu().numpy(), ref) <= SPLIT_FILTER_RTOL
 
 
+def test_split_filter_beyond_one_launch_exact_range():
+    # K = 2N = 45000 exceeds the exact int32 range of one launch (44000), so
+    # the product runs as K segments combined in FP64; sampled columns
+    n, b = 22500, 32
+    lam = synth.spectrum_dft(n, 261, device=DEV)
+    H = synth.hermitian_dft(lam, 262)
+    V = synth.gaussian_block(n, b, 263, device=DEV)
+    deg = np.array([2, 4, 8, 12, 16, 20, 24, 28, 32, 36] * 3 + [36, 2], dtype=np.int32)
+    l = lam.cpu().numpy()
+    Vin = V.clone()
+    chase.chase_filter(H, V, deg, 50.5, float(l[0]), float(l[1350]),
+                       precision=chase.CHASE_SPLIT_BF16)
+    cols = [0, 9, 17, 31]
+    ref = oracle_filter_any_order(H.cpu().numpy(), Vin[:, cols].cpu().numpy(), deg[cols], 50.5,
+                                  float(l[0]), float(l[1350]))
+    assert col_rel_err(V[:, cols].cpu().numpy(), ref) <= SPLIT_FILTER_RTOL
+    del H, V, Vin
+    torch.cuda.empty_cache()
+
+
 def check_solution(H, lam_true, ritz, resid, V, nev, tol):
     hn = float(np.abs(lam_true).max())
     assert np.max(np.abs(ritz[:nev] - lam_true[:nev])) <= EIG_RTOL * hn

@@ -361,6 +361,19 @@ def test_dos_two_clusters_quantile():
     assert abs(est["mu_nevnex"] - brentq(f, -5, 5)) < 1e-9
 
 
+# --------------------------------------------------------------- inputs ---
+
+def test_hermitian_dft_equals_dense_construction():
+    # the FFT construction of Q diag(lam) Q^H equals the dense product
+    n = 96
+    lam = synth.spectrum_dft(n, 5)
+    dense = synth.hermitian_from(synth.unitary_dft(n, 6), lam).numpy()
+    fast = synth.hermitian_dft(lam, 6).numpy()
+    assert np.linalg.norm(dense - fast) <= 1e-13 * np.linalg.norm(dense)
+    assert np.allclose(np.linalg.eigvalsh(fast), lam.numpy(), atol=1e-12 * 50)
+    assert np.array_equal(fast, fast.conj().T)
+
+
 # ------------------------------------------------------------- full solve ---
 
 def known_problem(n, seed, n_cluster):
