@@ -48,10 +48,15 @@ def parse():
     p.add_argument("--tol", type=float, default=1e-10)
     p.add_argument("--seed", type=int, default=2024)
     p.add_argument("--precision", default="split", choices=["split", "fp64"])
-    p.add_argument("--workload", default="sequence", choices=["sequence", "filter"],
+    p.add_argument("--workload", default="sequence", choices=["sequence", "filter", "serve"],
                    help="sequence: timed solves of the correlated sequence (default); "
                         "filter: timed degree-m filter calls on one problem, split vs FP64")
     p.add_argument("--filter-degree", type=int, default=20)
+    p.add_argument("--serve-requests", type=int, default=10)
+    p.add_argument("--serve-rate", type=float, default=20.0)
+    p.add_argument("--serve-slots", type=int, default=4)
+    p.add_argument("--serve-cap-gb", type=float, default=150.0)
+    p.add_argument("--serve-sizes", default="2048,4096,8192,16384")
     p.add_argument("--no-fp64-compare", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -354,6 +359,68 @@ def run_filter_workload(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def run_serve_workload(args, rank, world, local):
+    """Replay a seeded Poisson trace of sequence-solve requests through the
+    continuous-batching server; report throughput and p50/p99 latency."""
+    from paper_1805_10121_gb300 import build, chase, serve
+    build.build()
+    chase.lib()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    split = args.precision == "split"
+    prec = chase.CHASE_SPLIT_BF16 if split else chase.CHASE_FP64
+    sizes = tuple(int(x) for x in args.serve_sizes.split(","))
+    weights = (4, 3, 2, 1)[:len(sizes)]
+    trace = serve.poisson_trace(args.serve_requests, args.serve_rate, args.seed + 1000 * rank,
+                                sizes=sizes, weights=weights)
+    fp = lambda r: serve.footprint_bytes(r.n, r.nev, r.nex, split)
+    solver = serve.gpu_sequence_solver(dev, prec, tol=args.tol)
+    # warm-up: one small request (library load, handles, kernels)
+    small = serve.Request(-1, min(sizes), int(np.ceil(0.04 * min(sizes))),
+                          int(np.ceil(0.008 * min(sizes))), 2, 99, 0.0)
+    serve.Server(solver, args.serve_cap_gb * 1e9, 1, fp).run([small])
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    launches0 = chase.chase_kernel_launches()
+    clocks.start()
+    t0 = time.perf_counter()
+    srv = serve.Server(solver, args.serve_cap_gb * 1e9, args.serve_slots, fp)
+    res = srv.run(trace)
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    lat = [r.latency for r in res]
+    flops = sum(r.flops for r in res)
+    nprob = sum(r.nprob for r in res)
+    ok = all(st == 0 for r in res for st in r.statuses)
+    cfg = workload_config(args, world)
+    cfg["workload"] = (f"serving: {len(trace)} sequence-solve requests, Poisson {args.serve_rate}/s, "
+                       f"N in {sizes} weighted {weights}, 5-10 problems each, nev = 4% N, "
+                       f"nex = 20% nev, admission cap {args.serve_cap_gb} GB, "
+                       f"{args.serve_slots} slots; step = the whole trace")
+    line = {
+        "metric": METRIC, "value": round(flops / wall / 1e12, 3), "unit": "TFLOP/s",
+        "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": round(1e3 * wall, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16-split+f64" if split else "f64", "data": "synthetic", "config": cfg,
+        "serve": {"p50_latency_s": round(serve.percentile(lat, 50), 3),
+                  "p99_latency_s": round(serve.percentile(lat, 99), 3),
+                  "mean_queueing_s": round(float(np.mean([r.queueing for r in res])), 3),
+                  "requests_per_s": round(len(res) / wall, 4),
+                  "problems_per_s": round(nprob / wall, 4),
+                  "all_converged": ok, "peak_concurrency": srv.peak_concurrency,
+                  "peak_admitted_gb": round(srv.peak_mem / 1e9, 2),
+                  "max_resid_over_norm": max(max(r.resid_max_over_norm) for r in res),
+                  "per_request": [{"rid": r.rid, "n": r.n, "problems": r.nprob,
+                                   "arrival": round(r.arrival, 3),
+                                   "queueing": round(r.queueing, 3),
+                                   "latency": round(r.latency, 3),
+                                   "iterations": r.iterations} for r in res]},
+        "gpu_launches": int(chase.chase_kernel_launches() - launches0), "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -362,6 +429,9 @@ def main():
         return
     if args.workload == "filter":
         run_filter_workload(args, rank, world, local)
+        return
+    if args.workload == "serve":
+        run_serve_workload(args, rank, world, local)
         return
     from paper_1805_10121_gb300 import build, chase, synth
     build.build()
