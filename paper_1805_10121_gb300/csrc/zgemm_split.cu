@@ -25,21 +25,23 @@
 //
 // Exactness.  Products of slices are integers below 2^14, so a level-d sum is
 // exact in an FP32 accumulator while it stays below 2^24: levels 0-2 are
-// flushed from TMEM into exact int32 sums in shared memory every 256 K
+// flushed from TMEM into exact int32 sums (in the flush warps' registers) every 256 K
 // (3 * 256 * 127^2 < 2^24); levels 3-6, already scaled by 2^-21 or less,
 // accumulate in FP32 over the whole K.  The int32 sums bound one launch's K
 // below 44380; longer K (N > 22000), and narrow blocks that would leave SMs
 // idle, are split into K segments whose FP64 partial products a combine
 // kernel sums before the epilogue.
 //
-// Structure (one CTA = 128 rows of H x 32 complex columns, 192 threads):
+// Structure (one CTA = 128 rows of H x 32 complex columns, 320 threads):
 //  * warp 0: TMA producer, one 3-D box per operand per stage loads all S
-//    slices of a 16-wide K block (SWIZZLE_32B), 3-stage mbarrier ring;
+//    slices of a 16-wide K block (SWIZZLE_32B), 5-stage mbarrier ring (the
+//    depth hides the L2 latency of the narrow 32-byte box rows);
 //  * warp 1: allocates 512 TMEM columns (7 levels x 64 FP32 columns) and one
 //    thread issues the 28 tcgen05.mma (M=128, N=64, K=16) per K block,
 //    committing stages back to the producer and chunks to the flush warps;
-//  * warps 2-5: flush the exact levels every chunk, then combine all levels in
-//    FP64 and apply the recurrence's shift, scale and axpby (Eq. 7) while
+//  * warps 2-9 (two per TMEM lane quarter, 32 columns each): flush the exact
+//    levels every chunk into int32 registers, then combine all levels in
+//    FP64 and apply the diagonal, shift, scale and axpby (Eq. 7) while
 //    writing the FP64 output.
 // Every wait is bounded; a wait that gives up sets the error flag.
 #include <cuda_bf16.h>
@@ -55,7 +57,7 @@ constexpr int S = 7;                 // 7-bit slices per operand
 constexpr int BM = 128;              // rows per CTA (TMEM lanes)
 constexpr int BN = 64;               // real columns of the product per CTA (32 complex)
 constexpr int BK = 16;               // K per stage (one 32-byte swizzle row)
-constexpr int NSTAGE = 3;
+constexpr int NSTAGE = 5;
 constexpr int CHUNK = 16;            // k-blocks per exact chunk (256 K)
 constexpr int NEXACT = 3;            // levels accumulated exactly
 constexpr int A_TILE = BM * BK * 2;  // 4096 B per slice
@@ -63,10 +65,10 @@ constexpr int B_TILE = BN * BK * 2;  // 2048 B per slice
 constexpr int STAGE_A = S * A_TILE;
 constexpr int STAGE_B = S * B_TILE;
 constexpr int STAGE_BYTES = STAGE_A + STAGE_B;
-constexpr int SUM_BYTES = NEXACT * BM * BN * 4;
 constexpr int TMEM_COLS = 512;
-constexpr int kThreads = 192;
-constexpr int SMEM = 1024 + NSTAGE * STAGE_BYTES + SUM_BYTES + 256;
+constexpr int kFlushWarps = 8;       // two per TMEM lane quarter, 32 columns each
+constexpr int kThreads = (2 + kFlushWarps) * 32;
+constexpr int SMEM = 1024 + NSTAGE * STAGE_BYTES + 256;
 
 __device__ __forceinline__ uint64_t desc_sw32(uint32_t saddr) {
   uint64_t d = 0;
@@ -112,6 +114,15 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
         "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])                                           \
       : "r"(taddr))
 
+#define TMEM_LD16(taddr, r)                                                                          \
+  asm volatile(                                                                                      \
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}," \
+      " [%16];\n"                                                                                    \
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),         \
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),      \
+        "=r"(r[14]), "=r"(r[15])                                                                     \
+      : "r"(taddr))
+
 __global__ void __launch_bounds__(kThreads, 1)
     zgemm_split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     const int* __restrict__ Erow, const int* __restrict__ Fcol,
@@ -124,8 +135,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   unsigned char* sA = sm;
   unsigned char* sB = sm + NSTAGE * STAGE_A;
-  int* sums = reinterpret_cast<int*>(sm + NSTAGE * STAGE_BYTES);  // [NEXACT][BN][BM]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + NSTAGE * STAGE_BYTES + SUM_BYTES);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + NSTAGE * STAGE_BYTES);
   uint64_t* full = bars;                 // [NSTAGE]
   uint64_t* empty = bars + NSTAGE;       // [NSTAGE]
   uint64_t* chunk_full = bars + 2 * NSTAGE;
@@ -144,7 +154,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&empty[s], 1);
     }
     mbar_init(chunk_full, 1);
-    mbar_init(chunk_empty, 4);
+    mbar_init(chunk_empty, kFlushWarps);
     mbar_init(done, 1);
     fence_barrier_init();
   }
@@ -217,10 +227,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!mbar_wait_bounded(done, 0)) atomicOr(err, KERR_TIMEOUT_FULL);
     }
   } else {
-    // ---------------- flush and epilogue (warps 2..5)
+    // ---------------- flush and epilogue (warps 2..9): warp w reads TMEM
+    // lanes 32 (w % 4) .. +31 (one row each) and 32 columns, half hf.
     const int q = warp & 3;
+    const int hf = (warp - 2) >> 2;
     const int row = q * 32 + lane;
-    const uint32_t tbase = tmem + (static_cast<uint32_t>(q * 32) << 16);
+    const uint32_t tbase = tmem + (static_cast<uint32_t>(q * 32) << 16) + hf * 32;
+    int sums[NEXACT][32];  // exact level sums of this row, 32 columns
     bool ok = true;
     for (int ch = 0; ch < nchunks; ++ch) {
       if (!mbar_wait_bounded(chunk_full, ch & 1)) {
@@ -229,19 +242,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-#pragma unroll 1
-      for (int d = 0; d < NEXACT; ++d) {
-#pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 32) {
-          uint32_t r[32];
-          TMEM_LD32(tbase + d * BN + c0, r);
-          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-          int* dst = sums + (d * BN + c0) * BM + row;
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int v = __float2int_rn(__uint_as_float(r[j]));
-            dst[j * BM] = (ch == 0) ? v : dst[j * BM] + v;
-          }
+      for (int d = 0; d < NEXACT; ++d) {
+        uint32_t r[32];
+        TMEM_LD32(tbase + d * BN, r);
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int v = __float2int_rn(__uint_as_float(r[j]));
+          sums[d][j] = (ch == 0) ? v : sums[d][j] + v;
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -249,35 +258,30 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (lane == 0) mbar_arrive(chunk_empty);
     }
     if (ok) {
-      // last chunk_full covers every MMA, tail levels included
+      // the last chunk_full covers every MMA, tail levels included
       const int grow = row0 + row;
       const int er = grow < M ? Erow[grow] : 0;
-#pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 32) {
-        double acc[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) acc[j] = 0.0;
-        // exact levels, highest scale first
-#pragma unroll 1
-        for (int d = 0; d < NEXACT; ++d) {
-          const int* src = sums + (d * BN + c0) * BM + row;
-          const double f = ldexp(1.0, -7 * d);
+      for (int c0 = 0; c0 < 32; c0 += 16) {
+        double acc[16];
 #pragma unroll
-          for (int j = 0; j < 32; ++j) acc[j] += f * static_cast<double>(src[j * BM]);
-        }
+        for (int j = 0; j < 16; ++j)
+          acc[j] = static_cast<double>(sums[0][c0 + j]) +
+                   ldexp(static_cast<double>(sums[1][c0 + j]), -7) +
+                   ldexp(static_cast<double>(sums[2][c0 + j]), -14);
 #pragma unroll 1
         for (int d = NEXACT; d < S; ++d) {
-          uint32_t r[32];
-          TMEM_LD32(tbase + d * BN + c0, r);
+          uint32_t r[16];
+          TMEM_LD16(tbase + d * BN + c0, r);
           asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
           const double f = ldexp(1.0, -7 * d);
 #pragma unroll
-          for (int j = 0; j < 32; ++j) acc[j] += f * static_cast<double>(__uint_as_float(r[j]));
+          for (int j = 0; j < 16; ++j) acc[j] += f * static_cast<double>(__uint_as_float(r[j]));
         }
         if (grow < M) {
 #pragma unroll
-          for (int j = 0; j < 32; j += 2) {
-            const int cc = (colr0 + c0 + j) >> 1;  // complex column relative to the block
+          for (int j = 0; j < 16; j += 2) {
+            const int cc = (colr0 + hf * 32 + c0 + j) >> 1;  // complex column in the block
             if (cc >= ncols) continue;
             const int ex = er + Fcol[cc] - 14;
             double vr = ldexp(acc[j], ex), vi = ldexp(acc[j + 1], ex);
