@@ -37,7 +37,8 @@
 //    slices of a 16-wide K block (SWIZZLE_32B), 5-stage mbarrier ring (the
 //    depth hides the L2 latency of the narrow 32-byte box rows);
 //  * warp 1: allocates 512 TMEM columns (7 levels x 64 FP32 columns) and one
-//    thread issues the 28 tcgen05.mma (M=128, N=64, K=16) per K block,
+//    thread issues the 28 tcgen05.mma (M=128, N=64, K=16) per K block (at a
+//    chunk boundary the tail levels first, so the flush overlaps them),
 //    committing stages back to the producer and chunks to the flush warps;
 //  * warps 2-9 (two per TMEM lane quarter, 32 columns each): flush the exact
 //    levels every chunk into int32 registers, then combine all levels in
@@ -196,11 +197,6 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int kb = 0; kb < nkb && ok; ++kb) {
         const int st = kb % NSTAGE;
         const int ch = kb / CHUNK, kin = kb % CHUNK;
-        if (kin == 0 && ch > 0 && !mbar_wait_bounded(chunk_empty, (ch - 1) & 1)) {
-          atomicOr(err, KERR_TIMEOUT_FULL);
-          ok = false;
-          break;
-        }
         if (!mbar_wait_bounded(&full[st], (kb / NSTAGE) & 1)) {
           atomicOr(err, KERR_TIMEOUT_FULL);
           ok = false;
@@ -209,17 +205,32 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         const uint32_t a0 = smem_u32(sA + st * STAGE_A);
         const uint32_t b0 = smem_u32(sB + st * STAGE_B);
+        // At a chunk boundary the tail levels (3-6) go first: they do not touch
+        // the exact levels that the flush warps are still reading, so the
+        // tensor pipe works while the flush runs.
+        const bool boundary = (kin == 0 && ch > 0);
 #pragma unroll
-        for (int s = 0; s < S; ++s) {
+        for (int pass = 0; pass < 2; ++pass) {
+          const bool exact_pass = (pass == 1);
+          if (boundary && exact_pass && !mbar_wait_bounded(chunk_empty, (ch - 1) & 1)) {
+            atomicOr(err, KERR_TIMEOUT_FULL);
+            ok = false;
+            break;
+          }
 #pragma unroll
-          for (int t = 0; t + s < S; ++t) {
-            const int d = s + t;
-            // first contribution to level d in this accumulation window?
-            const bool first = (s == 0) && (d < NEXACT ? kin == 0 : kb == 0);
-            umma_bf16(tmem + d * BN, desc_sw32(a0 + s * A_TILE), desc_sw32(b0 + t * B_TILE), idesc,
-                      first ? 0u : 1u);
+          for (int s = 0; s < S; ++s) {
+            const uint64_t da = desc_sw32(a0 + s * A_TILE);
+#pragma unroll
+            for (int t = 0; t + s < S; ++t) {
+              const int d = s + t;
+              if ((d < NEXACT) != exact_pass) continue;
+              // first contribution to level d in this accumulation window?
+              const bool first = (s == 0) && (d < NEXACT ? kin == 0 : kb == 0);
+              umma_bf16(tmem + d * BN, da, desc_sw32(b0 + t * B_TILE), idesc, first ? 0u : 1u);
+            }
           }
         }
+        if (!ok) break;
         umma_commit(smem_u32(&empty[st]));
         if (kin == CHUNK - 1 || kb == nkb - 1) umma_commit(smem_u32(chunk_full));
       }
@@ -499,7 +510,9 @@ int split_segments(int64_t N, int ncols) {
   const int64_t nkb = k_padded(N) / split::BK;
   int nseg = static_cast<int>((nkb + kMaxKBlocksPerSegment - 1) / kMaxKBlocksPerSegment);
   // Narrow blocks leave SMs idle: split K until the grid covers the SMs,
-  // keeping every segment at least 64 K blocks long.
+  // keeping every segment at least 64 K blocks long.  (Splitting wider
+  // grids to trim the last wave costs more in the combine pass and the
+  // extra epilogues than it recovers: measured on the N = 8000 solve.)
   const int64_t tiles = ((2LL * ncols + split::BN - 1) / split::BN) * ((N + split::BM - 1) / split::BM);
   while (tiles * nseg < 152 && nkb / (nseg + 1) >= 64 && nseg < 8) ++nseg;
   return nseg;
