@@ -59,7 +59,9 @@ __global__ void __launch_bounds__(128)
   const long long kbeg = blockIdx.z * kchunk;
   const long long kend = min(N, kbeg + kchunk);
 
-  double acr[2][2][2] = {}, aci[2][2][2] = {};
+  // conj(x) y with three real products: T1 = xr yr, T2 = xi yi,
+  // T3 = (xr - xi)(yr + yi); re = T1 + T2, im = T3 - T1 + T2
+  double t1[2][2][2] = {}, t2[2][2][2] = {}, t3[2][2][2] = {};
   for (long long k0 = kbeg; k0 < kend; k0 += GK) {
     // load: 32 columns x 16 rows of X and of Y (column-contiguous in k)
     for (int e = threadIdx.x; e < GT * GK; e += 128) {
@@ -77,19 +79,24 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
     for (int kk = 0; kk < GK; kk += 4) {
       double2 a[2], b[2];
+      double ad[2], bsum[2];
 #pragma unroll
-      for (int mi = 0; mi < 2; ++mi) a[mi] = sX[wm * 16 + mi * 8 + g][kk + t];
+      for (int mi = 0; mi < 2; ++mi) {
+        a[mi] = sX[wm * 16 + mi * 8 + g][kk + t];
+        ad[mi] = a[mi].x - a[mi].y;
+      }
 #pragma unroll
-      for (int ni = 0; ni < 2; ++ni) b[ni] = sY[wn * 16 + ni * 8 + g][kk + t];
+      for (int ni = 0; ni < 2; ++ni) {
+        b[ni] = sY[wn * 16 + ni * 8 + g][kk + t];
+        bsum[ni] = b[ni].x + b[ni].y;
+      }
 #pragma unroll
       for (int mi = 0; mi < 2; ++mi)
 #pragma unroll
         for (int ni = 0; ni < 2; ++ni) {
-          // conj(x) y = (xr yr + xi yi) + i (xr yi - xi yr)
-          dmma_8x8x4(acr[mi][ni][0], acr[mi][ni][1], a[mi].x, b[ni].x);
-          dmma_8x8x4(acr[mi][ni][0], acr[mi][ni][1], a[mi].y, b[ni].y);
-          dmma_8x8x4(aci[mi][ni][0], aci[mi][ni][1], a[mi].x, b[ni].y);
-          dmma_8x8x4(aci[mi][ni][0], aci[mi][ni][1], -a[mi].y, b[ni].x);
+          dmma_8x8x4(t1[mi][ni][0], t1[mi][ni][1], a[mi].x, b[ni].x);
+          dmma_8x8x4(t2[mi][ni][0], t2[mi][ni][1], a[mi].y, b[ni].y);
+          dmma_8x8x4(t3[mi][ni][0], t3[mi][ni][1], ad[mi], bsum[ni]);
         }
     }
     __syncthreads();
@@ -103,7 +110,9 @@ __global__ void __launch_bounds__(128)
       for (int h = 0; h < 2; ++h) {
         const int r = p0 + wm * 16 + mi * 8 + g;
         const int c = q0 + wn * 16 + ni * 8 + 2 * t + h;
-        if (r < p && c < q) Pz[(long long)c * ldp + r] = make_double2(acr[mi][ni][h], aci[mi][ni][h]);
+        if (r < p && c < q)
+          Pz[(long long)c * ldp + r] =
+              make_double2(t1[mi][ni][h] + t2[mi][ni][h], t3[mi][ni][h] - t1[mi][ni][h] + t2[mi][ni][h]);
       }
 }
 

@@ -18,8 +18,11 @@
 //    of shared-memory stages guarded by mbarriers; one producer warp issues
 //    the copies, four consumer warps issue DMMAs, so address generation and
 //    copies never occupy the math warps;
-//  * a complex product is four real DMMAs on the interleaved (re, im)
-//    operands read as 16-byte pairs from shared memory;
+//  * a complex product is three real DMMAs (the 3M / Gauss form:
+//    T1 = ar br, T2 = ai bi, T3 = (ar + ai)(br + bi), re = T1 - T2,
+//    im = T3 - T1 - T2) on the interleaved (re, im) operands read as 16-byte
+//    pairs from shared memory: 6 N^2 b executed FLOPs per 8 N^2 b of the
+//    complex product, still all FP64;
 //  * the shift, scale and axpby of the recurrence are applied while the
 //    accumulators are still in registers, so the filter makes one pass over
 //    its output per degree step;
@@ -117,14 +120,16 @@ __global__ void __launch_bounds__(C::kThreads)
   const int g = lane >> 2;  // fragment row (A, C) / column (B)
   const int t = lane & 3;   // fragment k index (A, B) / column pair (C)
 
-  double acr[C::MI][C::NI][2];
-  double aci[C::MI][C::NI][2];
+  double t1[C::MI][C::NI][2];  // sum ar br
+  double t2[C::MI][C::NI][2];  // sum ai bi
+  double t3[C::MI][C::NI][2];  // sum (ar + ai)(br + bi)
 #pragma unroll
   for (int mi = 0; mi < C::MI; ++mi)
 #pragma unroll
     for (int ni = 0; ni < C::NI; ++ni) {
-      acr[mi][ni][0] = acr[mi][ni][1] = 0.0;
-      aci[mi][ni][0] = aci[mi][ni][1] = 0.0;
+      t1[mi][ni][0] = t1[mi][ni][1] = 0.0;
+      t2[mi][ni][0] = t2[mi][ni][1] = 0.0;
+      t3[mi][ni][0] = t3[mi][ni][1] = 0.0;
     }
 
   for (int kt = 0; kt < nk; ++kt) {
@@ -138,21 +143,24 @@ __global__ void __launch_bounds__(C::kThreads)
 #pragma unroll
     for (int kk = 0; kk < C::BK; kk += 4) {
       double2 af[C::MI], bf[C::NI];
+      double as[C::MI], bs[C::NI];
 #pragma unroll
-      for (int mi = 0; mi < C::MI; ++mi)
+      for (int mi = 0; mi < C::MI; ++mi) {
         af[mi] = a_s[(kk + t) * C::BM + wm * C::WTM + mi * 8 + g];
+        as[mi] = af[mi].x + af[mi].y;
+      }
 #pragma unroll
-      for (int ni = 0; ni < C::NI; ++ni)
+      for (int ni = 0; ni < C::NI; ++ni) {
         bf[ni] = b_s[(wn * C::WTN + ni * 8 + g) * C::BK + kk + t];
+        bs[ni] = bf[ni].x + bf[ni].y;
+      }
 #pragma unroll
       for (int mi = 0; mi < C::MI; ++mi)
 #pragma unroll
         for (int ni = 0; ni < C::NI; ++ni) {
-          // (ar + i ai)(br + i bi) = (ar br - ai bi) + i (ar bi + ai br)
-          dmma_8x8x4(acr[mi][ni][0], acr[mi][ni][1], af[mi].x, bf[ni].x);
-          dmma_8x8x4(acr[mi][ni][0], acr[mi][ni][1], af[mi].y, -bf[ni].y);
-          dmma_8x8x4(aci[mi][ni][0], aci[mi][ni][1], af[mi].x, bf[ni].y);
-          dmma_8x8x4(aci[mi][ni][0], aci[mi][ni][1], af[mi].y, bf[ni].x);
+          dmma_8x8x4(t1[mi][ni][0], t1[mi][ni][1], af[mi].x, bf[ni].x);
+          dmma_8x8x4(t2[mi][ni][0], t2[mi][ni][1], af[mi].y, bf[ni].y);
+          dmma_8x8x4(t3[mi][ni][0], t3[mi][ni][1], as[mi], bs[ni]);
         }
     }
     __syncwarp();
@@ -170,7 +178,8 @@ __global__ void __launch_bounds__(C::kThreads)
       for (int h = 0; h < 2; ++h) {
         const int c = col0 + wn * C::WTN + ni * 8 + 2 * t + h;
         if (c >= j1) continue;
-        double vr = acr[mi][ni][h], vi = aci[mi][ni][h];
+        double vr = t1[mi][ni][h] - t2[mi][ni][h];
+        double vi = t3[mi][ni][h] - t1[mi][ni][h] - t2[mi][ni][h];
         if (shift != 0.0) {
           const double2 bv = Bsh[static_cast<long long>(c) * ldb + r];
           vr -= shift * bv.x;
