@@ -96,6 +96,27 @@ typedef struct {
   double t_total, t_lanczos, t_filter, t_qr, t_rr, t_eigh, t_resid, t_host; /* seconds */
 } chase_stats;
 
+/* Tile choice of the grouped FP64 filter: time the candidates on the first
+ * degree step (result cached per batch shape), or 0..3 for a fixed shape
+ * (0: 64 x 16, 1: 64 x 32, 2: 128 x 16, 3: 64 x 8 rows x complex columns). */
+#define CHASE_TILE_AUTO (-1)
+
+/* Counters and times of one chase_filter_batched call. */
+typedef struct {
+  int problems;            /* problems with work (N > 0 and b > 0) */
+  int steps;               /* degree steps (the largest degree of the batch; summed over
+                              the iterations of chase_solve_batched) */
+  int tile_config;         /* FP64 tile shape used (see CHASE_TILE_AUTO); -1 for split */
+  int launches;            /* kernel launches of the call (graph nodes counted once) */
+  long long matvecs;       /* column products with H over all problems (sum of the degrees) */
+  double flops;            /* 8 N^2 per column product, summed over problems */
+  double t_autotune;       /* host seconds spent choosing the tile shape (0 when cached) */
+  double t_graph_build;    /* host seconds to capture and instantiate the step graph */
+  double t_steps;          /* device seconds of the step graph (every degree step) */
+  double t_product;        /* device seconds of the grouped product launches alone */
+  double t_total;          /* host seconds of the whole call */
+} chase_batch_stats;
+
 /* Fill `opts` with the defaults of Table 1 (double precision column):
  * deg 20, optim 1 (the paper's default is false; this library's default is
  * the optimised filter of Sec. 4.1), deg_extra 2, deg_max 36, max_iter 25,
@@ -233,6 +254,37 @@ int chase_residuals(const chase_c64* H, int64_t N, int64_t ldh, const chase_c64*
 int chase_residuals_noalloc(const chase_c64* H, int64_t N, int64_t ldh, const chase_c64* V,
                             int64_t ldv, int b, const double* lambda, double* resid, void* stream);
 
+/* Chebyshev filter (Alg. 4, Eq. 7) of many independent problems at once.
+ * The paper filters one matrix per call; this entry point has no
+ * counterpart there: it runs Alg. 4 on P problems of different sizes with
+ * one grouped launch per degree step, every step of every problem in one
+ * CUDA graph.  Problem p is exactly chase_filter(H[p], N[p], ldh[p], V[p],
+ * ldv[p], b[p], degrees[p], b_sup[p], mu1[p], mu_nevnex[p], precision, NULL,
+ * stream): the same products, coefficients and column retirement.
+ * P         number of problems (>= 0).
+ * H, V      host arrays of P device pointers: H[p] N[p] x N[p] Hermitian
+ *           (leading dimension ldh[p] >= N[p]), V[p] N[p] x b[p] in/out
+ *           (ldv[p] >= N[p]), column-major complex128, 16-byte aligned.
+ *           V[p] doubles as the second buffer of the recurrence.
+ * N, ldh, ldv, b, b_sup, mu1, mu_nevnex   host arrays of P entries; every
+ *           problem needs mu1 < mu_nevnex < b_sup.  Problems with N == 0 or
+ *           b == 0 are skipped.
+ * degrees   host array of P host pointers, b[p] ints each, even and in
+ *           [2, 1024], any order.
+ * precision CHASE_FP64 or CHASE_SPLIT_BF16.
+ * tile      CHASE_TILE_AUTO or a fixed FP64 tile shape (ignored for split).
+ * stats     out, or NULL.
+ * Workspace: N[p] x b[p] per problem (FP64), plus the slices of every H
+ * (28 N[p]^2 bytes) for split; released before return.
+ * Errors: CHASE_INVALID_ARG (sizes, bounds, degrees, host H or V),
+ * CHASE_OUT_OF_MEMORY, CHASE_CUDA_ERROR, CHASE_TIMEOUT.  On error V may hold
+ * partial results. */
+int chase_filter_batched(int P, const chase_c64* const* H, const int64_t* N, const int64_t* ldh,
+                         chase_c64* const* V, const int64_t* ldv, const int* b,
+                         const int* const* degrees, const double* b_sup, const double* mu1,
+                         const double* mu_nevnex, int precision, int tile, chase_batch_stats* stats,
+                         void* stream);
+
 /* The ChASE eigensolver (Alg. 1) for the nev smallest eigenpairs of H.
  * H        N x N Hermitian, ldh (host or device)
  * V        N x (nev + nex), ldv, in/out (same kind as H).  In: random
@@ -253,6 +305,34 @@ int chase_solve(const chase_c64* H, int64_t N, int64_t ldh, int nev, int nex, do
                 chase_c64* V, int64_t ldv, double* Lambda, double* resid,
                 const chase_c64* lanczos_starts, const chase_opts* opts, chase_stats* stats,
                 void* stream);
+
+/* ChASE (Alg. 1) on P independent problems with the filter of every
+ * iteration grouped: each iteration runs Alg. 4 for all problems that are
+ * still iterating as one grouped launch per degree step (one CUDA graph, as
+ * chase_filter_batched), then Rayleigh-Ritz, QR, residuals, locking and the
+ * degree rule of each problem (lines 5-15).  The paper solves one problem
+ * per call; this batching has no counterpart there.  Problem p follows the
+ * same steps as chase_solve(H[p], N[p], ldh[p], nev[p], nex[p], tol[p], V[p],
+ * ldv[p], Lambda[p], resid[p], lanczos_starts[p], opts, stats + p, stream).
+ * H, V, lanczos_starts  host arrays of P device pointers (layouts as in
+ *          chase_solve; lanczos_starts[p] has leading dimension N[p]).
+ * N, ldh, nev, nex, tol, ldv   host arrays of P entries.
+ * Lambda, resid   host arrays of P host pointers (nev[p] + nex[p] doubles).
+ * opts     shared by every problem (NULL: chase_opts_default).
+ * status   out, P ints: each problem's chase_solve status.
+ * stats    out, P entries, or NULL; t_filter is the grouped filter's time
+ *          shared out by FLOPs, t_total the whole call.
+ * bstats   out (sums over all grouped filter calls), or NULL.
+ * Returns CHASE_OK when every problem converged, else the first problem
+ * status that is not CHASE_OK, or an error status of the call
+ * (CHASE_INVALID_ARG, CHASE_OUT_OF_MEMORY, CHASE_CUDA_ERROR, CHASE_TIMEOUT,
+ * CHASE_QR_BREAKDOWN, CHASE_EIGENSOLVER_ERROR), after which status is not
+ * written. */
+int chase_solve_batched(int P, const chase_c64* const* H, const int64_t* N, const int64_t* ldh,
+                        const int* nev, const int* nex, const double* tol, chase_c64* const* V,
+                        const int64_t* ldv, double* const* Lambda, double* const* resid,
+                        const chase_c64* const* lanczos_starts, const chase_opts* opts,
+                        int* status, chase_stats* stats, chase_batch_stats* bstats, void* stream);
 
 #ifdef __cplusplus
 }

@@ -25,7 +25,8 @@ __all__ = [
     "CHASE_OK", "CHASE_INVALID_ARG", "CHASE_NOT_CONVERGED", "CHASE_QR_BREAKDOWN",
     "CHASE_BOUND_VIOLATION", "CHASE_CUDA_ERROR", "CHASE_OUT_OF_MEMORY", "CHASE_TIMEOUT",
     "CHASE_EIGENSOLVER_ERROR", "CHASE_CONV_ABS", "CHASE_CONV_REL", "CHASE_FP64",
-    "CHASE_SPLIT_BF16",
+    "CHASE_SPLIT_BF16", "CHASE_TILE_AUTO", "ChaseBatchStats", "chase_filter_batched",
+    "chase_solve_batched",
 ]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -44,6 +45,7 @@ CHASE_FP64 = 0
 CHASE_SPLIT_BF16 = 1
 CHASE_CONV_ABS = 0
 CHASE_CONV_REL = 1
+CHASE_TILE_AUTO = -1
 
 
 class ChaseError(RuntimeError):
@@ -77,6 +79,18 @@ class ChaseStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ChaseBatchStats(ctypes.Structure):
+    _fields_ = [
+        ("problems", ctypes.c_int), ("steps", ctypes.c_int), ("tile_config", ctypes.c_int),
+        ("launches", ctypes.c_int), ("matvecs", ctypes.c_longlong), ("flops", ctypes.c_double),
+        ("t_autotune", ctypes.c_double), ("t_graph_build", ctypes.c_double),
+        ("t_steps", ctypes.c_double), ("t_product", ctypes.c_double), ("t_total", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _c_p = ctypes.c_void_p
 _i64 = ctypes.c_int64
 _int = ctypes.c_int
@@ -90,6 +104,11 @@ _SIGNATURES = {
     "chase_kernel_launches": (ctypes.c_longlong, []),
     "chase_filter": (_int, [_c_p, _i64, _i64, _c_p, _i64, _int, _c_p, _dbl, _dbl, _dbl, _int, _c_p,
                             _c_p]),
+    "chase_filter_batched": (_int, [_int, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p,
+                                    _c_p, _int, _int, ctypes.POINTER(ChaseBatchStats), _c_p]),
+    "chase_solve_batched": (_int, [_int, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p,
+                                   _c_p, ctypes.POINTER(ChaseOpts), _c_p, _c_p,
+                                   ctypes.POINTER(ChaseBatchStats), _c_p]),
     "chase_lanczos": (_int, [_c_p, _i64, _i64, _int, _int, _int, _int, _int, _dbl, _c_p, _c_p,
                              _i64, _dp, _dp, _dp, _dp, _c_p]),
     "chase_degrees": (_int, [_int, _dp, _dp, _dbl, _dbl, _dbl, _int, _int, _ip]),
@@ -217,6 +236,94 @@ def chase_filter(H, V, degrees, b_sup, mu1, mu_nevnex, work=None, stream=None,
                             float(mu_nevnex), int(precision), wp, _stream(V, stream))
     _check(st, "chase_filter")
     return V
+
+
+def chase_filter_batched(Hs, Vs, degrees, b_sup, mu1, mu_nevnex, precision=CHASE_FP64,
+                         tile=CHASE_TILE_AUTO, stream=None):
+    """Filter every V[p] in place with its own H[p], degrees and bounds, all
+    problems in one grouped launch per degree step.  ``Hs``, ``Vs``: lists
+    of column-major complex128 device tensors; ``degrees``: list of int
+    sequences.  Returns the call's counters and times as a dict."""
+    P = len(Hs)
+    if not (len(Vs) == len(degrees) == P):
+        raise ValueError("one V and one degree list per H")
+    hp = (ctypes.c_void_p * max(P, 1))()
+    vp = (ctypes.c_void_p * max(P, 1))()
+    dp = (ctypes.c_void_p * max(P, 1))()
+    n = np.zeros(max(P, 1), dtype=np.int64)
+    ldh = np.ones(max(P, 1), dtype=np.int64)
+    ldv = np.ones(max(P, 1), dtype=np.int64)
+    b = np.zeros(max(P, 1), dtype=np.int32)
+    keep = []
+    for p in range(P):
+        H, V = Hs[p], Vs[p]
+        n[p] = H.shape[0]
+        hp[p], ldh[p] = _mat(H, int(n[p]), "H")
+        vp[p], ldv[p] = _mat(V, int(n[p]), "V")
+        b[p] = V.shape[1]
+        d = np.ascontiguousarray(np.asarray(degrees[p], dtype=np.int32))
+        if d.shape != (int(b[p]),):
+            raise ValueError("one degree per column")
+        keep.append(d)
+        dp[p] = d.ctypes.data
+    bs, m1, mn = _f64(b_sup, P), _f64(mu1, P), _f64(mu_nevnex, P)
+    stats = ChaseBatchStats()
+    st = lib().chase_filter_batched(
+        P, ctypes.cast(hp, _c_p), n.ctypes.data, ldh.ctypes.data, ctypes.cast(vp, _c_p),
+        ldv.ctypes.data, b.ctypes.data, ctypes.cast(dp, _c_p), bs.ctypes.data, m1.ctypes.data,
+        mn.ctypes.data, int(precision), int(tile), ctypes.byref(stats),
+        _stream(Vs[0], stream) if P else ctypes.c_void_p(0 if stream is None else int(stream)))
+    _check(st, "chase_filter_batched")
+    return stats.as_dict()
+
+
+def chase_solve_batched(Hs, nev, nex, tol, Vs, lanczos_starts, opts=None, stream=None):
+    """ChASE on every problem of the batch with grouped filters.  ``Hs``,
+    ``Vs``, ``lanczos_starts``: lists of column-major complex128 device
+    tensors; ``nev``, ``nex``, ``tol``: one value per problem (or a scalar).
+    Returns (status, statuses, [Lambda], [resid], [stats], batch_stats)."""
+    P = len(Hs)
+    if not (len(Vs) == len(lanczos_starts) == P):
+        raise ValueError("one V and one start block per H")
+    nev = np.broadcast_to(np.asarray(nev, dtype=np.int32), (P,)).copy()
+    nex = np.broadcast_to(np.asarray(nex, dtype=np.int32), (P,)).copy()
+    tol = np.broadcast_to(np.asarray(tol, dtype=np.float64), (P,)).copy()
+    m = max(P, 1)
+    hp, vp, sp = (ctypes.c_void_p * m)(), (ctypes.c_void_p * m)(), (ctypes.c_void_p * m)()
+    lp, rp = (ctypes.c_void_p * m)(), (ctypes.c_void_p * m)()
+    n = np.zeros(m, dtype=np.int64)
+    ldh = np.ones(m, dtype=np.int64)
+    ldv = np.ones(m, dtype=np.int64)
+    lams, res = [], []
+    for p in range(P):
+        n[p] = Hs[p].shape[0]
+        hp[p], ldh[p] = _mat(Hs[p], int(n[p]), "H")
+        vp[p], ldv[p] = _mat(Vs[p], int(n[p]), "V")
+        sp[p], lds = _mat(lanczos_starts[p], int(n[p]), "lanczos_starts")
+        if lds != n[p] and lanczos_starts[p].shape[1] > 1:
+            raise ValueError("lanczos_starts must have leading dimension N")
+        nx = int(nev[p] + nex[p])
+        if Vs[p].shape[1] != nx:
+            raise ValueError("V must have nev + nex columns")
+        lams.append(np.zeros(nx))
+        res.append(np.zeros(nx))
+        lp[p] = lams[-1].ctypes.data
+        rp[p] = res[-1].ctypes.data
+    if opts is None:
+        opts = chase_opts_default()
+    statuses = np.zeros(m, dtype=np.int32)
+    stats = (ChaseStats * m)()
+    bstats = ChaseBatchStats()
+    st = lib().chase_solve_batched(
+        P, ctypes.cast(hp, _c_p), n.ctypes.data, ldh.ctypes.data, nev.ctypes.data,
+        nex.ctypes.data, tol.ctypes.data, ctypes.cast(vp, _c_p), ldv.ctypes.data,
+        ctypes.cast(lp, _c_p), ctypes.cast(rp, _c_p), ctypes.cast(sp, _c_p), ctypes.byref(opts),
+        statuses.ctypes.data, ctypes.cast(stats, _c_p), ctypes.byref(bstats),
+        _stream(Vs[0], stream) if P else ctypes.c_void_p(0 if stream is None else int(stream)))
+    _check(st, "chase_solve_batched",
+           allow=(CHASE_OK, CHASE_NOT_CONVERGED, CHASE_BOUND_VIOLATION))
+    return (st, statuses[:P].tolist(), lams, res, [stats[p].as_dict() for p in range(P)],
+            bstats.as_dict())
 
 
 def chase_lanczos(H, k, nvec, approx, nev, nex, starts, V=None, dos_sigma=0.25, stream=None):

@@ -375,6 +375,271 @@ int stage_in(Dev& d, bool on_dev, const chase_c64* src, int64_t ld, int64_t rows
 
 bool ld_ok(int64_t ld, int64_t n) { return ld >= std::max<int64_t>(1, n); }
 
+// One ChASE solve (Alg. 1) as a sequence of phases, so that the filter of
+// many solves can run as one grouped launch: setup (staging, workspace,
+// line 1-2), then per iteration begin_iteration (line 3 and the bound
+// check), the filter (line 4), after_filter (lines 5-15), and finally
+// finish (ascending output).
+struct Solver {
+  // arguments
+  const chase_c64* H = nullptr;
+  int64_t N = 0, ldh = 0;
+  int nev = 0, nex = 0, nx = 0;
+  double tol = 0;
+  chase_c64* V = nullptr;
+  int64_t ldv = 0;
+  double* Lambda = nullptr;
+  double* resid = nullptr;
+  const chase_c64* starts = nullptr;
+  chase_opts o{};
+  bool dev = true;
+  // device state
+  chase_c64 *dH = nullptr, *dV = nullptr, *dS = nullptr, *Wk = nullptr;
+  int64_t lh = 0, lv = 0, ls = 0;
+  OrthWork ow;
+  RRWork rw;
+  SplitH sh;
+  SplitX sx;
+  bool split = false;
+  double *dw = nullptr, *dres = nullptr;
+  int* dperm = nullptr;
+  // host state
+  double N2 = 0, b_sup = 0, mu1 = 0, mu_nn = 0, h = 0, tol_eff = 0;
+  int d0 = 0, nconv = 0, iter = 0, status = CHASE_OK, maxdeg = 0;
+  std::vector<int> m, order, perm, start;
+  std::vector<double> ritz, res, ra, rr;
+  chase_stats S{};
+
+  // active block of the current iteration
+  int b() const { return nx - nconv; }
+  chase_c64* Va() const { return dV + static_cast<size_t>(nconv) * lv; }
+  bool more() const { return status == CHASE_OK && nconv < nev && iter < o.max_iter; }
+
+  // Everything before the loop of Alg. 1; `grouped_split` leaves the slices
+  // of H to the caller.
+  int setup(Dev& d, bool grouped_split) {
+    std::memset(&S, 0, sizeof(S));
+    nx = nev + nex;
+    PhaseTimer tm(d.st);
+    const int r = o.approx ? 1 : 1 + o.num_lanczos;
+    CHASE_TRY(stage_in(d, dev, H, ldh, N, N, &dH, &lh));
+    CHASE_TRY(stage_in(d, dev, V, ldv, N, nx, &dV, &lv));
+    CHASE_TRY(stage_in(d, dev, starts, N, N, r, &dS, &ls));
+    CHASE_TRY(d.alloc(&Wk, static_cast<size_t>(N) * nx));  // filter double buffer / permutation scratch
+    CHASE_TRY(orth_alloc(d, N, nx, nx, ow));
+    CHASE_TRY(rr_alloc(d, N, nx, rw));
+    split = o.precision == CHASE_SPLIT_BF16;
+    if (split && !grouped_split) {  // slices of H once per solve, slice workspace for the block
+      CHASE_TRY(split_prepare_h(d, dH, N, lh, sh));
+      CHASE_TRY(split_alloc_x(d, N, nx, sx));
+    }
+    CHASE_TRY(d.alloc(&dw, nx));
+    CHASE_TRY(d.alloc(&dres, nx));
+    CHASE_TRY(d.alloc(&dperm, nx));
+    N2 = static_cast<double>(N) * static_cast<double>(N);
+    // Alg. 1 line 1: constant initial degree, rounded up to even
+    d0 = std::min(o.deg + o.deg % 2, kMaxDegAllowed);
+    m.assign(nx, d0);
+    // line 2: bounds (and start vectors when approx == 0)
+    LanczosOut lz;
+    tm.begin(&S.t_lanczos);
+    CHASE_TRY(lanczos_core(d, dH, N, lh, o.lanczos_iter, o.num_lanczos, o.approx != 0, nev, nex,
+                           o.dos_sigma, dS, o.approx ? nullptr : dV, lv, o.approx ? 0 : nx, lz));
+    tm.end();
+    S.matvecs += lz.matvecs;
+    S.flops_total += 8.0 * N2 * lz.matvecs;
+    b_sup = lz.b_sup;
+    if (o.approx) {
+      mu1 = *std::min_element(Lambda, Lambda + nx);
+      mu_nn = *std::max_element(Lambda, Lambda + nx);
+    } else {
+      mu1 = lz.mu1;
+      mu_nn = lz.mu_nn;
+    }
+    h = lz.theta_absmax;
+    ritz.assign(nx, 0.0);
+    res.assign(nx, HUGE_VAL);
+    ra.assign(nx, 0.0);
+    rr.assign(nx, 0.0);
+    order.assign(nx, 0);
+    perm.assign(nx, 0);
+    tol_eff = o.conv_mode == CHASE_CONV_REL ? tol * h : tol;
+    return CHASE_OK;
+  }
+
+  // Line 3 of an iteration; false when the bounds are out of order.
+  bool begin_iteration() {
+    ++iter;
+    if (!(mu1 < mu_nn && mu_nn < b_sup)) {
+      set_error("chase_solve: spectral estimates out of order (mu1=%g, mu_nevnex=%g, b_sup=%g)",
+                mu1, mu_nn, b_sup);
+      status = CHASE_BOUND_VIOLATION;
+      return false;
+    }
+    // line 4: the active columns are sorted by degree (line 15)
+    maxdeg = m[nx - 1];
+    starts_from_sorted(m.data() + nconv, b(), maxdeg, start);
+    return true;
+  }
+
+  // The filter of this solve alone (line 4).
+  int filter(Dev& d) {
+    PhaseTimer tm(d.st);
+    long long fm = 0;
+    tm.begin(&S.t_filter);
+    CHASE_TRY(filter_sorted(d, dH, N, lh, Va(), lv, Wk, N, b(), start.data(), maxdeg, b_sup, mu1,
+                            mu_nn, &fm, split ? &sh : nullptr, &sx));
+    tm.end();
+    count_filter(fm);
+    return CHASE_OK;
+  }
+
+  // The grouped filter's view of this solve's line 4.
+  GroupedFilterInput filter_input() const {
+    GroupedFilterInput g;
+    g.H = dH;
+    g.ldh = lh;
+    g.n = static_cast<int>(N);
+    g.X = Va();
+    g.ldx = lv;
+    g.W = Wk;
+    g.ldw = N;
+    g.b = b();
+    g.start = start.data();
+    g.maxdeg = maxdeg;
+    g.b_sup = b_sup;
+    g.mu1 = mu1;
+    g.mu_nn = mu_nn;
+    return g;
+  }
+
+  long long filter_matvecs() const {
+    long long fm = 0;
+    for (int i = 1; i <= maxdeg; ++i) fm += b() - start[i];
+    return fm;
+  }
+
+  void count_filter(long long fm) {
+    S.filter_matvecs += fm;
+    S.matvecs += fm;
+    S.flops_filter += 8.0 * N2 * fm;
+    S.flops_total += 8.0 * N2 * fm;
+  }
+
+  // Lines 5-15 of an iteration.
+  int after_filter(Dev& d) {
+    PhaseTimer tm(d.st);
+    const int nb = b();
+    chase_c64* va = Va();
+    // lines 5-6: orthonormalise the active block against the locked one
+    tm.begin(&S.t_qr);
+    CHASE_TRY(orth_core(d, N, dV, lv, nconv, va, lv, nb, ow, &S.flops_total));
+    tm.end();
+    // lines 7-8: Rayleigh-Ritz on the active block, residuals
+    tm.begin(&S.t_rr);
+    CHASE_TRY(rr_core(d, dH, N, lh, va, lv, nb, dw, dres, rw, &S.t_eigh, &S.flops_total));
+    CHASE_CUDA(cudaMemcpyAsync(ra.data(), dw, sizeof(double) * nb, cudaMemcpyDeviceToHost, d.st));
+    CHASE_CUDA(cudaMemcpyAsync(rr.data(), dres, sizeof(double) * nb, cudaMemcpyDeviceToHost, d.st));
+    tm.end();
+    CHASE_TRY(d.sync_check("chase_solve iteration"));
+    S.matvecs += nb;
+    // host decisions
+    const auto t_host0 = std::chrono::steady_clock::now();
+    for (int a = 0; a < nb; ++a) h = std::max(h, std::fabs(ra[a]));
+    tol_eff = o.conv_mode == CHASE_CONV_REL ? tol * h : tol;
+    if (ra[nb - 1] > b_sup + 1e-10 * std::max(1.0, std::fabs(b_sup))) {
+      set_error("chase_solve: Ritz value %g above b_sup %g", ra[nb - 1], b_sup);
+      status = CHASE_BOUND_VIOLATION;
+    }
+    int n_new = 0;
+    chase_lock(nb, ra.data(), rr.data(), tol_eff, order.data(), &n_new);  // line 9 (Alg. 3)
+    for (int a = 0; a < nb; ++a) {
+      ritz[nconv + a] = ra[order[a]];
+      res[nconv + a] = rr[order[a]];
+    }
+    const int nconv_new = nconv + n_new;
+    mu1 = *std::min_element(ritz.begin(), ritz.end());  // line 10
+    mu_nn = *std::max_element(ritz.begin(), ritz.end());
+    const double c = 0.5 * (b_sup + mu_nn);  // line 11
+    const double e = 0.5 * (b_sup - mu_nn);
+    const int nrest = nx - nconv_new;
+    std::vector<int> ord2(nrest);
+    if (nrest > 0) {
+      if (o.optim && e > 0.0)  // lines 12-14
+        chase_degrees(nrest, res.data() + nconv_new, ritz.data() + nconv_new, c, e, tol_eff,
+                      o.deg_extra, std::min(o.deg_max, kMaxDegAllowed), m.data() + nconv_new);
+      else
+        std::fill(m.begin() + nconv_new, m.end(), d0);
+      std::iota(ord2.begin(), ord2.end(), 0);  // line 15: stable sort by degree
+      std::stable_sort(ord2.begin(), ord2.end(), [&](int x, int y) {
+        return m[nconv_new + x] < m[nconv_new + y];
+      });
+    }
+    // one gather over the active block: locked first (Ritz order), then the
+    // rest by degree
+    for (int a = 0; a < n_new; ++a) perm[a] = order[a];
+    for (int a = 0; a < nrest; ++a) perm[n_new + a] = order[n_new + ord2[a]];
+    std::vector<double> r2(nrest), s2(nrest);
+    std::vector<int> m2(nrest);
+    for (int a = 0; a < nrest; ++a) {
+      r2[a] = ritz[nconv_new + ord2[a]];
+      s2[a] = res[nconv_new + ord2[a]];
+      m2[a] = m[nconv_new + ord2[a]];
+    }
+    for (int a = 0; a < nrest; ++a) {
+      ritz[nconv_new + a] = r2[a];
+      res[nconv_new + a] = s2[a];
+      m[nconv_new + a] = m2[a];
+    }
+    S.t_host += std::chrono::duration<double>(std::chrono::steady_clock::now() - t_host0).count();
+    CHASE_CUDA(cudaMemcpyAsync(dperm, perm.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, d.st));
+    CHASE_TRY(launch_permute_cols(d, va, lv, Wk, N, N, nb, dperm, false));
+    CHASE_TRY(copy_block(d, va, lv, Wk, N, N, nb, cudaMemcpyDeviceToDevice));
+    // the host arrays read by the copies above change in the next iteration
+    CHASE_TRY(d.sync_check("chase_solve permutation"));
+    nconv = nconv_new;
+    return CHASE_OK;
+  }
+
+  // Output: all pairs ascending by Ritz value; returns the solve's status.
+  int finish(Dev& d) {
+    std::vector<int> fin(nx);
+    std::iota(fin.begin(), fin.end(), 0);
+    std::stable_sort(fin.begin(), fin.end(), [&](int x, int y) { return ritz[x] < ritz[y]; });
+    CHASE_CUDA(cudaMemcpyAsync(dperm, fin.data(), sizeof(int) * nx, cudaMemcpyHostToDevice, d.st));
+    CHASE_TRY(launch_permute_cols(d, dV, lv, Wk, N, N, nx, dperm, false));
+    CHASE_TRY(copy_block(d, dV, lv, Wk, N, N, nx, cudaMemcpyDeviceToDevice));
+    if (!dev) CHASE_TRY(copy_block(d, V, ldv, dV, lv, N, nx, cudaMemcpyDeviceToHost));
+    CHASE_TRY(d.sync_check("chase_solve output"));
+    for (int a = 0; a < nx; ++a) {
+      Lambda[a] = ritz[fin[a]];
+      resid[a] = res[fin[a]];
+    }
+    S.iterations = iter;
+    S.nconv = nconv;
+    S.b_sup = b_sup;
+    S.mu1 = mu1;
+    S.mu_nevnex = mu_nn;
+    S.tol_eff = tol_eff;
+    if (status != CHASE_OK) return status;
+    return nconv >= nev ? CHASE_OK : CHASE_NOT_CONVERGED;
+  }
+};
+
+// Arguments of one solve, checked as chase_solve does.
+bool solve_args_ok(int64_t N, int64_t ldh, int nev, int nex, double tol, int64_t ldv,
+                   const void* H, const void* V, const void* Lambda, const void* resid,
+                   const void* starts, const chase_opts& o) {
+  const int nx = nev + nex;
+  return !(N < 1 || nev < 1 || nex < 0 || nx > N || !ld_ok(ldh, N) || !ld_ok(ldv, N) ||
+           !(tol > 0.0) || !H || !V || !Lambda || !resid || !starts || o.deg < 1 ||
+           o.deg > kMaxDegAllowed - 1 || o.deg_max < 2 || o.deg_max > kMaxDegAllowed ||
+           o.deg_extra < 0 || o.max_iter < 0 || o.lanczos_iter < 1 || o.lanczos_iter > N ||
+           (!o.approx && o.num_lanczos < 1) ||
+           (o.precision != CHASE_FP64 && o.precision != CHASE_SPLIT_BF16) ||
+           (o.conv_mode != CHASE_CONV_ABS && o.conv_mode != CHASE_CONV_REL));
+}
+
 }  // namespace
 }  // namespace chase
 
@@ -601,191 +866,165 @@ extern "C" int chase_solve(const chase_c64* H, int64_t N, int64_t ldh, int nev, 
     o = *opts_in;
   else
     chase_opts_default(&o);
-  const int nx = nev + nex;
-  if (N < 1 || nev < 1 || nex < 0 || nx > N || !ld_ok(ldh, N) || !ld_ok(ldv, N) || !(tol > 0.0) ||
-      !H || !V || !Lambda || !resid || !lanczos_starts || o.deg < 1 ||
-      o.deg > kMaxDegAllowed - 1 || o.deg_max < 2 || o.deg_max > kMaxDegAllowed ||
-      o.deg_extra < 0 || o.max_iter < 0 || o.lanczos_iter < 1 || o.lanczos_iter > N ||
-      (!o.approx && o.num_lanczos < 1) ||
-      (o.precision != CHASE_FP64 && o.precision != CHASE_SPLIT_BF16) ||
-      (o.conv_mode != CHASE_CONV_ABS && o.conv_mode != CHASE_CONV_REL)) {
+  if (!solve_args_ok(N, ldh, nev, nex, tol, ldv, H, V, Lambda, resid, lanczos_starts, o)) {
     set_error("chase_solve: invalid argument");
     return CHASE_INVALID_ARG;
   }
-  chase_stats S;
-  std::memset(&S, 0, sizeof(S));
   Dev d(stream);
   CHASE_TRY(d.init());
-  PhaseTimer total(d.st), tm(d.st);
-  total.begin(&S.t_total);
   const bool dev = is_device_ptr(H);
   if (is_device_ptr(V) != dev || is_device_ptr(lanczos_starts) != dev) {
     set_error("chase_solve: H, V and lanczos_starts must all be host or all be device");
     return CHASE_INVALID_ARG;
   }
-  const int r = o.approx ? 1 : 1 + o.num_lanczos;
-  chase_c64 *dH, *dV, *dS;
-  int64_t lh, lv, ls;
-  CHASE_TRY(stage_in(d, dev, H, ldh, N, N, &dH, &lh));
-  CHASE_TRY(stage_in(d, dev, V, ldv, N, nx, &dV, &lv));
-  CHASE_TRY(stage_in(d, dev, lanczos_starts, N, N, r, &dS, &ls));
-
-  chase_c64* Wk = nullptr;  // filter double buffer / permutation scratch
-  CHASE_TRY(d.alloc(&Wk, static_cast<size_t>(N) * nx));
-  OrthWork ow;
-  CHASE_TRY(orth_alloc(d, N, nx, nx, ow));
-  RRWork rw;
-  CHASE_TRY(rr_alloc(d, N, nx, rw));
-  SplitH sh;
-  SplitX sx;
-  const bool split = o.precision == CHASE_SPLIT_BF16;
-  if (split) {  // slices of H once per solve, slice workspace for the block
-    CHASE_TRY(split_prepare_h(d, dH, N, lh, sh));
-    CHASE_TRY(split_alloc_x(d, N, nx, sx));
+  Solver sv;
+  sv.H = H;
+  sv.N = N;
+  sv.ldh = ldh;
+  sv.nev = nev;
+  sv.nex = nex;
+  sv.tol = tol;
+  sv.V = V;
+  sv.ldv = ldv;
+  sv.Lambda = Lambda;
+  sv.resid = resid;
+  sv.starts = lanczos_starts;
+  sv.o = o;
+  sv.dev = dev;
+  PhaseTimer total(d.st);
+  double t_total = 0.0;
+  total.begin(&t_total);
+  CHASE_TRY(sv.setup(d, false));
+  while (sv.more()) {  // line 3
+    if (!sv.begin_iteration()) break;
+    CHASE_TRY(sv.filter(d));
+    CHASE_TRY(sv.after_filter(d));
   }
-  double *dw = nullptr, *dres = nullptr;
-  int* dperm = nullptr;
-  CHASE_TRY(d.alloc(&dw, nx));
-  CHASE_TRY(d.alloc(&dres, nx));
-  CHASE_TRY(d.alloc(&dperm, nx));
-
-  const double N2 = static_cast<double>(N) * static_cast<double>(N);
-  // Alg. 1 line 1: constant initial degree, rounded up to even
-  const int d0 = std::min(o.deg + o.deg % 2, kMaxDegAllowed);
-  std::vector<int> m(nx, d0);
-  // line 2: bounds (and start vectors when approx == 0)
-  LanczosOut lz;
-  tm.begin(&S.t_lanczos);
-  CHASE_TRY(lanczos_core(d, dH, N, lh, o.lanczos_iter, o.num_lanczos, o.approx != 0, nev, nex,
-                         o.dos_sigma, dS, o.approx ? nullptr : dV, lv, o.approx ? 0 : nx, lz));
-  tm.end();
-  S.matvecs += lz.matvecs;
-  S.flops_total += 8.0 * N2 * lz.matvecs;
-  const double b_sup = lz.b_sup;
-  double mu1, mu_nn;
-  if (o.approx) {
-    mu1 = *std::min_element(Lambda, Lambda + nx);
-    mu_nn = *std::max_element(Lambda, Lambda + nx);
-  } else {
-    mu1 = lz.mu1;
-    mu_nn = lz.mu_nn;
-  }
-  double h = lz.theta_absmax;
-  std::vector<double> ritz(nx, 0.0), res(nx, HUGE_VAL), ra(nx), rr(nx);
-  std::vector<int> order(nx), perm(nx), start;
-  int nconv = 0, iter = 0, status = CHASE_OK;
-  double tol_eff = o.conv_mode == CHASE_CONV_REL ? tol * h : tol;
-
-  while (nconv < nev && iter < o.max_iter) {  // line 3
-    ++iter;
-    const int b = nx - nconv;
-    chase_c64* Va = dV + static_cast<size_t>(nconv) * lv;
-    // line 4: filter; the active columns are sorted by degree (line 15)
-    if (!(mu1 < mu_nn && mu_nn < b_sup)) {
-      set_error("chase_solve: spectral estimates out of order (mu1=%g, mu_nevnex=%g, b_sup=%g)",
-                mu1, mu_nn, b_sup);
-      status = CHASE_BOUND_VIOLATION;
-      break;
-    }
-    const int maxdeg = m[nx - 1];
-    starts_from_sorted(m.data() + nconv, b, maxdeg, start);
-    long long fm = 0;
-    tm.begin(&S.t_filter);
-    CHASE_TRY(filter_sorted(d, dH, N, lh, Va, lv, Wk, N, b, start.data(), maxdeg, b_sup, mu1, mu_nn,
-                            &fm, split ? &sh : nullptr, &sx));
-    tm.end();
-    S.filter_matvecs += fm;
-    S.matvecs += fm;
-    S.flops_filter += 8.0 * N2 * fm;
-    S.flops_total += 8.0 * N2 * fm;
-    // lines 5-6: orthonormalise the active block against the locked one
-    tm.begin(&S.t_qr);
-    CHASE_TRY(orth_core(d, N, dV, lv, nconv, Va, lv, b, ow, &S.flops_total));
-    tm.end();
-    // lines 7-8: Rayleigh-Ritz on the active block, residuals
-    tm.begin(&S.t_rr);
-    CHASE_TRY(rr_core(d, dH, N, lh, Va, lv, b, dw, dres, rw, &S.t_eigh, &S.flops_total));
-    CHASE_CUDA(cudaMemcpyAsync(ra.data(), dw, sizeof(double) * b, cudaMemcpyDeviceToHost, d.st));
-    CHASE_CUDA(cudaMemcpyAsync(rr.data(), dres, sizeof(double) * b, cudaMemcpyDeviceToHost, d.st));
-    tm.end();
-    CHASE_TRY(d.sync_check("chase_solve iteration"));
-    S.matvecs += b;
-    // host decisions
-    const auto t_host0 = std::chrono::steady_clock::now();
-    for (int a = 0; a < b; ++a) h = std::max(h, std::fabs(ra[a]));
-    tol_eff = o.conv_mode == CHASE_CONV_REL ? tol * h : tol;
-    if (ra[b - 1] > b_sup + 1e-10 * std::max(1.0, std::fabs(b_sup))) {
-      set_error("chase_solve: Ritz value %g above b_sup %g", ra[b - 1], b_sup);
-      status = CHASE_BOUND_VIOLATION;
-    }
-    int n_new = 0;
-    chase_lock(b, ra.data(), rr.data(), tol_eff, order.data(), &n_new);  // line 9 (Alg. 3)
-    for (int a = 0; a < b; ++a) {
-      ritz[nconv + a] = ra[order[a]];
-      res[nconv + a] = rr[order[a]];
-    }
-    const int nconv_new = nconv + n_new;
-    mu1 = *std::min_element(ritz.begin(), ritz.end());  // line 10
-    mu_nn = *std::max_element(ritz.begin(), ritz.end());
-    const double c = 0.5 * (b_sup + mu_nn);  // line 11
-    const double e = 0.5 * (b_sup - mu_nn);
-    const int nrest = nx - nconv_new;
-    std::vector<int> ord2(nrest);
-    if (nrest > 0) {
-      if (o.optim && e > 0.0)  // lines 12-14
-        chase_degrees(nrest, res.data() + nconv_new, ritz.data() + nconv_new, c, e, tol_eff,
-                      o.deg_extra, std::min(o.deg_max, kMaxDegAllowed), m.data() + nconv_new);
-      else
-        std::fill(m.begin() + nconv_new, m.end(), d0);
-      std::iota(ord2.begin(), ord2.end(), 0);  // line 15: stable sort by degree
-      std::stable_sort(ord2.begin(), ord2.end(), [&](int x, int y) {
-        return m[nconv_new + x] < m[nconv_new + y];
-      });
-    }
-    // one gather over the active block: locked first (Ritz order), then the
-    // rest by degree
-    for (int a = 0; a < n_new; ++a) perm[a] = order[a];
-    for (int a = 0; a < nrest; ++a) perm[n_new + a] = order[n_new + ord2[a]];
-    std::vector<double> r2(nrest), s2(nrest);
-    std::vector<int> m2(nrest);
-    for (int a = 0; a < nrest; ++a) {
-      r2[a] = ritz[nconv_new + ord2[a]];
-      s2[a] = res[nconv_new + ord2[a]];
-      m2[a] = m[nconv_new + ord2[a]];
-    }
-    for (int a = 0; a < nrest; ++a) {
-      ritz[nconv_new + a] = r2[a];
-      res[nconv_new + a] = s2[a];
-      m[nconv_new + a] = m2[a];
-    }
-    S.t_host += std::chrono::duration<double>(std::chrono::steady_clock::now() - t_host0).count();
-    CHASE_CUDA(cudaMemcpyAsync(dperm, perm.data(), sizeof(int) * b, cudaMemcpyHostToDevice, d.st));
-    CHASE_TRY(launch_permute_cols(d, Va, lv, Wk, N, N, b, dperm, false));
-    CHASE_TRY(copy_block(d, Va, lv, Wk, N, N, b, cudaMemcpyDeviceToDevice));
-    nconv = nconv_new;
-    if (status != CHASE_OK) break;
-  }
-  // output: all pairs ascending by Ritz value
-  std::vector<int> fin(nx);
-  std::iota(fin.begin(), fin.end(), 0);
-  std::stable_sort(fin.begin(), fin.end(), [&](int x, int y) { return ritz[x] < ritz[y]; });
-  CHASE_CUDA(cudaMemcpyAsync(dperm, fin.data(), sizeof(int) * nx, cudaMemcpyHostToDevice, d.st));
-  CHASE_TRY(launch_permute_cols(d, dV, lv, Wk, N, N, nx, dperm, false));
-  CHASE_TRY(copy_block(d, dV, lv, Wk, N, N, nx, cudaMemcpyDeviceToDevice));
-  if (!dev) CHASE_TRY(copy_block(d, V, ldv, dV, lv, N, nx, cudaMemcpyDeviceToHost));
-  CHASE_TRY(d.sync_check("chase_solve output"));
-  for (int a = 0; a < nx; ++a) {
-    Lambda[a] = ritz[fin[a]];
-    resid[a] = res[fin[a]];
-  }
+  const int st = sv.finish(d);
+  if (st != CHASE_OK && st != CHASE_NOT_CONVERGED && st != CHASE_BOUND_VIOLATION) return st;
   total.end();
-  S.iterations = iter;
-  S.nconv = nconv;
-  S.b_sup = b_sup;
-  S.mu1 = mu1;
-  S.mu_nevnex = mu_nn;
-  S.tol_eff = tol_eff;
-  if (stats) *stats = S;
-  if (status != CHASE_OK) return status;
-  return nconv >= nev ? CHASE_OK : CHASE_NOT_CONVERGED;
+  sv.S.t_total = t_total;
+  if (stats) *stats = sv.S;
+  return st;
+}
+
+extern "C" int chase_solve_batched(int P, const chase_c64* const* H, const int64_t* N,
+                                   const int64_t* ldh, const int* nev, const int* nex,
+                                   const double* tol, chase_c64* const* V, const int64_t* ldv,
+                                   double* const* Lambda, double* const* resid,
+                                   const chase_c64* const* lanczos_starts, const chase_opts* opts_in,
+                                   int* status, chase_stats* stats, chase_batch_stats* bstats,
+                                   void* stream) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const long long launches0 = chase_kernel_launches();
+  if (bstats) *bstats = chase_batch_stats{};
+  chase_opts o;
+  if (opts_in)
+    o = *opts_in;
+  else
+    chase_opts_default(&o);
+  if (P < 0 || (P > 0 && (!H || !N || !ldh || !nev || !nex || !tol || !V || !ldv || !Lambda ||
+                          !resid || !lanczos_starts || !status))) {
+    set_error("chase_solve_batched: invalid problem count or NULL array");
+    return CHASE_INVALID_ARG;
+  }
+  for (int p = 0; p < P; ++p) {
+    if (!solve_args_ok(N[p], ldh[p], nev[p], nex[p], tol[p], ldv[p], H[p], V[p], Lambda[p],
+                       resid[p], lanczos_starts[p], o)) {
+      set_error("chase_solve_batched: problem %d: invalid argument", p);
+      return CHASE_INVALID_ARG;
+    }
+    if (!is_device_ptr(H[p]) || !is_device_ptr(V[p]) || !is_device_ptr(lanczos_starts[p])) {
+      set_error("chase_solve_batched: problem %d: H, V and lanczos_starts must be device arrays", p);
+      return CHASE_INVALID_ARG;
+    }
+  }
+  if (P == 0) return CHASE_OK;
+  Dev d(stream);
+  CHASE_TRY(d.init());
+  const bool split = o.precision == CHASE_SPLIT_BF16;
+  std::vector<Solver> sv(P);
+  for (int p = 0; p < P; ++p) {  // Alg. 1 lines 1-2 of every problem
+    Solver& s = sv[p];
+    s.H = H[p];
+    s.N = N[p];
+    s.ldh = ldh[p];
+    s.nev = nev[p];
+    s.nex = nex[p];
+    s.tol = tol[p];
+    s.V = V[p];
+    s.ldv = ldv[p];
+    s.Lambda = Lambda[p];
+    s.resid = resid[p];
+    s.starts = lanczos_starts[p];
+    s.o = o;
+    s.dev = true;
+    CHASE_TRY(s.setup(d, true));
+  }
+  std::vector<GroupedFilterInput> slices(P);  // split: slices of every H, made once
+  if (split) {
+    std::vector<int> bcap(P);
+    for (int p = 0; p < P; ++p) {
+      slices[p].H = sv[p].dH;
+      slices[p].ldh = sv[p].lh;
+      slices[p].n = static_cast<int>(sv[p].N);
+      bcap[p] = sv[p].nx;
+    }
+    CHASE_TRY(grouped_split_prepare(d, slices, bcap));
+  }
+  chase_batch_stats bs{};
+  bs.problems = P;
+  while (true) {  // line 3 of every problem still iterating
+    std::vector<int> act;
+    for (int p = 0; p < P; ++p)
+      if (sv[p].more() && sv[p].begin_iteration()) act.push_back(p);
+    if (act.empty()) break;
+    std::vector<GroupedFilterInput> in;
+    in.reserve(act.size());
+    for (int p : act) {
+      GroupedFilterInput g = sv[p].filter_input();
+      if (split) {
+        g.A = slices[p].A;
+        g.E = slices[p].E;
+        g.Dg = slices[p].Dg;
+        g.Bsl = slices[p].Bsl;
+        g.F = slices[p].F;
+        g.bcap = slices[p].bcap;
+      }
+      in.push_back(g);
+    }
+    GroupedFilterTimes tt;
+    CHASE_TRY(grouped_filter_sorted(d, in, split, CHASE_TILE_AUTO, &tt));  // line 4, grouped
+    bs.steps += tt.steps;
+    bs.tile_config = tt.tile_config;
+    bs.matvecs += tt.matvecs;
+    bs.flops += tt.flops;
+    bs.t_autotune += tt.t_autotune;
+    bs.t_graph_build += tt.t_graph_build;
+    bs.t_steps += tt.t_steps;
+    bs.t_product += tt.t_product;
+    for (int p : act) {
+      Solver& s = sv[p];
+      const long long fm = s.filter_matvecs();
+      s.count_filter(fm);
+      // the grouped filter's time, shared out by each problem's FLOPs
+      if (tt.flops > 0) s.S.t_filter += tt.t_steps * 8.0 * s.N2 * fm / tt.flops;
+    }
+    for (int p : act) CHASE_TRY(sv[p].after_filter(d));  // lines 5-15
+  }
+  int worst = CHASE_OK;
+  const double t_total =
+      std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  for (int p = 0; p < P; ++p) {
+    const int st = sv[p].finish(d);
+    if (st != CHASE_OK && st != CHASE_NOT_CONVERGED && st != CHASE_BOUND_VIOLATION) return st;
+    status[p] = st;
+    if (worst == CHASE_OK && st != CHASE_OK) worst = st;
+    sv[p].S.t_total = t_total;
+    if (stats) stats[p] = sv[p].S;
+  }
+  bs.launches = static_cast<int>(chase_kernel_launches() - launches0);
+  bs.t_total = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (bstats) *bstats = bs;
+  return worst;
 }

@@ -100,6 +100,113 @@ int split_alloc_x(Dev& d, int64_t N, int max_cols, SplitX& out);
 int zgemm_split(Dev& d, const SplitH& h, SplitX& x, const chase_c64* X, int64_t ldx, int j0, int j1,
                 chase_c64* C, int64_t ldc, double alpha, double beta, double shift);
 
+// ---- grouped filter: many independent problems per launch ----------------
+// One problem of a grouped filter, in device memory.  buf0 holds the block
+// sorted by degree (the filter's input and final output), buf1 is the second
+// buffer of the three-term recurrence; their tensor maps (FP64 path) or the
+// slice planes and maps (split path) live in device memory too.
+struct GroupedProblem {
+  const CUtensorMap* mapA;   // H (FP64) or the slice planes of H (split)
+  const CUtensorMap* mapB0;  // FP64: buf0; split: the slices of the active block
+  const CUtensorMap* mapB1;  // FP64: buf1
+  double2* buf0;
+  double2* buf1;
+  long long ld0, ld1;
+  const int* E;       // split: row exponents of H
+  int* F;             // split: column exponents of the active block
+  const double* Dg;   // split: real diagonal of H
+  void* Bsl;          // split: slice planes of the block [S][2 bcap][Kp]
+  long long Kp;       // split: padded K = 2N rounded up to 16
+  int n, b, bcap;     // rows, columns of the block, column capacity of Bsl
+};
+// One active problem of one degree step: columns [s, b) of problem `prob`
+// are filtered; its output tiles are CTAs [tile0, next.tile0) and its
+// columns [col0, next.col0) of the step's column range.  A step's list ends
+// with a sentinel entry holding the totals.
+struct GroupedStep {
+  int prob, s, tile0, col0;
+  double alpha, beta, shift;
+};
+// FP64 tile shapes of the grouped product (rows x complex columns per CTA).
+constexpr int kGroupedFp64Cfgs = 4;
+void grouped_fp64_tile(int cfg, int* bm, int* bn);
+// One degree step of the FP64 grouped filter: X = parity ? buf1 : buf0,
+// Y = the other buffer.
+int zgemm_grouped_fp64(Dev& d, int cfg, const GroupedProblem* probs, const GroupedStep* steps,
+                       int nact, int ntiles, int parity);
+// Kernel attributes (shared memory size) set outside any stream capture.
+int zgemm_grouped_fp64_prepare(int cfg);
+int zgemm_split_grouped_prepare();
+// Split path: slice the active columns of every active problem (one CTA per
+// column), then the grouped tensor-core product (one CTA per output tile).
+int split_grouped_slice_x(Dev& d, const GroupedProblem* probs, const GroupedStep* steps, int nact,
+                          int ncols, int parity);
+int zgemm_split_grouped(Dev& d, const GroupedProblem* probs, const GroupedStep* steps, int nact,
+                        int ntiles, int parity);
+constexpr int kSplitTileRows = 128;      // rows of H per split tile
+constexpr int kSplitTileRealCols = 64;   // real columns (32 complex) per split tile
+constexpr int kSplitSlices = 7;
+int64_t split_k_padded(int64_t N);
+// Slices of every problem's H: one CTA per row over all problems; row_prob
+// holds the first global row of each problem (P + 1 entries).
+struct GroupedSliceH {
+  const double2* H;
+  long long ldh;
+  void* A;
+  int* E;
+  double* Dg;
+  long long Kp;
+  int n, row0;
+};
+int split_grouped_prepare_h(Dev& d, const GroupedSliceH* probs, int P, int total_rows);
+// One problem of grouped_filter_sorted: the block X (b columns, sorted by
+// ascending degree) is filtered in place with W as the second buffer;
+// start[i] (host, i = 0 .. maxdeg + 1) counts the columns of degree < i.
+// Split path: the slices of H (A, E, Dg) and a slice workspace of bcap >= b
+// columns (Bsl, F), as made by grouped_split_prepare.
+struct GroupedFilterInput {
+  const chase_c64* H = nullptr;
+  int64_t ldh = 0;
+  int n = 0;
+  chase_c64* X = nullptr;
+  int64_t ldx = 0;
+  chase_c64* W = nullptr;
+  int64_t ldw = 0;
+  int b = 0;
+  const int* start = nullptr;
+  int maxdeg = 0;
+  double b_sup = 0, mu1 = 0, mu_nn = 0;
+  void* A = nullptr;
+  int* E = nullptr;
+  double* Dg = nullptr;
+  void* Bsl = nullptr;
+  int* F = nullptr;
+  int bcap = 0;
+};
+struct GroupedFilterTimes {
+  int tile_config = -1, steps = 0, launches = 0;
+  long long matvecs = 0;
+  double flops = 0, t_autotune = 0, t_graph_build = 0, t_steps = 0, t_product = 0;
+};
+// Slices of every problem's H and the slice workspace for bcap[q] columns
+// (one grouped slicing launch); fills the split fields of `in`.
+int grouped_split_prepare(Dev& d, std::vector<GroupedFilterInput>& in, const std::vector<int>& bcap);
+// Alg. 4 on every problem of `in` (problems with b == 0 are skipped), one
+// grouped launch per degree step, all steps in one CUDA graph.  tile:
+// CHASE_TILE_AUTO or a fixed FP64 tile shape.  Synchronises the stream.
+int grouped_filter_sorted(Dev& d, const std::vector<GroupedFilterInput>& in, bool split, int tile,
+                          GroupedFilterTimes* times);
+
+// Column gather / scatter for many problems: one CTA per column.
+struct GroupedPermute {
+  const double2* src;
+  double2* dst;
+  long long lds, ldd;
+  const int* perm;
+  int n, col0;
+};
+int launch_grouped_permute(Dev& d, const GroupedPermute* probs, int P, int total_cols, bool scatter);
+
 // ---- eigh (cuSOLVER, the small projected eigensolve of Alg. 2 line 3) -----
 int eigh_device(Dev& d, chase_c64* G, int64_t ldg, int p, double* w_dev);
 

@@ -208,6 +208,23 @@ __global__ void permute_cols_kernel(const double2* __restrict__ X, long long ldx
     Y[(long long)dst * ldy + i] = X[(long long)src * ldx + i];
 }
 
+// One column of one problem per CTA: problem by binary search over col0.
+__global__ void grouped_permute_kernel(const GroupedPermute* __restrict__ probs, int P, int scatter) {
+  const int g = blockIdx.x;
+  int lo = 0, hi = P;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (probs[mid].col0 <= g) lo = mid; else hi = mid;
+  }
+  const GroupedPermute& pr = probs[lo];
+  const int j = g - pr.col0;
+  const int src = scatter ? j : pr.perm[j];
+  const int dst = scatter ? pr.perm[j] : j;
+  const double2* x = pr.src + static_cast<long long>(src) * pr.lds;
+  double2* y = pr.dst + static_cast<long long>(dst) * pr.ldd;
+  for (int i = threadIdx.x; i < pr.n; i += blockDim.x) y[i] = x[i];
+}
+
 __global__ void __launch_bounds__(kRed) col_norms_kernel(const double2* __restrict__ X, long long ldx,
                                                          long long N, double* __restrict__ out) {
   __shared__ double scratch[33];
@@ -509,6 +526,15 @@ int launch_filter_plan(Dev& d, const int* deg, int b, int max_allowed, int* perm
                        int* info) {
   if (max_allowed > kMaxDeg) max_allowed = kMaxDeg;
   filter_plan_kernel<<<1, 32, 0, d.st>>>(deg, b, max_allowed, perm, start, info, d.err);
+  note_launch();
+  CHASE_CUDA(cudaGetLastError());
+  return CHASE_OK;
+}
+
+int launch_grouped_permute(Dev& d, const GroupedPermute* probs, int P, int total_cols, bool scatter) {
+  if (total_cols <= 0) return CHASE_OK;
+  grouped_permute_kernel<<<static_cast<unsigned>(total_cols), 256, 0, d.st>>>(probs, P,
+                                                                               scatter ? 1 : 0);
   note_launch();
   CHASE_CUDA(cudaGetLastError());
   return CHASE_OK;

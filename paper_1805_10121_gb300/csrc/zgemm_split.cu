@@ -124,13 +124,39 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
         "=r"(r[14]), "=r"(r[15])                                                                     \
       : "r"(taddr))
 
-__global__ void __launch_bounds__(kThreads, 1)
-    zgemm_split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                    const int* __restrict__ Erow, const int* __restrict__ Fcol,
-                    const double* __restrict__ Dg, int M, int kb0, int nkb,
-                    int ncols, int j0, const double2* __restrict__ Xsh, long long ldx,
-                    double2* __restrict__ Y, long long ldy, double alpha, double beta, double shift,
-                    double2* __restrict__ P, long long ldp, int* __restrict__ err) {
+// One output tile of the split product: where its operands are (tensor maps
+// and coordinates) and where its result goes.  Columns are counted in the
+// B map: real column 2c / 2c+1 of the product belong to complex column c,
+// whose exponent is F[c] and whose output column is c + joff.
+struct SplitTile {
+  const CUtensorMap* mapA;
+  const CUtensorMap* mapB;
+  int maps_in_global;  // maps live in global memory: acquire them for the async proxy
+  int arow;            // first row of H (A map row) of the tile
+  int brow;            // first B map row (real product column) of the tile
+  int cend;            // complex columns >= cend are outside the block
+  int joff;            // output / shift column = complex column + joff
+  int kb0, nkb;        // K blocks of this launch
+  int M;               // rows of H
+  const int* E;
+  const int* F;
+  const double* Dg;
+  const double2* X;
+  long long ldx;
+  double2* Y;
+  long long ldy;
+  double alpha, beta, shift;
+  double2* P;  // K-segment partial products (nullptr: fused epilogue)
+  long long ldp;
+};
+
+__device__ __forceinline__ void acquire_tmap(const CUtensorMap* map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(
+                   reinterpret_cast<uint64_t>(map))
+               : "memory");
+}
+
+__device__ __forceinline__ void split_tile_body(const SplitTile& T, int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -145,8 +171,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(chunk_full + 3);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row0 = blockIdx.y * BM;
-  const int colr0 = blockIdx.x * BN;  // first real column (relative to the active block)
+  const int row0 = T.arow;
+  const int colr0 = T.brow;
+  const int nkb = T.nkb;
+  const int kb0 = T.kb0;
+  const int M = T.M;
   const int nchunks = (nkb + CHUNK - 1) / CHUNK;
 
   if (threadIdx.x == 0) {
@@ -172,8 +201,12 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp == 0) {
     if (lane == 0) {  // ---------------- TMA producer
-      prefetch_tmap(&tmA);
-      prefetch_tmap(&tmB);
+      if (T.maps_in_global) {
+        acquire_tmap(T.mapA);
+        acquire_tmap(T.mapB);
+      }
+      prefetch_tmap(T.mapA);
+      prefetch_tmap(T.mapB);
       int issued = 0;
       for (int kb = 0; kb < nkb; ++kb) {
         const int st = kb % NSTAGE;
@@ -182,8 +215,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         mbar_arrive_expect_tx(&full[st], STAGE_BYTES);
-        tma_load_3d(smem_u32(sA + st * STAGE_A), &tmA, (kb0 + kb) * BK, row0, 0, smem_u32(&full[st]));
-        tma_load_3d(smem_u32(sB + st * STAGE_B), &tmB, (kb0 + kb) * BK, colr0, 0, smem_u32(&full[st]));
+        tma_load_3d(smem_u32(sA + st * STAGE_A), T.mapA, (kb0 + kb) * BK, row0, 0, smem_u32(&full[st]));
+        tma_load_3d(smem_u32(sB + st * STAGE_B), T.mapB, (kb0 + kb) * BK, colr0, 0, smem_u32(&full[st]));
         ++issued;
       }
       for (int kb = (issued > NSTAGE ? issued - NSTAGE : 0); kb < issued; ++kb)
@@ -271,7 +304,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (ok) {
       // the last chunk_full covers every MMA, tail levels included
       const int grow = row0 + row;
-      const int er = grow < M ? Erow[grow] : 0;
+      const int er = grow < M ? T.E[grow] : 0;
 #pragma unroll
       for (int c0 = 0; c0 < 32; c0 += 16) {
         double acc[16];
@@ -292,28 +325,28 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (grow < M) {
 #pragma unroll
           for (int j = 0; j < 16; j += 2) {
-            const int cc = (colr0 + hf * 32 + c0 + j) >> 1;  // complex column in the block
-            if (cc >= ncols) continue;
-            const int ex = er + Fcol[cc] - 14;
+            const int cc = (colr0 + hf * 32 + c0 + j) >> 1;  // complex column (B map)
+            if (cc >= T.cend) continue;
+            const int ex = er + T.F[cc] - 14;
             double vr = ldexp(acc[j], ex), vi = ldexp(acc[j + 1], ex);
-            if (P) {  // one K segment: raw product, the combine kernel finishes
-              P[static_cast<long long>(cc) * ldp + grow] = make_double2(vr, vi);
+            if (T.P) {  // one K segment: raw product, the combine kernel finishes
+              T.P[static_cast<long long>(cc) * T.ldp + grow] = make_double2(vr, vi);
               continue;
             }
-            const long long jc = j0 + cc;
-            const double dshift = (Dg ? Dg[grow] : 0.0) - shift;
+            const long long jc = cc + T.joff;
+            const double dshift = (T.Dg ? T.Dg[grow] : 0.0) - T.shift;
             if (dshift != 0.0) {
-              const double2 xv = Xsh[jc * ldx + grow];
+              const double2 xv = T.X[jc * T.ldx + grow];
               vr += dshift * xv.x;
               vi += dshift * xv.y;
             }
-            vr *= alpha;
-            vi *= alpha;
-            double2* yp = Y + jc * ldy + grow;
-            if (beta != 0.0) {
+            vr *= T.alpha;
+            vi *= T.alpha;
+            double2* yp = T.Y + jc * T.ldy + grow;
+            if (T.beta != 0.0) {
               const double2 yv = *yp;
-              vr += beta * yv.x;
-              vi += beta * yv.y;
+              vr += T.beta * yv.x;
+              vi += T.beta * yv.y;
             }
             *yp = make_double2(vr, vi);
           }
@@ -327,6 +360,91 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
+// One problem: grid (column tiles, row tiles), B map over the active block.
+__global__ void __launch_bounds__(kThreads, 1)
+    zgemm_split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                       const int* __restrict__ Erow, const int* __restrict__ Fcol,
+                       const double* __restrict__ Dg, int M, int kb0, int nkb, int ncols, int j0,
+                       const double2* __restrict__ Xsh, long long ldx, double2* __restrict__ Y,
+                       long long ldy, double alpha, double beta, double shift,
+                       double2* __restrict__ P, long long ldp, int* __restrict__ err) {
+  SplitTile T;
+  T.mapA = &tmA;
+  T.mapB = &tmB;
+  T.maps_in_global = 0;
+  T.arow = blockIdx.y * BM;
+  T.brow = blockIdx.x * BN;
+  T.cend = ncols;
+  T.joff = j0;
+  T.kb0 = kb0;
+  T.nkb = nkb;
+  T.M = M;
+  T.E = Erow;
+  T.F = Fcol;
+  T.Dg = Dg;
+  T.X = Xsh;
+  T.ldx = ldx;
+  T.Y = Y;
+  T.ldy = ldy;
+  T.alpha = alpha;
+  T.beta = beta;
+  T.shift = shift;
+  T.P = P;
+  T.ldp = ldp;
+  split_tile_body(T, err);
+}
+
+// Problem of CTA `bid` in a grouped step list: the last entry with
+// key <= bid (keys ascending; entry nact is the sentinel with the total).
+__device__ __forceinline__ int grouped_find(const GroupedStep* __restrict__ steps, int nact, int bid,
+                                            bool by_tile) {
+  int lo = 0, hi = nact;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    const int key = by_tile ? steps[mid].tile0 : steps[mid].col0;
+    if (key <= bid) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Many problems in one launch: one CTA per output tile of every active
+// problem of one degree step.  Within a problem the column tile runs
+// fastest, so CTAs that run together share rows of H in L2.
+__global__ void __launch_bounds__(kThreads, 1)
+    zgemm_split_grouped_kernel(const GroupedProblem* __restrict__ probs,
+                               const GroupedStep* __restrict__ steps, int nact, int parity,
+                               int* __restrict__ err) {
+  const int bid = blockIdx.x;
+  const int e = grouped_find(steps, nact, bid, true);
+  const GroupedStep stp = steps[e];
+  const GroupedProblem& pr = probs[stp.prob];
+  const int local = bid - stp.tile0;
+  const int ncol_tiles = (2 * (pr.b - stp.s) + BN - 1) / BN;
+  SplitTile T;
+  T.mapA = pr.mapA;
+  T.mapB = pr.mapB0;
+  T.maps_in_global = 1;
+  T.arow = (local / ncol_tiles) * BM;
+  T.brow = 2 * stp.s + (local % ncol_tiles) * BN;
+  T.cend = pr.b;
+  T.joff = 0;
+  T.kb0 = 0;
+  T.nkb = static_cast<int>(pr.Kp / BK);
+  T.M = pr.n;
+  T.E = pr.E;
+  T.F = pr.F;
+  T.Dg = pr.Dg;
+  T.X = parity ? pr.buf1 : pr.buf0;
+  T.ldx = parity ? pr.ld1 : pr.ld0;
+  T.Y = parity ? pr.buf0 : pr.buf1;
+  T.ldy = parity ? pr.ld0 : pr.ld1;
+  T.alpha = stp.alpha;
+  T.beta = stp.beta;
+  T.shift = stp.shift;
+  T.P = nullptr;
+  T.ldp = 0;
+  split_tile_body(T, err);
+}
 
 // ---------------------------------------------------------------------------
 // Slicing.  For |y| < 1: a = trunc(128 y), y <- 128 y - a, S times; every step
@@ -367,13 +485,10 @@ __device__ double block_max(double v, double* scratch) {
 
 // Row r of Ht from column r of the Hermitian H: Re H[r, k] = Re H[k, r],
 // Im H[r, k] = -Im H[k, r].  A: [S][N][Kp] bf16, E: [N].
-__global__ void __launch_bounds__(256) slice_h_kernel(const double2* __restrict__ H, long long ldh,
-                                                      int N, __nv_bfloat16* __restrict__ A,
-                                                      long long Kp, int* __restrict__ E,
-                                                      double* __restrict__ Dg) {
-  __shared__ double scratch[33];
-  const int r = blockIdx.x;
-  const double2* col = H + static_cast<long long>(r) * ldh;
+__device__ __forceinline__ void slice_h_row(const double2* __restrict__ col, int r, int N,
+                                            __nv_bfloat16* __restrict__ A, long long Kp,
+                                            int* __restrict__ E, double* __restrict__ Dg,
+                                            double* scratch) {
   double m = 0.0;
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
     if (k == r) continue;  // the diagonal is applied in FP64 by the epilogue
@@ -401,15 +516,38 @@ __global__ void __launch_bounds__(256) slice_h_kernel(const double2* __restrict_
   }
 }
 
-// Rows 2c and 2c+1 of Xt^T for the columns c of X in [j0, j0 + ncols):
-// B: [S][rows_cap][Kp] bf16, F: [ncols].
-__global__ void __launch_bounds__(256) slice_x_kernel(const double2* __restrict__ X, long long ldx,
-                                                      int N, int j0, __nv_bfloat16* __restrict__ B,
-                                                      long long Kp, long long rows_cap,
-                                                      int* __restrict__ F) {
+__global__ void __launch_bounds__(256) slice_h_kernel(const double2* __restrict__ H, long long ldh,
+                                                      int N, __nv_bfloat16* __restrict__ A,
+                                                      long long Kp, int* __restrict__ E,
+                                                      double* __restrict__ Dg) {
   __shared__ double scratch[33];
-  const int c = blockIdx.x;
-  const double2* col = X + static_cast<long long>(j0 + c) * ldx;
+  const int r = blockIdx.x;
+  slice_h_row(H + static_cast<long long>(r) * ldh, r, N, A, Kp, E, Dg, scratch);
+}
+
+// All problems' H at once: CTA g slices global row g (problem by binary
+// search over the first rows).
+__global__ void __launch_bounds__(256) slice_h_grouped_kernel(const GroupedSliceH* __restrict__ probs,
+                                                              int P) {
+  __shared__ double scratch[33];
+  const int g = blockIdx.x;
+  int lo = 0, hi = P;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (probs[mid].row0 <= g) lo = mid; else hi = mid;
+  }
+  const GroupedSliceH& pr = probs[lo];
+  const int r = g - pr.row0;
+  slice_h_row(pr.H + static_cast<long long>(r) * pr.ldh, r, pr.n,
+              static_cast<__nv_bfloat16*>(pr.A), pr.Kp, pr.E, pr.Dg, scratch);
+}
+
+// Rows 2c and 2c+1 of Xt^T from column c of X (exponent to *Fc):
+// r0 points at row 2c of slice plane 0 of B, planes are `plane` apart.
+__device__ __forceinline__ void slice_x_col(const double2* __restrict__ col, int N,
+                                            __nv_bfloat16* __restrict__ r0, long long Kp,
+                                            long long plane, int* __restrict__ Fc,
+                                            double* scratch) {
   double m = 0.0;
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
     const double2 v = col[k];
@@ -417,9 +555,7 @@ __global__ void __launch_bounds__(256) slice_x_kernel(const double2* __restrict_
   }
   m = block_max(m, scratch);
   const int fc = exponent_above(m);
-  if (threadIdx.x == 0) F[c] = fc;
-  const long long plane = rows_cap * Kp;
-  __nv_bfloat16* r0 = B + static_cast<long long>(2 * c) * Kp;
+  if (threadIdx.x == 0) *Fc = fc;
   __nv_bfloat16* r1 = r0 + Kp;
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
     const double2 v = col[k];
@@ -434,6 +570,35 @@ __global__ void __launch_bounds__(256) slice_x_kernel(const double2* __restrict_
       r1[s * plane + N + k] = __float2bfloat16_rn(sr[s]);
     }
   }
+}
+
+// Columns c of X in [j0, j0 + ncols) to rows 2c, 2c+1 (c relative to j0):
+// B: [S][rows_cap][Kp] bf16, F: [ncols].
+__global__ void __launch_bounds__(256) slice_x_kernel(const double2* __restrict__ X, long long ldx,
+                                                      int N, int j0, __nv_bfloat16* __restrict__ B,
+                                                      long long Kp, long long rows_cap,
+                                                      int* __restrict__ F) {
+  __shared__ double scratch[33];
+  const int c = blockIdx.x;
+  slice_x_col(X + static_cast<long long>(j0 + c) * ldx, N, B + static_cast<long long>(2 * c) * Kp, Kp,
+              rows_cap * Kp, F + c, scratch);
+}
+
+// Grouped: the active columns [s, b) of every active problem of a degree
+// step, column c to rows 2c, 2c+1 of the problem's slice planes.
+__global__ void __launch_bounds__(256) slice_x_grouped_kernel(const GroupedProblem* __restrict__ probs,
+                                                              const GroupedStep* __restrict__ steps,
+                                                              int nact, int parity) {
+  __shared__ double scratch[33];
+  const int e = grouped_find(steps, nact, blockIdx.x, false);
+  const GroupedStep stp = steps[e];
+  const GroupedProblem& pr = probs[stp.prob];
+  const int c = stp.s + (blockIdx.x - stp.col0);
+  const double2* X = parity ? pr.buf1 : pr.buf0;
+  const long long ldx = parity ? pr.ld1 : pr.ld0;
+  __nv_bfloat16* B = static_cast<__nv_bfloat16*>(pr.Bsl);
+  slice_x_col(X + static_cast<long long>(c) * ldx, pr.n, B + static_cast<long long>(2 * c) * pr.Kp,
+              pr.Kp, 2LL * pr.bcap * pr.Kp, pr.F + c, scratch);
 }
 
 // Sum of the K segments' products plus the FP64 epilogue:
@@ -476,7 +641,12 @@ __global__ void split_combine_kernel(const double2* __restrict__ P, int nseg, lo
 // ---------------------------------------------------------------------------
 namespace {
 int64_t k_padded(int64_t N) { return ((2 * N + split::BK - 1) / split::BK) * split::BK; }
+static_assert(kSplitTileRows == split::BM && kSplitTileRealCols == split::BN &&
+                  kSplitSlices == split::S,
+              "grouped tile constants");
 }  // namespace
+
+int64_t split_k_padded(int64_t N) { return k_padded(N); }
 
 int split_prepare_h(Dev& d, const chase_c64* H, int64_t N, int64_t ldh, SplitH& out) {
   out.N = N;
@@ -585,6 +755,45 @@ int zgemm_split(Dev& d, const SplitH& h, SplitX& x, const chase_c64* X, int64_t 
   split::split_combine_kernel<<<blocks, 256, 0, d.st>>>(
       P, nseg, pstride, N, h.Dg, reinterpret_cast<const double2*>(X), ldx, j0, ncols,
       static_cast<int>(N), reinterpret_cast<double2*>(C), ldc, alpha, beta, shift);
+  note_launch();
+  CHASE_CUDA(cudaGetLastError());
+  return CHASE_OK;
+}
+
+int split_grouped_prepare_h(Dev& d, const GroupedSliceH* probs, int P, int total_rows) {
+  if (total_rows <= 0) return CHASE_OK;
+  split::slice_h_grouped_kernel<<<static_cast<unsigned>(total_rows), 256, 0, d.st>>>(probs, P);
+  note_launch();
+  CHASE_CUDA(cudaGetLastError());
+  return CHASE_OK;
+}
+
+int split_grouped_slice_x(Dev& d, const GroupedProblem* probs, const GroupedStep* steps, int nact,
+                          int ncols, int parity) {
+  if (ncols <= 0) return CHASE_OK;
+  split::slice_x_grouped_kernel<<<static_cast<unsigned>(ncols), 256, 0, d.st>>>(probs, steps, nact,
+                                                                                 parity);
+  note_launch();
+  CHASE_CUDA(cudaGetLastError());
+  return CHASE_OK;
+}
+
+int zgemm_split_grouped_prepare() {
+  static bool attr_done = false;
+  if (!attr_done) {
+    CHASE_CUDA(cudaFuncSetAttribute(split::zgemm_split_grouped_kernel,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, split::SMEM));
+    attr_done = true;
+  }
+  return CHASE_OK;
+}
+
+int zgemm_split_grouped(Dev& d, const GroupedProblem* probs, const GroupedStep* steps, int nact,
+                        int ntiles, int parity) {
+  if (ntiles <= 0) return CHASE_OK;
+  CHASE_TRY(zgemm_split_grouped_prepare());
+  split::zgemm_split_grouped_kernel<<<static_cast<unsigned>(ntiles), split::kThreads, split::SMEM,
+                                      d.st>>>(probs, steps, nact, parity, d.err);
   note_launch();
   CHASE_CUDA(cudaGetLastError());
   return CHASE_OK;

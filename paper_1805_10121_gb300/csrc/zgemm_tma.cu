@@ -57,12 +57,28 @@ struct Cfg {
   static_assert(2 * BM <= 256 && 2 * BK <= 256 && BN <= 256, "TMA box limit");
 };
 
+// One output tile: its operand maps and coordinates and its epilogue.
+struct Fp64Tile {
+  const CUtensorMap* mapA;
+  const CUtensorMap* mapB;
+  int maps_in_global;  // maps live in global memory: acquire them for the async proxy
+  int row0, col0;      // first row of A / first (absolute) column of B of the tile
+  int M, K, j1;        // rows of A, K extent, columns >= j1 are outside the block
+  const double2* Bsh;  // B again, for the shift term
+  long long ldb;
+  double2* Cout;
+  long long ldc;
+  double alpha, beta, shift;
+};
+
+__device__ __forceinline__ void acquire_tmap_global(const CUtensorMap* map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(
+                   reinterpret_cast<uint64_t>(map))
+               : "memory");
+}
+
 template <class C>
-__global__ void __launch_bounds__(C::kThreads)
-    zgemm_tma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                     int M, int K, int j0, int j1, const double2* __restrict__ Bsh, long long ldb,
-                     double2* __restrict__ Cout, long long ldc, double alpha, double beta,
-                     double shift, int* __restrict__ err) {
+__device__ __forceinline__ void zgemm_tile_body(const Fp64Tile& T, int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
@@ -73,9 +89,10 @@ __global__ void __launch_bounds__(C::kThreads)
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int row0 = blockIdx.x * C::BM;
-  const int col0 = j0 + blockIdx.y * C::BN;
-  const int nk = (K + C::BK - 1) / C::BK;
+  const int row0 = T.row0;
+  const int col0 = T.col0;
+  const int M = T.M;
+  const int nk = (T.K + C::BK - 1) / C::BK;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
@@ -89,8 +106,12 @@ __global__ void __launch_bounds__(C::kThreads)
   if (warp == C::kConsumerWarps) {
     // ---------------- producer: one thread issues every TMA copy ----------
     if (lane == 0) {
-      prefetch_tmap(&tmA);
-      prefetch_tmap(&tmB);
+      if (T.maps_in_global) {
+        acquire_tmap_global(T.mapA);
+        acquire_tmap_global(T.mapB);
+      }
+      prefetch_tmap(T.mapA);
+      prefetch_tmap(T.mapB);
       int issued = 0;
       for (int kt = 0; kt < nk; ++kt) {
         const int s = kt % C::STAGES;
@@ -101,8 +122,8 @@ __global__ void __launch_bounds__(C::kThreads)
           }
         }
         mbar_arrive_expect_tx(&full[s], C::STAGE_BYTES);
-        tma_load_2d(sA + s * C::BK * C::BM, &tmA, 2 * row0, kt * C::BK, &full[s]);
-        tma_load_2d(sB + s * C::BN * C::BK, &tmB, 2 * kt * C::BK, col0, &full[s]);
+        tma_load_2d(sA + s * C::BK * C::BM, T.mapA, 2 * row0, kt * C::BK, &full[s]);
+        tma_load_2d(sB + s * C::BN * C::BK, T.mapB, 2 * kt * C::BK, col0, &full[s]);
         ++issued;
       }
       // Drain: no copy of this CTA may still be landing when it exits.
@@ -177,26 +198,87 @@ __global__ void __launch_bounds__(C::kThreads)
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int c = col0 + wn * C::WTN + ni * 8 + 2 * t + h;
-        if (c >= j1) continue;
+        if (c >= T.j1) continue;
         double vr = t1[mi][ni][h] - t2[mi][ni][h];
         double vi = t3[mi][ni][h] - t1[mi][ni][h] - t2[mi][ni][h];
-        if (shift != 0.0) {
-          const double2 bv = Bsh[static_cast<long long>(c) * ldb + r];
-          vr -= shift * bv.x;
-          vi -= shift * bv.y;
+        if (T.shift != 0.0) {
+          const double2 bv = T.Bsh[static_cast<long long>(c) * T.ldb + r];
+          vr -= T.shift * bv.x;
+          vi -= T.shift * bv.y;
         }
-        vr *= alpha;
-        vi *= alpha;
-        double2* cp = Cout + static_cast<long long>(c) * ldc + r;
-        if (beta != 0.0) {
+        vr *= T.alpha;
+        vi *= T.alpha;
+        double2* cp = T.Cout + static_cast<long long>(c) * T.ldc + r;
+        if (T.beta != 0.0) {
           const double2 cv = *cp;
-          vr += beta * cv.x;
-          vi += beta * cv.y;
+          vr += T.beta * cv.x;
+          vi += T.beta * cv.y;
         }
         *cp = make_double2(vr, vi);
       }
     }
   }
+}
+
+template <class C>
+__global__ void __launch_bounds__(C::kThreads)
+    zgemm_tma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                     int M, int K, int j0, int j1, const double2* __restrict__ Bsh, long long ldb,
+                     double2* __restrict__ Cout, long long ldc, double alpha, double beta,
+                     double shift, int* __restrict__ err) {
+  Fp64Tile T;
+  T.mapA = &tmA;
+  T.mapB = &tmB;
+  T.maps_in_global = 0;
+  T.row0 = blockIdx.x * C::BM;
+  T.col0 = j0 + blockIdx.y * C::BN;
+  T.M = M;
+  T.K = K;
+  T.j1 = j1;
+  T.Bsh = Bsh;
+  T.ldb = ldb;
+  T.Cout = Cout;
+  T.ldc = ldc;
+  T.alpha = alpha;
+  T.beta = beta;
+  T.shift = shift;
+  zgemm_tile_body<C>(T, err);
+}
+
+// Grouped: one CTA per output tile of every active problem of one degree
+// step of the filter; X = parity ? buf1 : buf0, Y = the other buffer.
+template <class C>
+__global__ void __launch_bounds__(C::kThreads)
+    zgemm_grouped_kernel(const GroupedProblem* __restrict__ probs,
+                         const GroupedStep* __restrict__ steps, int nact, int parity,
+                         int* __restrict__ err) {
+  const int bid = blockIdx.x;
+  int lo = 0, hi = nact;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (steps[mid].tile0 <= bid) lo = mid; else hi = mid;
+  }
+  const GroupedStep stp = steps[lo];
+  const GroupedProblem& pr = probs[stp.prob];
+  const int local = bid - stp.tile0;
+  const int ncol_tiles = (pr.b - stp.s + C::BN - 1) / C::BN;
+  Fp64Tile T;
+  T.mapA = pr.mapA;
+  T.mapB = parity ? pr.mapB1 : pr.mapB0;
+  T.maps_in_global = 1;
+  T.row0 = (local / ncol_tiles) * C::BM;
+  T.col0 = stp.s + (local % ncol_tiles) * C::BN;
+  T.M = pr.n;
+  T.K = pr.n;
+  T.j1 = pr.b;
+  T.Bsh = parity ? pr.buf1 : pr.buf0;
+  T.ldb = parity ? pr.ld1 : pr.ld0;
+  T.Cout = parity ? pr.buf0 : pr.buf1;
+  T.ldc = parity ? pr.ld0 : pr.ld1;
+  T.alpha = stp.alpha;
+  T.beta = stp.beta;
+  T.shift = stp.shift;
+  zgemm_tile_body<C>(T, err);
 }
 
 template <class C>
@@ -226,8 +308,61 @@ int launch_cfg(Dev& d, int64_t M, int64_t K, const chase_c64* A, int64_t lda, co
 using CfgWide = Cfg<64, 32, 16, 2, 2>;    // 64 x 32 tile, warps 2 x 2 (32 x 16 each)
 using CfgMid = Cfg<64, 16, 16, 2, 4>;     // 64 x 16 tile, warps 4 x 1 (16 x 16 each)
 using CfgNarrow = Cfg<64, 8, 16, 2, 4>;   // 64 x 8 tile, warps 4 x 1 (16 x 8 each)
+using CfgTall = Cfg<128, 16, 16, 2, 4>;   // 128 x 16 tile, warps 4 x 1 (32 x 16 each)
+
+template <class C>
+int grouped_attr() {
+  static bool attr_done = false;  // per instantiation
+  if (!attr_done) {
+    CHASE_CUDA(cudaFuncSetAttribute(zgemm_grouped_kernel<C>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    attr_done = true;
+  }
+  return CHASE_OK;
+}
+
+template <class C>
+int launch_grouped(Dev& d, const GroupedProblem* probs, const GroupedStep* steps, int nact,
+                   int ntiles, int parity) {
+  CHASE_TRY(grouped_attr<C>());
+  zgemm_grouped_kernel<C><<<static_cast<unsigned>(ntiles), C::kThreads, C::SMEM, d.st>>>(
+      probs, steps, nact, parity, d.err);
+  note_launch();
+  CHASE_CUDA(cudaGetLastError());
+  return CHASE_OK;
+}
 
 }  // namespace
+
+// Candidate tile shapes of the grouped FP64 filter, in autotuning order.
+void grouped_fp64_tile(int cfg, int* bm, int* bn) {
+  switch (cfg) {
+    case 0: *bm = CfgMid::BM; *bn = CfgMid::BN; break;
+    case 1: *bm = CfgWide::BM; *bn = CfgWide::BN; break;
+    case 2: *bm = CfgTall::BM; *bn = CfgTall::BN; break;
+    default: *bm = CfgNarrow::BM; *bn = CfgNarrow::BN; break;
+  }
+}
+
+int zgemm_grouped_fp64_prepare(int cfg) {
+  switch (cfg) {
+    case 0: return grouped_attr<CfgMid>();
+    case 1: return grouped_attr<CfgWide>();
+    case 2: return grouped_attr<CfgTall>();
+    default: return grouped_attr<CfgNarrow>();
+  }
+}
+
+int zgemm_grouped_fp64(Dev& d, int cfg, const GroupedProblem* probs, const GroupedStep* steps,
+                       int nact, int ntiles, int parity) {
+  if (ntiles <= 0) return CHASE_OK;
+  switch (cfg) {
+    case 0: return launch_grouped<CfgMid>(d, probs, steps, nact, ntiles, parity);
+    case 1: return launch_grouped<CfgWide>(d, probs, steps, nact, ntiles, parity);
+    case 2: return launch_grouped<CfgTall>(d, probs, steps, nact, ntiles, parity);
+    default: return launch_grouped<CfgNarrow>(d, probs, steps, nact, ntiles, parity);
+  }
+}
 
 int zgemm(Dev& d, int64_t M, int64_t K, const chase_c64* A, int64_t lda, const chase_c64* B,
           int64_t ldb, int64_t ncols_b, chase_c64* Cm, int64_t ldc, int j0, int j1, double alpha,

@@ -28,6 +28,7 @@ __all__ = [
     "hermitian_from",
     "hermitian_dft",
     "hermitian_noise",
+    "batched_shapes",
 ]
 
 
@@ -142,3 +143,12 @@ def hermitian_noise(n: int, seed: int, device="cpu") -> torch.Tensor:
     z = torch.complex(re, im).mul_(1.0 / math.sqrt(2.0))
     e = (z + z.conj().t()) * (1.0 / (2.0 * math.sqrt(2.0 * n)))
     return e.t().contiguous().t()
+
+
+def batched_shapes(P: int, seed: int, n_lo: int = 256, n_hi: int = 2048,
+                   nev_frac: float = 0.05, nex_frac: float = 0.02):
+    """Sizes of a batch of independent problems: N uniform in [n_lo, n_hi],
+    nev = ceil(nev_frac N), nex = ceil(nex_frac N); a list of (N, nev, nex)."""
+    g = generator(seed, "cpu")
+    ns = torch.randint(n_lo, n_hi + 1, (P,), generator=g).tolist()
+    return [(int(n), int(math.ceil(nev_frac * n)), int(math.ceil(nex_frac * n))) for n in ns]

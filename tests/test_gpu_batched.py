@@ -1,0 +1,205 @@
+"""GPU parity of the grouped (batched) filter: every problem of a ragged
+batch must match the oracle's Alg. 4 on that problem alone, with the same
+tolerances as the single-problem filter (FP64: 1e-11 per column; split-BF16:
+1e-9 per column, from its 2^-49 per-product error summed over at most 36
+products)."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1805_10121_gb300 import chase, synth
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+TOL = {chase.CHASE_FP64: 1e-11, chase.CHASE_SPLIT_BF16: 1e-9}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1805_10121_gb300 import build
+    build.build()
+    chase.lib()
+
+
+def oracle_filter_any_order(H, V, deg, b_sup, mu1, mu_nn):
+    order = np.argsort(deg, kind="stable")
+    out = np.empty_like(V)
+    out[:, order] = oracle.cheb_filter(H, V[:, order], np.asarray(deg)[order], b_sup, mu1, mu_nn)
+    return out
+
+
+def col_rel_err(a, b):
+    return np.max(np.linalg.norm(a - b, axis=0) / np.linalg.norm(b, axis=0))
+
+
+def make_batch(shapes, seed, max_deg=36):
+    """shapes: list of (n, b).  Uniform spectra in [-1, 1] (FFT-built H),
+    Gaussian blocks, random even degrees, bounds from the known spectrum."""
+    Hs, Vs, degs, bs, m1, mn = [], [], [], [], [], []
+    rng = np.random.default_rng(seed)
+    for k, (n, b) in enumerate(shapes):
+        lam = synth.spectrum_uniform(max(n, 1), seed + 10 * k, device=DEV)
+        H = synth.hermitian_dft(lam, seed + 10 * k + 1) if n > 0 else \
+            torch.zeros(0, 0, dtype=torch.complex128, device=DEV)
+        V = synth.gaussian_block(n, b, seed + 10 * k + 2, device=DEV)
+        Hs.append(H)
+        Vs.append(V)
+        degs.append((2 * rng.integers(1, max_deg // 2 + 1, size=b)).astype(np.int32))
+        l = lam.cpu().numpy()
+        bs.append(1.01)
+        m1.append(float(l[0]))
+        mn.append(float(l[min(len(l) - 1, max(1, b))]) if n > 1 else 0.0)
+    return Hs, Vs, degs, bs, m1, mn
+
+
+@pytest.mark.parametrize("precision", [chase.CHASE_FP64, chase.CHASE_SPLIT_BF16])
+def test_batched_filter_ragged_matches_oracle(precision):
+    shapes = [(300, 37), (129, 1), (1000, 33), (64, 64), (517, 70), (257, 8), (700, 130)]
+    Hs, Vs, degs, bs, m1, mn = make_batch(shapes, 500 + precision)
+    V0 = [v.clone() for v in Vs]
+    st = chase.chase_filter_batched(Hs, Vs, degs, bs, m1, mn, precision=precision)
+    assert st["problems"] == len(shapes)
+    assert st["steps"] == max(int(d.max()) for d in degs)
+    for k in range(len(shapes)):
+        ref = oracle_filter_any_order(Hs[k].cpu().numpy(), V0[k].cpu().numpy(), degs[k], bs[k],
+                                      m1[k], mn[k])
+        assert col_rel_err(Vs[k].cpu().numpy(), ref) <= TOL[precision], f"problem {k}"
+
+
+@pytest.mark.parametrize("tile", [0, 1, 2, 3])
+def test_batched_filter_every_fp64_tile_shape(tile):
+    shapes = [(200, 40), (333, 17), (96, 9)]
+    Hs, Vs, degs, bs, m1, mn = make_batch(shapes, 600 + tile, max_deg=12)
+    V0 = [v.clone() for v in Vs]
+    st = chase.chase_filter_batched(Hs, Vs, degs, bs, m1, mn, tile=tile)
+    assert st["tile_config"] == tile
+    for k in range(len(shapes)):
+        ref = oracle_filter_any_order(Hs[k].cpu().numpy(), V0[k].cpu().numpy(), degs[k], bs[k],
+                                      m1[k], mn[k])
+        assert col_rel_err(Vs[k].cpu().numpy(), ref) <= TOL[chase.CHASE_FP64]
+
+
+def test_batched_filter_matches_single_problem_calls():
+    # the grouped launch filters each problem exactly as chase_filter does
+    shapes = [(400, 24), (150, 5), (800, 48)]
+    for precision in (chase.CHASE_FP64, chase.CHASE_SPLIT_BF16):
+        Hs, Vs, degs, bs, m1, mn = make_batch(shapes, 700 + precision, max_deg=20)
+        singles = [v.clone() for v in Vs]
+        chase.chase_filter_batched(Hs, Vs, degs, bs, m1, mn, precision=precision)
+        for k in range(len(shapes)):
+            chase.chase_filter(Hs[k], singles[k], degs[k], bs[k], m1[k], mn[k],
+                               precision=precision)
+            d = (Vs[k] - singles[k]).abs().max().item() / singles[k].abs().max().item()
+            assert d <= TOL[precision]
+
+
+def test_batched_filter_skips_empty_problems_and_autotunes():
+    shapes = [(0, 0), (200, 0), (250, 12), (1, 1)]
+    Hs, Vs, degs, bs, m1, mn = make_batch(shapes, 800, max_deg=8)
+    m1[3], mn[3] = -1.0, -0.5  # N = 1: any ordered bounds
+    V0 = [v.clone() for v in Vs]
+    st = chase.chase_filter_batched(Hs, Vs, degs, bs, m1, mn)
+    assert st["problems"] == 2
+    assert 0 <= st["tile_config"] < 4
+    for k in (2, 3):
+        ref = oracle_filter_any_order(Hs[k].cpu().numpy(), V0[k].cpu().numpy(), degs[k], bs[k],
+                                      m1[k], mn[k])
+        assert col_rel_err(Vs[k].cpu().numpy(), ref) <= TOL[chase.CHASE_FP64]
+    assert chase.chase_filter_batched([], [], [], [], [], [])["problems"] == 0
+
+
+def test_batched_filter_rejects_bad_input():
+    Hs, Vs, degs, bs, m1, mn = make_batch([(100, 4), (120, 3)], 900, max_deg=6)
+    bad = [degs[0], np.array([2, 3, 4], dtype=np.int32)]
+    with pytest.raises(chase.ChaseError) as e:
+        chase.chase_filter_batched(Hs, Vs, bad, bs, m1, mn)
+    assert e.value.status == chase.CHASE_INVALID_ARG
+    with pytest.raises(chase.ChaseError) as e:
+        chase.chase_filter_batched(Hs, Vs, degs, bs, [m1[0], 5.0], mn)
+    assert e.value.status == chase.CHASE_INVALID_ARG
+    with pytest.raises(chase.ChaseError) as e:
+        chase.chase_filter_batched([Hs[0].cpu()], [Vs[0].cpu()], degs[:1], bs[:1], m1[:1], mn[:1])
+    assert e.value.status == chase.CHASE_INVALID_ARG
+
+
+@pytest.mark.parametrize("precision", [chase.CHASE_FP64, chase.CHASE_SPLIT_BF16])
+def test_batched_filter_full_size_sampled_problems(precision):
+    # 512 problems, N uniform in [256, 2048], b = nev + nex = 7% of N, degrees
+    # up to 36; the smallest, the largest and one middle problem are checked
+    # against the oracle on sampled columns
+    shapes = [(n, nev + nex) for n, nev, nex in synth.batched_shapes(512, 1234)]
+    Hs, Vs, degs, bs, m1, mn = make_batch(shapes, 1300)
+    order = np.argsort([n for n, _ in shapes])
+    pick = [int(order[0]), int(order[len(order) // 2]), int(order[-1])]
+    V0 = {k: Vs[k].clone() for k in pick}
+    st = chase.chase_filter_batched(Hs, Vs, degs, bs, m1, mn, precision=precision)
+    assert st["problems"] == 512
+    for k in pick:
+        cols = sorted({0, shapes[k][1] // 2, shapes[k][1] - 1})
+        ref = oracle_filter_any_order(Hs[k].cpu().numpy(), V0[k][:, cols].cpu().numpy(),
+                                      degs[k][cols], bs[k], m1[k], mn[k])
+        assert col_rel_err(Vs[k][:, cols].cpu().numpy(), ref) <= TOL[precision]
+    del Hs, Vs
+    torch.cuda.empty_cache()
+
+
+def _solve_inputs(shapes, seed):
+    """Known spectra: uniform in [-1, 1], FFT-built H; random start blocks."""
+    Hs, lams, Vs, Ss = [], [], [], []
+    for k, (n, nev, nex) in enumerate(shapes):
+        lam = synth.spectrum_uniform(n, seed + 10 * k, device=DEV)
+        Hs.append(synth.hermitian_dft(lam, seed + 10 * k + 1))
+        lams.append(lam.cpu().numpy())
+        Vs.append(synth.gaussian_block(n, nev + nex, seed + 10 * k + 2, device=DEV))
+        Ss.append(synth.gaussian_block(n, 5, seed + 10 * k + 3, device=DEV))
+    return Hs, lams, Vs, Ss
+
+
+@pytest.mark.parametrize("precision", [chase.CHASE_FP64, chase.CHASE_SPLIT_BF16])
+def test_batched_solve_matches_single_solves(precision):
+    shapes = [(300, 15, 6), (517, 26, 11), (129, 7, 3), (1000, 50, 20), (64, 4, 2)]
+    tol = 1e-10
+    Hs, lams, Vs, Ss = _solve_inputs(shapes, 1500 + precision)
+    singles = [v.clone() for v in Vs]
+    o = chase.chase_opts_default(precision=precision)
+    st, sts, ritz, res, stats, bst = chase.chase_solve_batched(
+        Hs, [s[1] for s in shapes], [s[2] for s in shapes], tol, Vs, Ss, opts=o)
+    assert st == chase.CHASE_OK and all(s == chase.CHASE_OK for s in sts)
+    assert bst["problems"] == len(shapes) and bst["matvecs"] > 0
+    for k, (n, nev, nex) in enumerate(shapes):
+        hn = float(np.abs(lams[k]).max())
+        assert np.max(np.abs(ritz[k][:nev] - lams[k][:nev])) <= 1e-10 * hn
+        assert np.all(res[k][:nev] <= tol * hn)
+        V = Vs[k].cpu().numpy()
+        assert np.linalg.norm(V.conj().T @ V - np.eye(nev + nex)) < 1e-12
+        r = oracle.residuals(Hs[k].cpu().numpy(), V[:, :nev], ritz[k][:nev])
+        assert np.all(r <= tol * hn * 1.05)
+        # the same problem through chase_solve
+        s1, r1, _, st1 = chase.chase_solve(Hs[k], nev, nex, tol, singles[k], Ss[k], opts=o)
+        assert s1 == chase.CHASE_OK
+        assert np.max(np.abs(r1[:nev] - ritz[k][:nev])) <= 1e-10 * hn
+        if precision == chase.CHASE_FP64:
+            # grouped FP64 products accumulate every entry in the same order
+            assert stats[k]["iterations"] == st1["iterations"]
+            assert stats[k]["filter_matvecs"] == st1["filter_matvecs"]
+
+
+def test_batched_solve_config_shapes():
+    # 32 problems drawn from the batch law: N uniform in [256, 2048],
+    # nev = 5% N, nex = 2% N; split-BF16 filter, FP64 everything else
+    shapes = synth.batched_shapes(32, 77)
+    tol = 1e-10
+    Hs, lams, Vs, Ss = _solve_inputs(shapes, 1700)
+    o = chase.chase_opts_default(precision=chase.CHASE_SPLIT_BF16)
+    st, sts, ritz, res, stats, bst = chase.chase_solve_batched(
+        Hs, [s[1] for s in shapes], [s[2] for s in shapes], tol, Vs, Ss, opts=o)
+    assert st == chase.CHASE_OK
+    for k, (n, nev, nex) in enumerate(shapes):
+        hn = float(np.abs(lams[k]).max())
+        assert np.max(np.abs(ritz[k][:nev] - lams[k][:nev])) <= 1e-10 * hn, k
+        assert np.all(res[k][:nev] <= tol * hn), k
+    del Hs, Vs
+    torch.cuda.empty_cache()
