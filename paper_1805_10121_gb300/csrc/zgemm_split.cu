@@ -115,6 +115,12 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
         "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])                                           \
       : "r"(taddr))
 
+#define TMEM_LD8(taddr, r)                                                                           \
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"          \
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), \
+                 "=r"(r[7])                                                                          \
+               : "r"(taddr))
+
 #define TMEM_LD16(taddr, r)                                                                          \
   asm volatile(                                                                                      \
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}," \
@@ -123,6 +129,11 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
         "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),      \
         "=r"(r[14]), "=r"(r[15])                                                                     \
       : "r"(taddr))
+
+// 2^e as a double from its exponent bits, for -1022 <= e <= 1023.
+__device__ __forceinline__ double pow2_normal(int e) {
+  return __longlong_as_double(static_cast<long long>(e + 1023) << 52);
+}
 
 // One output tile of the split product: where its operands are (tensor maps
 // and coordinates) and where its result goes.  Columns are counted in the
@@ -302,53 +313,70 @@ __device__ __forceinline__ void split_tile_body(const SplitTile& T, int* __restr
       if (lane == 0) mbar_arrive(chunk_empty);
     }
     if (ok) {
-      // the last chunk_full covers every MMA, tail levels included
+      // The last chunk_full covers every MMA, tail levels included.  With
+      // S = 2^14 L0 + 2^7 L1 + L2 (exact in int64) and the tail
+      // T = L3 + 2^-7 L4 + 2^-14 L5 + 2^-21 L6 (FP32, Horner), an entry is
+      // 2^(E_r + F_c - 28) (S + 2^-7 T); the FP64 work per entry is one add,
+      // one scale and the two fused multiply-adds of the recurrence (the
+      // FP64 pipe is narrow on this GPU, so the epilogue keeps it short).
       const int grow = row0 + row;
-      const int er = grow < M ? T.E[grow] : 0;
+      const bool in_rows = grow < M;
+      const int er = in_rows ? T.E[grow] : 0;
+      const bool raw = T.P != nullptr;  // one K segment: the combine kernel finishes
+      const double alpha = raw ? 1.0 : T.alpha;
+      const double adsh = raw ? 0.0 : T.alpha * ((T.Dg && in_rows ? T.Dg[grow] : 0.0) - T.shift);
 #pragma unroll
-      for (int c0 = 0; c0 < 32; c0 += 16) {
-        double acc[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j)
-          acc[j] = static_cast<double>(sums[0][c0 + j]) +
-                   ldexp(static_cast<double>(sums[1][c0 + j]), -7) +
-                   ldexp(static_cast<double>(sums[2][c0 + j]), -14);
-#pragma unroll 1
-        for (int d = NEXACT; d < S; ++d) {
-          uint32_t r[16];
-          TMEM_LD16(tbase + d * BN + c0, r);
+      for (int c0 = 0; c0 < 32; c0 += 8) {
+        float t[8];
+        {
+          uint32_t r[8];
+          TMEM_LD8(tbase + (S - 1) * BN + c0, r);
           asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-          const double f = ldexp(1.0, -7 * d);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) acc[j] += f * static_cast<double>(__uint_as_float(r[j]));
+          for (int j = 0; j < 8; ++j) t[j] = __uint_as_float(r[j]);
         }
-        if (grow < M) {
+#pragma unroll 1
+        for (int d = S - 2; d >= NEXACT; --d) {
+          uint32_t r[8];
+          TMEM_LD8(tbase + d * BN + c0, r);
+          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-          for (int j = 0; j < 16; j += 2) {
+          for (int j = 0; j < 8; ++j) t[j] = fmaf(t[j], 0.0078125f, __uint_as_float(r[j]));
+        }
+        if (in_rows) {
+#pragma unroll
+          for (int j = 0; j < 8; j += 2) {
             const int cc = (colr0 + hf * 32 + c0 + j) >> 1;  // complex column (B map)
             if (cc >= T.cend) continue;
-            const int ex = er + T.F[cc] - 14;
-            double vr = ldexp(acc[j], ex), vi = ldexp(acc[j + 1], ex);
-            if (T.P) {  // one K segment: raw product, the combine kernel finishes
-              T.P[static_cast<long long>(cc) * T.ldp + grow] = make_double2(vr, vi);
+            const int ex = er + T.F[cc] - 28;
+            const bool normal = ex >= -1022 && ex <= 1023;
+            const double sc = normal ? pow2_normal(ex) * alpha : alpha;
+            double v[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const long long Sx = (static_cast<long long>(sums[0][c0 + j + h]) << 14) +
+                                   (static_cast<long long>(sums[1][c0 + j + h]) << 7) +
+                                   static_cast<long long>(sums[2][c0 + j + h]);
+              v[h] = (static_cast<double>(Sx) + static_cast<double>(t[j + h] * 0.0078125f)) * sc;
+              if (!normal) v[h] = ldexp(v[h], ex);  // subnormal or overflowing scale
+            }
+            if (raw) {
+              T.P[static_cast<long long>(cc) * T.ldp + grow] = make_double2(v[0], v[1]);
               continue;
             }
             const long long jc = cc + T.joff;
-            const double dshift = (T.Dg ? T.Dg[grow] : 0.0) - T.shift;
-            if (dshift != 0.0) {
+            if (adsh != 0.0) {
               const double2 xv = T.X[jc * T.ldx + grow];
-              vr += dshift * xv.x;
-              vi += dshift * xv.y;
+              v[0] = fma(adsh, xv.x, v[0]);
+              v[1] = fma(adsh, xv.y, v[1]);
             }
-            vr *= T.alpha;
-            vi *= T.alpha;
             double2* yp = T.Y + jc * T.ldy + grow;
             if (T.beta != 0.0) {
               const double2 yv = *yp;
-              vr += T.beta * yv.x;
-              vi += T.beta * yv.y;
+              v[0] = fma(T.beta, yv.x, v[0]);
+              v[1] = fma(T.beta, yv.y, v[1]);
             }
-            *yp = make_double2(vr, vi);
+            *yp = make_double2(v[0], v[1]);
           }
         }
       }
@@ -447,36 +475,60 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // ---------------------------------------------------------------------------
-// Slicing.  For |y| < 1: a = trunc(128 y), y <- 128 y - a, S times; every step
-// is exact in FP64 and every a is an integer in [-127, 127].
+// Slicing.  For |y| < 1 the slices are the 7-bit digits of y's binary
+// fraction with y's sign: a_s = sign(y) floor(|y| 2^(7(s+1))) mod 128, the
+// values that a = trunc(128 y), y <- 128 y - a gives (S times, every step
+// exact).  They are read off the IEEE bits with integer instructions: this
+// GPU's FP64 pipe is narrow, and the scaling y = v 2^-E is an exponent shift.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int exponent_above(double m) {
-  // smallest E with m < 2^E (0 for m == 0)
-  if (!(m > 0.0)) return 0;
-  int e;
-  frexp(m, &e);
-  return e;
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+  return static_cast<unsigned long long>(__double_as_longlong(v)) & 0x7FFFFFFFFFFFFFFFull;
 }
 
-__device__ __forceinline__ void slice7(double y, float* a) {
-#pragma unroll
-  for (int s = 0; s < S; ++s) {
-    const double t = y * 128.0;
-    const double q = trunc(t);
-    a[s] = static_cast<float>(q);
-    y = t - q;
+// Smallest E with m < 2^E for the magnitude m with bits mb (0 for m == 0);
+// the order of non-negative doubles is the order of their bit patterns.
+__device__ __forceinline__ int exponent_above_bits(unsigned long long mb) {
+  if (mb == 0) return 0;
+  const int eb = static_cast<int>(mb >> 52);
+  if (eb != 0) return eb - 1022;
+  return (63 - __clzll(static_cast<long long>(mb))) - 1073;  // subnormal
+}
+
+// Digits of |v| 2^-e (< 1) into a[0..S-1], signed like v.
+__device__ __forceinline__ void slice7_bits(double v, int e, float* a) {
+  const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(v));
+  const int eb = static_cast<int>((bits >> 52) & 0x7FF);
+  unsigned long long m = bits & ((1ull << 52) - 1);
+  int ex;  // |v| = m 2^(ex - 52)
+  if (eb == 0) {
+    ex = -1022;
+  } else {
+    m |= 1ull << 52;
+    ex = eb - 1023;
   }
+  // F = floor(|v| 2^-e 2^49) = m 2^(ex - e - 3); |v| < 2^e keeps F < 2^49
+  const int sh = e + 3 - ex;
+  const unsigned long long F = sh >= 64 ? 0ull : (sh >= 0 ? (m >> sh) : (m << (-sh)));
+  const float sg = (bits >> 63) ? -1.0f : 1.0f;
+#pragma unroll
+  for (int s = 0; s < S; ++s) a[s] = sg * static_cast<float>((F >> (42 - 7 * s)) & 127u);
 }
 
-__device__ double block_max(double v, double* scratch) {
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+__device__ unsigned long long block_max_u64(unsigned long long v, unsigned long long* scratch) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __syncthreads();
   if (lane == 0) scratch[warp] = v;
   __syncthreads();
   if (warp == 0) {
-    double w = lane < static_cast<int>((blockDim.x + 31) >> 5) ? scratch[lane] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) w = fmax(w, __shfl_xor_sync(0xffffffffu, w, o));
+    unsigned long long w = lane < static_cast<int>((blockDim.x + 31) >> 5) ? scratch[lane] : 0ull;
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long x = __shfl_xor_sync(0xffffffffu, w, o);
+      w = x > w ? x : w;
+    }
     if (lane == 0) scratch[32] = w;
   }
   __syncthreads();
@@ -488,15 +540,17 @@ __device__ double block_max(double v, double* scratch) {
 __device__ __forceinline__ void slice_h_row(const double2* __restrict__ col, int r, int N,
                                             __nv_bfloat16* __restrict__ A, long long Kp,
                                             int* __restrict__ E, double* __restrict__ Dg,
-                                            double* scratch) {
-  double m = 0.0;
+                                            unsigned long long* scratch) {
+  unsigned long long mb = 0;
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
     if (k == r) continue;  // the diagonal is applied in FP64 by the epilogue
     const double2 v = col[k];
-    m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+    const unsigned long long x = abs_bits(v.x), y = abs_bits(v.y);
+    mb = x > mb ? x : mb;
+    mb = y > mb ? y : mb;
   }
-  m = block_max(m, scratch);
-  const int er = exponent_above(m);
+  mb = block_max_u64(mb, scratch);
+  const int er = exponent_above_bits(mb);
   if (threadIdx.x == 0) {
     E[r] = er;
     Dg[r] = col[r].x;
@@ -506,8 +560,8 @@ __device__ __forceinline__ void slice_h_row(const double2* __restrict__ col, int
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
     const double2 v = k == r ? make_double2(0.0, 0.0) : col[k];
     float ar[S], ai[S];
-    slice7(ldexp(v.x, -er), ar);
-    slice7(ldexp(-v.y, -er), ai);
+    slice7_bits(v.x, er, ar);
+    slice7_bits(-v.y, er, ai);
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       row[s * plane + k] = __float2bfloat16_rn(ar[s]);
@@ -520,7 +574,7 @@ __global__ void __launch_bounds__(256) slice_h_kernel(const double2* __restrict_
                                                       int N, __nv_bfloat16* __restrict__ A,
                                                       long long Kp, int* __restrict__ E,
                                                       double* __restrict__ Dg) {
-  __shared__ double scratch[33];
+  __shared__ unsigned long long scratch[33];
   const int r = blockIdx.x;
   slice_h_row(H + static_cast<long long>(r) * ldh, r, N, A, Kp, E, Dg, scratch);
 }
@@ -529,7 +583,7 @@ __global__ void __launch_bounds__(256) slice_h_kernel(const double2* __restrict_
 // search over the first rows).
 __global__ void __launch_bounds__(256) slice_h_grouped_kernel(const GroupedSliceH* __restrict__ probs,
                                                               int P) {
-  __shared__ double scratch[33];
+  __shared__ unsigned long long scratch[33];
   const int g = blockIdx.x;
   int lo = 0, hi = P;
   while (hi - lo > 1) {
@@ -547,21 +601,23 @@ __global__ void __launch_bounds__(256) slice_h_grouped_kernel(const GroupedSlice
 __device__ __forceinline__ void slice_x_col(const double2* __restrict__ col, int N,
                                             __nv_bfloat16* __restrict__ r0, long long Kp,
                                             long long plane, int* __restrict__ Fc,
-                                            double* scratch) {
-  double m = 0.0;
+                                            unsigned long long* scratch) {
+  unsigned long long mb = 0;
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
     const double2 v = col[k];
-    m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+    const unsigned long long x = abs_bits(v.x), y = abs_bits(v.y);
+    mb = x > mb ? x : mb;
+    mb = y > mb ? y : mb;
   }
-  m = block_max(m, scratch);
-  const int fc = exponent_above(m);
+  mb = block_max_u64(mb, scratch);
+  const int fc = exponent_above_bits(mb);
   if (threadIdx.x == 0) *Fc = fc;
   __nv_bfloat16* r1 = r0 + Kp;
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
     const double2 v = col[k];
     float sr[S], si[S];
-    slice7(ldexp(v.x, -fc), sr);
-    slice7(ldexp(v.y, -fc), si);
+    slice7_bits(v.x, fc, sr);
+    slice7_bits(v.y, fc, si);
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       r0[s * plane + k] = __float2bfloat16_rn(sr[s]);
@@ -578,7 +634,7 @@ __global__ void __launch_bounds__(256) slice_x_kernel(const double2* __restrict_
                                                       int N, int j0, __nv_bfloat16* __restrict__ B,
                                                       long long Kp, long long rows_cap,
                                                       int* __restrict__ F) {
-  __shared__ double scratch[33];
+  __shared__ unsigned long long scratch[33];
   const int c = blockIdx.x;
   slice_x_col(X + static_cast<long long>(j0 + c) * ldx, N, B + static_cast<long long>(2 * c) * Kp, Kp,
               rows_cap * Kp, F + c, scratch);
@@ -589,7 +645,7 @@ __global__ void __launch_bounds__(256) slice_x_kernel(const double2* __restrict_
 __global__ void __launch_bounds__(256) slice_x_grouped_kernel(const GroupedProblem* __restrict__ probs,
                                                               const GroupedStep* __restrict__ steps,
                                                               int nact, int parity) {
-  __shared__ double scratch[33];
+  __shared__ unsigned long long scratch[33];
   const int e = grouped_find(steps, nact, blockIdx.x, false);
   const GroupedStep stp = steps[e];
   const GroupedProblem& pr = probs[stp.prob];
