@@ -52,10 +52,11 @@ def parse():
     p.add_argument("--seed", type=int, default=2024)
     p.add_argument("--precision", default="split", choices=["split", "fp64"])
     p.add_argument("--workload", default="sequence",
-                   choices=["sequence", "filter", "serve", "batched"],
+                   choices=["sequence", "filter", "serve", "batched", "degree-sweep"],
                    help="sequence: timed solves of the correlated sequence (default); "
                         "filter: timed degree-m filter calls on one problem, split vs FP64")
     p.add_argument("--filter-degree", type=int, default=20)
+    p.add_argument("--sweep-degrees", default="6,10,14,18,22,26,30,34,40")
     p.add_argument("--batch-problems", type=int, default=512)
     p.add_argument("--batch-degrees", default="const", choices=["const", "mixed"],
                    help="const: every column at --filter-degree; mixed: seeded even degrees "
@@ -546,6 +547,70 @@ def batched_cpu_baseline(shapes, degs, seed, budget_s):
             "seconds": round(spent, 2)}
 
 
+def run_degree_sweep(args, rank, world, local):
+    """Fig. 1a/2 on synthetic data: total and filter FLOPs and time of one
+    cold solve against the (initial) degree, with the per-column degree
+    optimisation (Alg. 5) off and on.  The problem is problem 1 of the
+    sequence workload (--n, --nev, --nex)."""
+    from paper_1805_10121_gb300 import build, chase, synth
+    build.build()
+    chase.lib()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n, nev, nex, tol = args.n, args.nev, args.nex, args.tol
+    seed = args.seed + 1000 * rank
+    seq, lam, hnorm = make_sequence(n, 1, seed, dev)
+    H = seq[0]
+    V0 = synth.gaussian_block(n, nev + nex, seed + 7, device=dev)
+    S = synth.gaussian_block(n, 5, seed + 8, device=dev)
+    prec = chase.CHASE_SPLIT_BF16 if args.precision == "split" else chase.CHASE_FP64
+    degs = [int(x) for x in args.sweep_degrees.split(",")]
+    rows = []
+    # warm-up: one solve (library load, cuSOLVER handle)
+    chase.chase_solve(H, nev, nex, tol, V0.clone(), S,
+                      opts=chase.chase_opts_default(precision=prec, deg=degs[0]))
+    torch.cuda.synchronize()
+    launches0 = chase.chase_kernel_launches()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_all = time.perf_counter()
+    for optim in (0, 1):
+        for deg in degs:
+            V = V0.clone()
+            o = chase.chase_opts_default(precision=prec, deg=deg, optim=optim)
+            t0 = time.perf_counter()
+            st, ritz, res, stt = chase.chase_solve(H, nev, nex, tol, V, S, opts=o)
+            dt = time.perf_counter() - t0
+            rows.append({"optim": optim, "deg": deg, "status": int(st),
+                         "iterations": stt["iterations"],
+                         "gflops_total": round(stt["flops_total"] / 1e9, 1),
+                         "gflops_filter": round(stt["flops_filter"] / 1e9, 1),
+                         "filter_matvecs": stt["filter_matvecs"], "seconds": round(dt, 3),
+                         "max_resid_over_norm": float(np.max(res[:nev])) / hnorm})
+    wall = time.perf_counter() - t_all
+    clk = clocks.stop()
+    fl = sum(r["gflops_total"] for r in rows) * 1e9
+    spread = {}
+    for optim in (0, 1):
+        g = [r["gflops_total"] for r in rows if r["optim"] == optim and r["status"] == 0]
+        spread[f"optim{optim}"] = round(max(g) / min(g), 3) if g else None
+    cfg = workload_config(args, world)
+    cfg["workload"] = (f"degree sweep (Fig. 1a/2 on synthetic data): one cold solve of problem 1 "
+                       f"of the sequence workload, N={n}, nev={nev}, nex={nex}, tol={tol}, "
+                       f"deg in {degs}, optim off and on; step = the whole sweep")
+    line = {
+        "metric": METRIC, "value": round(fl / wall / 1e12, 4), "unit": "TFLOP/s", "n_gpus": world,
+        "steps": 1, "warmup": 1, "ms_per_step": round(1e3 * wall, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16-split+f64" if prec == chase.CHASE_SPLIT_BF16 else "f64",
+        "data": "synthetic", "config": cfg,
+        "sweep": rows, "gflops_max_over_min": spread,
+        "gpu_launches": int(chase.chase_kernel_launches() - launches0), "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_serve_workload(args, rank, world, local):
     """Replay a seeded Poisson trace of sequence-solve requests through the
     continuous-batching server; report throughput and p50/p99 latency."""
@@ -622,6 +687,9 @@ def main():
         return
     if args.workload == "batched":
         run_batched_workload(args, rank, world, local)
+        return
+    if args.workload == "degree-sweep":
+        run_degree_sweep(args, rank, world, local)
         return
     from paper_1805_10121_gb300 import build, chase, synth
     build.build()
