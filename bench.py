@@ -50,7 +50,9 @@ def parse():
     p.add_argument("--nex", type=int, default=80)
     p.add_argument("--tol", type=float, default=1e-10)
     p.add_argument("--seed", type=int, default=2024)
-    p.add_argument("--precision", default="split", choices=["split", "fp64"])
+    p.add_argument("--precision", default="split", choices=["split", "split_rr", "fp64"],
+                   help="split: split-BF16 filter; split_rr: also Rayleigh-Ritz's H Q on the "
+                        "split product; fp64: FP64 throughout")
     p.add_argument("--workload", default="sequence",
                    choices=["sequence", "filter", "serve", "batched", "degree-sweep"],
                    help="sequence: timed solves of the correlated sequence (default); "
@@ -164,6 +166,12 @@ def make_sequence(n, count, seed, device):
     return seq, lam, hnorm
 
 
+def prec_code(name):
+    from paper_1805_10121_gb300 import chase
+    return {"split": chase.CHASE_SPLIT_BF16, "split_rr": chase.CHASE_SPLIT_BF16_RR,
+            "fp64": chase.CHASE_FP64}[name]
+
+
 # Slice-pair products the split-BF16 kernel executes per FP64-equivalent
 # product: pairs (s, t) of 7 slices with s + t <= 6.
 SPLIT_PAIRS = 28
@@ -173,7 +181,7 @@ def roofline_entry(stats_list, pk, src, precision):
     flops = sum(s["flops_filter"] for s in stats_list)
     secs = sum(s["t_filter"] for s in stats_list)
     fp64_equiv = flops / secs / 1e12 if secs > 0 else 0.0
-    if precision == "split":
+    if precision in ("split", "split_rr"):
         # BF16 tensor work the algorithm executes: 28 slice products, each a
         # real GEMM of 8 N^2 b FLOPs per b complex columns.  The kernel runs
         # inside a multi-second solve: sustained bf16 peak.
@@ -426,7 +434,7 @@ def run_batched_workload(args, rank, world, local):
         return (a.elapsed_time(b) / 1e3 / reps, st, clk,
                 chase.chase_kernel_launches() - launches0)
 
-    split = args.precision == "split"
+    split = args.precision != "fp64"
     prec = chase.CHASE_SPLIT_BF16 if split else chase.CHASE_FP64
     t_main, st_main, clk, launches = timed(prec, args.steps, args.warmup)
     flops = st_main[0]["flops"]
@@ -563,7 +571,7 @@ def run_degree_sweep(args, rank, world, local):
     H = seq[0]
     V0 = synth.gaussian_block(n, nev + nex, seed + 7, device=dev)
     S = synth.gaussian_block(n, 5, seed + 8, device=dev)
-    prec = chase.CHASE_SPLIT_BF16 if args.precision == "split" else chase.CHASE_FP64
+    prec = prec_code(args.precision)
     degs = [int(x) for x in args.sweep_degrees.split(",")]
     rows = []
     # warm-up: one solve (library load, cuSOLVER handle)
@@ -619,8 +627,8 @@ def run_serve_workload(args, rank, world, local):
     chase.lib()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    split = args.precision == "split"
-    prec = chase.CHASE_SPLIT_BF16 if split else chase.CHASE_FP64
+    split = args.precision != "fp64"
+    prec = prec_code(args.precision)
     sizes = tuple(int(x) for x in args.serve_sizes.split(","))
     weights = (4, 3, 2, 1)[:len(sizes)]
     trace = serve.poisson_trace(args.serve_requests, args.serve_rate, args.seed + 1000 * rank,
@@ -708,7 +716,7 @@ def main():
     starts = synth.gaussian_block(n, 5, seed + 8, device=dev).t().contiguous().t()
     Lam = None
 
-    prec = chase.CHASE_SPLIT_BF16 if args.precision == "split" else chase.CHASE_FP64
+    prec = prec_code(args.precision)
 
     def solve(k, Vb, Lamb, precision=None):
         o = chase.chase_opts_default(approx=0 if k == 0 else 1,
@@ -766,7 +774,7 @@ def main():
 
     # ---------------- the same problem on the FP64 path ----------------
     fp64 = None
-    if args.precision == "split" and not args.no_fp64_compare:
+    if args.precision != "fp64" and not args.no_fp64_compare:
         Vc = V_before.clone()
         torch.cuda.synchronize()
         c0 = torch.cuda.Event(enable_timing=True)
@@ -782,6 +790,27 @@ def main():
                 "max_abs_eig_diff_vs_split_over_norm":
                     float(np.max(np.abs(lam_c[:nev] - first_lam[:nev]))) / hnorm,
                 "speedup_split_vs_fp64": round(t_c / first_time, 2)}
+        del Vc
+
+    # ------- the same problem with Rayleigh-Ritz's H Q on the split product -------
+    split_rr = None
+    if args.precision == "split" and not args.no_fp64_compare:
+        Vc = V_before.clone()
+        torch.cuda.synchronize()
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        st_c, lam_c, res_c, s_c = solve(W, Vc, Lam_before.copy(),
+                                        precision=chase.CHASE_SPLIT_BF16_RR)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        t_c = c0.elapsed_time(c1) / 1e3
+        split_rr = {"s_per_solve": round(t_c, 3), "iterations": s_c["iterations"], "status": st_c,
+                    "t_rr": round(s_c["t_rr"], 3),
+                    "resid_max_over_norm": float(np.max(res_c[:nev])) / hnorm,
+                    "max_abs_eig_diff_vs_split_over_norm":
+                        float(np.max(np.abs(lam_c[:nev] - first_lam[:nev]))) / hnorm,
+                    "speedup_vs_split": round(first_time / t_c, 3)}
         del Vc
 
     # ---------------- end-to-end through host buffers ----------------
@@ -828,7 +857,7 @@ def main():
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "bf16-split+f64" if args.precision == "split" else "f64",
+        "dtype": "bf16-split+f64" if args.precision != "fp64" else "f64",
         "data": "synthetic",
         "config": workload_config(args, world),
         "s_per_solve": round(t_max / K, 3),
@@ -843,6 +872,7 @@ def main():
         "warmup_iterations": [s["iterations"] for _, s in stats_w],
         "roofline": roofline_entry(stats_t, pk, src, args.precision),
         "fp64_same_problem": fp64,
+        "split_rr_same_problem": split_rr,
         "cpu_baseline": cb,
         "e2e": e2e,
         "gpu_launches": int(launches),

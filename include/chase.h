@@ -63,6 +63,13 @@ typedef struct {
  * Reads H through its Hermitian symmetry.  QR, Rayleigh-Ritz, residuals
  * and Lanczos stay FP64. */
 #define CHASE_SPLIT_BF16 1
+/* Split-BF16 filter as above, and the product H Q of Rayleigh-Ritz (Alg. 2
+ * line 2, reused for the residuals) on the same split product: each entry
+ * carries the same 2^-49 relative bound, against the K u |H||Q| of an FP64
+ * GEMM.  The projected eigenproblem, QR, the Gram products and Lanczos stay
+ * FP64.  chase_solve and chase_solve_batched only (the filter entry points
+ * take CHASE_FP64 or CHASE_SPLIT_BF16). */
+#define CHASE_SPLIT_BF16_RR 2
 
 /* ---- residual test used for locking (Alg. 3 line 4) ---- */
 #define CHASE_CONV_ABS 0 /* Res <= tol (the paper's absolute criterion, Sec. 6.1) */
@@ -80,7 +87,7 @@ typedef struct {
   int approx;       /* 1: V and Lambda hold an approximate solution (Sec. 3.3) */
   double dos_sigma; /* Gaussian width of Eq. 10 in the variable mapped to [-1, 1] (Sec. 4.2: 0.25) */
   int conv_mode;    /* CHASE_CONV_ABS or CHASE_CONV_REL */
-  int precision;    /* filter arithmetic: CHASE_FP64 or CHASE_SPLIT_BF16 */
+  int precision;    /* CHASE_FP64, CHASE_SPLIT_BF16 or CHASE_SPLIT_BF16_RR */
 } chase_opts;
 
 /* Counters and per-phase times of one chase_solve call. */
@@ -91,7 +98,7 @@ typedef struct {
   long long filter_matvecs;/* column products inside the filter (= sum of the degrees) */
   double b_sup, mu1, mu_nevnex; /* final spectral estimates (Sec. 4.2) */
   double tol_eff;          /* the absolute residual threshold used for locking */
-  double flops_filter;     /* 8 N^2 * filter_matvecs + 8 N * (columns touched) */
+  double flops_filter;     /* 8 N^2 * filter_matvecs (2 N^2 for real problems) */
   double flops_total;      /* all algorithmic FLOPs of the solve */
   double t_total, t_lanczos, t_filter, t_qr, t_rr, t_eigh, t_resid, t_host; /* seconds */
 } chase_stats;
@@ -253,6 +260,23 @@ int chase_residuals(const chase_c64* H, int64_t N, int64_t ldh, const chase_c64*
  * CHASE_TIMEOUT. */
 int chase_residuals_noalloc(const chase_c64* H, int64_t N, int64_t ldh, const chase_c64* V,
                             int64_t ldv, int b, const double* lambda, double* resid, void* stream);
+
+/* Real symmetric problems (Sec. 5.1: the library is templated on the field
+ * as well as the precision).  Same arguments, layouts, ownership and errors
+ * as chase_filter, chase_residuals and chase_solve, with float64 matrices
+ * and real symmetric H (both triangles stored; the split-BF16 slices read
+ * row r of H from its column r).  Flop counts use 2 N^2 per column product
+ * (8 N^2 for complex).  Leading dimensions need not be even: odd ones are
+ * staged through padded device buffers inside the call. */
+int chase_filter_real(const double* H, int64_t N, int64_t ldh, double* V, int64_t ldv, int b,
+                      const int* degrees, double b_sup, double mu1, double mu_nevnex, int precision,
+                      double* work, void* stream);
+int chase_residuals_real(const double* H, int64_t N, int64_t ldh, const double* V, int64_t ldv,
+                         int b, const double* lambda, double* resid, void* stream);
+int chase_solve_real(const double* H, int64_t N, int64_t ldh, int nev, int nex, double tol,
+                     double* V, int64_t ldv, double* Lambda, double* resid,
+                     const double* lanczos_starts, const chase_opts* opts, chase_stats* stats,
+                     void* stream);
 
 /* Chebyshev filter (Alg. 4, Eq. 7) of many independent problems at once.
  * The paper filters one matrix per call; this entry point has no

@@ -25,8 +25,8 @@ __all__ = [
     "CHASE_OK", "CHASE_INVALID_ARG", "CHASE_NOT_CONVERGED", "CHASE_QR_BREAKDOWN",
     "CHASE_BOUND_VIOLATION", "CHASE_CUDA_ERROR", "CHASE_OUT_OF_MEMORY", "CHASE_TIMEOUT",
     "CHASE_EIGENSOLVER_ERROR", "CHASE_CONV_ABS", "CHASE_CONV_REL", "CHASE_FP64",
-    "CHASE_SPLIT_BF16", "CHASE_TILE_AUTO", "ChaseBatchStats", "chase_filter_batched",
-    "chase_solve_batched",
+    "CHASE_SPLIT_BF16", "CHASE_SPLIT_BF16_RR", "CHASE_TILE_AUTO", "ChaseBatchStats", "chase_filter_batched",
+    "chase_solve_batched", "chase_filter_real", "chase_residuals_real", "chase_solve_real",
 ]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -43,6 +43,7 @@ CHASE_TIMEOUT = 7
 CHASE_EIGENSOLVER_ERROR = 8
 CHASE_FP64 = 0
 CHASE_SPLIT_BF16 = 1
+CHASE_SPLIT_BF16_RR = 2
 CHASE_CONV_ABS = 0
 CHASE_CONV_REL = 1
 CHASE_TILE_AUTO = -1
@@ -118,6 +119,11 @@ _SIGNATURES = {
     "chase_rayleigh_ritz": (_int, [_c_p, _i64, _i64, _c_p, _i64, _int, _dp, _dp, _c_p]),
     "chase_residuals": (_int, [_c_p, _i64, _i64, _c_p, _i64, _int, _dp, _dp, _c_p]),
     "chase_residuals_noalloc": (_int, [_c_p, _i64, _i64, _c_p, _i64, _int, _c_p, _c_p, _c_p]),
+    "chase_filter_real": (_int, [_c_p, _i64, _i64, _c_p, _i64, _int, _c_p, _dbl, _dbl, _dbl, _int,
+                                 _c_p, _c_p]),
+    "chase_residuals_real": (_int, [_c_p, _i64, _i64, _c_p, _i64, _int, _dp, _dp, _c_p]),
+    "chase_solve_real": (_int, [_c_p, _i64, _i64, _int, _int, _dbl, _c_p, _i64, _dp, _dp, _c_p,
+                                ctypes.POINTER(ChaseOpts), ctypes.POINTER(ChaseStats), _c_p]),
     "chase_solve": (_int, [_c_p, _i64, _i64, _int, _int, _dbl, _c_p, _i64, _dp, _dp, _c_p,
                            ctypes.POINTER(ChaseOpts), ctypes.POINTER(ChaseStats), _c_p]),
 }
@@ -166,10 +172,11 @@ def _check(status: int, where: str, allow=(CHASE_OK,)):
     return status
 
 
-def _mat(t: torch.Tensor, rows: int, name: str):
-    """Pointer and leading dimension of a column-major complex128 matrix."""
-    if t.dtype != torch.complex128:
-        raise TypeError(f"{name} must be complex128")
+def _mat(t: torch.Tensor, rows: int, name: str, dtype=torch.complex128):
+    """Pointer and leading dimension of a column-major complex128 (or, for
+    the real entry points, float64) matrix."""
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}")
     if t.dim() != 2 or t.shape[0] != rows:
         raise ValueError(f"{name} must have {rows} rows")
     if t.shape[1] > 1 and t.stride(0) != 1:
@@ -213,13 +220,10 @@ def chase_opts_default(**overrides) -> ChaseOpts:
     return o
 
 
-def chase_filter(H, V, degrees, b_sup, mu1, mu_nevnex, work=None, stream=None,
-                 precision=CHASE_FP64):
-    """Filter the columns of V in place (Alg. 4).  ``degrees``: int32 tensor
-    (host or device) or a sequence of ints."""
+def _filter(entry, dtype, H, V, degrees, b_sup, mu1, mu_nevnex, work, stream, precision):
     n = H.shape[0]
-    hp, ldh = _mat(H, n, "H")
-    vp, ldv = _mat(V, n, "V")
+    hp, ldh = _mat(H, n, "H", dtype)
+    vp, ldv = _mat(V, n, "V", dtype)
     b = V.shape[1]
     if isinstance(degrees, torch.Tensor):
         if degrees.dtype != torch.int32 or not degrees.is_contiguous():
@@ -232,10 +236,25 @@ def chase_filter(H, V, degrees, b_sup, mu1, mu_nevnex, work=None, stream=None,
     if len(deg_keep) != b:
         raise ValueError("one degree per column")
     wp = ctypes.c_void_p(work.data_ptr()) if work is not None else None
-    st = lib().chase_filter(hp, n, ldh, vp, ldv, b, dptr, float(b_sup), float(mu1),
-                            float(mu_nevnex), int(precision), wp, _stream(V, stream))
-    _check(st, "chase_filter")
+    st = getattr(lib(), entry)(hp, n, ldh, vp, ldv, b, dptr, float(b_sup), float(mu1),
+                               float(mu_nevnex), int(precision), wp, _stream(V, stream))
+    _check(st, entry)
     return V
+
+
+def chase_filter(H, V, degrees, b_sup, mu1, mu_nevnex, work=None, stream=None,
+                 precision=CHASE_FP64):
+    """Filter the columns of V in place (Alg. 4).  ``degrees``: int32 tensor
+    (host or device) or a sequence of ints."""
+    return _filter("chase_filter", torch.complex128, H, V, degrees, b_sup, mu1, mu_nevnex, work,
+                   stream, precision)
+
+
+def chase_filter_real(H, V, degrees, b_sup, mu1, mu_nevnex, work=None, stream=None,
+                      precision=CHASE_FP64):
+    """Alg. 4 for a real symmetric H (float64 tensors)."""
+    return _filter("chase_filter_real", torch.float64, H, V, degrees, b_sup, mu1, mu_nevnex, work,
+                   stream, precision)
 
 
 def chase_filter_batched(Hs, Vs, degrees, b_sup, mu1, mu_nevnex, precision=CHASE_FP64,
@@ -400,16 +419,24 @@ def chase_rayleigh_ritz(H, Q, want_resid=True, stream=None):
     return ritz, resid
 
 
-def chase_residuals(H, V, lam, stream=None):
+def _residuals(entry, dtype, H, V, lam, stream):
     n = H.shape[0]
-    hp, ldh = _mat(H, n, "H")
-    vp, ldv = _mat(V, n, "V")
+    hp, ldh = _mat(H, n, "H", dtype)
+    vp, ldv = _mat(V, n, "V", dtype)
     b = V.shape[1]
     lam = _f64(lam, b)
     out = np.zeros(b)
-    _check(lib().chase_residuals(hp, n, ldh, vp, ldv, b, _dptr(lam), _dptr(out),
-                                 _stream(V, stream)), "chase_residuals")
+    _check(getattr(lib(), entry)(hp, n, ldh, vp, ldv, b, _dptr(lam), _dptr(out),
+                                 _stream(V, stream)), entry)
     return out
+
+
+def chase_residuals(H, V, lam, stream=None):
+    return _residuals("chase_residuals", torch.complex128, H, V, lam, stream)
+
+
+def chase_residuals_real(H, V, lam, stream=None):
+    return _residuals("chase_residuals_real", torch.float64, H, V, lam, stream)
 
 
 def chase_residuals_noalloc(H, V, lam, resid, stream=None):
@@ -428,15 +455,13 @@ def chase_residuals_noalloc(H, V, lam, resid, stream=None):
     return resid
 
 
-def chase_solve(H, nev, nex, tol, V, lanczos_starts, Lambda=None, opts=None, stream=None,
-                raise_not_converged=False):
-    """Alg. 1.  V (N x (nev+nex)) is overwritten with the Ritz vectors.
-    Returns ``(status, Lambda, resid, stats_dict)``."""
+def _solve(entry, dtype, H, nev, nex, tol, V, lanczos_starts, Lambda, opts, stream,
+           raise_not_converged):
     n = H.shape[0]
     nx = nev + nex
-    hp, ldh = _mat(H, n, "H")
-    vp, ldv = _mat(V, n, "V")
-    sp, lds = _mat(lanczos_starts, n, "lanczos_starts")
+    hp, ldh = _mat(H, n, "H", dtype)
+    vp, ldv = _mat(V, n, "V", dtype)
+    sp, lds = _mat(lanczos_starts, n, "lanczos_starts", dtype)
     if lanczos_starts.shape[1] > 1 and lds != n:
         raise ValueError("lanczos_starts must have leading dimension N")
     lam = np.zeros(nx) if Lambda is None else np.array(Lambda, dtype=np.float64, copy=True)
@@ -445,9 +470,24 @@ def chase_solve(H, nev, nex, tol, V, lanczos_starts, Lambda=None, opts=None, str
     resid = np.zeros(nx)
     o = opts if opts is not None else chase_opts_default()
     stats = ChaseStats()
-    st = lib().chase_solve(hp, n, ldh, int(nev), int(nex), float(tol), vp, ldv, _dptr(lam),
-                           _dptr(resid), sp, ctypes.byref(o), ctypes.byref(stats),
-                           _stream(H, stream))
+    st = getattr(lib(), entry)(hp, n, ldh, int(nev), int(nex), float(tol), vp, ldv, _dptr(lam),
+                               _dptr(resid), sp, ctypes.byref(o), ctypes.byref(stats),
+                               _stream(H, stream))
     allow = (CHASE_OK,) if raise_not_converged else (CHASE_OK, CHASE_NOT_CONVERGED)
-    _check(st, "chase_solve", allow)
+    _check(st, entry, allow)
     return st, lam, resid, stats.as_dict()
+
+
+def chase_solve(H, nev, nex, tol, V, lanczos_starts, Lambda=None, opts=None, stream=None,
+                raise_not_converged=False):
+    """Alg. 1.  V (N x (nev+nex)) is overwritten with the Ritz vectors.
+    Returns ``(status, Lambda, resid, stats_dict)``."""
+    return _solve("chase_solve", torch.complex128, H, nev, nex, tol, V, lanczos_starts, Lambda,
+                  opts, stream, raise_not_converged)
+
+
+def chase_solve_real(H, nev, nex, tol, V, lanczos_starts, Lambda=None, opts=None, stream=None,
+                     raise_not_converged=False):
+    """Alg. 1 for a real symmetric H (float64 tensors)."""
+    return _solve("chase_solve_real", torch.float64, H, nev, nex, tol, V, lanczos_starts, Lambda,
+                  opts, stream, raise_not_converged)

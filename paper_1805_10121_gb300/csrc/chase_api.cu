@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstring>
 #include <numeric>
+#include <type_traits>
 #include <vector>
 
 #include "chase.h"
@@ -22,6 +23,26 @@ namespace chase {
 namespace {
 
 constexpr int kMaxDegAllowed = 1024;
+
+// Real problems: every matrix handed to the TMA product has an even leading
+// dimension (TMA strides are multiples of 16 bytes), so internal buffers pad
+// their rows to even; complex128 columns are already 16-byte multiples.
+template <class T>
+constexpr bool is_cplx = std::is_same<T, chase_c64>::value;
+template <class T>
+int64_t ld_pad(int64_t n) {
+  return is_cplx<T> ? std::max<int64_t>(n, 1) : std::max<int64_t>((n + 1) / 2 * 2, 2);
+}
+template <class T>
+T from_real(double v);
+template <>
+chase_c64 from_real<chase_c64>(double v) {
+  return chase_c64{v, 0.0};
+}
+template <>
+double from_real<double>(double v) {
+  return v;
+}
 
 // Events bracketing the phases of one call, accumulated into seconds.
 struct PhaseTimer {
@@ -56,15 +77,17 @@ struct PhaseTimer {
 // have retired before step i).  Returns the column-product count.
 // One filter product: the FP64 DMMA kernel, or the split-BF16 tensor-core
 // kernel when slices of H are given.
-int filter_product(Dev& d, const chase_c64* H, int64_t N, int64_t ldh, const SplitH* sh, SplitX* sx,
-                   const chase_c64* X, int64_t ldx, int b, chase_c64* Y, int64_t ldy, int j0,
+template <class T>
+int filter_product(Dev& d, const T* H, int64_t N, int64_t ldh, const SplitH* sh, SplitX* sx,
+                   const T* X, int64_t ldx, int b, T* Y, int64_t ldy, int j0,
                    double alpha, double beta, double shift) {
   if (sh) return zgemm_split(d, *sh, *sx, X, ldx, j0, b, Y, ldy, alpha, beta, shift);
-  return zgemm(d, N, N, H, ldh, X, ldx, b, Y, ldy, j0, b, alpha, beta, shift);
+  return gemm(d, N, N, H, ldh, X, ldx, b, Y, ldy, j0, b, alpha, beta, shift);
 }
 
-int filter_sorted(Dev& d, const chase_c64* H, int64_t N, int64_t ldh, chase_c64* X, int64_t ldx,
-                  chase_c64* Wk, int64_t ldw, int b, const int* start, int maxdeg, double b_sup,
+template <class T>
+int filter_sorted(Dev& d, const T* H, int64_t N, int64_t ldh, T* X, int64_t ldx,
+                  T* Wk, int64_t ldw, int b, const int* start, int maxdeg, double b_sup,
                   double mu1, double mu_nn, long long* matvecs, const SplitH* sh = nullptr,
                   SplitX* sx = nullptr) {
   const double c = 0.5 * (b_sup + mu_nn);  // Alg. 4 line 2
@@ -74,8 +97,8 @@ int filter_sorted(Dev& d, const chase_c64* H, int64_t N, int64_t ldh, chase_c64*
   CHASE_TRY(filter_product(d, H, N, ldh, sh, sx, X, ldx, b, Wk, ldw, 0, sigma1 / e, 0.0, c));
   long long mv = b;
   double sigma = sigma1;  // line 5
-  chase_c64* Vb = X;
-  chase_c64* Wb = Wk;
+  T* Vb = X;
+  T* Wb = Wk;
   int64_t ldV = ldx, ldW = ldw;
   for (int i = 2; i <= maxdeg; ++i) {  // line 7
     const double tau = 1.0 / (2.0 / sigma1 - sigma);  // line 8
@@ -111,45 +134,50 @@ void starts_from_sorted(const int* m, int b, int maxdeg, std::vector<int>& start
 // block Y and Cholesky QR, twice; shifted Cholesky QR first when a pivot is
 // not safely positive.
 // ---------------------------------------------------------------------------
+template <class T>
 struct OrthWork {
-  chase_c64* T = nullptr;     // N x b
-  chase_c64* P = nullptr;     // nconv x b
-  chase_c64* G = nullptr;     // b x b
-  chase_c64* Rinv = nullptr;  // panel workspace of the blocked Cholesky / solve, >= 32 b
-  double* nrm = nullptr;      // b
+  T* P = nullptr;     // nconv x b, leading dimension ld_pad(nconv)
+  T* G = nullptr;     // b x b, leading dimension ld_pad(b)
+  T* Rinv = nullptr;  // panel workspace of the blocked Cholesky / solve, >= 32 b
+  double* nrm = nullptr;  // b
 };
 
-int orth_alloc(Dev& d, int64_t N, int nconv, int b, OrthWork& w) {
-  CHASE_TRY(d.alloc(&w.T, static_cast<size_t>(N) * b));
-  CHASE_TRY(d.alloc(&w.P, static_cast<size_t>(std::max(nconv, 1)) * b));
-  CHASE_TRY(d.alloc(&w.G, static_cast<size_t>(b) * b));
+template <class T>
+int orth_alloc(Dev& d, int64_t N, int nconv, int b, OrthWork<T>& w) {
+  (void)N;
+  CHASE_TRY(d.alloc(&w.P, static_cast<size_t>(ld_pad<T>(std::max(nconv, 1))) * b));
+  CHASE_TRY(d.alloc(&w.G, static_cast<size_t>(ld_pad<T>(b)) * b));
   CHASE_TRY(d.alloc(&w.Rinv, static_cast<size_t>(std::max(b, 32)) * b));
   CHASE_TRY(d.alloc(&w.nrm, static_cast<size_t>(b)));
   return CHASE_OK;
 }
 
-int cholqr_pass(Dev& d, int64_t N, const chase_c64* Y, int64_t ldy, int nconv, chase_c64* V,
-                int64_t ldv, int b, OrthWork& w, double shift, double* flops) {
+template <class T>
+int cholqr_pass(Dev& d, int64_t N, const T* Y, int64_t ldy, int nconv, T* V,
+                int64_t ldv, int b, OrthWork<T>& w, double shift, double* flops) {
+  const int64_t ldp = ld_pad<T>(nconv), ldg = ld_pad<T>(b);
   if (nconv > 0) {  // V <- V - Y (Y^H V)
-    CHASE_TRY(zgram(d, N, Y, ldy, nconv, V, ldv, b, w.P, nconv));
-    CHASE_TRY(zgemm(d, N, nconv, Y, ldy, w.P, nconv, b, V, ldv, 0, b, -1.0, 1.0, 0.0));
-    *flops += 16.0 * N * nconv * b;
+    CHASE_TRY(gram(d, N, Y, ldy, nconv, V, ldv, b, w.P, ldp));
+    CHASE_TRY(gemm(d, N, nconv, Y, ldy, w.P, ldp, b, V, ldv, 0, b, -1.0, 1.0, 0.0));
+    *flops += (is_cplx<T> ? 16.0 : 4.0) * N * nconv * b;
   }
-  CHASE_TRY(zgram(d, N, V, ldv, b, V, ldv, b, w.G, b));
-  CHASE_TRY(cholesky_blocked(d, w.G, b, b, 1e-12, shift, w.nrm, w.Rinv));
+  CHASE_TRY(gram(d, N, V, ldv, b, V, ldv, b, w.G, ldg));
+  CHASE_TRY(cholesky_blocked(d, w.G, ldg, b, 1e-12, shift, w.nrm, w.Rinv));
   int st = d.sync_check("cholesky");
   if (st != CHASE_OK) {
     cudaMemsetAsync(d.err, 0, sizeof(int), d.st);
     return st;
   }
   // V <- V L^-H (= V R^-1 with R = L^H), in place
-  CHASE_TRY(trsm_right_lh(d, V, ldv, N, w.G, b, b, w.Rinv));
-  *flops += 8.0 * N * b * b + 4.0 * N * b * b + 8.0 * b * b * b / 3.0;
+  CHASE_TRY(trsm_right_lh(d, V, ldv, N, w.G, ldg, b, w.Rinv));
+  *flops += (is_cplx<T> ? 1.0 : 0.25) *
+            (8.0 * N * b * b + 4.0 * N * b * b + 8.0 * b * b * b / 3.0);
   return CHASE_OK;
 }
 
-int orth_core(Dev& d, int64_t N, const chase_c64* Y, int64_t ldy, int nconv, chase_c64* V,
-              int64_t ldv, int b, OrthWork& w, double* flops) {
+template <class T>
+int orth_core(Dev& d, int64_t N, const T* Y, int64_t ldy, int nconv, T* V,
+              int64_t ldv, int b, OrthWork<T>& w, double* flops) {
   if (b == 0) return CHASE_OK;
   // QR of V D equals QR of V for any positive diagonal D: normalise columns.
   CHASE_TRY(launch_col_norms(d, V, ldv, N, b, w.nrm));
@@ -178,39 +206,48 @@ int orth_core(Dev& d, int64_t N, const chase_c64* Y, int64_t ldy, int nconv, cha
 // ---------------------------------------------------------------------------
 // Rayleigh-Ritz (Alg. 2) with residuals (Alg. 1 line 8)
 // ---------------------------------------------------------------------------
+template <class T>
 struct RRWork {
-  chase_c64* HQ = nullptr;  // N x b
-  chase_c64* T2 = nullptr;  // N x b
-  chase_c64* T3 = nullptr;  // N x b
-  chase_c64* G = nullptr;   // b x b
+  T* HQ = nullptr;  // N x b (leading dimension ld_pad(N) here and below)
+  T* T2 = nullptr;  // N x b
+  T* T3 = nullptr;  // N x b
+  T* G = nullptr;   // b x b, leading dimension ld_pad(b)
 };
 
-int rr_alloc(Dev& d, int64_t N, int b, RRWork& w) {
-  CHASE_TRY(d.alloc(&w.HQ, static_cast<size_t>(N) * b));
-  CHASE_TRY(d.alloc(&w.T2, static_cast<size_t>(N) * b));
-  CHASE_TRY(d.alloc(&w.T3, static_cast<size_t>(N) * b));
-  CHASE_TRY(d.alloc(&w.G, static_cast<size_t>(b) * b));
+template <class T>
+int rr_alloc(Dev& d, int64_t N, int b, RRWork<T>& w) {
+  const size_t nb = static_cast<size_t>(ld_pad<T>(N)) * b;
+  CHASE_TRY(d.alloc(&w.HQ, nb));
+  CHASE_TRY(d.alloc(&w.T2, nb));
+  CHASE_TRY(d.alloc(&w.T3, nb));
+  CHASE_TRY(d.alloc(&w.G, static_cast<size_t>(ld_pad<T>(b)) * b));
   return CHASE_OK;
 }
 
-int rr_core(Dev& d, const chase_c64* H, int64_t N, int64_t ldh, chase_c64* Q, int64_t ldq, int b,
-            double* w_dev, double* res_dev, RRWork& w, double* t_eigh, double* flops) {
+template <class T>
+int rr_core(Dev& d, const T* H, int64_t N, int64_t ldh, T* Q, int64_t ldq, int b,
+            double* w_dev, double* res_dev, RRWork<T>& w, double* t_eigh, double* flops,
+            const SplitH* sh = nullptr, SplitX* sx = nullptr) {
   if (b == 0) return CHASE_OK;
-  CHASE_TRY(zgemm(d, N, N, H, ldh, Q, ldq, b, w.HQ, N, 0, b, 1.0, 0.0, 0.0));  // H Q
-  CHASE_TRY(zgram(d, N, Q, ldq, b, w.HQ, N, b, w.G, b));                       // G = Q^H H Q
-  CHASE_TRY(launch_hermitize(d, w.G, b, b));
+  const int64_t lN = ld_pad<T>(N), lg = ld_pad<T>(b);
+  if (sh)  // H Q on the split product (CHASE_SPLIT_BF16_RR)
+    CHASE_TRY(zgemm_split(d, *sh, *sx, Q, ldq, 0, b, w.HQ, lN, 1.0, 0.0, 0.0));
+  else
+    CHASE_TRY(gemm(d, N, N, H, ldh, Q, ldq, b, w.HQ, lN, 0, b, 1.0, 0.0, 0.0));  // H Q
+  CHASE_TRY(gram(d, N, Q, ldq, b, w.HQ, lN, b, w.G, lg));                       // G = Q^H H Q
+  CHASE_TRY(launch_hermitize(d, w.G, lg, b));
   PhaseTimer tm(d.st);
   tm.begin(t_eigh);
-  CHASE_TRY(eigh_device(d, w.G, b, b, w_dev));  // (W, Lambda) = TSOLVE(G)
+  CHASE_TRY(eigh_device(d, w.G, lg, b, w_dev));  // (W, Lambda) = TSOLVE(G)
   tm.end();
-  CHASE_TRY(zgemm(d, N, b, Q, ldq, w.G, b, b, w.T2, N, 0, b, 1.0, 0.0, 0.0));  // Q W
+  CHASE_TRY(gemm(d, N, b, Q, ldq, w.G, lg, b, w.T2, lN, 0, b, 1.0, 0.0, 0.0));  // Q W
   if (res_dev) {
     // H (Q W) = (H Q) W: the residual reuses the product with H
-    CHASE_TRY(zgemm(d, N, b, w.HQ, N, w.G, b, b, w.T3, N, 0, b, 1.0, 0.0, 0.0));
-    CHASE_TRY(launch_resid_norms(d, w.T3, N, w.T2, N, N, b, w_dev, res_dev));
+    CHASE_TRY(gemm(d, N, b, w.HQ, lN, w.G, lg, b, w.T3, lN, 0, b, 1.0, 0.0, 0.0));
+    CHASE_TRY(launch_resid_norms(d, w.T3, lN, w.T2, lN, N, b, w_dev, res_dev));
   }
-  CHASE_TRY(copy_block(d, Q, ldq, w.T2, N, N, b, cudaMemcpyDeviceToDevice));
-  *flops += 8.0 * N * N * b + 8.0 * N * b * b * (res_dev ? 3.0 : 2.0);
+  CHASE_TRY(copy_block(d, Q, ldq, w.T2, lN, N, b, cudaMemcpyDeviceToDevice));
+  *flops += (is_cplx<T> ? 1.0 : 0.25) * (8.0 * N * N * b + 8.0 * N * b * b * (res_dev ? 3.0 : 2.0));
   return CHASE_OK;
 }
 
@@ -226,31 +263,33 @@ double normal_cdf(double x) { return 0.5 * (1.0 + std::erf(x / std::sqrt(2.0)));
 
 // starts: N x r device (ld N), r = 1 (approx) or 1 + nvec.  V: N x ncolv
 // device or NULL.
-int lanczos_core(Dev& d, const chase_c64* H, int64_t N, int64_t ldh, int k, int nvec, bool approx,
-                 int nev, int nex, double dos_sigma, const chase_c64* starts, chase_c64* V,
+template <class T>
+int lanczos_core(Dev& d, const T* H, int64_t N, int64_t ldh, int k, int nvec, bool approx,
+                 int nev, int nex, double dos_sigma, const T* starts, int64_t lds, T* V,
                  int64_t ldv, int ncolv, LanczosOut& out) {
   const int r = approx ? 1 : 1 + nvec;
-  chase_c64* U = nullptr;   // N x (k r): vector j of run c is column j r + c
-  chase_c64* Wt = nullptr;  // N x r
+  const int64_t lN = ld_pad<T>(N);
+  T* U = nullptr;   // N x (k r), leading dimension lN: vector j of run c is column j r + c
+  T* Wt = nullptr;  // N x r
   double *alpha = nullptr, *beta = nullptr;
-  CHASE_TRY(d.alloc(&U, static_cast<size_t>(N) * k * r));
-  CHASE_TRY(d.alloc(&Wt, static_cast<size_t>(N) * r));
+  CHASE_TRY(d.alloc(&U, static_cast<size_t>(lN) * k * r));
+  CHASE_TRY(d.alloc(&Wt, static_cast<size_t>(lN) * r));
   CHASE_TRY(d.alloc(&alpha, static_cast<size_t>(k) * r));
   CHASE_TRY(d.alloc(&beta, static_cast<size_t>(k) * r));
-  CHASE_TRY(copy_block(d, U, N, starts, N, N, r, cudaMemcpyDeviceToDevice));
-  CHASE_TRY(launch_normalize_cols(d, U, N, N, r));
+  CHASE_TRY(copy_block(d, U, lN, starts, lds, N, r, cudaMemcpyDeviceToDevice));
+  CHASE_TRY(launch_normalize_cols(d, U, lN, N, r));
   for (int j = 0; j < k; ++j) {
-    chase_c64* Vj = U + static_cast<size_t>(j) * r * N;
-    const chase_c64* Vp = j > 0 ? U + static_cast<size_t>(j - 1) * r * N : nullptr;
-    chase_c64* Vn = j + 1 < k ? U + static_cast<size_t>(j + 1) * r * N : nullptr;
-    CHASE_TRY(zgemm(d, N, N, H, ldh, Vj, N, r, Wt, N, 0, r, 1.0, 0.0, 0.0));  // A v_j
-    CHASE_TRY(launch_lanczos_step(d, N, r, j, Vj, Vp, Wt, Vn, alpha, beta));
+    T* Vj = U + static_cast<size_t>(j) * r * lN;
+    const T* Vp = j > 0 ? U + static_cast<size_t>(j - 1) * r * lN : nullptr;
+    T* Vn = j + 1 < k ? U + static_cast<size_t>(j + 1) * r * lN : nullptr;
+    CHASE_TRY(gemm(d, N, N, H, ldh, Vj, lN, r, Wt, lN, 0, r, 1.0, 0.0, 0.0));  // A v_j
+    CHASE_TRY(launch_lanczos_step(d, N, lN, r, j, Vj, Vp, Wt, Vn, alpha, beta));
   }
   std::vector<double> ha(static_cast<size_t>(k) * r), hb(static_cast<size_t>(k) * r);
   CHASE_CUDA(cudaMemcpyAsync(ha.data(), alpha, ha.size() * sizeof(double), cudaMemcpyDeviceToHost, d.st));
   CHASE_CUDA(cudaMemcpyAsync(hb.data(), beta, hb.size() * sizeof(double), cudaMemcpyDeviceToHost, d.st));
   CHASE_TRY(d.sync_check("lanczos"));
-  out.matvecs = static_cast<long long>(k) * r;
+  out.matvecs = static_cast<long long>(k) * r;  // column products with H
 
   // per run: truncate at the first step whose beta is rounding noise
   std::vector<std::vector<double>> theta(r), Z(r);
@@ -343,34 +382,45 @@ int lanczos_core(Dev& d, const chase_c64* H, int64_t N, int64_t ldh, int k, int 
       if (theta[1][i] < out.mu_nn) sel.push_back(i);
     if (!sel.empty()) {
       const int ns = static_cast<int>(sel.size());
-      std::vector<chase_c64> zs(static_cast<size_t>(st) * ns);
+      const int64_t lz = ld_pad<T>(st);
+      std::vector<T> zs(static_cast<size_t>(lz) * ns, from_real<T>(0.0));
       for (int a = 0; a < ns; ++a)
         for (int i = 0; i < st; ++i)
-          zs[static_cast<size_t>(a) * st + i] = {Z[1][static_cast<size_t>(sel[a]) * st + i], 0.0};
-      chase_c64* dz = nullptr;
+          zs[static_cast<size_t>(a) * lz + i] = from_real<T>(Z[1][static_cast<size_t>(sel[a]) * st + i]);
+      T* dz = nullptr;
       CHASE_TRY(d.alloc(&dz, zs.size()));
-      CHASE_CUDA(cudaMemcpyAsync(dz, zs.data(), zs.size() * sizeof(chase_c64),
+      CHASE_CUDA(cudaMemcpyAsync(dz, zs.data(), zs.size() * sizeof(T),
                                  cudaMemcpyHostToDevice, d.st));
-      // U_1 Z_sel: basis of run 1 is columns j r + 1, i.e. leading dimension r N
-      CHASE_TRY(zgemm(d, N, st, U + N, static_cast<int64_t>(r) * N, dz, st, ns, V, ldv, 0, ns,
-                      1.0, 0.0, 0.0));
+      // U_1 Z_sel: basis of run 1 is columns j r + 1, i.e. leading dimension r lN
+      CHASE_TRY(gemm(d, N, st, U + lN, static_cast<int64_t>(r) * lN, dz, lz, ns, V, ldv, 0, ns,
+                     1.0, 0.0, 0.0));
       CHASE_TRY(d.sync_check("lanczos ritz vectors"));
     }
   }
   return CHASE_OK;
 }
 
-// Stage an array that may live on the host into device memory.
-int stage_in(Dev& d, bool on_dev, const chase_c64* src, int64_t ld, int64_t rows, int64_t cols,
-             chase_c64** dst, int64_t* ldd) {
-  if (on_dev) {
-    *dst = const_cast<chase_c64*>(src);
+// Stage an array that may live on the host into device memory.  Real
+// device arrays whose leading dimension is odd are staged too (the TMA
+// products need even leading dimensions).
+template <class T>
+bool needs_stage(bool on_dev, int64_t ld) {
+  return !on_dev || (!is_cplx<T> && (ld & 1));
+}
+
+template <class T>
+int stage_in(Dev& d, bool on_dev, const T* src, int64_t ld, int64_t rows, int64_t cols, T** dst,
+             int64_t* ldd) {
+  if (!needs_stage<T>(on_dev, ld)) {
+    *dst = const_cast<T*>(src);
     *ldd = ld;
     return CHASE_OK;
   }
-  CHASE_TRY(d.alloc(dst, static_cast<size_t>(rows) * std::max<int64_t>(cols, 1)));
-  *ldd = rows;
-  return copy_block(d, *dst, rows, src, ld, rows, cols, cudaMemcpyHostToDevice);
+  const int64_t lp = ld_pad<T>(rows);
+  CHASE_TRY(d.alloc(dst, static_cast<size_t>(lp) * std::max<int64_t>(cols, 1)));
+  *ldd = lp;
+  return copy_block(d, *dst, lp, src, ld, rows, cols,
+                    on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
 }
 
 bool ld_ok(int64_t ld, int64_t n) { return ld >= std::max<int64_t>(1, n); }
@@ -380,27 +430,31 @@ bool ld_ok(int64_t ld, int64_t n) { return ld >= std::max<int64_t>(1, n); }
 // line 1-2), then per iteration begin_iteration (line 3 and the bound
 // check), the filter (line 4), after_filter (lines 5-15), and finally
 // finish (ascending output).
+template <class T>
 struct Solver {
   // arguments
-  const chase_c64* H = nullptr;
+  const T* H = nullptr;
   int64_t N = 0, ldh = 0;
   int nev = 0, nex = 0, nx = 0;
   double tol = 0;
-  chase_c64* V = nullptr;
+  T* V = nullptr;
   int64_t ldv = 0;
   double* Lambda = nullptr;
   double* resid = nullptr;
-  const chase_c64* starts = nullptr;
+  const T* starts = nullptr;
   chase_opts o{};
   bool dev = true;
   // device state
-  chase_c64 *dH = nullptr, *dV = nullptr, *dS = nullptr, *Wk = nullptr;
-  int64_t lh = 0, lv = 0, ls = 0;
-  OrthWork ow;
-  RRWork rw;
+  T *dH = nullptr, *dV = nullptr, *dS = nullptr, *Wk = nullptr;
+  int64_t lh = 0, lv = 0, ls = 0, lw = 0;
+  OrthWork<T> ow;
+  RRWork<T> rw;
   SplitH sh;
   SplitX sx;
   bool split = false;
+  bool split_rr = false;            // H Q of Rayleigh-Ritz on the split product too
+  const SplitH* rr_slices = nullptr;  // the slices of H used there
+  SplitX* rr_sx = nullptr;
   double *dw = nullptr, *dres = nullptr;
   int* dperm = nullptr;
   // host state
@@ -410,9 +464,12 @@ struct Solver {
   std::vector<double> ritz, res, ra, rr;
   chase_stats S{};
 
+  // FLOPs per entry of a product with H: complex multiply-add 8, real 2
+  static constexpr double kMv = is_cplx<T> ? 8.0 : 2.0;
+
   // active block of the current iteration
   int b() const { return nx - nconv; }
-  chase_c64* Va() const { return dV + static_cast<size_t>(nconv) * lv; }
+  T* Va() const { return dV + static_cast<size_t>(nconv) * lv; }
   bool more() const { return status == CHASE_OK && nconv < nev && iter < o.max_iter; }
 
   // Everything before the loop of Alg. 1; `grouped_split` leaves the slices
@@ -425,13 +482,17 @@ struct Solver {
     CHASE_TRY(stage_in(d, dev, H, ldh, N, N, &dH, &lh));
     CHASE_TRY(stage_in(d, dev, V, ldv, N, nx, &dV, &lv));
     CHASE_TRY(stage_in(d, dev, starts, N, N, r, &dS, &ls));
-    CHASE_TRY(d.alloc(&Wk, static_cast<size_t>(N) * nx));  // filter double buffer / permutation scratch
+    lw = ld_pad<T>(N);
+    CHASE_TRY(d.alloc(&Wk, static_cast<size_t>(lw) * nx));  // filter double buffer / permutation scratch
     CHASE_TRY(orth_alloc(d, N, nx, nx, ow));
     CHASE_TRY(rr_alloc(d, N, nx, rw));
-    split = o.precision == CHASE_SPLIT_BF16;
+    split = o.precision == CHASE_SPLIT_BF16 || o.precision == CHASE_SPLIT_BF16_RR;
+    split_rr = o.precision == CHASE_SPLIT_BF16_RR;
     if (split && !grouped_split) {  // slices of H once per solve, slice workspace for the block
       CHASE_TRY(split_prepare_h(d, dH, N, lh, sh));
-      CHASE_TRY(split_alloc_x(d, N, nx, sx));
+      CHASE_TRY(split_alloc_x(d, N, nx, sx, is_cplx<T>));
+      rr_slices = &sh;
+      rr_sx = &sx;
     }
     CHASE_TRY(d.alloc(&dw, nx));
     CHASE_TRY(d.alloc(&dres, nx));
@@ -444,10 +505,11 @@ struct Solver {
     LanczosOut lz;
     tm.begin(&S.t_lanczos);
     CHASE_TRY(lanczos_core(d, dH, N, lh, o.lanczos_iter, o.num_lanczos, o.approx != 0, nev, nex,
-                           o.dos_sigma, dS, o.approx ? nullptr : dV, lv, o.approx ? 0 : nx, lz));
+                           o.dos_sigma, dS, ls, o.approx ? nullptr : dV, lv, o.approx ? 0 : nx,
+                           lz));
     tm.end();
     S.matvecs += lz.matvecs;
-    S.flops_total += 8.0 * N2 * lz.matvecs;
+    S.flops_total += kMv * N2 * lz.matvecs;
     b_sup = lz.b_sup;
     if (o.approx) {
       mu1 = *std::min_element(Lambda, Lambda + nx);
@@ -487,7 +549,7 @@ struct Solver {
     PhaseTimer tm(d.st);
     long long fm = 0;
     tm.begin(&S.t_filter);
-    CHASE_TRY(filter_sorted(d, dH, N, lh, Va(), lv, Wk, N, b(), start.data(), maxdeg, b_sup, mu1,
+    CHASE_TRY(filter_sorted(d, dH, N, lh, Va(), lv, Wk, lw, b(), start.data(), maxdeg, b_sup, mu1,
                             mu_nn, &fm, split ? &sh : nullptr, &sx));
     tm.end();
     count_filter(fm);
@@ -503,7 +565,7 @@ struct Solver {
     g.X = Va();
     g.ldx = lv;
     g.W = Wk;
-    g.ldw = N;
+    g.ldw = lw;
     g.b = b();
     g.start = start.data();
     g.maxdeg = maxdeg;
@@ -522,22 +584,23 @@ struct Solver {
   void count_filter(long long fm) {
     S.filter_matvecs += fm;
     S.matvecs += fm;
-    S.flops_filter += 8.0 * N2 * fm;
-    S.flops_total += 8.0 * N2 * fm;
+    S.flops_filter += kMv * N2 * fm;
+    S.flops_total += kMv * N2 * fm;
   }
 
   // Lines 5-15 of an iteration.
   int after_filter(Dev& d) {
     PhaseTimer tm(d.st);
     const int nb = b();
-    chase_c64* va = Va();
+    T* va = Va();
     // lines 5-6: orthonormalise the active block against the locked one
     tm.begin(&S.t_qr);
     CHASE_TRY(orth_core(d, N, dV, lv, nconv, va, lv, nb, ow, &S.flops_total));
     tm.end();
     // lines 7-8: Rayleigh-Ritz on the active block, residuals
     tm.begin(&S.t_rr);
-    CHASE_TRY(rr_core(d, dH, N, lh, va, lv, nb, dw, dres, rw, &S.t_eigh, &S.flops_total));
+    CHASE_TRY(rr_core(d, dH, N, lh, va, lv, nb, dw, dres, rw, &S.t_eigh, &S.flops_total,
+                      split_rr ? rr_slices : nullptr, split_rr ? rr_sx : nullptr));
     CHASE_CUDA(cudaMemcpyAsync(ra.data(), dw, sizeof(double) * nb, cudaMemcpyDeviceToHost, d.st));
     CHASE_CUDA(cudaMemcpyAsync(rr.data(), dres, sizeof(double) * nb, cudaMemcpyDeviceToHost, d.st));
     tm.end();
@@ -593,8 +656,8 @@ struct Solver {
     }
     S.t_host += std::chrono::duration<double>(std::chrono::steady_clock::now() - t_host0).count();
     CHASE_CUDA(cudaMemcpyAsync(dperm, perm.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, d.st));
-    CHASE_TRY(launch_permute_cols(d, va, lv, Wk, N, N, nb, dperm, false));
-    CHASE_TRY(copy_block(d, va, lv, Wk, N, N, nb, cudaMemcpyDeviceToDevice));
+    CHASE_TRY(launch_permute_cols(d, va, lv, Wk, lw, N, nb, dperm, false));
+    CHASE_TRY(copy_block(d, va, lv, Wk, lw, N, nb, cudaMemcpyDeviceToDevice));
     // the host arrays read by the copies above change in the next iteration
     CHASE_TRY(d.sync_check("chase_solve permutation"));
     nconv = nconv_new;
@@ -607,9 +670,11 @@ struct Solver {
     std::iota(fin.begin(), fin.end(), 0);
     std::stable_sort(fin.begin(), fin.end(), [&](int x, int y) { return ritz[x] < ritz[y]; });
     CHASE_CUDA(cudaMemcpyAsync(dperm, fin.data(), sizeof(int) * nx, cudaMemcpyHostToDevice, d.st));
-    CHASE_TRY(launch_permute_cols(d, dV, lv, Wk, N, N, nx, dperm, false));
-    CHASE_TRY(copy_block(d, dV, lv, Wk, N, N, nx, cudaMemcpyDeviceToDevice));
-    if (!dev) CHASE_TRY(copy_block(d, V, ldv, dV, lv, N, nx, cudaMemcpyDeviceToHost));
+    CHASE_TRY(launch_permute_cols(d, dV, lv, Wk, lw, N, nx, dperm, false));
+    CHASE_TRY(copy_block(d, dV, lv, Wk, lw, N, nx, cudaMemcpyDeviceToDevice));
+    if (dV != V)
+      CHASE_TRY(copy_block(d, V, ldv, dV, lv, N, nx,
+                           dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
     CHASE_TRY(d.sync_check("chase_solve output"));
     for (int a = 0; a < nx; ++a) {
       Lambda[a] = ritz[fin[a]];
@@ -636,7 +701,8 @@ bool solve_args_ok(int64_t N, int64_t ldh, int nev, int nex, double tol, int64_t
            o.deg > kMaxDegAllowed - 1 || o.deg_max < 2 || o.deg_max > kMaxDegAllowed ||
            o.deg_extra < 0 || o.max_iter < 0 || o.lanczos_iter < 1 || o.lanczos_iter > N ||
            (!o.approx && o.num_lanczos < 1) ||
-           (o.precision != CHASE_FP64 && o.precision != CHASE_SPLIT_BF16) ||
+           (o.precision != CHASE_FP64 && o.precision != CHASE_SPLIT_BF16 &&
+            o.precision != CHASE_SPLIT_BF16_RR) ||
            (o.conv_mode != CHASE_CONV_ABS && o.conv_mode != CHASE_CONV_REL));
 }
 
@@ -664,9 +730,11 @@ extern "C" int chase_opts_default(chase_opts* o) {
   return CHASE_OK;
 }
 
-extern "C" int chase_filter(const chase_c64* H, int64_t N, int64_t ldh, chase_c64* V, int64_t ldv,
-                            int b, const int* degrees, double b_sup, double mu1, double mu_nevnex,
-                            int precision, chase_c64* work, void* stream) {
+namespace chase {
+namespace {
+template <class T>
+int filter_impl(const T* H, int64_t N, int64_t ldh, T* V, int64_t ldv, int b, const int* degrees,
+                double b_sup, double mu1, double mu_nevnex, int precision, T* work, void* stream) {
   if (precision != CHASE_FP64 && precision != CHASE_SPLIT_BF16) {
     set_error("chase_filter: unknown precision %d", precision);
     return CHASE_INVALID_ARG;
@@ -691,12 +759,14 @@ extern "C" int chase_filter(const chase_c64* H, int64_t N, int64_t ldh, chase_c6
     set_error("chase_filter: H and V must both be host or both be device arrays");
     return CHASE_INVALID_ARG;
   }
-  chase_c64 *dH = nullptr, *dV = nullptr;
+  T *dH = nullptr, *dV = nullptr;
   int64_t lh = 0, lv = 0;
   CHASE_TRY(stage_in(d, dev, H, ldh, N, N, &dH, &lh));
   CHASE_TRY(stage_in(d, dev, V, ldv, N, b, &dV, &lv));
-  chase_c64* wk = dev ? work : nullptr;
-  if (!wk) CHASE_TRY(d.alloc(&wk, static_cast<size_t>(N) * b));
+  // the workspace (leading dimension ld_pad(N)) must suit the TMA products
+  const int64_t lw = ld_pad<T>(N);
+  T* wk = dev && lw == N ? work : nullptr;
+  if (!wk) CHASE_TRY(d.alloc(&wk, static_cast<size_t>(lw) * b));
   // degrees -> device, plan on the device (stable sort by degree)
   int *ddeg = nullptr, *dperm = nullptr, *dstart = nullptr, *dinfo = nullptr;
   if (is_device_ptr(degrees)) {
@@ -718,16 +788,33 @@ extern "C" int chase_filter(const chase_c64* H, int64_t N, int64_t ldh, chase_c6
   SplitX sx;
   if (precision == CHASE_SPLIT_BF16) {
     CHASE_TRY(split_prepare_h(d, dH, N, lh, sh));
-    CHASE_TRY(split_alloc_x(d, N, b, sx));
+    CHASE_TRY(split_alloc_x(d, N, b, sx, is_cplx<T>));
   }
   // sorted copy into the workspace; V becomes the second buffer
-  CHASE_TRY(launch_permute_cols(d, dV, lv, wk, N, N, b, dperm, false));
-  CHASE_TRY(filter_sorted(d, dH, N, lh, wk, N, dV, lv, b, start.data(), maxdeg, b_sup, mu1,
+  CHASE_TRY(launch_permute_cols(d, dV, lv, wk, lw, N, b, dperm, false));
+  CHASE_TRY(filter_sorted(d, dH, N, lh, wk, lw, dV, lv, b, start.data(), maxdeg, b_sup, mu1,
                           mu_nevnex, nullptr, precision == CHASE_SPLIT_BF16 ? &sh : nullptr, &sx));
-  CHASE_TRY(launch_permute_cols(d, wk, N, dV, lv, N, b, dperm, true));
-  if (!dev) CHASE_TRY(copy_block(d, V, ldv, dV, lv, N, b, cudaMemcpyDeviceToHost));
+  CHASE_TRY(launch_permute_cols(d, wk, lw, dV, lv, N, b, dperm, true));
+  if (dV != V)
+    CHASE_TRY(copy_block(d, V, ldv, dV, lv, N, b,
+                         dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
   return d.sync_check("chase_filter");
 }
+}  // namespace
+}  // namespace chase
+
+extern "C" int chase_filter(const chase_c64* H, int64_t N, int64_t ldh, chase_c64* V, int64_t ldv,
+                            int b, const int* degrees, double b_sup, double mu1, double mu_nevnex,
+                            int precision, chase_c64* work, void* stream) {
+  return filter_impl(H, N, ldh, V, ldv, b, degrees, b_sup, mu1, mu_nevnex, precision, work, stream);
+}
+
+extern "C" int chase_filter_real(const double* H, int64_t N, int64_t ldh, double* V, int64_t ldv,
+                                 int b, const int* degrees, double b_sup, double mu1,
+                                 double mu_nevnex, int precision, double* work, void* stream) {
+  return filter_impl(H, N, ldh, V, ldv, b, degrees, b_sup, mu1, mu_nevnex, precision, work, stream);
+}
+
 
 extern "C" int chase_lanczos(const chase_c64* H, int64_t N, int64_t ldh, int k, int nvec, int approx,
                              int nev, int nex, double dos_sigma, const chase_c64* starts,
@@ -754,7 +841,7 @@ extern "C" int chase_lanczos(const chase_c64* H, int64_t N, int64_t ldh, int k, 
   const int ncolv = V && !approx ? nev + nex : 0;
   if (ncolv) CHASE_TRY(stage_in(d, dev, V, ldv, N, ncolv, &dV, &lv));
   LanczosOut out;
-  CHASE_TRY(lanczos_core(d, dH, N, lh, k, nvec, approx != 0, nev, nex, dos_sigma, dS, dV, lv,
+  CHASE_TRY(lanczos_core(d, dH, N, lh, k, nvec, approx != 0, nev, nex, dos_sigma, dS, ls, dV, lv,
                          ncolv, out));
   if (ncolv && !dev) CHASE_TRY(copy_block(d, V, ldv, dV, lv, N, ncolv, cudaMemcpyDeviceToHost));
   CHASE_TRY(d.sync_check("chase_lanczos"));
@@ -786,7 +873,7 @@ extern "C" int chase_orthonormalize(const chase_c64* Y, int64_t N, int64_t ldy, 
   int64_t ly = N, lv = 0;
   if (nconv > 0) CHASE_TRY(stage_in(d, dev, Y, ldy, N, nconv, &dY, &ly));
   CHASE_TRY(stage_in(d, dev, V, ldv, N, b, &dV, &lv));
-  OrthWork w;
+  OrthWork<chase_c64> w;
   CHASE_TRY(orth_alloc(d, N, nconv, b, w));
   double fl = 0.0;
   CHASE_TRY(orth_core(d, N, dY, ly, nconv, dV, lv, b, w, &fl));
@@ -813,7 +900,7 @@ extern "C" int chase_rayleigh_ritz(const chase_c64* H, int64_t N, int64_t ldh, c
   int64_t lh, lq;
   CHASE_TRY(stage_in(d, dev, H, ldh, N, N, &dH, &lh));
   CHASE_TRY(stage_in(d, dev, Q, ldq, N, b, &dQ, &lq));
-  RRWork w;
+  RRWork<chase_c64> w;
   CHASE_TRY(rr_alloc(d, N, b, w));
   double *dw = nullptr, *dr = nullptr;
   CHASE_TRY(d.alloc(&dw, b));
@@ -826,9 +913,11 @@ extern "C" int chase_rayleigh_ritz(const chase_c64* H, int64_t N, int64_t ldh, c
   return d.sync_check("chase_rayleigh_ritz");
 }
 
-extern "C" int chase_residuals(const chase_c64* H, int64_t N, int64_t ldh, const chase_c64* V,
-                               int64_t ldv, int b, const double* lambda, double* resid,
-                               void* stream) {
+namespace chase {
+namespace {
+template <class T>
+int residuals_impl(const T* H, int64_t N, int64_t ldh, const T* V, int64_t ldv, int b,
+                   const double* lambda, double* resid, void* stream) {
   if (N < 0 || b < 0 || !ld_ok(ldh, N) || !ld_ok(ldv, N) ||
       (b > 0 && (!H || !V || !lambda || !resid))) {
     set_error("chase_residuals: invalid argument");
@@ -842,25 +931,42 @@ extern "C" int chase_residuals(const chase_c64* H, int64_t N, int64_t ldh, const
     set_error("chase_residuals: H and V must be of the same kind");
     return CHASE_INVALID_ARG;
   }
-  chase_c64 *dH, *dV, *HV = nullptr;
+  T *dH, *dV, *HV = nullptr;
   int64_t lh, lv;
   CHASE_TRY(stage_in(d, dev, H, ldh, N, N, &dH, &lh));
   CHASE_TRY(stage_in(d, dev, V, ldv, N, b, &dV, &lv));
   double *dl = nullptr, *dr = nullptr;
-  CHASE_TRY(d.alloc(&HV, static_cast<size_t>(N) * b));
+  const int64_t lw = ld_pad<T>(N);
+  CHASE_TRY(d.alloc(&HV, static_cast<size_t>(lw) * b));
   CHASE_TRY(d.alloc(&dl, b));
   CHASE_TRY(d.alloc(&dr, b));
   CHASE_CUDA(cudaMemcpyAsync(dl, lambda, sizeof(double) * b, cudaMemcpyHostToDevice, d.st));
-  CHASE_TRY(zgemm(d, N, N, dH, lh, dV, lv, b, HV, N, 0, b, 1.0, 0.0, 0.0));
-  CHASE_TRY(launch_resid_norms(d, HV, N, dV, lv, N, b, dl, dr));
+  CHASE_TRY(gemm(d, N, N, dH, lh, dV, lv, b, HV, lw, 0, b, 1.0, 0.0, 0.0));
+  CHASE_TRY(launch_resid_norms(d, HV, lw, dV, lv, N, b, dl, dr));
   CHASE_CUDA(cudaMemcpyAsync(resid, dr, sizeof(double) * b, cudaMemcpyDeviceToHost, d.st));
   return d.sync_check("chase_residuals");
 }
+}  // namespace
+}  // namespace chase
 
-extern "C" int chase_solve(const chase_c64* H, int64_t N, int64_t ldh, int nev, int nex, double tol,
-                           chase_c64* V, int64_t ldv, double* Lambda, double* resid,
-                           const chase_c64* lanczos_starts, const chase_opts* opts_in,
-                           chase_stats* stats, void* stream) {
+extern "C" int chase_residuals(const chase_c64* H, int64_t N, int64_t ldh, const chase_c64* V,
+                               int64_t ldv, int b, const double* lambda, double* resid,
+                               void* stream) {
+  return residuals_impl(H, N, ldh, V, ldv, b, lambda, resid, stream);
+}
+
+extern "C" int chase_residuals_real(const double* H, int64_t N, int64_t ldh, const double* V,
+                                    int64_t ldv, int b, const double* lambda, double* resid,
+                                    void* stream) {
+  return residuals_impl(H, N, ldh, V, ldv, b, lambda, resid, stream);
+}
+
+namespace chase {
+namespace {
+template <class T>
+int solve_impl(const T* H, int64_t N, int64_t ldh, int nev, int nex, double tol, T* V, int64_t ldv,
+               double* Lambda, double* resid, const T* lanczos_starts, const chase_opts* opts_in,
+               chase_stats* stats, void* stream) {
   chase_opts o;
   if (opts_in)
     o = *opts_in;
@@ -877,7 +983,7 @@ extern "C" int chase_solve(const chase_c64* H, int64_t N, int64_t ldh, int nev, 
     set_error("chase_solve: H, V and lanczos_starts must all be host or all be device");
     return CHASE_INVALID_ARG;
   }
-  Solver sv;
+  Solver<T> sv;
   sv.H = H;
   sv.N = N;
   sv.ldh = ldh;
@@ -906,6 +1012,24 @@ extern "C" int chase_solve(const chase_c64* H, int64_t N, int64_t ldh, int nev, 
   sv.S.t_total = t_total;
   if (stats) *stats = sv.S;
   return st;
+}
+}  // namespace
+}  // namespace chase
+
+extern "C" int chase_solve(const chase_c64* H, int64_t N, int64_t ldh, int nev, int nex, double tol,
+                           chase_c64* V, int64_t ldv, double* Lambda, double* resid,
+                           const chase_c64* lanczos_starts, const chase_opts* opts_in,
+                           chase_stats* stats, void* stream) {
+  return solve_impl(H, N, ldh, nev, nex, tol, V, ldv, Lambda, resid, lanczos_starts, opts_in, stats,
+                    stream);
+}
+
+extern "C" int chase_solve_real(const double* H, int64_t N, int64_t ldh, int nev, int nex,
+                                double tol, double* V, int64_t ldv, double* Lambda, double* resid,
+                                const double* lanczos_starts, const chase_opts* opts_in,
+                                chase_stats* stats, void* stream) {
+  return solve_impl(H, N, ldh, nev, nex, tol, V, ldv, Lambda, resid, lanczos_starts, opts_in, stats,
+                    stream);
 }
 
 extern "C" int chase_solve_batched(int P, const chase_c64* const* H, const int64_t* N,
@@ -942,10 +1066,10 @@ extern "C" int chase_solve_batched(int P, const chase_c64* const* H, const int64
   if (P == 0) return CHASE_OK;
   Dev d(stream);
   CHASE_TRY(d.init());
-  const bool split = o.precision == CHASE_SPLIT_BF16;
-  std::vector<Solver> sv(P);
+  const bool split = o.precision != CHASE_FP64;
+  std::vector<Solver<chase_c64>> sv(P);
   for (int p = 0; p < P; ++p) {  // Alg. 1 lines 1-2 of every problem
-    Solver& s = sv[p];
+    Solver<chase_c64>& s = sv[p];
     s.H = H[p];
     s.N = N[p];
     s.ldh = ldh[p];
@@ -971,6 +1095,19 @@ extern "C" int chase_solve_batched(int P, const chase_c64* const* H, const int64
       bcap[p] = sv[p].nx;
     }
     CHASE_TRY(grouped_split_prepare(d, slices, bcap));
+    for (int p = 0; p < P; ++p) {  // the same slices serve Rayleigh-Ritz's H Q
+      Solver<chase_c64>& s = sv[p];
+      s.sh.A = slices[p].A;
+      s.sh.E = slices[p].E;
+      s.sh.Dg = slices[p].Dg;
+      s.sh.N = s.N;
+      s.sh.Kp = split_k_padded(s.N);
+      s.sx.B = slices[p].Bsl;
+      s.sx.F = slices[p].F;
+      s.sx.cap_cols = slices[p].bcap;
+      s.rr_slices = &s.sh;
+      s.rr_sx = &s.sx;
+    }
   }
   chase_batch_stats bs{};
   bs.problems = P;
@@ -1004,7 +1141,7 @@ extern "C" int chase_solve_batched(int P, const chase_c64* const* H, const int64
     bs.t_steps += tt.t_steps;
     bs.t_product += tt.t_product;
     for (int p : act) {
-      Solver& s = sv[p];
+      Solver<chase_c64>& s = sv[p];
       const long long fm = s.filter_matvecs();
       s.count_filter(fm);
       // the grouped filter's time, shared out by each problem's FLOPs

@@ -124,6 +124,10 @@ __device__ __forceinline__ void dmma_8x8x4(double& d0, double& d1, double a, dou
 // as a 2-D float64 tensor {2*rows, cols}; box {2*box_rows, box_cols}.
 int make_tmap_c64(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld,
                   int box_rows, int box_cols);
+// A float64 column-major matrix (rows x cols, leading dimension ld) as a 2-D
+// tensor {rows, cols}; box {box_rows, box_cols}.
+int make_tmap_f64(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld,
+                  int box_rows, int box_cols);
 // A 3-D bf16 tensor {d0, d1, d2} with byte strides s1 (dim 1) and s2 (dim 2),
 // box {b0, b1, b2}, 32-byte swizzle (b0 * 2 must be 32).
 int make_tmap_bf16_3d(CUtensorMap* map, const void* base, int64_t d0, int64_t d1, int64_t d2,
@@ -139,6 +143,21 @@ struct Dev;  // per-call device context (stream, error flag, workspace)
 int zgemm(Dev& d, int64_t M, int64_t K, const chase_c64* A, int64_t lda, const chase_c64* B,
           int64_t ldb, int64_t ncols_b, chase_c64* C, int64_t ldc, int j0, int j1, double alpha,
           double beta, double shift);
+
+// The same for real matrices (one DMMA per fragment instead of the 3M form).
+int dgemm(Dev& d, int64_t M, int64_t K, const double* A, int64_t lda, const double* B, int64_t ldb,
+          int64_t ncols_b, double* C, int64_t ldc, int j0, int j1, double alpha, double beta,
+          double shift);
+inline int gemm(Dev& d, int64_t M, int64_t K, const chase_c64* A, int64_t lda, const chase_c64* B,
+                int64_t ldb, int64_t ncols_b, chase_c64* C, int64_t ldc, int j0, int j1,
+                double alpha, double beta, double shift) {
+  return zgemm(d, M, K, A, lda, B, ldb, ncols_b, C, ldc, j0, j1, alpha, beta, shift);
+}
+inline int gemm(Dev& d, int64_t M, int64_t K, const double* A, int64_t lda, const double* B,
+                int64_t ldb, int64_t ncols_b, double* C, int64_t ldc, int j0, int j1, double alpha,
+                double beta, double shift) {
+  return dgemm(d, M, K, A, lda, B, ldb, ncols_b, C, ldc, j0, j1, alpha, beta, shift);
+}
 
 // C (p x q, ldc) = X^H Y with X: N x p (ldx), Y: N x q (ldy).
 int zgram(Dev& d, int64_t N, const chase_c64* X, int64_t ldx, int p, const chase_c64* Y,

@@ -37,68 +37,100 @@ bool is_device_ptr(const void* p);
 // 2-D copies of column-major complex128 blocks (rows x cols).
 int copy_block(Dev& d, chase_c64* dst, int64_t ldd, const chase_c64* src, int64_t lds, int64_t rows,
                int64_t cols, cudaMemcpyKind kind);
+int copy_block(Dev& d, double* dst, int64_t ldd, const double* src, int64_t lds, int64_t rows,
+               int64_t cols, cudaMemcpyKind kind);
 
 // ---- kernels.cu ------------------------------------------------------------
+// Element launchers are templates over the scalar T: chase_c64 (Hermitian
+// problems) or double (real symmetric ones); both are instantiated.
 // Stable counting sort of the degrees (warp-level match/popc scans):
 // perm[pos] = original column at sorted position pos; start[i] = number of
 // columns with degree < i (i = 0 .. max_deg + 1); info[0] = max degree.
 int launch_filter_plan(Dev& d, const int* deg, int b, int max_allowed, int* perm, int* start,
                        int* info);
 // Y[:, j] = X[:, perm[j]]  (gather) or Y[:, perm[j]] = X[:, j] (scatter)
-int launch_permute_cols(Dev& d, const chase_c64* X, int64_t ldx, chase_c64* Y, int64_t ldy,
-                        int64_t N, int b, const int* perm, bool scatter);
+template <class T>
+int launch_permute_cols(Dev& d, const T* X, int64_t ldx, T* Y, int64_t ldy, int64_t N, int b,
+                        const int* perm, bool scatter);
 // out[j] = ||X[:, j]||_2
-int launch_col_norms(Dev& d, const chase_c64* X, int64_t ldx, int64_t N, int b, double* out);
+template <class T>
+int launch_col_norms(Dev& d, const T* X, int64_t ldx, int64_t N, int b, double* out);
 // X[:, j] *= 1 / s[j]   (s[j] == 0 leaves the column)
-int launch_col_inv_scale(Dev& d, chase_c64* X, int64_t ldx, int64_t N, int b, const double* s);
+template <class T>
+int launch_col_inv_scale(Dev& d, T* X, int64_t ldx, int64_t N, int b, const double* s);
 // res[j] = ||HV[:, j] - lam[j] V[:, j]||_2
-int launch_resid_norms(Dev& d, const chase_c64* HV, int64_t ldhv, const chase_c64* V, int64_t ldv,
-                       int64_t N, int b, const double* lam, double* res);
+template <class T>
+int launch_resid_norms(Dev& d, const T* HV, int64_t ldhv, const T* V, int64_t ldv, int64_t N, int b,
+                       const double* lam, double* res);
 // G <- (G + G^H) / 2 for a p x p matrix
-int launch_hermitize(Dev& d, chase_c64* G, int64_t ldg, int p);
+template <class T>
+int launch_hermitize(Dev& d, T* G, int64_t ldg, int p);
 // In-place lower Cholesky G = L L^H (one CTA); sets KERR_CHOL_BREAKDOWN when a
 // pivot is not above rel_tol * G_jj.  `shift` is added to the diagonal first.
-int launch_cholesky(Dev& d, chase_c64* G, int64_t ldg, int p, double rel_tol, double shift);
+template <class T>
+int launch_cholesky(Dev& d, T* G, int64_t ldg, int p, double rel_tol, double shift);
 // Blocked Cholesky (32-wide panels, trailing updates on the FP64 GEMM); the
 // pivot test uses the diagonal of G + shift before any update (diag_ref, p
 // doubles of workspace); work holds >= 32 p entries.
-int cholesky_blocked(Dev& d, chase_c64* G, int64_t ldg, int p, double rel_tol, double shift,
-                     double* diag_ref, chase_c64* work);
+template <class T>
+int cholesky_blocked(Dev& d, T* G, int64_t ldg, int p, double rel_tol, double shift,
+                     double* diag_ref, T* work);
 // X (N x p) <- X L^-H (blocked right-side triangular solve); work >= 32 p entries.
-int trsm_right_lh(Dev& d, chase_c64* X, int64_t ldx, int64_t N, const chase_c64* L, int64_t ldl,
-                  int p, chase_c64* work);
-// One Lanczos three-term step on r independent runs (one CTA per run):
+template <class T>
+int trsm_right_lh(Dev& d, T* X, int64_t ldx, int64_t N, const T* L, int64_t ldl, int p, T* work);
+// One Lanczos three-term step on r independent runs (one CTA per run, run c
+// in column c of each N x r block, leading dimension ld):
 // alpha = Re(v^H w); w -= alpha v + beta_prev v_prev; beta = ||w||;
 // v_next = w / beta (zero when beta is rounding noise).  alpha/beta arrays
 // are indexed [step * r + run].
-int launch_lanczos_step(Dev& d, int64_t N, int r, int step, const chase_c64* Vj, const chase_c64* Vprev,
-                        chase_c64* W, chase_c64* Vnext, double* alpha, double* beta);
+template <class T>
+int launch_lanczos_step(Dev& d, int64_t N, int64_t ld, int r, int step, const T* Vj,
+                        const T* Vprev, T* W, T* Vnext, double* alpha, double* beta);
 // Normalise r columns in place (Lanczos start vectors).
-int launch_normalize_cols(Dev& d, chase_c64* X, int64_t ldx, int64_t N, int r);
+template <class T>
+int launch_normalize_cols(Dev& d, T* X, int64_t ldx, int64_t N, int r);
 // Fill the strict lower (lower=true) or upper part of a p x p matrix with zero.
-int launch_zero_triangle(Dev& d, chase_c64* A, int64_t lda, int p, bool lower);
+template <class T>
+int launch_zero_triangle(Dev& d, T* A, int64_t lda, int p, bool lower);
+// Real Gram product C = X^T Y (X N x p, Y N x q) on the FP64 tensor pipe.
+int dgram(Dev& d, int64_t N, const double* X, int64_t ldx, int p, const double* Y, int64_t ldy,
+          int q, double* C, int64_t ldc);
+inline int gram(Dev& d, int64_t N, const chase_c64* X, int64_t ldx, int p, const chase_c64* Y,
+                int64_t ldy, int q, chase_c64* C, int64_t ldc) {
+  return zgram(d, N, X, ldx, p, Y, ldy, q, C, ldc);
+}
+inline int gram(Dev& d, int64_t N, const double* X, int64_t ldx, int p, const double* Y,
+                int64_t ldy, int q, double* C, int64_t ldc) {
+  return dgram(d, N, X, ldx, p, Y, ldy, q, C, ldc);
+}
 
 // ---- zgemm_split.cu: split-BF16 filter product on the tensor cores --------
-// Slices of Ht = [Re H | Im H] (S planes of N x Kp bf16) and row exponents.
+// Slices of H (S planes of N x Kp bf16) and row exponents: complex H gives
+// Ht = [Re H | Im H] (Kp >= 2N), real symmetric H itself (Kp >= N).
 struct SplitH {
   void* A = nullptr;
   int* E = nullptr;
   double* Dg = nullptr;  // real diagonal of H, applied in FP64 by the epilogue
   int64_t N = 0, Kp = 0;
+  int cplx = 1;
 };
-// Slice workspace for up to max_cols complex columns of the filter block.
+// Slice workspace for up to max_cols columns of the filter block.
 struct SplitX {
   void* B = nullptr;
   int* F = nullptr;
   int cap_cols = 0;
+  int cplx = 1;
   void* P = nullptr;  // FP64 partial products of K segments (grow-only)
-  size_t P_cap = 0;   // in complex entries
+  size_t P_cap = 0;   // in units of 16 bytes
 };
 int split_prepare_h(Dev& d, const chase_c64* H, int64_t N, int64_t ldh, SplitH& out);
-int split_alloc_x(Dev& d, int64_t N, int max_cols, SplitX& out);
+int split_prepare_h(Dev& d, const double* H, int64_t N, int64_t ldh, SplitH& out);
+int split_alloc_x(Dev& d, int64_t N, int max_cols, SplitX& out, bool cplx = true);
 // C[:, j0:j1] = alpha (H X[:, j0:j1] - shift X[:, j0:j1]) + beta C[:, j0:j1]
 int zgemm_split(Dev& d, const SplitH& h, SplitX& x, const chase_c64* X, int64_t ldx, int j0, int j1,
                 chase_c64* C, int64_t ldc, double alpha, double beta, double shift);
+int zgemm_split(Dev& d, const SplitH& h, SplitX& x, const double* X, int64_t ldx, int j0, int j1,
+                double* C, int64_t ldc, double alpha, double beta, double shift);
 
 // ---- grouped filter: many independent problems per launch ----------------
 // One problem of a grouped filter, in device memory.  buf0 holds the block
@@ -209,6 +241,7 @@ int launch_grouped_permute(Dev& d, const GroupedPermute* probs, int P, int total
 
 // ---- eigh (cuSOLVER, the small projected eigensolve of Alg. 2 line 3) -----
 int eigh_device(Dev& d, chase_c64* G, int64_t ldg, int p, double* w_dev);
+int eigh_device(Dev& d, double* G, int64_t ldg, int p, double* w_dev);
 
 // ---- host_alg.cpp ----------------------------------------------------------
 // Symmetric tridiagonal eigenproblem (implicit QL with Wilkinson shifts):

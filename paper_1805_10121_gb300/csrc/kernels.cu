@@ -1,7 +1,10 @@
 // Supporting kernels of the ChASE iteration on sm_103a: Gram products for
 // the orthogonalisation and the Rayleigh quotient, the degree plan of the
-// filter, column permutations, norms, residuals, the small Cholesky and
-// triangular inverse of Cholesky QR, and the Lanczos three-term step.
+// filter, column permutations, norms, residuals, the blocked Cholesky and
+// triangular solve of Cholesky QR, and the Lanczos three-term step.  The
+// element kernels are templates over the scalar: complex128 (double2) for
+// Hermitian problems, double for real symmetric ones (Sec. 5.1: the library
+// is templated on the field as well as the precision).
 #include <cusolverDn.h>
 
 #include <algorithm>
@@ -38,6 +41,94 @@ __device__ double block_sum(double v, double* scratch /* >= 33 doubles */) {
   }
   __syncthreads();
   return scratch[32];
+}
+
+
+// Scalar arithmetic of the element kernels: complex128 or real double.
+template <class T>
+struct Sc;
+template <>
+struct Sc<double2> {
+  static __device__ __forceinline__ double2 zero() { return make_double2(0.0, 0.0); }
+  static __device__ __forceinline__ double2 real(double r) { return make_double2(r, 0.0); }
+  static __device__ __forceinline__ double re(double2 a) { return a.x; }
+  static __device__ __forceinline__ double abs2(double2 a) { return a.x * a.x + a.y * a.y; }
+  static __device__ __forceinline__ double2 scale(double2 a, double f) {
+    return make_double2(a.x * f, a.y * f);
+  }
+  static __device__ __forceinline__ double2 conj(double2 a) { return make_double2(a.x, -a.y); }
+  // acc - a conj(b)
+  static __device__ __forceinline__ double2 sub_mul_conj(double2 acc, double2 a, double2 b) {
+    acc.x -= a.x * b.x + a.y * b.y;
+    acc.y -= a.y * b.x - a.x * b.y;
+    return acc;
+  }
+  // Re(conj(a) b)
+  static __device__ __forceinline__ double re_dot(double2 a, double2 b) {
+    return a.x * b.x + a.y * b.y;
+  }
+  // a - f b
+  static __device__ __forceinline__ double2 sub_scaled(double2 a, double f, double2 b) {
+    return make_double2(a.x - f * b.x, a.y - f * b.y);
+  }
+  static __device__ __forceinline__ void add_re(double2& a, double v) { a.x += v; }
+  static __device__ __forceinline__ double2 add(double2 a, double2 b) {
+    return make_double2(a.x + b.x, a.y + b.y);
+  }
+  // (a, b) <- ((a + conj(b)) / 2, conj of that): entries (r, c) and (c, r)
+  static __device__ __forceinline__ void hermitize_pair(double2& a, double2& b) {
+    const double2 x = a, y = b;
+    const double re = 0.5 * (x.x + y.x), im = 0.5 * (x.y - y.y);
+    a = make_double2(re, im);
+    b = make_double2(re, -im);
+  }
+  static __device__ __forceinline__ void hermitize_diag(double2& a) { a.y = 0.0; }
+};
+template <>
+struct Sc<double> {
+  static __device__ __forceinline__ double zero() { return 0.0; }
+  static __device__ __forceinline__ double real(double r) { return r; }
+  static __device__ __forceinline__ double re(double a) { return a; }
+  static __device__ __forceinline__ double abs2(double a) { return a * a; }
+  static __device__ __forceinline__ double scale(double a, double f) { return a * f; }
+  static __device__ __forceinline__ double conj(double a) { return a; }
+  static __device__ __forceinline__ double sub_mul_conj(double acc, double a, double b) {
+    return acc - a * b;
+  }
+  static __device__ __forceinline__ double re_dot(double a, double b) { return a * b; }
+  static __device__ __forceinline__ double sub_scaled(double a, double f, double b) {
+    return a - f * b;
+  }
+  static __device__ __forceinline__ void add_re(double& a, double v) { a += v; }
+  static __device__ __forceinline__ double add(double a, double b) { return a + b; }
+  static __device__ __forceinline__ void hermitize_pair(double& a, double& b) {
+    const double m = 0.5 * (a + b);
+    a = m;
+    b = m;
+  }
+  static __device__ __forceinline__ void hermitize_diag(double&) {}
+};
+
+// Device element type of a host scalar type.
+template <class T>
+struct Dv;
+template <>
+struct Dv<chase_c64> {
+  using type = double2;
+};
+template <>
+struct Dv<double> {
+  using type = double;
+};
+template <class T>
+using elem_t = typename Dv<T>::type;
+template <class T>
+elem_t<T>* dp(T* p) {
+  return reinterpret_cast<elem_t<T>*>(p);
+}
+template <class T>
+const elem_t<T>* dp(const T* p) {
+  return reinterpret_cast<const elem_t<T>*>(p);
 }
 
 // ---------------------------------------------------------------------------
@@ -116,19 +207,70 @@ __global__ void __launch_bounds__(128)
       }
 }
 
-__global__ void sum_partials_kernel(const double2* __restrict__ P, int p, int q, int nsplit,
-                                    long long pstride, double2* __restrict__ C, long long ldc) {
+// Real Gram product C = X^T Y: one DMMA per fragment.
+__global__ void __launch_bounds__(128)
+    gram_real_kernel(const double* __restrict__ X, long long ldx, int p, const double* __restrict__ Y,
+                     long long ldy, int q, long long N, long long kchunk, double* __restrict__ P,
+                     long long ldp, long long pstride) {
+  __shared__ double sX[GT][GK + 1];
+  __shared__ double sY[GT][GK + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int wm = warp & 1, wn = warp >> 1;  // 2 x 2 warps, 16 x 16 each
+  const int p0 = blockIdx.x * GT, q0 = blockIdx.y * GT;
+  const long long kbeg = blockIdx.z * kchunk;
+  const long long kend = min(N, kbeg + kchunk);
+  double acc[2][2][2] = {};
+  for (long long k0 = kbeg; k0 < kend; k0 += GK) {
+    for (int e = threadIdx.x; e < GT * GK; e += 128) {
+      const int col = e / GK, kk = e % GK;
+      const long long k = k0 + kk;
+      double xv = 0.0, yv = 0.0;
+      if (k < kend) {
+        if (p0 + col < p) xv = X[(long long)(p0 + col) * ldx + k];
+        if (q0 + col < q) yv = Y[(long long)(q0 + col) * ldy + k];
+      }
+      sX[col][kk] = xv;
+      sY[col][kk] = yv;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; kk += 4) {
+      double a[2], b[2];
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi) a[mi] = sX[wm * 16 + mi * 8 + g][kk + t];
+#pragma unroll
+      for (int ni = 0; ni < 2; ++ni) b[ni] = sY[wn * 16 + ni * 8 + g][kk + t];
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 2; ++ni) dmma_8x8x4(acc[mi][ni][0], acc[mi][ni][1], a[mi], b[ni]);
+    }
+    __syncthreads();
+  }
+  double* Pz = P + blockIdx.z * pstride;
+#pragma unroll
+  for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int r = p0 + wm * 16 + mi * 8 + g;
+        const int c = q0 + wn * 16 + ni * 8 + 2 * t + h;
+        if (r < p && c < q) Pz[(long long)c * ldp + r] = acc[mi][ni][h];
+      }
+}
+
+template <class T>
+__global__ void sum_partials_kernel(const T* __restrict__ P, int p, int q, int nsplit,
+                                    long long pstride, T* __restrict__ C, long long ldc) {
   const long long n = (long long)p * q;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
-    double sr = 0.0, si = 0.0;
-    for (int z = 0; z < nsplit; ++z) {
-      const double2 v = P[z * pstride + e];
-      sr += v.x;
-      si += v.y;
-    }
+    T acc = Sc<T>::zero();
+    for (int z = 0; z < nsplit; ++z) acc = Sc<T>::add(acc, P[z * pstride + e]);
     const long long r = e % p, c = e / p;
-    C[c * ldc + r] = make_double2(sr, si);
+    C[c * ldc + r] = acc;
   }
 }
 
@@ -197,9 +339,10 @@ __global__ void filter_plan_kernel(const int* __restrict__ deg, int b, int max_a
 // ---------------------------------------------------------------------------
 // Column permutations, norms, scaling, residuals
 // ---------------------------------------------------------------------------
-__global__ void permute_cols_kernel(const double2* __restrict__ X, long long ldx,
-                                    double2* __restrict__ Y, long long ldy, long long N,
-                                    const int* __restrict__ perm, int scatter) {
+template <class T>
+__global__ void permute_cols_kernel(const T* __restrict__ X, long long ldx, T* __restrict__ Y,
+                                    long long ldy, long long N, const int* __restrict__ perm,
+                                    int scatter) {
   const int j = blockIdx.y;
   const int src = scatter ? j : perm[j];
   const int dst = scatter ? perm[j] : j;
@@ -225,103 +368,94 @@ __global__ void grouped_permute_kernel(const GroupedPermute* __restrict__ probs,
   for (int i = threadIdx.x; i < pr.n; i += blockDim.x) y[i] = x[i];
 }
 
-__global__ void __launch_bounds__(kRed) col_norms_kernel(const double2* __restrict__ X, long long ldx,
+template <class T>
+__global__ void __launch_bounds__(kRed) col_norms_kernel(const T* __restrict__ X, long long ldx,
                                                          long long N, double* __restrict__ out) {
   __shared__ double scratch[33];
-  const double2* x = X + (long long)blockIdx.x * ldx;
+  const T* x = X + (long long)blockIdx.x * ldx;
   double s = 0.0;
-  for (long long i = threadIdx.x; i < N; i += blockDim.x) {
-    const double2 v = x[i];
-    s += v.x * v.x + v.y * v.y;
-  }
+  for (long long i = threadIdx.x; i < N; i += blockDim.x) s += Sc<T>::abs2(x[i]);
   s = block_sum(s, scratch);
   if (threadIdx.x == 0) out[blockIdx.x] = sqrt(s);
 }
 
-__global__ void col_inv_scale_kernel(double2* __restrict__ X, long long ldx, long long N,
+template <class T>
+__global__ void col_inv_scale_kernel(T* __restrict__ X, long long ldx, long long N,
                                      const double* __restrict__ s) {
   const int j = blockIdx.y;
   const double sj = s[j];
   if (sj == 0.0) return;
   const double f = 1.0 / sj;
-  double2* x = X + (long long)j * ldx;
+  T* x = X + (long long)j * ldx;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
-       i += (long long)gridDim.x * blockDim.x) {
-    const double2 v = x[i];
-    x[i] = make_double2(v.x * f, v.y * f);
-  }
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] = Sc<T>::scale(x[i], f);
 }
 
+template <class T>
 __global__ void __launch_bounds__(kRed)
-    resid_norms_kernel(const double2* __restrict__ HV, long long ldhv, const double2* __restrict__ V,
+    resid_norms_kernel(const T* __restrict__ HV, long long ldhv, const T* __restrict__ V,
                        long long ldv, long long N, const double* __restrict__ lam,
                        double* __restrict__ res) {
   __shared__ double scratch[33];
   const int j = blockIdx.x;
   const double l = lam[j];
-  const double2* hv = HV + (long long)j * ldhv;
-  const double2* v = V + (long long)j * ldv;
+  const T* hv = HV + (long long)j * ldhv;
+  const T* v = V + (long long)j * ldv;
   double s = 0.0;
-  for (long long i = threadIdx.x; i < N; i += blockDim.x) {
-    const double2 a = hv[i], b = v[i];
-    const double dr = a.x - l * b.x, di = a.y - l * b.y;
-    s += dr * dr + di * di;
-  }
+  for (long long i = threadIdx.x; i < N; i += blockDim.x)
+    s += Sc<T>::abs2(Sc<T>::sub_scaled(hv[i], l, v[i]));
   s = block_sum(s, scratch);
   if (threadIdx.x == 0) res[j] = sqrt(s);
 }
 
-__global__ void hermitize_kernel(double2* __restrict__ G, long long ldg, int p) {
+template <class T>
+__global__ void hermitize_kernel(T* __restrict__ G, long long ldg, int p) {
   const long long n = (long long)p * p;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(e % p), c = (int)(e / p);
     if (r > c) continue;
-    double2* a = G + (long long)c * ldg + r;  // (r, c), upper
-    double2* b = G + (long long)r * ldg + c;  // (c, r), lower
-    if (r == c) {
-      a->y = 0.0;
-      continue;
-    }
-    const double2 x = *a, y = *b;
-    const double re = 0.5 * (x.x + y.x), im = 0.5 * (x.y - y.y);
-    *a = make_double2(re, im);
-    *b = make_double2(re, -im);
+    T* a = G + (long long)c * ldg + r;  // (r, c), upper
+    T* b = G + (long long)r * ldg + c;  // (c, r), lower
+    if (r == c)
+      Sc<T>::hermitize_diag(*a);
+    else
+      Sc<T>::hermitize_pair(*a, *b);
   }
 }
 
-__global__ void zero_triangle_kernel(double2* __restrict__ A, long long lda, int p, int lower) {
+template <class T>
+__global__ void zero_triangle_kernel(T* __restrict__ A, long long lda, int p, int lower) {
   const long long n = (long long)p * p;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(e % p), c = (int)(e / p);
-    if (lower ? (r > c) : (r < c)) A[(long long)c * lda + r] = make_double2(0.0, 0.0);
+    if (lower ? (r > c) : (r < c)) A[(long long)c * lda + r] = Sc<T>::zero();
   }
 }
 
 // ---------------------------------------------------------------------------
 // Cholesky (left-looking, one CTA) and triangular inverse
 // ---------------------------------------------------------------------------
+template <class T>
 __global__ void __launch_bounds__(1024)
-    cholesky_kernel(double2* __restrict__ G, long long ld, int p, double rel_tol, double shift,
+    cholesky_kernel(T* __restrict__ G, long long ld, int p, double rel_tol, double shift,
                     const double* __restrict__ diag_ref, int* __restrict__ err) {
   __shared__ double scratch[33];
   __shared__ double s_ljj;
   __shared__ int s_fail;
   if (threadIdx.x == 0) s_fail = 0;
   if (shift != 0.0)
-    for (int j = threadIdx.x; j < p; j += blockDim.x) G[(long long)j * ld + j].x += shift;
+    for (int j = threadIdx.x; j < p; j += blockDim.x) Sc<T>::add_re(G[(long long)j * ld + j], shift);
   __syncthreads();
   for (int j = 0; j < p; ++j) {
     // pivot: d = G_jj - sum_k |L_jk|^2
     double part = 0.0;
-    for (int k = threadIdx.x; k < j; k += blockDim.x) {
-      const double2 l = G[(long long)k * ld + j];
-      part += l.x * l.x + l.y * l.y;
-    }
+    for (int k = threadIdx.x; k < j; k += blockDim.x) part += Sc<T>::abs2(G[(long long)k * ld + j]);
     part = block_sum(part, scratch);
     if (threadIdx.x == 0) {
-      const double gjj = G[(long long)j * ld + j].x;
+      const double gjj = Sc<T>::re(G[(long long)j * ld + j]);
       const double dj = gjj - part;
       const double ref = diag_ref ? diag_ref[j] : gjj;
       const bool bad = !(dj > rel_tol * fabs(ref)) || !isfinite(dj);
@@ -330,21 +464,16 @@ __global__ void __launch_bounds__(1024)
         atomicOr(err, KERR_CHOL_BREAKDOWN);
       }
       s_ljj = bad ? 1.0 : sqrt(dj);
-      G[(long long)j * ld + j] = make_double2(s_ljj, 0.0);
+      G[(long long)j * ld + j] = Sc<T>::real(s_ljj);
     }
     __syncthreads();
     if (s_fail) return;
     const double inv = 1.0 / s_ljj;
     for (int i = j + 1 + threadIdx.x; i < p; i += blockDim.x) {
-      double2 acc = G[(long long)j * ld + i];
-      for (int k = 0; k < j; ++k) {
-        const double2 lik = G[(long long)k * ld + i];
-        const double2 ljk = G[(long long)k * ld + j];
-        // acc -= lik * conj(ljk)
-        acc.x -= lik.x * ljk.x + lik.y * ljk.y;
-        acc.y -= lik.y * ljk.x - lik.x * ljk.y;
-      }
-      G[(long long)j * ld + i] = make_double2(acc.x * inv, acc.y * inv);
+      T acc = G[(long long)j * ld + i];
+      for (int k = 0; k < j; ++k)  // acc -= L_ik conj(L_jk)
+        acc = Sc<T>::sub_mul_conj(acc, G[(long long)k * ld + i], G[(long long)k * ld + j]);
+      G[(long long)j * ld + i] = Sc<T>::scale(acc, inv);
     }
     __syncthreads();
   }
@@ -353,92 +482,79 @@ __global__ void __launch_bounds__(1024)
 // Rows of X (nrows x kb, leading dimension ldx) are replaced by the solution y
 // of y L^H = x, with L the kb x kb lower factor at (Lp, ldl): thread per row,
 // y_j = (x_j - sum_{m<j} y_m conj(L_jm)) / L_jj.  kb <= 32.
+template <class T>
 __global__ void __launch_bounds__(128)
-    row_trsm_lh_kernel(double2* __restrict__ X, long long ldx, long long nrows,
-                       const double2* __restrict__ Lp, long long ldl, int kb) {
-  __shared__ double2 sL[32][33];
+    row_trsm_lh_kernel(T* __restrict__ X, long long ldx, long long nrows, const T* __restrict__ Lp,
+                       long long ldl, int kb) {
+  __shared__ T sL[32][33];
   for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
     const int r = e % kb, c = e / kb;
-    sL[r][c] = r >= c ? Lp[(long long)c * ldl + r] : make_double2(0.0, 0.0);
+    sL[r][c] = r >= c ? Lp[(long long)c * ldl + r] : Sc<T>::zero();
   }
   __syncthreads();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nrows;
        i += (long long)gridDim.x * blockDim.x) {
-    double2 y[32];
+    T y[32];
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
       if (j >= kb) break;
-      double2 a = X[(long long)j * ldx + i];
-      for (int m = 0; m < j; ++m) {
-        const double2 l = sL[j][m];
-        // a -= y_m * conj(l)
-        a.x -= y[m].x * l.x + y[m].y * l.y;
-        a.y -= y[m].y * l.x - y[m].x * l.y;
-      }
-      const double inv = 1.0 / sL[j][j].x;
-      y[j] = make_double2(a.x * inv, a.y * inv);
+      T a = X[(long long)j * ldx + i];
+      for (int m = 0; m < j; ++m) a = Sc<T>::sub_mul_conj(a, y[m], sL[j][m]);
+      y[j] = Sc<T>::scale(a, 1.0 / Sc<T>::re(sL[j][j]));
       X[(long long)j * ldx + i] = y[j];
     }
   }
 }
 
 // dst (cols x rows, leading dimension ldd) = conj(src)^T, src rows x cols (lds)
-__global__ void conj_transpose_kernel(const double2* __restrict__ src, long long lds, int rows,
-                                      int cols, double2* __restrict__ dst, long long ldd) {
+template <class T>
+__global__ void conj_transpose_kernel(const T* __restrict__ src, long long lds, int rows, int cols,
+                                      T* __restrict__ dst, long long ldd) {
   const long long n = (long long)rows * cols;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(e % rows), c = (int)(e / rows);
-    const double2 v = src[(long long)c * lds + r];
-    dst[(long long)r * ldd + c] = make_double2(v.x, -v.y);
+    dst[(long long)r * ldd + c] = Sc<T>::conj(src[(long long)c * lds + r]);
   }
 }
 
-__global__ void copy_diag_kernel(const double2* __restrict__ G, long long ld, int p,
+template <class T>
+__global__ void copy_diag_kernel(const T* __restrict__ G, long long ld, int p,
                                  double* __restrict__ out, double shift) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < p; j += gridDim.x * blockDim.x)
-    out[j] = G[(long long)j * ld + j].x + shift;
+    out[j] = Sc<T>::re(G[(long long)j * ld + j]) + shift;
 }
 
-__global__ void add_diag_kernel(double2* __restrict__ G, long long ld, int p, double shift) {
+template <class T>
+__global__ void add_diag_kernel(T* __restrict__ G, long long ld, int p, double shift) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < p; j += gridDim.x * blockDim.x)
-    G[(long long)j * ld + j].x += shift;
+    Sc<T>::add_re(G[(long long)j * ld + j], shift);
 }
 
 // ---------------------------------------------------------------------------
 // Lanczos
 // ---------------------------------------------------------------------------
+template <class T>
 __global__ void __launch_bounds__(kRed)
-    lanczos_step_kernel(long long N, int r, int step, const double2* __restrict__ Vj,
-                        const double2* __restrict__ Vprev, double2* __restrict__ W,
-                        double2* __restrict__ Vnext, double* __restrict__ alpha,
-                        double* __restrict__ beta) {
+    lanczos_step_kernel(long long N, long long ld, int r, int step, const T* __restrict__ Vj,
+                        const T* __restrict__ Vprev, T* __restrict__ W, T* __restrict__ Vnext,
+                        double* __restrict__ alpha, double* __restrict__ beta) {
   __shared__ double scratch[33];
   const int c = blockIdx.x;
-  const double2* v = Vj + (long long)c * N;
-  double2* w = W + (long long)c * N;
+  const T* v = Vj + (long long)c * ld;
+  T* w = W + (long long)c * ld;
   // alpha = Re(v^H w)
   double s = 0.0;
-  for (long long i = threadIdx.x; i < N; i += blockDim.x) {
-    const double2 a = v[i], b = w[i];
-    s += a.x * b.x + a.y * b.y;
-  }
+  for (long long i = threadIdx.x; i < N; i += blockDim.x) s += Sc<T>::re_dot(v[i], w[i]);
   const double al = block_sum(s, scratch);
   const double bprev = step > 0 ? beta[(step - 1) * r + c] : 0.0;
-  const double2* vp = step > 0 ? Vprev + (long long)c * N : nullptr;
+  const T* vp = step > 0 ? Vprev + (long long)c * ld : nullptr;
   double nrm = 0.0;
   for (long long i = threadIdx.x; i < N; i += blockDim.x) {
-    const double2 a = v[i];
-    double2 b = w[i];
-    b.x -= al * a.x;
-    b.y -= al * a.y;
-    if (vp) {
-      const double2 pv = vp[i];
-      b.x -= bprev * pv.x;
-      b.y -= bprev * pv.y;
-    }
+    T b = Sc<T>::sub_scaled(w[i], al, v[i]);
+    if (vp) b = Sc<T>::sub_scaled(b, bprev, vp[i]);
     w[i] = b;
-    nrm += b.x * b.x + b.y * b.y;
+    nrm += Sc<T>::abs2(b);
   }
   const double be = sqrt(block_sum(nrm, scratch));
   // beta is rounding noise once the Krylov space is invariant: stop the run
@@ -450,30 +566,22 @@ __global__ void __launch_bounds__(kRed)
     beta[step * r + c] = be;
   }
   if (Vnext) {
-    double2* vn = Vnext + (long long)c * N;
+    T* vn = Vnext + (long long)c * ld;
     const double f = stop ? 0.0 : 1.0 / be;
-    for (long long i = threadIdx.x; i < N; i += blockDim.x) {
-      const double2 b = w[i];
-      vn[i] = make_double2(b.x * f, b.y * f);
-    }
+    for (long long i = threadIdx.x; i < N; i += blockDim.x) vn[i] = Sc<T>::scale(w[i], f);
   }
 }
 
-__global__ void __launch_bounds__(kRed) normalize_cols_kernel(double2* __restrict__ X, long long ldx,
+template <class T>
+__global__ void __launch_bounds__(kRed) normalize_cols_kernel(T* __restrict__ X, long long ldx,
                                                               long long N) {
   __shared__ double scratch[33];
-  double2* x = X + (long long)blockIdx.x * ldx;
+  T* x = X + (long long)blockIdx.x * ldx;
   double s = 0.0;
-  for (long long i = threadIdx.x; i < N; i += blockDim.x) {
-    const double2 v = x[i];
-    s += v.x * v.x + v.y * v.y;
-  }
+  for (long long i = threadIdx.x; i < N; i += blockDim.x) s += Sc<T>::abs2(x[i]);
   s = block_sum(s, scratch);
   const double f = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
-  for (long long i = threadIdx.x; i < N; i += blockDim.x) {
-    const double2 v = x[i];
-    x[i] = make_double2(v.x * f, v.y * f);
-  }
+  for (long long i = threadIdx.x; i < N; i += blockDim.x) x[i] = Sc<T>::scale(x[i], f);
 }
 
 unsigned grid_for(long long n, int threads, unsigned cap = 65535u) {
@@ -487,39 +595,63 @@ unsigned grid_for(long long n, int threads, unsigned cap = 65535u) {
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
+namespace {
+// Gram launch shape: split K so that the grid covers the 152 SMs about four times.
+void gram_shape(int64_t N, int p, int q, dim3* grid, long long* kchunk, long long* nsplit) {
+  const int tp = (p + GT - 1) / GT, tq = (q + GT - 1) / GT;
+  long long ns = std::max<long long>(1, (4 * 152) / std::max(1, tp * tq));
+  ns = std::min<long long>(ns, std::max<long long>(1, N / 256));
+  long long kc = (N + ns - 1) / ns;
+  kc = ((kc + GK - 1) / GK) * GK;
+  ns = (N + kc - 1) / kc;
+  if (ns < 1) ns = 1;
+  *grid = dim3(tp, tq, static_cast<unsigned>(ns));
+  *kchunk = kc;
+  *nsplit = ns;
+}
+
+template <class T>
+int gram_impl(Dev& d, int64_t N, const T* X, int64_t ldx, int p, const T* Y, int64_t ldy, int q,
+              T* C, int64_t ldc) {
+  if (p == 0 || q == 0) return CHASE_OK;
+  using D = elem_t<T>;
+  dim3 grid;
+  long long kchunk = 0, nsplit = 1;
+  gram_shape(N, p, q, &grid, &kchunk, &nsplit);
+  D* out = dp(C);
+  long long ldo = ldc, pstride = 0;
+  D* P = nullptr;
+  if (nsplit > 1) {
+    pstride = (long long)p * q;
+    CHASE_TRY(d.alloc(&P, static_cast<size_t>(pstride * nsplit)));
+    out = P;
+    ldo = p;
+  }
+  if constexpr (sizeof(D) == 16)
+    gram_kernel<<<grid, 128, 0, d.st>>>(dp(X), ldx, p, dp(Y), ldy, q, N, kchunk, out, ldo, pstride);
+  else
+    gram_real_kernel<<<grid, 128, 0, d.st>>>(dp(X), ldx, p, dp(Y), ldy, q, N, kchunk, out, ldo,
+                                             pstride);
+  note_launch();
+  CHASE_CUDA(cudaGetLastError());
+  if (nsplit > 1) {
+    sum_partials_kernel<D><<<grid_for(pstride, 256, 4096), 256, 0, d.st>>>(
+        P, p, q, static_cast<int>(nsplit), pstride, dp(C), ldc);
+    note_launch();
+    CHASE_CUDA(cudaGetLastError());
+  }
+  return CHASE_OK;
+}
+}  // namespace
+
 int zgram(Dev& d, int64_t N, const chase_c64* X, int64_t ldx, int p, const chase_c64* Y,
           int64_t ldy, int q, chase_c64* C, int64_t ldc) {
-  if (p == 0 || q == 0) return CHASE_OK;
-  const int tp = (p + GT - 1) / GT, tq = (q + GT - 1) / GT;
-  // split K so that the grid covers the 152 SMs about four times
-  long long nsplit = std::max<long long>(1, (4 * 152) / std::max(1, tp * tq));
-  nsplit = std::min<long long>(nsplit, std::max<long long>(1, N / 256));
-  long long kchunk = (N + nsplit - 1) / nsplit;
-  kchunk = ((kchunk + GK - 1) / GK) * GK;
-  nsplit = (N + kchunk - 1) / kchunk;
-  if (nsplit < 1) nsplit = 1;
-  dim3 grid(tp, tq, static_cast<unsigned>(nsplit));
-  if (nsplit == 1) {
-    gram_kernel<<<grid, 128, 0, d.st>>>(reinterpret_cast<const double2*>(X), ldx, p,
-                                        reinterpret_cast<const double2*>(Y), ldy, q, N, kchunk,
-                                        reinterpret_cast<double2*>(C), ldc, 0);
-    note_launch();
-  CHASE_CUDA(cudaGetLastError());
-    return CHASE_OK;
-  }
-  double2* P = nullptr;
-  const long long pstride = (long long)p * q;
-  CHASE_TRY(d.alloc(&P, static_cast<size_t>(pstride * nsplit)));
-  gram_kernel<<<grid, 128, 0, d.st>>>(reinterpret_cast<const double2*>(X), ldx, p,
-                                      reinterpret_cast<const double2*>(Y), ldy, q, N, kchunk, P, p,
-                                      pstride);
-  note_launch();
-  CHASE_CUDA(cudaGetLastError());
-  sum_partials_kernel<<<grid_for(pstride, 256, 4096), 256, 0, d.st>>>(
-      P, p, q, static_cast<int>(nsplit), pstride, reinterpret_cast<double2*>(C), ldc);
-  note_launch();
-  CHASE_CUDA(cudaGetLastError());
-  return CHASE_OK;
+  return gram_impl(d, N, X, ldx, p, Y, ldy, q, C, ldc);
+}
+
+int dgram(Dev& d, int64_t N, const double* X, int64_t ldx, int p, const double* Y, int64_t ldy,
+          int q, double* C, int64_t ldc) {
+  return gram_impl(d, N, X, ldx, p, Y, ldy, q, C, ldc);
 }
 
 int launch_filter_plan(Dev& d, const int* deg, int b, int max_allowed, int* perm, int* start,
@@ -540,184 +672,255 @@ int launch_grouped_permute(Dev& d, const GroupedPermute* probs, int P, int total
   return CHASE_OK;
 }
 
-int launch_permute_cols(Dev& d, const chase_c64* X, int64_t ldx, chase_c64* Y, int64_t ldy,
-                        int64_t N, int b, const int* perm, bool scatter) {
+template <class T>
+int launch_permute_cols(Dev& d, const T* X, int64_t ldx, T* Y, int64_t ldy, int64_t N, int b,
+                        const int* perm, bool scatter) {
   if (b == 0 || N == 0) return CHASE_OK;
   if (b > 65535) {
     set_error("permute: too many columns");
     return CHASE_INVALID_ARG;
   }
   dim3 grid(grid_for(N, 256, 64), b);
-  permute_cols_kernel<<<grid, 256, 0, d.st>>>(reinterpret_cast<const double2*>(X), ldx,
-                                              reinterpret_cast<double2*>(Y), ldy, N, perm,
-                                              scatter ? 1 : 0);
+  permute_cols_kernel<<<grid, 256, 0, d.st>>>(dp(X), ldx, dp(Y), ldy, N, perm, scatter ? 1 : 0);
   note_launch();
   CHASE_CUDA(cudaGetLastError());
   return CHASE_OK;
 }
 
-int launch_col_norms(Dev& d, const chase_c64* X, int64_t ldx, int64_t N, int b, double* out) {
+template <class T>
+int launch_col_norms(Dev& d, const T* X, int64_t ldx, int64_t N, int b, double* out) {
   if (b == 0) return CHASE_OK;
-  col_norms_kernel<<<b, kRed, 0, d.st>>>(reinterpret_cast<const double2*>(X), ldx, N, out);
+  col_norms_kernel<<<b, kRed, 0, d.st>>>(dp(X), ldx, N, out);
   note_launch();
   CHASE_CUDA(cudaGetLastError());
   return CHASE_OK;
 }
 
-int launch_col_inv_scale(Dev& d, chase_c64* X, int64_t ldx, int64_t N, int b, const double* s) {
+template <class T>
+int launch_col_inv_scale(Dev& d, T* X, int64_t ldx, int64_t N, int b, const double* s) {
   if (b == 0 || N == 0) return CHASE_OK;
   if (b > 65535) {
     set_error("column scaling: too many columns");
     return CHASE_INVALID_ARG;
   }
   dim3 grid(grid_for(N, 256, 64), b);
-  col_inv_scale_kernel<<<grid, 256, 0, d.st>>>(reinterpret_cast<double2*>(X), ldx, N, s);
+  col_inv_scale_kernel<<<grid, 256, 0, d.st>>>(dp(X), ldx, N, s);
   note_launch();
   CHASE_CUDA(cudaGetLastError());
   return CHASE_OK;
 }
 
-int launch_resid_norms(Dev& d, const chase_c64* HV, int64_t ldhv, const chase_c64* V, int64_t ldv,
-                       int64_t N, int b, const double* lam, double* res) {
+template <class T>
+int launch_resid_norms(Dev& d, const T* HV, int64_t ldhv, const T* V, int64_t ldv, int64_t N, int b,
+                       const double* lam, double* res) {
   if (b == 0) return CHASE_OK;
-  resid_norms_kernel<<<b, kRed, 0, d.st>>>(reinterpret_cast<const double2*>(HV), ldhv,
-                                           reinterpret_cast<const double2*>(V), ldv, N, lam, res);
+  resid_norms_kernel<<<b, kRed, 0, d.st>>>(dp(HV), ldhv, dp(V), ldv, N, lam, res);
   note_launch();
   CHASE_CUDA(cudaGetLastError());
   return CHASE_OK;
 }
 
-int launch_hermitize(Dev& d, chase_c64* G, int64_t ldg, int p) {
+template <class T>
+int launch_hermitize(Dev& d, T* G, int64_t ldg, int p) {
   if (p == 0) return CHASE_OK;
-  hermitize_kernel<<<grid_for((long long)p * p, 256, 4096), 256, 0, d.st>>>(
-      reinterpret_cast<double2*>(G), ldg, p);
+  hermitize_kernel<<<grid_for((long long)p * p, 256, 4096), 256, 0, d.st>>>(dp(G), ldg, p);
   note_launch();
   CHASE_CUDA(cudaGetLastError());
   return CHASE_OK;
 }
 
-int launch_zero_triangle(Dev& d, chase_c64* A, int64_t lda, int p, bool lower) {
+template <class T>
+int launch_zero_triangle(Dev& d, T* A, int64_t lda, int p, bool lower) {
   if (p == 0) return CHASE_OK;
-  zero_triangle_kernel<<<grid_for((long long)p * p, 256, 4096), 256, 0, d.st>>>(
-      reinterpret_cast<double2*>(A), lda, p, lower ? 1 : 0);
+  zero_triangle_kernel<<<grid_for((long long)p * p, 256, 4096), 256, 0, d.st>>>(dp(A), lda, p,
+                                                                                 lower ? 1 : 0);
   note_launch();
   CHASE_CUDA(cudaGetLastError());
   return CHASE_OK;
 }
 
-int launch_cholesky(Dev& d, chase_c64* G, int64_t ldg, int p, double rel_tol, double shift) {
+template <class T>
+int launch_cholesky(Dev& d, T* G, int64_t ldg, int p, double rel_tol, double shift) {
   if (p == 0) return CHASE_OK;
-  cholesky_kernel<<<1, 1024, 0, d.st>>>(reinterpret_cast<double2*>(G), ldg, p, rel_tol, shift,
-                                        nullptr, d.err);
+  cholesky_kernel<<<1, 1024, 0, d.st>>>(dp(G), ldg, p, rel_tol, shift, nullptr, d.err);
   note_launch();
   CHASE_CUDA(cudaGetLastError());
   return CHASE_OK;
 }
 
-int launch_row_trsm_lh(Dev& d, chase_c64* X, int64_t ldx, int64_t nrows, const chase_c64* L,
-                       int64_t ldl, int kb) {
+namespace {
+template <class T>
+int launch_row_trsm_lh(Dev& d, T* X, int64_t ldx, int64_t nrows, const T* L, int64_t ldl, int kb) {
   if (nrows <= 0 || kb <= 0) return CHASE_OK;
   if (kb > 32) {
     set_error("row_trsm: block wider than 32");
     return CHASE_INVALID_ARG;
   }
-  row_trsm_lh_kernel<<<grid_for(nrows, 128, 152 * 8), 128, 0, d.st>>>(
-      reinterpret_cast<double2*>(X), ldx, nrows, reinterpret_cast<const double2*>(L), ldl, kb);
+  row_trsm_lh_kernel<<<grid_for(nrows, 128, 152 * 8), 128, 0, d.st>>>(dp(X), ldx, nrows, dp(L),
+                                                                       ldl, kb);
   note_launch();
   CHASE_CUDA(cudaGetLastError());
   return CHASE_OK;
 }
 
-int launch_conj_transpose(Dev& d, const chase_c64* src, int64_t lds, int rows, int cols,
-                          chase_c64* dst, int64_t ldd) {
+template <class T>
+int launch_conj_transpose(Dev& d, const T* src, int64_t lds, int rows, int cols, T* dst,
+                          int64_t ldd) {
   if (rows <= 0 || cols <= 0) return CHASE_OK;
   conj_transpose_kernel<<<grid_for((long long)rows * cols, 256, 4096), 256, 0, d.st>>>(
-      reinterpret_cast<const double2*>(src), lds, rows, cols, reinterpret_cast<double2*>(dst),
-      ldd);
+      dp(src), lds, rows, cols, dp(dst), ldd);
   note_launch();
   CHASE_CUDA(cudaGetLastError());
   return CHASE_OK;
 }
+}  // namespace
 
 // Blocked right-looking Cholesky G = L L^H (lower, in place), 32-wide panels:
 // the diagonal block by the one-CTA kernel, the panel below it by row
 // triangular solves, the trailing matrix by the FP64 tensor-pipe GEMM.  The
 // pivot test compares against the diagonal of G + shift before any update.
-int cholesky_blocked(Dev& d, chase_c64* G, int64_t ldg, int p, double rel_tol, double shift,
-                     double* diag_ref, chase_c64* work /* >= 32 * p */) {
+template <class T>
+int cholesky_blocked(Dev& d, T* G, int64_t ldg, int p, double rel_tol, double shift,
+                     double* diag_ref, T* work /* >= 32 * p */) {
   if (p == 0) return CHASE_OK;
   constexpr int nb = 32;
-  copy_diag_kernel<<<grid_for(p, 256, 64), 256, 0, d.st>>>(reinterpret_cast<double2*>(G), ldg, p,
-                                                           diag_ref, shift);
+  copy_diag_kernel<<<grid_for(p, 256, 64), 256, 0, d.st>>>(dp(G), ldg, p, diag_ref, shift);
   note_launch();
   if (shift != 0.0) {
-    add_diag_kernel<<<grid_for(p, 256, 64), 256, 0, d.st>>>(reinterpret_cast<double2*>(G), ldg, p,
-                                                            shift);
+    add_diag_kernel<<<grid_for(p, 256, 64), 256, 0, d.st>>>(dp(G), ldg, p, shift);
     note_launch();
   }
   CHASE_CUDA(cudaGetLastError());
   for (int k0 = 0; k0 < p; k0 += nb) {
     const int kb = std::min(nb, p - k0);
-    chase_c64* Akk = G + static_cast<size_t>(k0) * ldg + k0;
-    cholesky_kernel<<<1, 1024, 0, d.st>>>(reinterpret_cast<double2*>(Akk), ldg, kb, rel_tol, 0.0,
-                                          diag_ref + k0, d.err);
+    T* Akk = G + static_cast<size_t>(k0) * ldg + k0;
+    cholesky_kernel<<<1, 1024, 0, d.st>>>(dp(Akk), ldg, kb, rel_tol, 0.0, diag_ref + k0, d.err);
     note_launch();
     CHASE_CUDA(cudaGetLastError());
     const int m = p - k0 - kb;
     if (m <= 0) break;
-    chase_c64* Pn = Akk + kb;  // panel rows k0+kb .. p-1, columns k0 .. k0+kb-1
+    T* Pn = Akk + kb;  // panel rows k0+kb .. p-1, columns k0 .. k0+kb-1
     CHASE_TRY(launch_row_trsm_lh(d, Pn, ldg, m, Akk, ldg, kb));
     // trailing A22 -= Pn Pn^H
     CHASE_TRY(launch_conj_transpose(d, Pn, ldg, m, kb, work, kb));
-    chase_c64* A22 = Akk + static_cast<size_t>(kb) * ldg + kb;
-    CHASE_TRY(zgemm(d, m, kb, Pn, ldg, work, kb, m, A22, ldg, 0, m, -1.0, 1.0, 0.0));
+    T* A22 = Akk + static_cast<size_t>(kb) * ldg + kb;
+    CHASE_TRY(gemm(d, m, kb, Pn, ldg, work, kb, m, A22, ldg, 0, m, -1.0, 1.0, 0.0));
   }
   return CHASE_OK;
 }
 
 // X (N x p) <- X L^-H with L the lower Cholesky factor (p x p): blocked
 // right-side triangular solve, column blocks of 32.
-int trsm_right_lh(Dev& d, chase_c64* X, int64_t ldx, int64_t N, const chase_c64* L, int64_t ldl,
-                  int p, chase_c64* work /* >= 32 * p */) {
+template <class T>
+int trsm_right_lh(Dev& d, T* X, int64_t ldx, int64_t N, const T* L, int64_t ldl, int p,
+                  T* work /* >= 32 * p */) {
   constexpr int nb = 32;
   for (int k0 = 0; k0 < p; k0 += nb) {
     const int kb = std::min(nb, p - k0);
-    chase_c64* Xk = X + static_cast<size_t>(k0) * ldx;
+    T* Xk = X + static_cast<size_t>(k0) * ldx;
     if (k0 > 0) {
       // X[:, k0:k0+kb] -= X[:, 0:k0] R[0:k0, k0:k0+kb],  R = L^H
       CHASE_TRY(launch_conj_transpose(d, L + k0, ldl, kb, k0, work, k0));
-      CHASE_TRY(zgemm(d, N, k0, X, ldx, work, k0, kb, Xk, ldx, 0, kb, -1.0, 1.0, 0.0));
+      CHASE_TRY(gemm(d, N, k0, X, ldx, work, k0, kb, Xk, ldx, 0, kb, -1.0, 1.0, 0.0));
     }
     CHASE_TRY(launch_row_trsm_lh(d, Xk, ldx, N, L + static_cast<size_t>(k0) * ldl + k0, ldl, kb));
   }
   return CHASE_OK;
 }
 
-int launch_lanczos_step(Dev& d, int64_t N, int r, int step, const chase_c64* Vj,
-                        const chase_c64* Vprev, chase_c64* W, chase_c64* Vnext, double* alpha,
-                        double* beta) {
-  lanczos_step_kernel<<<r, kRed, 0, d.st>>>(N, r, step, reinterpret_cast<const double2*>(Vj),
-                                            reinterpret_cast<const double2*>(Vprev),
-                                            reinterpret_cast<double2*>(W),
-                                            reinterpret_cast<double2*>(Vnext), alpha, beta);
+template <class T>
+int launch_lanczos_step(Dev& d, int64_t N, int64_t ld, int r, int step, const T* Vj,
+                        const T* Vprev, T* W, T* Vnext, double* alpha, double* beta) {
+  lanczos_step_kernel<<<r, kRed, 0, d.st>>>(N, ld, r, step, dp(Vj), dp(Vprev), dp(W), dp(Vnext),
+                                            alpha, beta);
   note_launch();
   CHASE_CUDA(cudaGetLastError());
   return CHASE_OK;
 }
 
-int launch_normalize_cols(Dev& d, chase_c64* X, int64_t ldx, int64_t N, int r) {
+template <class T>
+int launch_normalize_cols(Dev& d, T* X, int64_t ldx, int64_t N, int r) {
   if (r == 0) return CHASE_OK;
-  normalize_cols_kernel<<<r, kRed, 0, d.st>>>(reinterpret_cast<double2*>(X), ldx, N);
+  normalize_cols_kernel<<<r, kRed, 0, d.st>>>(dp(X), ldx, N);
   note_launch();
   CHASE_CUDA(cudaGetLastError());
   return CHASE_OK;
 }
+
+#define CHASE_INSTANTIATE_ELEMENT_LAUNCHERS(T)                                                     \
+  template int launch_permute_cols<T>(Dev&, const T*, int64_t, T*, int64_t, int64_t, int,         \
+                                      const int*, bool);                                           \
+  template int launch_col_norms<T>(Dev&, const T*, int64_t, int64_t, int, double*);                \
+  template int launch_col_inv_scale<T>(Dev&, T*, int64_t, int64_t, int, const double*);            \
+  template int launch_resid_norms<T>(Dev&, const T*, int64_t, const T*, int64_t, int64_t, int,     \
+                                     const double*, double*);                                      \
+  template int launch_hermitize<T>(Dev&, T*, int64_t, int);                                        \
+  template int launch_zero_triangle<T>(Dev&, T*, int64_t, int, bool);                              \
+  template int launch_cholesky<T>(Dev&, T*, int64_t, int, double, double);                         \
+  template int cholesky_blocked<T>(Dev&, T*, int64_t, int, double, double, double*, T*);           \
+  template int trsm_right_lh<T>(Dev&, T*, int64_t, int64_t, const T*, int64_t, int, T*);           \
+  template int launch_lanczos_step<T>(Dev&, int64_t, int64_t, int, int, const T*, const T*, T*,    \
+                                      T*, double*, double*);                                       \
+  template int launch_normalize_cols<T>(Dev&, T*, int64_t, int64_t, int);
+CHASE_INSTANTIATE_ELEMENT_LAUNCHERS(chase_c64)
+CHASE_INSTANTIATE_ELEMENT_LAUNCHERS(double)
+#undef CHASE_INSTANTIATE_ELEMENT_LAUNCHERS
 
 // ---------------------------------------------------------------------------
 // Projected eigensolve (Alg. 2 line 3): cuSOLVER zheevd, eigenvalues ascending
 // ---------------------------------------------------------------------------
 namespace {
 thread_local cusolverDnHandle_t t_solver = nullptr;
+}
+
+namespace {
+int solver_handle(Dev& d) {
+  if (!t_solver) {
+    if (cusolverDnCreate(&t_solver) != CUSOLVER_STATUS_SUCCESS) {
+      t_solver = nullptr;
+      set_error("cusolverDnCreate failed");
+      return CHASE_EIGENSOLVER_ERROR;
+    }
+  }
+  if (cusolverDnSetStream(t_solver, d.st) != CUSOLVER_STATUS_SUCCESS) {
+    set_error("cusolverDnSetStream failed");
+    return CHASE_EIGENSOLVER_ERROR;
+  }
+  return CHASE_OK;
+}
+
+int eigh_info(Dev& d, int* info, const char* what) {
+  int h_info = 0;
+  CHASE_CUDA(cudaMemcpyAsync(&h_info, info, sizeof(int), cudaMemcpyDeviceToHost, d.st));
+  CHASE_CUDA(cudaStreamSynchronize(d.st));
+  if (h_info != 0) {
+    set_error("%s returned info = %d", what, h_info);
+    return CHASE_EIGENSOLVER_ERROR;
+  }
+  return CHASE_OK;
+}
+}  // namespace
+
+// Real symmetric projected eigenproblem: cuSOLVER dsyevd.
+int eigh_device(Dev& d, double* G, int64_t ldg, int p, double* w_dev) {
+  if (p == 0) return CHASE_OK;
+  CHASE_TRY(solver_handle(d));
+  int lwork = 0;
+  if (cusolverDnDsyevd_bufferSize(t_solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, p, G,
+                                  static_cast<int>(ldg), w_dev, &lwork) != CUSOLVER_STATUS_SUCCESS) {
+    set_error("cusolverDnDsyevd_bufferSize failed");
+    return CHASE_EIGENSOLVER_ERROR;
+  }
+  double* work = nullptr;
+  int* info = nullptr;
+  CHASE_TRY(d.alloc(&work, static_cast<size_t>(std::max(lwork, 1))));
+  CHASE_TRY(d.alloc(&info, 1));
+  if (cusolverDnDsyevd(t_solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, p, G,
+                       static_cast<int>(ldg), w_dev, work, lwork, info) != CUSOLVER_STATUS_SUCCESS) {
+    set_error("cusolverDnDsyevd failed to launch");
+    return CHASE_EIGENSOLVER_ERROR;
+  }
+  return eigh_info(d, info, "dsyevd");
 }
 
 int eigh_device(Dev& d, chase_c64* G, int64_t ldg, int p, double* w_dev) {

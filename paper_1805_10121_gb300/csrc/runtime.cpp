@@ -47,8 +47,8 @@ EncodeTiledFn g_encode = nullptr;
 std::once_flag g_encode_once;
 }  // namespace
 
-int make_tmap_c64(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld,
-                  int box_rows, int box_cols) {
+namespace {
+EncodeTiledFn encoder() {
   std::call_once(g_encode_once, [] {
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q;
@@ -57,7 +57,14 @@ int make_tmap_c64(CUtensorMap* map, const void* base, int64_t rows, int64_t cols
         q == cudaDriverEntryPointSuccess)
       g_encode = reinterpret_cast<EncodeTiledFn>(fn);
   });
-  if (!g_encode) {
+  return g_encode;
+}
+
+// 2-D float64 tensor {d0, d1} with row stride ld_bytes, box {b0, b1}.
+int make_tmap_2d_f64(CUtensorMap* map, const void* base, int64_t d0, int64_t d1, int64_t ld_bytes,
+                     int b0, int b1) {
+  EncodeTiledFn enc = encoder();
+  if (!enc) {
     set_error("cuTensorMapEncodeTiled is not available from the driver");
     return CHASE_CUDA_ERROR;
   }
@@ -65,34 +72,39 @@ int make_tmap_c64(CUtensorMap* map, const void* base, int64_t rows, int64_t cols
     set_error("TMA operand base address is not 16-byte aligned");
     return CHASE_INVALID_ARG;
   }
-  cuuint64_t gdim[2] = {static_cast<cuuint64_t>(2 * rows), static_cast<cuuint64_t>(cols)};
-  cuuint64_t gstride[1] = {static_cast<cuuint64_t>(ld) * 16u};
-  cuuint32_t box[2] = {static_cast<cuuint32_t>(2 * box_rows), static_cast<cuuint32_t>(box_cols)};
+  if ((ld_bytes & 15) != 0) {
+    set_error("TMA operand leading dimension is not a multiple of 16 bytes");
+    return CHASE_INVALID_ARG;
+  }
+  cuuint64_t gdim[2] = {static_cast<cuuint64_t>(d0), static_cast<cuuint64_t>(d1)};
+  cuuint64_t gstride[1] = {static_cast<cuuint64_t>(ld_bytes)};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(b0), static_cast<cuuint32_t>(b1)};
   cuuint32_t estride[2] = {1, 1};
-  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<void*>(base), gdim,
-                        gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<void*>(base), gdim, gstride,
+                   box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
-    set_error("cuTensorMapEncodeTiled failed (%d) rows=%lld cols=%lld ld=%lld box=%dx%d", (int)r,
-              (long long)rows, (long long)cols, (long long)ld, box_rows, box_cols);
+    set_error("cuTensorMapEncodeTiled failed (%d) dims=%lldx%lld ld=%lld B box=%dx%d", (int)r,
+              (long long)d0, (long long)d1, (long long)ld_bytes, b0, b1);
     return CHASE_INVALID_ARG;
   }
   return CHASE_OK;
 }
+}  // namespace
+
+int make_tmap_c64(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld,
+                  int box_rows, int box_cols) {
+  return make_tmap_2d_f64(map, base, 2 * rows, cols, ld * 16, 2 * box_rows, box_cols);
+}
+
+int make_tmap_f64(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld,
+                  int box_rows, int box_cols) {
+  return make_tmap_2d_f64(map, base, rows, cols, ld * 8, box_rows, box_cols);
+}
 
 int make_tmap_bf16_3d(CUtensorMap* map, const void* base, int64_t d0, int64_t d1, int64_t d2,
                       int64_t s1, int64_t s2, int b0, int b1, int b2) {
-  EncodeTiledFn enc = nullptr;
-  std::call_once(g_encode_once, [] {
-    void* fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      g_encode = reinterpret_cast<EncodeTiledFn>(fn);
-  });
-  enc = g_encode;
+  EncodeTiledFn enc = encoder();
   if (!enc) {
     set_error("cuTensorMapEncodeTiled is not available from the driver");
     return CHASE_CUDA_ERROR;
@@ -179,14 +191,25 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+namespace {
+int copy_block_bytes(Dev& d, void* dst, int64_t ldd, const void* src, int64_t lds, int64_t rows,
+                     int64_t cols, size_t es, cudaMemcpyKind kind) {
+  if (rows == 0 || cols == 0) return CHASE_OK;
+  CHASE_CUDA(cudaMemcpy2DAsync(dst, static_cast<size_t>(ldd) * es, src, static_cast<size_t>(lds) * es,
+                               static_cast<size_t>(rows) * es, static_cast<size_t>(cols), kind,
+                               d.st));
+  return CHASE_OK;
+}
+}  // namespace
+
 int copy_block(Dev& d, chase_c64* dst, int64_t ldd, const chase_c64* src, int64_t lds, int64_t rows,
                int64_t cols, cudaMemcpyKind kind) {
-  if (rows == 0 || cols == 0) return CHASE_OK;
-  CHASE_CUDA(cudaMemcpy2DAsync(dst, static_cast<size_t>(ldd) * sizeof(chase_c64), src,
-                               static_cast<size_t>(lds) * sizeof(chase_c64),
-                               static_cast<size_t>(rows) * sizeof(chase_c64),
-                               static_cast<size_t>(cols), kind, d.st));
-  return CHASE_OK;
+  return copy_block_bytes(d, dst, ldd, src, lds, rows, cols, sizeof(chase_c64), kind);
+}
+
+int copy_block(Dev& d, double* dst, int64_t ldd, const double* src, int64_t lds, int64_t rows,
+               int64_t cols, cudaMemcpyKind kind) {
+  return copy_block_bytes(d, dst, ldd, src, lds, rows, cols, sizeof(double), kind);
 }
 
 }  // namespace chase

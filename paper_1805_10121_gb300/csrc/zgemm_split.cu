@@ -143,6 +143,7 @@ struct SplitTile {
   const CUtensorMap* mapA;
   const CUtensorMap* mapB;
   int maps_in_global;  // maps live in global memory: acquire them for the async proxy
+  int cplx;            // 1: complex operands (B rows 2c, 2c+1 per column); 0: real
   int arow;            // first row of H (A map row) of the tile
   int brow;            // first B map row (real product column) of the tile
   int cend;            // complex columns >= cend are outside the block
@@ -343,7 +344,7 @@ __device__ __forceinline__ void split_tile_body(const SplitTile& T, int* __restr
 #pragma unroll
           for (int j = 0; j < 8; ++j) t[j] = fmaf(t[j], 0.0078125f, __uint_as_float(r[j]));
         }
-        if (in_rows) {
+        if (in_rows && T.cplx) {
 #pragma unroll
           for (int j = 0; j < 8; j += 2) {
             const int cc = (colr0 + hf * 32 + c0 + j) >> 1;  // complex column (B map)
@@ -378,6 +379,32 @@ __device__ __forceinline__ void split_tile_body(const SplitTile& T, int* __restr
             }
             *yp = make_double2(v[0], v[1]);
           }
+        } else if (in_rows) {  // real operands: one B-map row per column
+          const double* Xr = reinterpret_cast<const double*>(T.X);
+          double* Yr = reinterpret_cast<double*>(T.Y);
+          double* Pr = reinterpret_cast<double*>(T.P);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int cc = colr0 + hf * 32 + c0 + j;
+            if (cc >= T.cend) continue;
+            const int ex = er + T.F[cc] - 28;
+            const bool normal = ex >= -1022 && ex <= 1023;
+            const double sc = normal ? pow2_normal(ex) * alpha : alpha;
+            const long long Sx = (static_cast<long long>(sums[0][c0 + j]) << 14) +
+                                 (static_cast<long long>(sums[1][c0 + j]) << 7) +
+                                 static_cast<long long>(sums[2][c0 + j]);
+            double v = (static_cast<double>(Sx) + static_cast<double>(t[j] * 0.0078125f)) * sc;
+            if (!normal) v = ldexp(v, ex);
+            if (raw) {
+              Pr[static_cast<long long>(cc) * T.ldp + grow] = v;
+              continue;
+            }
+            const long long jc = cc + T.joff;
+            if (adsh != 0.0) v = fma(adsh, Xr[jc * T.ldx + grow], v);
+            double* yp = Yr + jc * T.ldy + grow;
+            if (T.beta != 0.0) v = fma(T.beta, *yp, v);
+            *yp = v;
+          }
         }
       }
     }
@@ -395,11 +422,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                        const double* __restrict__ Dg, int M, int kb0, int nkb, int ncols, int j0,
                        const double2* __restrict__ Xsh, long long ldx, double2* __restrict__ Y,
                        long long ldy, double alpha, double beta, double shift,
-                       double2* __restrict__ P, long long ldp, int* __restrict__ err) {
+                       double2* __restrict__ P, long long ldp, int cplx, int* __restrict__ err) {
   SplitTile T;
   T.mapA = &tmA;
   T.mapB = &tmB;
   T.maps_in_global = 0;
+  T.cplx = cplx;
   T.arow = blockIdx.y * BM;
   T.brow = blockIdx.x * BN;
   T.cend = ncols;
@@ -452,6 +480,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   T.mapA = pr.mapA;
   T.mapB = pr.mapB0;
   T.maps_in_global = 1;
+  T.cplx = 1;
   T.arow = (local / ncol_tiles) * BM;
   T.brow = 2 * stp.s + (local % ncol_tiles) * BN;
   T.cend = pr.b;
@@ -657,36 +686,93 @@ __global__ void __launch_bounds__(256) slice_x_grouped_kernel(const GroupedProbl
               pr.Kp, 2LL * pr.bcap * pr.Kp, pr.F + c, scratch);
 }
 
+// Real operands: row r of H from its column r (H symmetric), K = N.
+__global__ void __launch_bounds__(256) slice_h_real_kernel(const double* __restrict__ H, long long ldh,
+                                                           int N, __nv_bfloat16* __restrict__ A,
+                                                           long long Kp, int* __restrict__ E,
+                                                           double* __restrict__ Dg) {
+  __shared__ unsigned long long scratch[33];
+  const int r = blockIdx.x;
+  const double* col = H + static_cast<long long>(r) * ldh;
+  unsigned long long mb = 0;
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    if (k == r) continue;
+    const unsigned long long x = abs_bits(col[k]);
+    mb = x > mb ? x : mb;
+  }
+  mb = block_max_u64(mb, scratch);
+  const int er = exponent_above_bits(mb);
+  if (threadIdx.x == 0) {
+    E[r] = er;
+    Dg[r] = col[r];
+  }
+  const long long plane = static_cast<long long>(N) * Kp;
+  __nv_bfloat16* row = A + static_cast<long long>(r) * Kp;
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    float a[S];
+    slice7_bits(k == r ? 0.0 : col[k], er, a);
+#pragma unroll
+    for (int s = 0; s < S; ++s) row[s * plane + k] = __float2bfloat16_rn(a[s]);
+  }
+}
+
+// Real block: column c of X (c in [j0, j0 + ncols)) to B row c - j0, K = N.
+__global__ void __launch_bounds__(256) slice_x_real_kernel(const double* __restrict__ X, long long ldx,
+                                                           int N, int j0,
+                                                           __nv_bfloat16* __restrict__ B,
+                                                           long long Kp, long long rows_cap,
+                                                           int* __restrict__ F) {
+  __shared__ unsigned long long scratch[33];
+  const int c = blockIdx.x;
+  const double* col = X + static_cast<long long>(j0 + c) * ldx;
+  unsigned long long mb = 0;
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    const unsigned long long x = abs_bits(col[k]);
+    mb = x > mb ? x : mb;
+  }
+  mb = block_max_u64(mb, scratch);
+  const int fc = exponent_above_bits(mb);
+  if (threadIdx.x == 0) F[c] = fc;
+  const long long plane = rows_cap * Kp;
+  __nv_bfloat16* row = B + static_cast<long long>(c) * Kp;
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    float a[S];
+    slice7_bits(col[k], fc, a);
+#pragma unroll
+    for (int s = 0; s < S; ++s) row[s * plane + k] = __float2bfloat16_rn(a[s]);
+  }
+}
+
 // Sum of the K segments' products plus the FP64 epilogue:
 // C[r, j0+c] = alpha (sum_g P_g[r, c] + (H_rr - shift) X[r, j0+c]) + beta C[r, j0+c].
-__global__ void split_combine_kernel(const double2* __restrict__ P, int nseg, long long pstride,
+template <class E>
+__global__ void split_combine_kernel(const E* __restrict__ P, int nseg, long long pstride,
                                      long long ldp, const double* __restrict__ Dg,
-                                     const double2* __restrict__ X, long long ldx, int j0, int ncols,
-                                     int N, double2* __restrict__ C, long long ldc, double alpha,
-                                     double beta, double shift) {
+                                     const E* __restrict__ X, long long ldx, int j0, int ncols, int N,
+                                     E* __restrict__ C, long long ldc, double alpha, double beta,
+                                     double shift) {
+  constexpr int W = sizeof(E) / sizeof(double);  // 2 complex, 1 real
   const long long total = static_cast<long long>(N) * ncols;
   for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
        e += static_cast<long long>(gridDim.x) * blockDim.x) {
     const int r = static_cast<int>(e % N);
     const int c = static_cast<int>(e / N);
-    double vr = 0.0, vi = 0.0;
+    double v[W] = {};
     for (int g = 0; g < nseg; ++g) {
-      const double2 p = P[g * pstride + c * ldp + r];
-      vr += p.x;
-      vi += p.y;
+      const double* p = reinterpret_cast<const double*>(P + g * pstride + c * ldp + r);
+#pragma unroll
+      for (int w = 0; w < W; ++w) v[w] += p[w];
     }
     const long long jc = j0 + c;
     const double ds = Dg[r] - shift;
-    const double2 xv = X[jc * ldx + r];
-    vr = alpha * (vr + ds * xv.x);
-    vi = alpha * (vi + ds * xv.y);
-    double2* cp = C + jc * ldc + r;
-    if (beta != 0.0) {
-      const double2 cv = *cp;
-      vr += beta * cv.x;
-      vi += beta * cv.y;
+    const double* xv = reinterpret_cast<const double*>(X + jc * ldx + r);
+    double* cp = reinterpret_cast<double*>(C + jc * ldc + r);
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      double o = alpha * (v[w] + ds * xv[w]);
+      if (beta != 0.0) o += beta * cp[w];
+      cp[w] = o;
     }
-    *cp = make_double2(vr, vi);
   }
 }
 
@@ -704,9 +790,14 @@ static_assert(kSplitTileRows == split::BM && kSplitTileRealCols == split::BN &&
 
 int64_t split_k_padded(int64_t N) { return k_padded(N); }
 
+namespace {
+int64_t k_padded_real(int64_t N) { return ((N + split::BK - 1) / split::BK) * split::BK; }
+}  // namespace
+
 int split_prepare_h(Dev& d, const chase_c64* H, int64_t N, int64_t ldh, SplitH& out) {
   out.N = N;
   out.Kp = k_padded(N);
+  out.cplx = 1;
   CHASE_TRY(d.alloc_bytes(&out.A, static_cast<size_t>(split::S) * N * out.Kp * 2));
   CHASE_TRY(d.alloc(&out.E, static_cast<size_t>(N)));
   CHASE_TRY(d.alloc(&out.Dg, static_cast<size_t>(N)));
@@ -718,10 +809,26 @@ int split_prepare_h(Dev& d, const chase_c64* H, int64_t N, int64_t ldh, SplitH& 
   return CHASE_OK;
 }
 
-int split_alloc_x(Dev& d, int64_t N, int max_cols, SplitX& out) {
+int split_prepare_h(Dev& d, const double* H, int64_t N, int64_t ldh, SplitH& out) {
+  out.N = N;
+  out.Kp = k_padded_real(N);
+  out.cplx = 0;
+  CHASE_TRY(d.alloc_bytes(&out.A, static_cast<size_t>(split::S) * N * out.Kp * 2));
+  CHASE_TRY(d.alloc(&out.E, static_cast<size_t>(N)));
+  CHASE_TRY(d.alloc(&out.Dg, static_cast<size_t>(N)));
+  split::slice_h_real_kernel<<<static_cast<unsigned>(N), 256, 0, d.st>>>(
+      H, ldh, static_cast<int>(N), static_cast<__nv_bfloat16*>(out.A), out.Kp, out.E, out.Dg);
+  note_launch();
+  CHASE_CUDA(cudaGetLastError());
+  return CHASE_OK;
+}
+
+int split_alloc_x(Dev& d, int64_t N, int max_cols, SplitX& out, bool cplx) {
   out.cap_cols = max_cols;
-  const int64_t Kp = k_padded(N);
-  CHASE_TRY(d.alloc_bytes(&out.B, static_cast<size_t>(split::S) * 2 * max_cols * Kp * 2));
+  out.cplx = cplx ? 1 : 0;
+  const int64_t Kp = cplx ? k_padded(N) : k_padded_real(N);
+  const int rows = cplx ? 2 * max_cols : max_cols;
+  CHASE_TRY(d.alloc_bytes(&out.B, static_cast<size_t>(split::S) * rows * Kp * 2));
   CHASE_TRY(d.alloc(&out.F, static_cast<size_t>(max_cols)));
   return CHASE_OK;
 }
@@ -730,90 +837,110 @@ namespace {
 // K blocks one launch may cover with exact int32 level sums: level 2 holds
 // 3 pairs, 3 * K * 127^2 < 2^31 gives K < 44380.
 constexpr int kMaxKBlocksPerSegment = 44000 / split::BK;
-}  // namespace
 
-int split_segments(int64_t N, int ncols) {
-  const int64_t nkb = k_padded(N) / split::BK;
+// nkb K blocks, `tiles` output tiles per segment
+int segments_for(int64_t nkb, int64_t tiles) {
   int nseg = static_cast<int>((nkb + kMaxKBlocksPerSegment - 1) / kMaxKBlocksPerSegment);
   // Narrow blocks leave SMs idle: split K until the grid covers the SMs,
   // keeping every segment at least 64 K blocks long.  (Splitting wider
   // grids to trim the last wave costs more in the combine pass and the
   // extra epilogues than it recovers: measured on the N = 8000 solve.)
-  const int64_t tiles = ((2LL * ncols + split::BN - 1) / split::BN) * ((N + split::BM - 1) / split::BM);
   while (tiles * nseg < 152 && nkb / (nseg + 1) >= 64 && nseg < 8) ++nseg;
   return nseg;
 }
 
-int zgemm_split(Dev& d, const SplitH& h, SplitX& x, const chase_c64* X, int64_t ldx, int j0, int j1,
-                chase_c64* C, int64_t ldc, double alpha, double beta, double shift) {
+// The split product for complex (E = double2) or real (E = double) operands.
+template <class E>
+int split_product(Dev& d, const SplitH& h, SplitX& x, const E* X, int64_t ldx, int j0, int j1, E* C,
+                  int64_t ldc, double alpha, double beta, double shift) {
+  constexpr bool cplx = sizeof(E) == 16;
   const int ncols = j1 - j0;
   if (ncols <= 0) return CHASE_OK;
-  if (ncols > x.cap_cols) {
-    set_error("zgemm_split: %d columns exceed the slice workspace (%d)", ncols, x.cap_cols);
+  if (ncols > x.cap_cols || h.cplx != (cplx ? 1 : 0) || x.cplx != h.cplx) {
+    set_error("split product: %d columns for a workspace of %d, or mixed real/complex slices",
+              ncols, x.cap_cols);
     return CHASE_INVALID_ARG;
   }
   const int64_t N = h.N, Kp = h.Kp;
-  const int64_t rows_cap = 2LL * x.cap_cols;
-  split::slice_x_kernel<<<static_cast<unsigned>(ncols), 256, 0, d.st>>>(
-      reinterpret_cast<const double2*>(X), ldx, static_cast<int>(N), j0,
-      static_cast<__nv_bfloat16*>(x.B), Kp, rows_cap, x.F);
+  const int64_t K = cplx ? 2 * N : N;            // real K extent of the product
+  const int64_t rows_cap = cplx ? 2LL * x.cap_cols : x.cap_cols;
+  const int64_t brows = cplx ? 2LL * ncols : ncols;  // B-map rows of the active block
+  if constexpr (cplx)
+    split::slice_x_kernel<<<static_cast<unsigned>(ncols), 256, 0, d.st>>>(
+        X, ldx, static_cast<int>(N), j0, static_cast<__nv_bfloat16*>(x.B), Kp, rows_cap, x.F);
+  else
+    split::slice_x_real_kernel<<<static_cast<unsigned>(ncols), 256, 0, d.st>>>(
+        X, ldx, static_cast<int>(N), j0, static_cast<__nv_bfloat16*>(x.B), Kp, rows_cap, x.F);
   note_launch();
   CHASE_CUDA(cudaGetLastError());
   CUtensorMap tmA, tmB;
-  CHASE_TRY(make_tmap_bf16_3d(&tmA, h.A, 2 * N, N, split::S, Kp * 2, Kp * 2 * N, split::BK,
-                              split::BM, split::S));
-  CHASE_TRY(make_tmap_bf16_3d(&tmB, x.B, 2 * N, 2LL * ncols, split::S, Kp * 2, Kp * 2 * rows_cap,
-                              split::BK, split::BN, split::S));
+  CHASE_TRY(make_tmap_bf16_3d(&tmA, h.A, K, N, split::S, Kp * 2, Kp * 2 * N, split::BK, split::BM,
+                              split::S));
+  CHASE_TRY(make_tmap_bf16_3d(&tmB, x.B, K, brows, split::S, Kp * 2, Kp * 2 * rows_cap, split::BK,
+                              split::BN, split::S));
   static bool attr_done = false;
   if (!attr_done) {
     CHASE_CUDA(cudaFuncSetAttribute(split::zgemm_split_kernel,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, split::SMEM));
     attr_done = true;
   }
-  dim3 grid(static_cast<unsigned>((2 * ncols + split::BN - 1) / split::BN),
-            static_cast<unsigned>((N + split::BM - 1) / split::BM));
+  const int64_t ctiles = (brows + split::BN - 1) / split::BN;
+  const int64_t rtiles = (N + split::BM - 1) / split::BM;
+  dim3 grid(static_cast<unsigned>(ctiles), static_cast<unsigned>(rtiles));
   const int nkb = static_cast<int>(Kp / split::BK);
-  const int nseg = split_segments(N, ncols);
+  const int nseg = segments_for(nkb, ctiles * rtiles);
+  const double2* Xd = reinterpret_cast<const double2*>(X);
+  double2* Cd = reinterpret_cast<double2*>(C);
   if (nseg == 1) {
     split::zgemm_split_kernel<<<grid, split::kThreads, split::SMEM, d.st>>>(
-        tmA, tmB, h.E, x.F, h.Dg, static_cast<int>(N), 0, nkb, ncols, j0,
-        reinterpret_cast<const double2*>(X), ldx, reinterpret_cast<double2*>(C), ldc, alpha, beta,
-        shift, nullptr, 0, d.err);
+        tmA, tmB, h.E, x.F, h.Dg, static_cast<int>(N), 0, nkb, ncols, j0, Xd, ldx, Cd, ldc, alpha,
+        beta, shift, nullptr, 0, cplx ? 1 : 0, d.err);
     note_launch();
     CHASE_CUDA(cudaGetLastError());
     return CHASE_OK;
   }
   // K segments write raw partial products; the combine kernel sums them and
   // applies the diagonal, the shift and the axpby in FP64.
-  const long long pstride = static_cast<long long>(N) * ncols;
-  const size_t need = static_cast<size_t>(pstride) * nseg;
+  const long long pstride = static_cast<long long>(N) * ncols;  // elements of E
+  const size_t need = static_cast<size_t>(pstride) * nseg * sizeof(E) / sizeof(double2) + 1;
   if (need > x.P_cap) {  // grow-only: released with the call's other workspace
     void* np = nullptr;
     CHASE_TRY(d.alloc_bytes(&np, std::max(need, 2 * x.P_cap) * sizeof(double2)));
     x.P = np;
     x.P_cap = std::max(need, 2 * x.P_cap);
   }
-  double2* P = static_cast<double2*>(x.P);
+  E* P = static_cast<E*>(x.P);
   const int per = (nkb + nseg - 1) / nseg;
   for (int g = 0; g < nseg; ++g) {
     const int kb0 = g * per;
     const int cnt = std::min(per, nkb - kb0);
     if (cnt <= 0) break;
     split::zgemm_split_kernel<<<grid, split::kThreads, split::SMEM, d.st>>>(
-        tmA, tmB, h.E, x.F, h.Dg, static_cast<int>(N), kb0, cnt, ncols, j0,
-        reinterpret_cast<const double2*>(X), ldx, reinterpret_cast<double2*>(C), ldc, alpha, beta,
-        shift, P + g * pstride, N, d.err);
+        tmA, tmB, h.E, x.F, h.Dg, static_cast<int>(N), kb0, cnt, ncols, j0, Xd, ldx, Cd, ldc,
+        alpha, beta, shift, reinterpret_cast<double2*>(P + g * pstride), N, cplx ? 1 : 0, d.err);
     note_launch();
     CHASE_CUDA(cudaGetLastError());
   }
   const long long total = pstride;
   const unsigned blocks = static_cast<unsigned>(std::min<long long>((total + 255) / 256, 152 * 16));
-  split::split_combine_kernel<<<blocks, 256, 0, d.st>>>(
-      P, nseg, pstride, N, h.Dg, reinterpret_cast<const double2*>(X), ldx, j0, ncols,
-      static_cast<int>(N), reinterpret_cast<double2*>(C), ldc, alpha, beta, shift);
+  split::split_combine_kernel<E><<<blocks, 256, 0, d.st>>>(P, nseg, pstride, N, h.Dg, X, ldx, j0,
+                                                           ncols, static_cast<int>(N), C, ldc,
+                                                           alpha, beta, shift);
   note_launch();
   CHASE_CUDA(cudaGetLastError());
   return CHASE_OK;
+}
+}  // namespace
+
+int zgemm_split(Dev& d, const SplitH& h, SplitX& x, const chase_c64* X, int64_t ldx, int j0, int j1,
+                chase_c64* C, int64_t ldc, double alpha, double beta, double shift) {
+  return split_product(d, h, x, reinterpret_cast<const double2*>(X), ldx, j0, j1,
+                       reinterpret_cast<double2*>(C), ldc, alpha, beta, shift);
+}
+
+int zgemm_split(Dev& d, const SplitH& h, SplitX& x, const double* X, int64_t ldx, int j0, int j1,
+                double* C, int64_t ldc, double alpha, double beta, double shift) {
+  return split_product(d, h, x, X, ldx, j0, j1, C, ldc, alpha, beta, shift);
 }
 
 int split_grouped_prepare_h(Dev& d, const GroupedSliceH* probs, int P, int total_rows) {

@@ -36,8 +36,9 @@ namespace chase {
 
 namespace {
 
-template <int BM_, int BN_, int BK_, int STAGES_, int WARPS_M_>
+template <int BM_, int BN_, int BK_, int STAGES_, int WARPS_M_, int ES_ = 16>
 struct Cfg {
+  static constexpr int ES = ES_;  // element bytes: 16 complex128, 8 float64
   static constexpr int BM = BM_, BN = BN_, BK = BK_, STAGES = STAGES_;
   static constexpr int WARPS_M = WARPS_M_;
   static constexpr int WARPS_N = 4 / WARPS_M_;
@@ -47,14 +48,14 @@ struct Cfg {
   static constexpr int WTN = BN / WARPS_N;
   static constexpr int MI = WTM / 8;
   static constexpr int NI = WTN / 8;
-  static constexpr int A_BYTES = BM * BK * 16;
-  static constexpr int B_BYTES = BK * BN * 16;
+  static constexpr int A_BYTES = BM * BK * ES;
+  static constexpr int B_BYTES = BK * BN * ES;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr int SMEM = STAGES * STAGE_BYTES + 2 * STAGES * 8 + 128;
   static_assert(MI >= 1 && NI >= 1, "warp tile too small");
   static_assert(WTM % 8 == 0 && WTN % 8 == 0, "warp tile must be a multiple of 8");
   static_assert(BK % 4 == 0, "BK must be a multiple of 4");
-  static_assert(2 * BM <= 256 && 2 * BK <= 256 && BN <= 256, "TMA box limit");
+  static_assert((ES / 8) * BM <= 256 && (ES / 8) * BK <= 256 && BN <= 256, "TMA box limit");
 };
 
 // One output tile: its operand maps and coordinates and its epilogue.
@@ -220,6 +221,147 @@ __device__ __forceinline__ void zgemm_tile_body(const Fp64Tile& T, int* __restri
   }
 }
 
+// The real (float64) tile: one DMMA per fragment pair, same pipeline and
+// epilogue as the complex tile.
+template <class C>
+__device__ __forceinline__ void dgemm_tile_body(const Fp64Tile& T, int* __restrict__ err) {
+  static_assert(C::ES == 8, "real configuration expected");
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+  double* sA = reinterpret_cast<double*>(smem);                         // [STAGES][BK][BM]
+  double* sB = reinterpret_cast<double*>(smem + C::STAGES * C::A_BYTES);  // [STAGES][BN][BK]
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE_BYTES);
+  uint64_t* empty = full + C::STAGES;
+  const double* Bsh = reinterpret_cast<const double*>(T.Bsh);
+  double* Cout = reinterpret_cast<double*>(T.Cout);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int row0 = T.row0;
+  const int col0 = T.col0;
+  const int M = T.M;
+  const int nk = (T.K + C::BK - 1) / C::BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], C::kConsumerWarps);
+    }
+    fence_barrier_init();
+  }
+  __syncthreads();
+
+  if (warp == C::kConsumerWarps) {
+    if (lane == 0) {  // producer
+      if (T.maps_in_global) {
+        acquire_tmap_global(T.mapA);
+        acquire_tmap_global(T.mapB);
+      }
+      prefetch_tmap(T.mapA);
+      prefetch_tmap(T.mapB);
+      int issued = 0;
+      for (int kt = 0; kt < nk; ++kt) {
+        const int s = kt % C::STAGES;
+        if (kt >= C::STAGES) {
+          if (!mbar_wait_bounded(&empty[s], ((kt / C::STAGES) & 1) ^ 1)) {
+            atomicOr(err, KERR_TIMEOUT_EMPTY);
+            break;
+          }
+        }
+        mbar_arrive_expect_tx(&full[s], C::STAGE_BYTES);
+        tma_load_2d(sA + s * C::BK * C::BM, T.mapA, row0, kt * C::BK, &full[s]);
+        tma_load_2d(sB + s * C::BN * C::BK, T.mapB, kt * C::BK, col0, &full[s]);
+        ++issued;
+      }
+      for (int kt = (issued > C::STAGES ? issued - C::STAGES : 0); kt < issued; ++kt) {
+        if (!mbar_wait_bounded(&full[kt % C::STAGES], (kt / C::STAGES) & 1))
+          atomicOr(err, KERR_TIMEOUT_FULL);
+      }
+    }
+    return;
+  }
+
+  const int wm = warp % C::WARPS_M;
+  const int wn = warp / C::WARPS_M;
+  const int g = lane >> 2;
+  const int t = lane & 3;
+  double acc[C::MI][C::NI][2];
+#pragma unroll
+  for (int mi = 0; mi < C::MI; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < C::NI; ++ni) acc[mi][ni][0] = acc[mi][ni][1] = 0.0;
+
+  for (int kt = 0; kt < nk; ++kt) {
+    const int s = kt % C::STAGES;
+    if (!mbar_wait_bounded(&full[s], (kt / C::STAGES) & 1)) {
+      if (lane == 0) atomicOr(err, KERR_TIMEOUT_FULL);
+      return;
+    }
+    const double* a_s = sA + s * C::BK * C::BM;
+    const double* b_s = sB + s * C::BN * C::BK;
+#pragma unroll
+    for (int kk = 0; kk < C::BK; kk += 4) {
+      double af[C::MI], bf[C::NI];
+#pragma unroll
+      for (int mi = 0; mi < C::MI; ++mi) af[mi] = a_s[(kk + t) * C::BM + wm * C::WTM + mi * 8 + g];
+#pragma unroll
+      for (int ni = 0; ni < C::NI; ++ni) bf[ni] = b_s[(wn * C::WTN + ni * 8 + g) * C::BK + kk + t];
+#pragma unroll
+      for (int mi = 0; mi < C::MI; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < C::NI; ++ni) dmma_8x8x4(acc[mi][ni][0], acc[mi][ni][1], af[mi], bf[ni]);
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+  }
+
+#pragma unroll
+  for (int mi = 0; mi < C::MI; ++mi) {
+    const int r = row0 + wm * C::WTM + mi * 8 + g;
+    if (r >= M) continue;
+#pragma unroll
+    for (int ni = 0; ni < C::NI; ++ni) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = col0 + wn * C::WTN + ni * 8 + 2 * t + h;
+        if (c >= T.j1) continue;
+        double v = acc[mi][ni][h];
+        if (T.shift != 0.0) v -= T.shift * Bsh[static_cast<long long>(c) * T.ldb + r];
+        v *= T.alpha;
+        double* cp = Cout + static_cast<long long>(c) * T.ldc + r;
+        if (T.beta != 0.0) v += T.beta * *cp;
+        *cp = v;
+      }
+    }
+  }
+}
+
+template <class C>
+__global__ void __launch_bounds__(C::kThreads)
+    dgemm_tma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                     int M, int K, int j0, int j1, const double* __restrict__ Bsh, long long ldb,
+                     double* __restrict__ Cout, long long ldc, double alpha, double beta,
+                     double shift, int* __restrict__ err) {
+  Fp64Tile T;
+  T.mapA = &tmA;
+  T.mapB = &tmB;
+  T.maps_in_global = 0;
+  T.row0 = blockIdx.x * C::BM;
+  T.col0 = j0 + blockIdx.y * C::BN;
+  T.M = M;
+  T.K = K;
+  T.j1 = j1;
+  T.Bsh = reinterpret_cast<const double2*>(Bsh);
+  T.ldb = ldb;
+  T.Cout = reinterpret_cast<double2*>(Cout);
+  T.ldc = ldc;
+  T.alpha = alpha;
+  T.beta = beta;
+  T.shift = shift;
+  dgemm_tile_body<C>(T, err);
+}
+
 template <class C>
 __global__ void __launch_bounds__(C::kThreads)
     zgemm_tma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -305,10 +447,36 @@ int launch_cfg(Dev& d, int64_t M, int64_t K, const chase_c64* A, int64_t lda, co
   return CHASE_OK;
 }
 
+template <class C>
+int launch_cfg_real(Dev& d, int64_t M, int64_t K, const double* A, int64_t lda, const double* B,
+                    int64_t ldb, int64_t ncols_b, double* Cm, int64_t ldc, int j0, int j1,
+                    double alpha, double beta, double shift) {
+  CUtensorMap tmA, tmB;
+  CHASE_TRY(make_tmap_f64(&tmA, A, M, K, lda, C::BM, C::BK));
+  CHASE_TRY(make_tmap_f64(&tmB, B, K, ncols_b, ldb, C::BK, C::BN));
+  static bool attr_done = false;  // per instantiation
+  if (!attr_done) {
+    CHASE_CUDA(cudaFuncSetAttribute(dgemm_tma_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    C::SMEM));
+    attr_done = true;
+  }
+  dim3 grid(static_cast<unsigned>((M + C::BM - 1) / C::BM),
+            static_cast<unsigned>((j1 - j0 + C::BN - 1) / C::BN));
+  dgemm_tma_kernel<C><<<grid, C::kThreads, C::SMEM, d.st>>>(
+      tmA, tmB, static_cast<int>(M), static_cast<int>(K), j0, j1, B, ldb, Cm, ldc, alpha, beta,
+      shift, d.err);
+  note_launch();
+  CHASE_CUDA(cudaGetLastError());
+  return CHASE_OK;
+}
+
 using CfgWide = Cfg<64, 32, 16, 2, 2>;    // 64 x 32 tile, warps 2 x 2 (32 x 16 each)
 using CfgMid = Cfg<64, 16, 16, 2, 4>;     // 64 x 16 tile, warps 4 x 1 (16 x 16 each)
 using CfgNarrow = Cfg<64, 8, 16, 2, 4>;   // 64 x 8 tile, warps 4 x 1 (16 x 8 each)
 using CfgTall = Cfg<128, 16, 16, 2, 4>;   // 128 x 16 tile, warps 4 x 1 (32 x 16 each)
+using RCfgWide = Cfg<64, 32, 16, 3, 2, 8>;    // real tiles: same shapes, float64 elements
+using RCfgMid = Cfg<64, 16, 16, 3, 4, 8>;
+using RCfgNarrow = Cfg<64, 8, 16, 3, 4, 8>;
 
 template <class C>
 int grouped_attr() {
@@ -380,6 +548,29 @@ int zgemm(Dev& d, int64_t M, int64_t K, const chase_c64* A, int64_t lda, const c
   if (w <= 8) return launch_cfg<CfgNarrow>(d, M, K, A, lda, B, ldb, ncols_b, Cm, ldc, j0, j1, alpha, beta, shift);
   if (w <= 16) return launch_cfg<CfgMid>(d, M, K, A, lda, B, ldb, ncols_b, Cm, ldc, j0, j1, alpha, beta, shift);
   return launch_cfg<CfgWide>(d, M, K, A, lda, B, ldb, ncols_b, Cm, ldc, j0, j1, alpha, beta, shift);
+}
+
+int dgemm(Dev& d, int64_t M, int64_t K, const double* A, int64_t lda, const double* B, int64_t ldb,
+          int64_t ncols_b, double* Cm, int64_t ldc, int j0, int j1, double alpha, double beta,
+          double shift) {
+  if (j1 <= j0 || M == 0) return CHASE_OK;
+  if (K == 0) {
+    set_error("dgemm: K == 0 is not supported");
+    return CHASE_INVALID_ARG;
+  }
+  if (shift != 0.0 && M != K) {
+    set_error("dgemm: the shifted product needs a square A");
+    return CHASE_INVALID_ARG;
+  }
+  const int w = j1 - j0;
+  if (w <= 8)
+    return launch_cfg_real<RCfgNarrow>(d, M, K, A, lda, B, ldb, ncols_b, Cm, ldc, j0, j1, alpha,
+                                       beta, shift);
+  if (w <= 16)
+    return launch_cfg_real<RCfgMid>(d, M, K, A, lda, B, ldb, ncols_b, Cm, ldc, j0, j1, alpha, beta,
+                                    shift);
+  return launch_cfg_real<RCfgWide>(d, M, K, A, lda, B, ldb, ncols_b, Cm, ldc, j0, j1, alpha, beta,
+                                   shift);
 }
 
 }  // namespace chase

@@ -29,6 +29,9 @@ __all__ = [
     "hermitian_dft",
     "hermitian_noise",
     "batched_shapes",
+    "orthogonal_qr",
+    "symmetric_from",
+    "gaussian_block_real",
 ]
 
 
@@ -152,3 +155,25 @@ def batched_shapes(P: int, seed: int, n_lo: int = 256, n_hi: int = 2048,
     g = generator(seed, "cpu")
     ns = torch.randint(n_lo, n_hi + 1, (P,), generator=g).tolist()
     return [(int(n), int(math.ceil(nev_frac * n)), int(math.ceil(nex_frac * n))) for n in ns]
+
+
+def orthogonal_qr(n: int, seed: int, device="cpu") -> torch.Tensor:
+    """Random orthogonal matrix: QR of an i.i.d. real Gaussian, signs fixed
+    so that R has a positive diagonal (Haar distributed)."""
+    g = generator(seed, device)
+    z = torch.randn(n, n, dtype=torch.float64, device=device, generator=g)
+    q, r = torch.linalg.qr(z)
+    return q * torch.sign(torch.diagonal(r))[None, :]
+
+
+def symmetric_from(q: torch.Tensor, lam: torch.Tensor) -> torch.Tensor:
+    """``H = Q diag(lam) Q^T`` (real symmetric, both triangles), column-major."""
+    h = (q * lam[None, :]) @ q.t()
+    h = 0.5 * (h + h.t())
+    return h.t().contiguous().t()
+
+
+def gaussian_block_real(n: int, b: int, seed: int, device="cpu") -> torch.Tensor:
+    """n x b real Gaussian block, column-major."""
+    g = generator(seed, device)
+    return torch.randn(b, n, dtype=torch.float64, device=device, generator=g).t()

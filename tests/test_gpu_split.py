@@ -173,3 +173,43 @@ def test_split_solve_sequence_matches_fp64():
     hn = float(lam.abs().max())
     assert np.max(np.abs(out[chase.CHASE_FP64][:nev] - out[chase.CHASE_SPLIT_BF16][:nev])) \
         <= EIG_RTOL * hn
+
+
+@pytest.mark.parametrize("n,nev,nex", [(1000, 50, 20), (700, 35, 14)])
+def test_split_rr_solve_matches_fp64(n, nev, nex):
+    # Rayleigh-Ritz's H Q on the split product as well: same eigenpairs as
+    # the FP64 solve, residuals re-checked by the oracle in FP64
+    tol = 1e-10
+    H, lam = known_h(n, 271 + n, n_cluster=60)
+    V0 = synth.gaussian_block(n, nev + nex, 272)
+    S = synth.gaussian_block(n, 5, 273)
+    out = {}
+    for prec in (chase.CHASE_FP64, chase.CHASE_SPLIT_BF16_RR):
+        Vd = dcol(V0)
+        o = chase.chase_opts_default(precision=prec)
+        st, ritz, resid, stats = chase.chase_solve(dcol(H), nev, nex, tol, Vd, dcol(S), opts=o)
+        assert st == chase.CHASE_OK
+        check_solution(H.numpy(), lam.numpy(), ritz, resid, Vd.cpu().numpy(), nev, tol)
+        out[prec] = ritz
+    hn = float(lam.abs().max())
+    assert np.max(np.abs(out[chase.CHASE_FP64][:nev] - out[chase.CHASE_SPLIT_BF16_RR][:nev])) \
+        <= EIG_RTOL * hn
+
+
+def test_split_rr_batched_solve():
+    shapes = [(300, 15, 6), (800, 40, 16), (129, 7, 3)]
+    tol = 1e-10
+    Hs, lams, Vs, Ss = [], [], [], []
+    for k, (n, nev, nex) in enumerate(shapes):
+        H, lam = known_h(n, 281 + k)
+        Hs.append(dcol(H))
+        lams.append(lam.numpy())
+        Vs.append(dcol(synth.gaussian_block(n, nev + nex, 282 + k)))
+        Ss.append(dcol(synth.gaussian_block(n, 5, 283 + k)))
+    o = chase.chase_opts_default(precision=chase.CHASE_SPLIT_BF16_RR)
+    st, sts, ritz, res, stats, bst = chase.chase_solve_batched(
+        Hs, [s[1] for s in shapes], [s[2] for s in shapes], tol, Vs, Ss, opts=o)
+    assert st == chase.CHASE_OK
+    for k, (n, nev, nex) in enumerate(shapes):
+        check_solution(Hs[k].cpu().numpy(), lams[k], ritz[k], res[k], Vs[k].cpu().numpy(), nev,
+                       tol)
