@@ -220,9 +220,9 @@ int grouped_filter_sorted(Dev& d, const std::vector<GroupedFilterInput>& in, boo
       g.Bsl = pi.Bsl;
       g.bcap = pi.bcap;
       CHASE_TRY(make_tmap_bf16_3d(&maps[nmaps * k], pi.A, 2LL * pi.n, pi.n, kSplitSlices, Kp * 2,
-                                  Kp * 2 * pi.n, 16, kSplitTileRows, kSplitSlices));
+                                  Kp * 2 * pi.n, kSplitStageK, kSplitTileRows, kSplitSlices));
       CHASE_TRY(make_tmap_bf16_3d(&maps[nmaps * k + 1], pi.Bsl, 2LL * pi.n, 2LL * pi.b, kSplitSlices,
-                                  Kp * 2, Kp * 2 * 2 * pi.bcap, 16, kSplitTileRealCols,
+                                  Kp * 2, Kp * 2 * 2 * pi.bcap, kSplitStageK, kSplitTileRealCols,
                                   kSplitSlices));
     }
   }

@@ -178,6 +178,7 @@ int zgemm_split_grouped(Dev& d, const GroupedProblem* probs, const GroupedStep* 
 constexpr int kSplitTileRows = 128;      // rows of H per split tile
 constexpr int kSplitTileRealCols = 64;   // real columns (32 complex) per split tile
 constexpr int kSplitSlices = 7;
+constexpr int kSplitStageK = 32;         // K per TMA stage box (64-byte swizzled rows)
 int64_t split_k_padded(int64_t N);
 // Slices of every problem's H: one CTA per row over all problems; row_prob
 // holds the first global row of each problem (P + 1 entries).

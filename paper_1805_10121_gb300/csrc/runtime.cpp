@@ -109,7 +109,8 @@ int make_tmap_bf16_3d(CUtensorMap* map, const void* base, int64_t d0, int64_t d1
     set_error("cuTensorMapEncodeTiled is not available from the driver");
     return CHASE_CUDA_ERROR;
   }
-  if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (s1 & 15) != 0 || (s2 & 15) != 0 || b0 * 2 != 32) {
+  if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (s1 & 15) != 0 || (s2 & 15) != 0 ||
+      (b0 * 2 != 32 && b0 * 2 != 64)) {
     set_error("bf16 tensor map: misaligned base/stride or box");
     return CHASE_INVALID_ARG;
   }
@@ -120,7 +121,8 @@ int make_tmap_bf16_3d(CUtensorMap* map, const void* base, int64_t d0, int64_t d1
                        static_cast<cuuint32_t>(b2)};
   cuuint32_t estride[3] = {1, 1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), gdim, gstride,
-                   box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
+                   box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   b0 * 2 == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     set_error("cuTensorMapEncodeTiled (bf16 3-D) failed (%d)", (int)r);

@@ -34,16 +34,23 @@
 //
 // Structure (one CTA = 128 rows of H x 32 complex columns, 320 threads):
 //  * warp 0: TMA producer, one 3-D box per operand per stage loads all S
-//    slices of a 16-wide K block (SWIZZLE_32B), 5-stage mbarrier ring (the
-//    depth hides the L2 latency of the narrow 32-byte box rows);
+//    slices of a 32-wide K range (64-byte rows, SWIZZLE_64B: the TMA unit
+//    moves one box row per cycle, so 32-byte rows would leave it as slow as
+//    the tensor pipe), 2-stage mbarrier ring;
 //  * warp 1: allocates 512 TMEM columns (7 levels x 64 FP32 columns) and one
-//    thread issues the 28 tcgen05.mma (M=128, N=64, K=16) per K block (at a
-//    chunk boundary the tail levels first, so the flush overlaps them),
-//    committing stages back to the producer and chunks to the flush warps;
+//    thread issues the MMAs of each 16-wide K block: per slice s of H one
+//    tcgen05.mma (M = 128, K = 16) against the slices t of the block whose
+//    levels s + t belong to the pass, N = 64 x (their count).  The B planes
+//    are consecutive rows of the B tile and the levels consecutive TMEM
+//    columns, so the 28 slice pairs take 10 MMAs (N up to 256), which read
+//    each slice of H from shared memory once instead of 7 - s times.  At a
+//    chunk boundary the tail levels go first, so the flush overlaps them;
+//    stages are committed back to the producer and chunks to the flush
+//    warps;
 //  * warps 2-9 (two per TMEM lane quarter, 32 columns each): flush the exact
-//    levels every chunk into int32 registers, then combine all levels in
-//    FP64 and apply the diagonal, shift, scale and axpby (Eq. 7) while
-//    writing the FP64 output.
+//    levels every chunk into int32 registers, then combine all levels and
+//    apply the diagonal, shift, scale and axpby (Eq. 7) while writing the
+//    FP64 output.
 // Every wait is bounded; a wait that gives up sets the error flag.
 #include <cuda_bf16.h>
 
@@ -57,12 +64,14 @@ namespace split {
 constexpr int S = 7;                 // 7-bit slices per operand
 constexpr int BM = 128;              // rows per CTA (TMEM lanes)
 constexpr int BN = 64;               // real columns of the product per CTA (32 complex)
-constexpr int BK = 16;               // K per stage (one 32-byte swizzle row)
-constexpr int NSTAGE = 5;
+constexpr int BK = 16;               // K per MMA (a K block)
+constexpr int KPS = 2;               // K blocks per stage: 32 K, one 64-byte swizzle row
+constexpr int BX = BK * KPS;         // K per stage
+constexpr int NSTAGE = 2;
 constexpr int CHUNK = 16;            // k-blocks per exact chunk (256 K)
 constexpr int NEXACT = 3;            // levels accumulated exactly
-constexpr int A_TILE = BM * BK * 2;  // 4096 B per slice
-constexpr int B_TILE = BN * BK * 2;  // 2048 B per slice
+constexpr int A_TILE = BM * BX * 2;  // 8192 B per slice
+constexpr int B_TILE = BN * BX * 2;  // 4096 B per slice
 constexpr int STAGE_A = S * A_TILE;
 constexpr int STAGE_B = S * B_TILE;
 constexpr int STAGE_BYTES = STAGE_A + STAGE_B;
@@ -71,13 +80,15 @@ constexpr int kFlushWarps = 8;       // two per TMEM lane quarter, 32 columns ea
 constexpr int kThreads = (2 + kFlushWarps) * 32;
 constexpr int SMEM = 1024 + NSTAGE * STAGE_BYTES + 256;
 
-__device__ __forceinline__ uint64_t desc_sw32(uint32_t saddr) {
+// K-major operand with 64-byte swizzled rows: 8-row atoms of 512 B stacked
+// along M (SBO); the second K block of a row starts 32 bytes in.
+__device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
   d |= (uint64_t)1 << 16;                 // LBO (unused for swizzled K-major)
-  d |= (uint64_t)(256 >> 4) << 32;        // SBO: 8 rows x 32 B
+  d |= (uint64_t)(512 >> 4) << 32;        // SBO: 8 rows x 64 B
   d |= (uint64_t)1 << 46;                 // version
-  d |= (uint64_t)6 << 61;                 // SWIZZLE_32B
+  d |= (uint64_t)4 << 61;                 // SWIZZLE_64B
   return d;
 }
 
@@ -189,6 +200,7 @@ __device__ __forceinline__ void split_tile_body(const SplitTile& T, int* __restr
   const int kb0 = T.kb0;
   const int M = T.M;
   const int nchunks = (nkb + CHUNK - 1) / CHUNK;
+  const int nst = (nkb + KPS - 1) / KPS;  // stages (the last may hold one K block)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NSTAGE; ++s) {
@@ -220,64 +232,72 @@ __device__ __forceinline__ void split_tile_body(const SplitTile& T, int* __restr
       prefetch_tmap(T.mapA);
       prefetch_tmap(T.mapB);
       int issued = 0;
-      for (int kb = 0; kb < nkb; ++kb) {
-        const int st = kb % NSTAGE;
-        if (kb >= NSTAGE && !mbar_wait_bounded(&empty[st], ((kb / NSTAGE) & 1) ^ 1)) {
+      for (int ks = 0; ks < nst; ++ks) {
+        const int st = ks % NSTAGE;
+        if (ks >= NSTAGE && !mbar_wait_bounded(&empty[st], ((ks / NSTAGE) & 1) ^ 1)) {
           atomicOr(err, KERR_TIMEOUT_EMPTY);
           break;
         }
         mbar_arrive_expect_tx(&full[st], STAGE_BYTES);
-        tma_load_3d(smem_u32(sA + st * STAGE_A), T.mapA, (kb0 + kb) * BK, row0, 0, smem_u32(&full[st]));
-        tma_load_3d(smem_u32(sB + st * STAGE_B), T.mapB, (kb0 + kb) * BK, colr0, 0, smem_u32(&full[st]));
+        tma_load_3d(smem_u32(sA + st * STAGE_A), T.mapA, (kb0 + ks * KPS) * BK, row0, 0, smem_u32(&full[st]));
+        tma_load_3d(smem_u32(sB + st * STAGE_B), T.mapB, (kb0 + ks * KPS) * BK, colr0, 0, smem_u32(&full[st]));
         ++issued;
       }
-      for (int kb = (issued > NSTAGE ? issued - NSTAGE : 0); kb < issued; ++kb)
-        if (!mbar_wait_bounded(&full[kb % NSTAGE], (kb / NSTAGE) & 1)) atomicOr(err, KERR_TIMEOUT_FULL);
+      for (int ks = (issued > NSTAGE ? issued - NSTAGE : 0); ks < issued; ++ks)
+        if (!mbar_wait_bounded(&full[ks % NSTAGE], (ks / NSTAGE) & 1)) atomicOr(err, KERR_TIMEOUT_FULL);
     }
   } else if (warp == 1) {
     if (lane == 0) {  // ---------------- MMA issuer
-      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                             ((uint32_t)(BM >> 4) << 24);
+      // kind::f16 instruction descriptor without N: FP32 D, BF16 A and B, K-major, M = 128
+      const uint32_t idesc_base = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BM >> 4) << 24);
       bool ok = true;
-      for (int kb = 0; kb < nkb && ok; ++kb) {
-        const int st = kb % NSTAGE;
-        const int ch = kb / CHUNK, kin = kb % CHUNK;
-        if (!mbar_wait_bounded(&full[st], (kb / NSTAGE) & 1)) {
+      for (int ks = 0; ks < nst && ok; ++ks) {
+        const int st = ks % NSTAGE;
+        if (!mbar_wait_bounded(&full[st], (ks / NSTAGE) & 1)) {
           atomicOr(err, KERR_TIMEOUT_FULL);
           ok = false;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        const uint32_t a0 = smem_u32(sA + st * STAGE_A);
-        const uint32_t b0 = smem_u32(sB + st * STAGE_B);
-        // At a chunk boundary the tail levels (3-6) go first: they do not touch
-        // the exact levels that the flush warps are still reading, so the
-        // tensor pipe works while the flush runs.
-        const bool boundary = (kin == 0 && ch > 0);
+        for (int kh = 0; kh < KPS && ok; ++kh) {
+          const int kb = ks * KPS + kh;
+          if (kb >= nkb) break;
+          const int ch = kb / CHUNK, kin = kb % CHUNK;
+          const uint32_t a0 = smem_u32(sA + st * STAGE_A) + kh * (BK * 2);
+          const uint32_t b0 = smem_u32(sB + st * STAGE_B) + kh * (BK * 2);
+          // At a chunk boundary the tail levels (3-6) go first: they do not touch
+          // the exact levels that the flush warps are still reading, so the
+          // tensor pipe works while the flush runs.
+          const bool boundary = (kin == 0 && ch > 0);
 #pragma unroll
-        for (int pass = 0; pass < 2; ++pass) {
-          const bool exact_pass = (pass == 1);
-          if (boundary && exact_pass && !mbar_wait_bounded(chunk_empty, (ch - 1) & 1)) {
-            atomicOr(err, KERR_TIMEOUT_FULL);
-            ok = false;
-            break;
-          }
+          for (int pass = 0; pass < 2; ++pass) {
+            const bool exact_pass = (pass == 1);
+            if (boundary && exact_pass && !mbar_wait_bounded(chunk_empty, (ch - 1) & 1)) {
+              atomicOr(err, KERR_TIMEOUT_FULL);
+              ok = false;
+              break;
+            }
 #pragma unroll
-          for (int s = 0; s < S; ++s) {
-            const uint64_t da = desc_sw32(a0 + s * A_TILE);
-#pragma unroll
-            for (int t = 0; t + s < S; ++t) {
-              const int d = s + t;
-              if ((d < NEXACT) != exact_pass) continue;
-              // first contribution to level d in this accumulation window?
-              const bool first = (s == 0) && (d < NEXACT ? kin == 0 : kb == 0);
-              umma_bf16(tmem + d * BN, da, desc_sw32(b0 + t * B_TILE), idesc, first ? 0u : 1u);
+            for (int s = 0; s < S; ++s) {
+              // Slice s of H against the slices t of the block that feed the levels
+              // d = s + t of this pass, as one MMA: the B planes t are consecutive
+              // rows of the B tile and the levels consecutive TMEM columns, so
+              // N = 64 x (number of levels).
+              const uint64_t da = desc_sw64(a0 + s * A_TILE);
+              const int d0 = exact_pass ? s : (s < NEXACT ? NEXACT : s);
+              const int nlev = exact_pass ? NEXACT - s : S - d0;
+              if (nlev <= 0) continue;
+              // first contribution to these levels in this accumulation window?
+              const bool first = (s == 0) && (exact_pass ? kin == 0 : kb == 0);
+              const uint32_t idn = idesc_base | ((uint32_t)((nlev * BN) >> 3) << 17);
+              umma_bf16(tmem + d0 * BN, da, desc_sw64(b0 + (d0 - s) * B_TILE), idn, first ? 0u : 1u);
             }
           }
+          if (!ok) break;
+          if (kin == CHUNK - 1 || kb == nkb - 1) umma_commit(smem_u32(chunk_full));
         }
         if (!ok) break;
         umma_commit(smem_u32(&empty[st]));
-        if (kin == CHUNK - 1 || kb == nkb - 1) umma_commit(smem_u32(chunk_full));
       }
       umma_commit(smem_u32(done));  // every MMA of this CTA has completed when this fires
       if (!mbar_wait_bounded(done, 0)) atomicOr(err, KERR_TIMEOUT_FULL);
@@ -784,7 +804,7 @@ __global__ void split_combine_kernel(const E* __restrict__ P, int nseg, long lon
 namespace {
 int64_t k_padded(int64_t N) { return ((2 * N + split::BK - 1) / split::BK) * split::BK; }
 static_assert(kSplitTileRows == split::BM && kSplitTileRealCols == split::BN &&
-                  kSplitSlices == split::S,
+                  kSplitSlices == split::S && kSplitStageK == split::BX,
               "grouped tile constants");
 }  // namespace
 
@@ -874,9 +894,9 @@ int split_product(Dev& d, const SplitH& h, SplitX& x, const E* X, int64_t ldx, i
   note_launch();
   CHASE_CUDA(cudaGetLastError());
   CUtensorMap tmA, tmB;
-  CHASE_TRY(make_tmap_bf16_3d(&tmA, h.A, K, N, split::S, Kp * 2, Kp * 2 * N, split::BK, split::BM,
+  CHASE_TRY(make_tmap_bf16_3d(&tmA, h.A, K, N, split::S, Kp * 2, Kp * 2 * N, split::BX, split::BM,
                               split::S));
-  CHASE_TRY(make_tmap_bf16_3d(&tmB, x.B, K, brows, split::S, Kp * 2, Kp * 2 * rows_cap, split::BK,
+  CHASE_TRY(make_tmap_bf16_3d(&tmB, x.B, K, brows, split::S, Kp * 2, Kp * 2 * rows_cap, split::BX,
                               split::BN, split::S));
   static bool attr_done = false;
   if (!attr_done) {
@@ -910,7 +930,8 @@ int split_product(Dev& d, const SplitH& h, SplitX& x, const E* X, int64_t ldx, i
     x.P_cap = std::max(need, 2 * x.P_cap);
   }
   E* P = static_cast<E*>(x.P);
-  const int per = (nkb + nseg - 1) / nseg;
+  int per = (nkb + nseg - 1) / nseg;
+  per = (per + split::KPS - 1) / split::KPS * split::KPS;  // segments start on stage boundaries
   for (int g = 0; g < nseg; ++g) {
     const int kb0 = g * per;
     const int cnt = std::min(per, nkb - kb0);
