@@ -54,7 +54,8 @@ def parse():
                    help="split: split-BF16 filter; split_rr: also Rayleigh-Ritz's H Q on the "
                         "split product; fp64: FP64 throughout")
     p.add_argument("--workload", default="sequence",
-                   choices=["sequence", "filter", "serve", "batched", "degree-sweep"],
+                   choices=["sequence", "filter", "serve", "batched", "batched-solve",
+                            "degree-sweep"],
                    help="sequence: timed solves of the correlated sequence (default); "
                         "filter: timed degree-m filter calls on one problem, split vs FP64")
     p.add_argument("--filter-degree", type=int, default=20)
@@ -177,35 +178,40 @@ def prec_code(name):
 SPLIT_PAIRS = 28
 
 
-def roofline_entry(stats_list, pk, src, precision):
+def _split_filter_roofline(stats_list, pk, src):
     flops = sum(s["flops_filter"] for s in stats_list)
     secs = sum(s["t_filter"] for s in stats_list)
     fp64_equiv = flops / secs / 1e12 if secs > 0 else 0.0
-    if precision in ("split", "split_rr"):
-        # BF16 tensor work the algorithm executes: 28 slice products, each a
-        # real GEMM of 8 N^2 b FLOPs per b complex columns.  The kernel runs
-        # inside a multi-second solve: sustained bf16 peak.
-        achieved = SPLIT_PAIRS * fp64_equiv
-        peak = pk.get("bf16_tflops_sustained", 1700.0)
-        return {
-            "bound": "tensor",
-            "kernel": "zgemm_split_kernel (tcgen05 BF16 slice products, exact level sums, "
-                      "fused recurrence epilogue)",
-            "achieved": round(achieved, 2),
-            "peak": round(peak, 1),
-            "unit": "TFLOP/s",
-            "frac": round(achieved / peak, 4),
-            "traffic": None,
-            "peak_source": f"{src} bf16_tflops_sustained",
-            "fp64_equivalent_tflops": round(fp64_equiv, 3),
-        }
-    # The FP64 filter draws little power and runs at the maximum SM clock
-    # (sampled below), so the burst figure is the applicable one.
-    peak = pk.get("bf16_tflops", 1900.0) * NOMINAL_FP64_OVER_BF16
-    executed = FP64_EXECUTED_PER_ALGORITHMIC * fp64_equiv
+    # BF16 tensor work the algorithm executes: 28 slice products, each a real
+    # GEMM of 8 N^2 b FLOPs per b complex columns.  The kernel runs inside a
+    # multi-second solve: sustained bf16 peak.
+    achieved = SPLIT_PAIRS * fp64_equiv
+    peak = pk.get("bf16_tflops_sustained", 1700.0)
     return {
         "bound": "tensor",
-        "kernel": "zgemm_tma_kernel (FP64 DMMA filter step, 3M complex form, fused shift/axpby)",
+        "kernel": "zgemm_split_kernel (tcgen05 BF16 slice products, exact level sums, "
+                  "fused recurrence epilogue): the filter steps",
+        "achieved": round(achieved, 2),
+        "peak": round(peak, 1),
+        "unit": "TFLOP/s",
+        "frac": round(achieved / peak, 4),
+        "traffic": None,
+        "peak_source": f"{src} bf16_tflops_sustained",
+        "fp64_equivalent_tflops": round(fp64_equiv, 3),
+        "timing": "filter phase (product launches and the slicing of the block), CUDA events "
+                  "on the solve's stream",
+    }
+
+
+def _fp64_roofline(flops, secs, pk, src, what):
+    # The FP64 products draw little power and run at the maximum SM clock
+    # (sampled below), so the burst figure is the applicable one.
+    alg = flops / secs / 1e12 if secs > 0 else 0.0
+    peak = pk.get("bf16_tflops", 1900.0) * NOMINAL_FP64_OVER_BF16
+    executed = FP64_EXECUTED_PER_ALGORITHMIC * alg
+    return {
+        "bound": "tensor",
+        "kernel": f"zgemm_tma_kernel (FP64 DMMA, 3M complex form): {what}",
         "achieved": round(executed, 4),
         "peak": round(peak, 4),
         "unit": "TFLOP/s",
@@ -214,8 +220,31 @@ def roofline_entry(stats_list, pk, src, precision):
         "peak_source": f"{src} bf16_tflops (burst) x nominal FP64/BF16 ratio (1.25/2250); "
                        "a DMMA-only probe kernel measured 1.05 TFLOP/s on this pool",
         "achieved_counts": "executed DMMA FLOPs (3M form: 6 per 8 algorithmic)",
-        "algorithmic_tflops": round(fp64_equiv, 4),
+        "algorithmic_tflops": round(alg, 4),
     }
+
+
+def roofline_entry(stats_list, pk, src, precision):
+    """(dominant kernel's roofline, the other hot kernel's) for a solve."""
+    if precision == "fp64":
+        flops = sum(s["flops_filter"] for s in stats_list)
+        secs = sum(s["t_filter"] for s in stats_list)
+        return _fp64_roofline(flops, secs, pk, src, "the filter steps"), None
+    filt = _split_filter_roofline(stats_list, pk, src)
+    rr_fl = sum(s["flops_rr_product"] for s in stats_list)
+    rr_t = sum(s["t_rr_product"] for s in stats_list)
+    if precision == "split_rr":
+        rr = {"kernel": "zgemm_split_kernel: Rayleigh-Ritz H Q",
+              "fp64_equivalent_tflops": round(rr_fl / rr_t / 1e12, 3) if rr_t > 0 else None,
+              "seconds": round(rr_t, 3)}
+        return filt, rr
+    # split: Rayleigh-Ritz's H Q stays FP64 and takes more device time than
+    # the filter (ncu launch list), so it is the dominant kernel
+    rr = _fp64_roofline(rr_fl, rr_t, pk, src, "Rayleigh-Ritz H Q (FP64 by specification)")
+    rr["timing"] = "H Q products, CUDA events on the solve's stream"
+    if rr_t >= sum(s["t_filter"] for s in stats_list):
+        return rr, filt
+    return filt, rr
 
 
 def workload_config(args, world):
@@ -529,6 +558,98 @@ def run_batched_workload(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def run_batched_solve_workload(args, rank, world, local):
+    """Many independent problems solved by chase_solve_batched: every
+    iteration's filters of all problems still iterating run as one grouped
+    launch per degree step.  Also times the first 32 problems solved one by
+    one with chase_solve against the batched solve of the same 32."""
+    from paper_1805_10121_gb300 import build, chase, synth
+    build.build()
+    chase.lib()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    P = args.batch_problems
+    seed = args.seed + 1000 * rank
+    shapes = synth.batched_shapes(P, seed)
+    Hs, lams, V0s, Ss = [], [], [], []
+    for k, (n, nev, nex) in enumerate(shapes):
+        lam = synth.spectrum_uniform(n, seed + 10 * k, device=dev)
+        Hs.append(synth.hermitian_dft(lam, seed + 10 * k + 1))
+        lams.append(lam.cpu().numpy())
+        V0s.append(synth.gaussian_block(n, nev + nex, seed + 10 * k + 2, device=dev))
+        Ss.append(synth.gaussian_block(n, 5, seed + 10 * k + 3, device=dev))
+    nevs = [s[1] for s in shapes]
+    nexs = [s[2] for s in shapes]
+    prec = prec_code(args.precision)
+    o = chase.chase_opts_default(precision=prec)
+
+    def batched(idx):
+        Vs = [V0s[i].clone() for i in idx]
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        out = chase.chase_solve_batched([Hs[i] for i in idx], [nevs[i] for i in idx],
+                                        [nexs[i] for i in idx], args.tol, Vs,
+                                        [Ss[i] for i in idx], opts=o)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t, out
+
+    sub = list(range(min(32, P)))
+    batched(sub[:4])  # warm-up: library, handles, kernels
+    for _ in range(max(0, args.warmup - 1)):
+        batched(sub[:4])
+    clocks = ClockSampler(local)
+    launches0 = chase.chase_kernel_launches()
+    clocks.start()
+    wall, (st, sts, ritz, res, stats, bst) = batched(list(range(P)))
+    clk = clocks.stop()
+    launches = chase.chase_kernel_launches() - launches0
+    flops = sum(s["flops_total"] for s in stats)
+    ok = all(x == 0 for x in sts)
+    err = max(float(np.max(np.abs(ritz[k][:nevs[k]] - lams[k][:nevs[k]]))) /
+              float(np.abs(lams[k]).max()) for k in range(P))
+    # the same 32 problems one by one
+    t_seq = 0.0
+    for i in sub:
+        V = V0s[i].clone()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        chase.chase_solve(Hs[i], nevs[i], nexs[i], args.tol, V, Ss[i], opts=o)
+        torch.cuda.synchronize()
+        t_seq += time.perf_counter() - t
+    t_b32, _ = batched(sub)
+    pk, src = peaks()
+    cfg = {
+        "workload": (f"batched solve of {P} independent problems, N uniform in [256, 2048], "
+                     f"nev = 5% N, nex = 2% N, eigenvalues uniform in [-1, 1], tol {args.tol}; "
+                     f"step = one chase_solve_batched call"),
+        "problems": P, "precision": args.precision,
+        "l2": "inputs larger than L2",
+        "parallelism": "replicas" if world > 1 else "single GPU",
+    }
+    its = [s["iterations"] for s in stats]
+    line = {
+        "metric": METRIC, "value": round(flops / wall / 1e12, 4), "unit": "TFLOP/s",
+        "n_gpus": world, "steps": 1, "warmup": args.warmup, "ms_per_step": round(1e3 * wall, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16-split+f64" if prec != chase.CHASE_FP64 else "f64", "data": "synthetic",
+        "config": cfg,
+        "batched_solve": {"all_converged": ok, "max_eig_err_over_norm": err,
+                          "iterations_min_mean_max": [min(its), round(float(np.mean(its)), 2),
+                                                      max(its)],
+                          "grouped_filter_seconds": round(bst["t_steps"], 3),
+                          "grouped_product_seconds": round(bst["t_product"], 3),
+                          "grouped_steps": bst["steps"],
+                          "qr_seconds_sum": round(sum(s["t_qr"] for s in stats), 3),
+                          "rr_seconds_sum": round(sum(s["t_rr"] for s in stats), 3),
+                          "first32_one_by_one_seconds": round(t_seq, 3),
+                          "first32_batched_seconds": round(t_b32, 3),
+                          "first32_speedup": round(t_seq / t_b32, 2)},
+        "gpu_launches": int(launches), "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def batched_cpu_baseline(shapes, degs, seed, budget_s):
     """The oracle's filter on the first problems of the same batch (inputs
     from the host generators), until the time budget is spent; only the
@@ -696,6 +817,9 @@ def main():
     if args.workload == "batched":
         run_batched_workload(args, rank, world, local)
         return
+    if args.workload == "batched-solve":
+        run_batched_solve_workload(args, rank, world, local)
+        return
     if args.workload == "degree-sweep":
         run_degree_sweep(args, rank, world, local)
         return
@@ -841,6 +965,7 @@ def main():
             torch.distributed.destroy_process_group()
         return
     pk, src = peaks()
+    roof_main, roof_other = roofline_entry(stats_t, pk, src, args.precision)
     cb = None
     if not args.no_cpu_baseline and world == 1:
         cb = cpu_baseline_sample(n, nev, nex, args.seed, args.cpu_sample_seconds)
@@ -870,7 +995,8 @@ def main():
         "phase_seconds": {k2: round(sum(s[k2] for s in stats_t), 3)
                           for k2 in ("t_lanczos", "t_filter", "t_qr", "t_rr", "t_eigh", "t_host")},
         "warmup_iterations": [s["iterations"] for _, s in stats_w],
-        "roofline": roofline_entry(stats_t, pk, src, args.precision),
+        "roofline": roof_main,
+        "roofline_other_kernel": roof_other,
         "fp64_same_problem": fp64,
         "split_rr_same_problem": split_rr,
         "cpu_baseline": cb,

@@ -71,6 +71,13 @@ typedef struct {
  * take CHASE_FP64 or CHASE_SPLIT_BF16). */
 #define CHASE_SPLIT_BF16_RR 2
 
+/* ---- which part of H the solver reads (chase_solve*, via chase_opts) ---- */
+#define CHASE_STORAGE_FULL 0  /* both triangles hold H */
+/* Only the lower triangle (diagonal included) is read, as a HEMM with
+ * uplo = 'L' would (Sec. 5.1); the strict upper triangle may hold anything.
+ * The solver forms the full matrix once in a workspace of N x N entries. */
+#define CHASE_STORAGE_LOWER 1
+
 /* ---- residual test used for locking (Alg. 3 line 4) ---- */
 #define CHASE_CONV_ABS 0 /* Res <= tol (the paper's absolute criterion, Sec. 6.1) */
 #define CHASE_CONV_REL 1 /* Res <= tol * h, h = largest |Ritz value| seen (<= ||H||_2) */
@@ -88,6 +95,7 @@ typedef struct {
   double dos_sigma; /* Gaussian width of Eq. 10 in the variable mapped to [-1, 1] (Sec. 4.2: 0.25) */
   int conv_mode;    /* CHASE_CONV_ABS or CHASE_CONV_REL */
   int precision;    /* CHASE_FP64, CHASE_SPLIT_BF16 or CHASE_SPLIT_BF16_RR */
+  int storage;      /* CHASE_STORAGE_FULL or CHASE_STORAGE_LOWER */
 } chase_opts;
 
 /* Counters and per-phase times of one chase_solve call. */
@@ -101,6 +109,8 @@ typedef struct {
   double flops_filter;     /* 8 N^2 * filter_matvecs (2 N^2 for real problems) */
   double flops_total;      /* all algorithmic FLOPs of the solve */
   double t_total, t_lanczos, t_filter, t_qr, t_rr, t_eigh, t_resid, t_host; /* seconds */
+  double t_rr_product;     /* seconds of Rayleigh-Ritz's H Q products (inside t_rr) */
+  double flops_rr_product; /* their algorithmic FLOPs (8 N^2 b complex, 2 N^2 b real) */
 } chase_stats;
 
 /* Tile choice of the grouped FP64 filter: time the candidates on the first

@@ -25,7 +25,8 @@ __all__ = [
     "CHASE_OK", "CHASE_INVALID_ARG", "CHASE_NOT_CONVERGED", "CHASE_QR_BREAKDOWN",
     "CHASE_BOUND_VIOLATION", "CHASE_CUDA_ERROR", "CHASE_OUT_OF_MEMORY", "CHASE_TIMEOUT",
     "CHASE_EIGENSOLVER_ERROR", "CHASE_CONV_ABS", "CHASE_CONV_REL", "CHASE_FP64",
-    "CHASE_SPLIT_BF16", "CHASE_SPLIT_BF16_RR", "CHASE_TILE_AUTO", "ChaseBatchStats", "chase_filter_batched",
+    "CHASE_SPLIT_BF16", "CHASE_SPLIT_BF16_RR", "CHASE_TILE_AUTO", "CHASE_STORAGE_FULL",
+    "CHASE_STORAGE_LOWER", "ChaseBatchStats", "chase_filter_batched",
     "chase_solve_batched", "chase_filter_real", "chase_residuals_real", "chase_solve_real",
 ]
 
@@ -47,6 +48,8 @@ CHASE_SPLIT_BF16_RR = 2
 CHASE_CONV_ABS = 0
 CHASE_CONV_REL = 1
 CHASE_TILE_AUTO = -1
+CHASE_STORAGE_FULL = 0
+CHASE_STORAGE_LOWER = 1
 
 
 class ChaseError(RuntimeError):
@@ -60,7 +63,7 @@ class ChaseOpts(ctypes.Structure):
         ("deg", ctypes.c_int), ("optim", ctypes.c_int), ("deg_extra", ctypes.c_int),
         ("deg_max", ctypes.c_int), ("max_iter", ctypes.c_int), ("lanczos_iter", ctypes.c_int),
         ("num_lanczos", ctypes.c_int), ("approx", ctypes.c_int), ("dos_sigma", ctypes.c_double),
-        ("conv_mode", ctypes.c_int), ("precision", ctypes.c_int),
+        ("conv_mode", ctypes.c_int), ("precision", ctypes.c_int), ("storage", ctypes.c_int),
     ]
 
 
@@ -73,7 +76,8 @@ class ChaseStats(ctypes.Structure):
         ("flops_total", ctypes.c_double), ("t_total", ctypes.c_double),
         ("t_lanczos", ctypes.c_double), ("t_filter", ctypes.c_double), ("t_qr", ctypes.c_double),
         ("t_rr", ctypes.c_double), ("t_eigh", ctypes.c_double), ("t_resid", ctypes.c_double),
-        ("t_host", ctypes.c_double),
+        ("t_host", ctypes.c_double), ("t_rr_product", ctypes.c_double),
+        ("flops_rr_product", ctypes.c_double),
     ]
 
     def as_dict(self):

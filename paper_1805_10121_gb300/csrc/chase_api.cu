@@ -10,7 +10,13 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <condition_variable>
+#include <functional>
+#include <memory>
+#include <mutex>
 #include <numeric>
+#include <string>
+#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -23,6 +29,7 @@ namespace chase {
 namespace {
 
 constexpr int kMaxDegAllowed = 1024;
+constexpr int kBatchWorkers = 8;  // host threads for the per-problem phases of a batched solve
 
 // Real problems: every matrix handed to the TMA product has an even leading
 // dimension (TMA strides are multiples of 16 bytes), so internal buffers pad
@@ -227,13 +234,16 @@ int rr_alloc(Dev& d, int64_t N, int b, RRWork<T>& w) {
 template <class T>
 int rr_core(Dev& d, const T* H, int64_t N, int64_t ldh, T* Q, int64_t ldq, int b,
             double* w_dev, double* res_dev, RRWork<T>& w, double* t_eigh, double* flops,
-            const SplitH* sh = nullptr, SplitX* sx = nullptr) {
+            const SplitH* sh = nullptr, SplitX* sx = nullptr, double* t_hq = nullptr) {
   if (b == 0) return CHASE_OK;
   const int64_t lN = ld_pad<T>(N), lg = ld_pad<T>(b);
+  PhaseTimer tq(d.st);
+  if (t_hq) tq.begin(t_hq);
   if (sh)  // H Q on the split product (CHASE_SPLIT_BF16_RR)
     CHASE_TRY(zgemm_split(d, *sh, *sx, Q, ldq, 0, b, w.HQ, lN, 1.0, 0.0, 0.0));
   else
     CHASE_TRY(gemm(d, N, N, H, ldh, Q, ldq, b, w.HQ, lN, 0, b, 1.0, 0.0, 0.0));  // H Q
+  if (t_hq) tq.end();
   CHASE_TRY(gram(d, N, Q, ldq, b, w.HQ, lN, b, w.G, lg));                       // G = Q^H H Q
   CHASE_TRY(launch_hermitize(d, w.G, lg, b));
   PhaseTimer tm(d.st);
@@ -480,6 +490,14 @@ struct Solver {
     PhaseTimer tm(d.st);
     const int r = o.approx ? 1 : 1 + o.num_lanczos;
     CHASE_TRY(stage_in(d, dev, H, ldh, N, N, &dH, &lh));
+    if (o.storage == CHASE_STORAGE_LOWER) {  // the full matrix from its lower triangle
+      T* full = nullptr;
+      const int64_t lf = ld_pad<T>(N);
+      CHASE_TRY(d.alloc(&full, static_cast<size_t>(lf) * N));
+      CHASE_TRY(launch_hermitian_from_lower(d, dH, lh, full, lf, N));
+      dH = full;
+      lh = lf;
+    }
     CHASE_TRY(stage_in(d, dev, V, ldv, N, nx, &dV, &lv));
     CHASE_TRY(stage_in(d, dev, starts, N, N, r, &dS, &ls));
     lw = ld_pad<T>(N);
@@ -600,7 +618,9 @@ struct Solver {
     // lines 7-8: Rayleigh-Ritz on the active block, residuals
     tm.begin(&S.t_rr);
     CHASE_TRY(rr_core(d, dH, N, lh, va, lv, nb, dw, dres, rw, &S.t_eigh, &S.flops_total,
-                      split_rr ? rr_slices : nullptr, split_rr ? rr_sx : nullptr));
+                      split_rr ? rr_slices : nullptr, split_rr ? rr_sx : nullptr,
+                      &S.t_rr_product));
+    S.flops_rr_product += kMv * N2 * nb;
     CHASE_CUDA(cudaMemcpyAsync(ra.data(), dw, sizeof(double) * nb, cudaMemcpyDeviceToHost, d.st));
     CHASE_CUDA(cudaMemcpyAsync(rr.data(), dres, sizeof(double) * nb, cudaMemcpyDeviceToHost, d.st));
     tm.end();
@@ -691,6 +711,105 @@ struct Solver {
   }
 };
 
+
+// Host threads, each with its own stream and device context, for the
+// per-problem phases of a batched solve (set-up, QR, Rayleigh-Ritz, locking):
+// the small launches and host round trips of different problems overlap.
+// The threads live as long as the pool; each destroys its cuSOLVER handle
+// before it ends.
+class WorkerPool {
+ public:
+  explicit WorkerPool(cudaStream_t main) : main_(main) {}
+  WorkerPool(const WorkerPool&) = delete;
+  WorkerPool& operator=(const WorkerPool&) = delete;
+
+  int init(int n) {
+    for (int w = 0; w < n; ++w) {
+      cudaStream_t s = nullptr;
+      CHASE_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+      streams_.push_back(s);
+      devs_.emplace_back(new Dev(s));
+      CHASE_TRY(devs_.back()->init());
+    }
+    nw_ = n;
+    rc_.assign(n, CHASE_OK);
+    msg_.assign(n, std::string());
+    threads_.reserve(n);
+    for (int w = 0; w < n; ++w) threads_.emplace_back([this, w] { loop(w); });
+    return CHASE_OK;
+  }
+
+  ~WorkerPool() {
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      stop_ = true;
+    }
+    cv_.notify_all();
+    for (auto& t : threads_) t.join();
+    cudaStreamSynchronize(main_);  // main-stream work may still read worker buffers
+    devs_.clear();                 // frees on each worker stream and synchronises it
+    for (auto s : streams_) cudaStreamDestroy(s);
+  }
+
+  // fn(worker context, item) for every item, round robin over the workers.
+  int run(const std::vector<int>& items, std::function<int(Dev&, int)> fn) {
+    std::unique_lock<std::mutex> lk(mu_);
+    items_ = &items;
+    job_ = std::move(fn);
+    finished_ = 0;
+    ++generation_;
+    cv_.notify_all();
+    done_.wait(lk, [&] { return finished_ == nw_; });
+    for (int w = 0; w < nw_; ++w)
+      if (rc_[w] != CHASE_OK) {
+        set_error("%s", msg_[w].c_str());
+        return rc_[w];
+      }
+    return CHASE_OK;
+  }
+
+ private:
+  void loop(int w) {
+    int seen = 0;
+    const size_t nw = static_cast<size_t>(nw_);
+    for (;;) {
+      std::unique_lock<std::mutex> lk(mu_);
+      cv_.wait(lk, [&] { return stop_ || generation_ != seen; });
+      if (stop_) break;
+      seen = generation_;
+      const std::vector<int>* items = items_;
+      lk.unlock();
+      int r = CHASE_OK;
+      std::string m;
+      for (size_t i = static_cast<size_t>(w); i < items->size(); i += nw) {
+        r = job_(*devs_[w], (*items)[i]);
+        if (r != CHASE_OK) {
+          m = chase_last_error();
+          break;
+        }
+      }
+      lk.lock();
+      rc_[w] = r;
+      msg_[w] = m;
+      if (++finished_ == nw_) done_.notify_one();
+    }
+    release_thread_solver();
+  }
+
+  cudaStream_t main_;
+  std::vector<cudaStream_t> streams_;
+  std::vector<std::unique_ptr<Dev>> devs_;
+  std::vector<std::thread> threads_;
+  std::mutex mu_;
+  std::condition_variable cv_, done_;
+  std::function<int(Dev&, int)> job_;
+  const std::vector<int>* items_ = nullptr;
+  int nw_ = 0, generation_ = 0, finished_ = 0;
+  bool stop_ = false;
+  std::vector<int> rc_;
+  std::vector<std::string> msg_;
+};
+
 // Arguments of one solve, checked as chase_solve does.
 bool solve_args_ok(int64_t N, int64_t ldh, int nev, int nex, double tol, int64_t ldv,
                    const void* H, const void* V, const void* Lambda, const void* resid,
@@ -703,7 +822,8 @@ bool solve_args_ok(int64_t N, int64_t ldh, int nev, int nex, double tol, int64_t
            (!o.approx && o.num_lanczos < 1) ||
            (o.precision != CHASE_FP64 && o.precision != CHASE_SPLIT_BF16 &&
             o.precision != CHASE_SPLIT_BF16_RR) ||
-           (o.conv_mode != CHASE_CONV_ABS && o.conv_mode != CHASE_CONV_REL));
+           (o.conv_mode != CHASE_CONV_ABS && o.conv_mode != CHASE_CONV_REL) ||
+           (o.storage != CHASE_STORAGE_FULL && o.storage != CHASE_STORAGE_LOWER));
 }
 
 }  // namespace
@@ -727,6 +847,7 @@ extern "C" int chase_opts_default(chase_opts* o) {
   o->dos_sigma = 0.25;
   o->conv_mode = CHASE_CONV_REL;
   o->precision = CHASE_FP64;
+  o->storage = CHASE_STORAGE_FULL;
   return CHASE_OK;
 }
 
@@ -1068,7 +1189,7 @@ extern "C" int chase_solve_batched(int P, const chase_c64* const* H, const int64
   CHASE_TRY(d.init());
   const bool split = o.precision != CHASE_FP64;
   std::vector<Solver<chase_c64>> sv(P);
-  for (int p = 0; p < P; ++p) {  // Alg. 1 lines 1-2 of every problem
+  for (int p = 0; p < P; ++p) {
     Solver<chase_c64>& s = sv[p];
     s.H = H[p];
     s.N = N[p];
@@ -1083,8 +1204,13 @@ extern "C" int chase_solve_batched(int P, const chase_c64* const* H, const int64
     s.starts = lanczos_starts[p];
     s.o = o;
     s.dev = true;
-    CHASE_TRY(s.setup(d, true));
   }
+  WorkerPool pool(d.st);
+  CHASE_TRY(pool.init(std::min(P, kBatchWorkers)));
+  std::vector<int> all(P);
+  std::iota(all.begin(), all.end(), 0);
+  // Alg. 1 lines 1-2 of every problem
+  CHASE_TRY(pool.run(all, [&](Dev& w, int p) { return sv[p].setup(w, true); }));
   std::vector<GroupedFilterInput> slices(P);  // split: slices of every H, made once
   if (split) {
     std::vector<int> bcap(P);
@@ -1147,14 +1273,19 @@ extern "C" int chase_solve_batched(int P, const chase_c64* const* H, const int64
       // the grouped filter's time, shared out by each problem's FLOPs
       if (tt.flops > 0) s.S.t_filter += tt.t_steps * 8.0 * s.N2 * fm / tt.flops;
     }
-    for (int p : act) CHASE_TRY(sv[p].after_filter(d));  // lines 5-15
+    CHASE_TRY(pool.run(act, [&](Dev& w, int p) { return sv[p].after_filter(w); }));  // lines 5-15
   }
   int worst = CHASE_OK;
   const double t_total =
       std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  std::vector<int> fin_st(P, CHASE_OK);
+  CHASE_TRY(pool.run(all, [&](Dev& w, int p) {
+    fin_st[p] = sv[p].finish(w);
+    const int st = fin_st[p];
+    return (st == CHASE_NOT_CONVERGED || st == CHASE_BOUND_VIOLATION) ? CHASE_OK : st;
+  }));
   for (int p = 0; p < P; ++p) {
-    const int st = sv[p].finish(d);
-    if (st != CHASE_OK && st != CHASE_NOT_CONVERGED && st != CHASE_BOUND_VIOLATION) return st;
+    const int st = fin_st[p];
     status[p] = st;
     if (worst == CHASE_OK && st != CHASE_OK) worst = st;
     sv[p].S.t_total = t_total;

@@ -89,6 +89,10 @@ int launch_lanczos_step(Dev& d, int64_t N, int64_t ld, int r, int step, const T*
 // Normalise r columns in place (Lanczos start vectors).
 template <class T>
 int launch_normalize_cols(Dev& d, T* X, int64_t ldx, int64_t N, int r);
+// F (n x n, ldf) = the Hermitian (real: symmetric) matrix whose lower
+// triangle, diagonal included, is that of L; L's strict upper part is not read.
+template <class T>
+int launch_hermitian_from_lower(Dev& d, const T* L, int64_t ldl, T* F, int64_t ldf, int64_t n);
 // Fill the strict lower (lower=true) or upper part of a p x p matrix with zero.
 template <class T>
 int launch_zero_triangle(Dev& d, T* A, int64_t lda, int p, bool lower);
@@ -243,6 +247,8 @@ int launch_grouped_permute(Dev& d, const GroupedPermute* probs, int P, int total
 // ---- eigh (cuSOLVER, the small projected eigensolve of Alg. 2 line 3) -----
 int eigh_device(Dev& d, chase_c64* G, int64_t ldg, int p, double* w_dev);
 int eigh_device(Dev& d, double* G, int64_t ldg, int p, double* w_dev);
+// Destroy the calling thread's cuSOLVER handle (worker threads, before they end).
+void release_thread_solver();
 
 // ---- host_alg.cpp ----------------------------------------------------------
 // Symmetric tridiagonal eigenproblem (implicit QL with Wilkinson shifts):

@@ -425,6 +425,21 @@ __global__ void hermitize_kernel(T* __restrict__ G, long long ldg, int p) {
   }
 }
 
+// F = the Hermitian matrix whose lower triangle (diagonal included) is L's:
+// F[r, c] = L[r, c] for r >= c, conj(L[c, r]) above; the diagonal is real.
+template <class T>
+__global__ void hermitian_from_lower_kernel(const T* __restrict__ L, long long ldl,
+                                            T* __restrict__ F, long long ldf, long long n) {
+  const long long total = n * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e % n, c = e / n;
+    T v = r >= c ? L[c * ldl + r] : Sc<T>::conj(L[r * ldl + c]);
+    if (r == c) Sc<T>::hermitize_diag(v);
+    F[c * ldf + r] = v;
+  }
+}
+
 template <class T>
 __global__ void zero_triangle_kernel(T* __restrict__ A, long long lda, int p, int lower) {
   const long long n = (long long)p * p;
@@ -730,6 +745,16 @@ int launch_hermitize(Dev& d, T* G, int64_t ldg, int p) {
 }
 
 template <class T>
+int launch_hermitian_from_lower(Dev& d, const T* L, int64_t ldl, T* F, int64_t ldf, int64_t n) {
+  if (n == 0) return CHASE_OK;
+  hermitian_from_lower_kernel<<<grid_for(n * n, 256, 152 * 16), 256, 0, d.st>>>(dp(L), ldl, dp(F),
+                                                                                 ldf, n);
+  note_launch();
+  CHASE_CUDA(cudaGetLastError());
+  return CHASE_OK;
+}
+
+template <class T>
 int launch_zero_triangle(Dev& d, T* A, int64_t lda, int p, bool lower) {
   if (p == 0) return CHASE_OK;
   zero_triangle_kernel<<<grid_for((long long)p * p, 256, 4096), 256, 0, d.st>>>(dp(A), lda, p,
@@ -856,6 +881,7 @@ int launch_normalize_cols(Dev& d, T* X, int64_t ldx, int64_t N, int r) {
                                      const double*, double*);                                      \
   template int launch_hermitize<T>(Dev&, T*, int64_t, int);                                        \
   template int launch_zero_triangle<T>(Dev&, T*, int64_t, int, bool);                              \
+  template int launch_hermitian_from_lower<T>(Dev&, const T*, int64_t, T*, int64_t, int64_t);      \
   template int launch_cholesky<T>(Dev&, T*, int64_t, int, double, double);                         \
   template int cholesky_blocked<T>(Dev&, T*, int64_t, int, double, double, double*, T*);           \
   template int trsm_right_lh<T>(Dev&, T*, int64_t, int64_t, const T*, int64_t, int, T*);           \
@@ -871,6 +897,13 @@ CHASE_INSTANTIATE_ELEMENT_LAUNCHERS(double)
 // ---------------------------------------------------------------------------
 namespace {
 thread_local cusolverDnHandle_t t_solver = nullptr;
+}
+
+void release_thread_solver() {
+  if (t_solver) {
+    cusolverDnDestroy(t_solver);
+    t_solver = nullptr;
+  }
 }
 
 namespace {
