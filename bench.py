@@ -178,6 +178,18 @@ def prec_code(name):
 SPLIT_PAIRS = 28
 
 
+# DRAM traffic of single launches measured with ncu (profiles/*_n4000_full.md):
+# the bench's own N = 8000 launches are larger than the capture size rule
+# allows, so "traffic" stays null and the small-case figures ride along.
+NCU_TRAFFIC = {
+    "zgemm_split_kernel": {"case": "N=4000, 480 real columns, full-width degree step",
+                           "dram_bytes": 588.6e6 + 41.9e6, "algorithmic_bytes": 548e6},
+    "zgemm_tma_kernel": {"case": "N=4000, 240 columns, FP64 filter step (same tile as the "
+                                 "Rayleigh-Ritz H Q)",
+                         "dram_bytes": 647.2e6 + 18.4e6, "algorithmic_bytes": 301e6},
+}
+
+
 def _split_filter_roofline(stats_list, pk, src):
     flops = sum(s["flops_filter"] for s in stats_list)
     secs = sum(s["t_filter"] for s in stats_list)
@@ -200,6 +212,7 @@ def _split_filter_roofline(stats_list, pk, src):
         "fp64_equivalent_tflops": round(fp64_equiv, 3),
         "timing": "filter phase (product launches and the slicing of the block), CUDA events "
                   "on the solve's stream",
+        "traffic_ncu_small_case": NCU_TRAFFIC["zgemm_split_kernel"],
     }
 
 
@@ -221,6 +234,7 @@ def _fp64_roofline(flops, secs, pk, src, what):
                        "a DMMA-only probe kernel measured 1.05 TFLOP/s on this pool",
         "achieved_counts": "executed DMMA FLOPs (3M form: 6 per 8 algorithmic)",
         "algorithmic_tflops": round(alg, 4),
+        "traffic_ncu_small_case": NCU_TRAFFIC["zgemm_tma_kernel"],
     }
 
 

@@ -41,6 +41,11 @@ typedef struct {
   double re, im;
 } chase_c64;
 
+/* complex64, interleaved (single-precision entry points) */
+typedef struct {
+  float re, im;
+} chase_c32;
+
 /* ---- status codes ---- */
 #define CHASE_OK 0
 #define CHASE_INVALID_ARG 1       /* a size, pointer, degree or option is invalid */
@@ -287,6 +292,35 @@ int chase_solve_real(const double* H, int64_t N, int64_t ldh, int nev, int nex, 
                      double* V, int64_t ldv, double* Lambda, double* resid,
                      const double* lanczos_starts, const chase_opts* opts, chase_stats* stats,
                      void* stream);
+
+/* Single precision (Sec. 5.1 templates the library on the precision too):
+ * complex64 (`_c32`) and float32 (`_f32`) versions of chase_filter,
+ * chase_residuals and chase_solve with the same arguments, layouts and
+ * errors.  Every product with H, the Gram products and the projected
+ * eigensolve (cheevd / ssyevd) run in FP32 on the CUDA cores; the
+ * orthogonalisation runs in double on widened copies of the block (Cholesky
+ * QR squares the condition number of a filtered block, which FP32 cannot
+ * hold) and rounds back.  Eigenvalues, residuals, bounds and tolerances are
+ * doubles.  Single precision reaches residuals of about 1e-6 ||H||, so tol
+ * should be 1e-5 or larger (Table 1's single-precision column).
+ * opts->precision is ignored. */
+int chase_filter_c32(const chase_c32* H, int64_t N, int64_t ldh, chase_c32* V, int64_t ldv, int b,
+                     const int* degrees, double b_sup, double mu1, double mu_nevnex,
+                     chase_c32* work, void* stream);
+int chase_filter_f32(const float* H, int64_t N, int64_t ldh, float* V, int64_t ldv, int b,
+                     const int* degrees, double b_sup, double mu1, double mu_nevnex, float* work,
+                     void* stream);
+int chase_residuals_c32(const chase_c32* H, int64_t N, int64_t ldh, const chase_c32* V,
+                        int64_t ldv, int b, const double* lambda, double* resid, void* stream);
+int chase_residuals_f32(const float* H, int64_t N, int64_t ldh, const float* V, int64_t ldv, int b,
+                        const double* lambda, double* resid, void* stream);
+int chase_solve_c32(const chase_c32* H, int64_t N, int64_t ldh, int nev, int nex, double tol,
+                    chase_c32* V, int64_t ldv, double* Lambda, double* resid,
+                    const chase_c32* lanczos_starts, const chase_opts* opts, chase_stats* stats,
+                    void* stream);
+int chase_solve_f32(const float* H, int64_t N, int64_t ldh, int nev, int nex, double tol, float* V,
+                    int64_t ldv, double* Lambda, double* resid, const float* lanczos_starts,
+                    const chase_opts* opts, chase_stats* stats, void* stream);
 
 /* Chebyshev filter (Alg. 4, Eq. 7) of many independent problems at once.
  * The paper filters one matrix per call; this entry point has no

@@ -28,6 +28,8 @@ __all__ = [
     "CHASE_SPLIT_BF16", "CHASE_SPLIT_BF16_RR", "CHASE_TILE_AUTO", "CHASE_STORAGE_FULL",
     "CHASE_STORAGE_LOWER", "ChaseBatchStats", "chase_filter_batched",
     "chase_solve_batched", "chase_filter_real", "chase_residuals_real", "chase_solve_real",
+    "chase_filter_c32", "chase_filter_f32", "chase_residuals_c32", "chase_residuals_f32",
+    "chase_solve_c32", "chase_solve_f32",
 ]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -128,6 +130,16 @@ _SIGNATURES = {
     "chase_residuals_real": (_int, [_c_p, _i64, _i64, _c_p, _i64, _int, _dp, _dp, _c_p]),
     "chase_solve_real": (_int, [_c_p, _i64, _i64, _int, _int, _dbl, _c_p, _i64, _dp, _dp, _c_p,
                                 ctypes.POINTER(ChaseOpts), ctypes.POINTER(ChaseStats), _c_p]),
+    "chase_filter_c32": (_int, [_c_p, _i64, _i64, _c_p, _i64, _int, _c_p, _dbl, _dbl, _dbl, _c_p,
+                                _c_p]),
+    "chase_filter_f32": (_int, [_c_p, _i64, _i64, _c_p, _i64, _int, _c_p, _dbl, _dbl, _dbl, _c_p,
+                                _c_p]),
+    "chase_residuals_c32": (_int, [_c_p, _i64, _i64, _c_p, _i64, _int, _dp, _dp, _c_p]),
+    "chase_residuals_f32": (_int, [_c_p, _i64, _i64, _c_p, _i64, _int, _dp, _dp, _c_p]),
+    "chase_solve_c32": (_int, [_c_p, _i64, _i64, _int, _int, _dbl, _c_p, _i64, _dp, _dp, _c_p,
+                               ctypes.POINTER(ChaseOpts), ctypes.POINTER(ChaseStats), _c_p]),
+    "chase_solve_f32": (_int, [_c_p, _i64, _i64, _int, _int, _dbl, _c_p, _i64, _dp, _dp, _c_p,
+                               ctypes.POINTER(ChaseOpts), ctypes.POINTER(ChaseStats), _c_p]),
     "chase_solve": (_int, [_c_p, _i64, _i64, _int, _int, _dbl, _c_p, _i64, _dp, _dp, _c_p,
                            ctypes.POINTER(ChaseOpts), ctypes.POINTER(ChaseStats), _c_p]),
 }
@@ -240,8 +252,10 @@ def _filter(entry, dtype, H, V, degrees, b_sup, mu1, mu_nevnex, work, stream, pr
     if len(deg_keep) != b:
         raise ValueError("one degree per column")
     wp = ctypes.c_void_p(work.data_ptr()) if work is not None else None
-    st = getattr(lib(), entry)(hp, n, ldh, vp, ldv, b, dptr, float(b_sup), float(mu1),
-                               float(mu_nevnex), int(precision), wp, _stream(V, stream))
+    args = [hp, n, ldh, vp, ldv, b, dptr, float(b_sup), float(mu1), float(mu_nevnex)]
+    if precision is not None:
+        args.append(int(precision))
+    st = getattr(lib(), entry)(*args, wp, _stream(V, stream))
     _check(st, entry)
     return V
 
@@ -252,6 +266,18 @@ def chase_filter(H, V, degrees, b_sup, mu1, mu_nevnex, work=None, stream=None,
     (host or device) or a sequence of ints."""
     return _filter("chase_filter", torch.complex128, H, V, degrees, b_sup, mu1, mu_nevnex, work,
                    stream, precision)
+
+
+def chase_filter_c32(H, V, degrees, b_sup, mu1, mu_nevnex, work=None, stream=None):
+    """Alg. 4 in single precision (complex64 tensors)."""
+    return _filter("chase_filter_c32", torch.complex64, H, V, degrees, b_sup, mu1, mu_nevnex,
+                   work, stream, None)
+
+
+def chase_filter_f32(H, V, degrees, b_sup, mu1, mu_nevnex, work=None, stream=None):
+    """Alg. 4 in single precision for a real symmetric H (float32 tensors)."""
+    return _filter("chase_filter_f32", torch.float32, H, V, degrees, b_sup, mu1, mu_nevnex, work,
+                   stream, None)
 
 
 def chase_filter_real(H, V, degrees, b_sup, mu1, mu_nevnex, work=None, stream=None,
@@ -443,6 +469,14 @@ def chase_residuals_real(H, V, lam, stream=None):
     return _residuals("chase_residuals_real", torch.float64, H, V, lam, stream)
 
 
+def chase_residuals_c32(H, V, lam, stream=None):
+    return _residuals("chase_residuals_c32", torch.complex64, H, V, lam, stream)
+
+
+def chase_residuals_f32(H, V, lam, stream=None):
+    return _residuals("chase_residuals_f32", torch.float32, H, V, lam, stream)
+
+
 def chase_residuals_noalloc(H, V, lam, resid, stream=None):
     """Residual norms into the device tensor ``resid`` (float64, b) from the
     device tensor ``lam``; the library allocates nothing for this call."""
@@ -494,4 +528,18 @@ def chase_solve_real(H, nev, nex, tol, V, lanczos_starts, Lambda=None, opts=None
                      raise_not_converged=False):
     """Alg. 1 for a real symmetric H (float64 tensors)."""
     return _solve("chase_solve_real", torch.float64, H, nev, nex, tol, V, lanczos_starts, Lambda,
+                  opts, stream, raise_not_converged)
+
+
+def chase_solve_c32(H, nev, nex, tol, V, lanczos_starts, Lambda=None, opts=None, stream=None,
+                    raise_not_converged=False):
+    """Alg. 1 in single precision (complex64 tensors)."""
+    return _solve("chase_solve_c32", torch.complex64, H, nev, nex, tol, V, lanczos_starts, Lambda,
+                  opts, stream, raise_not_converged)
+
+
+def chase_solve_f32(H, nev, nex, tol, V, lanczos_starts, Lambda=None, opts=None, stream=None,
+                    raise_not_converged=False):
+    """Alg. 1 in single precision for a real symmetric H (float32 tensors)."""
+    return _solve("chase_solve_f32", torch.float32, H, nev, nex, tol, V, lanczos_starts, Lambda,
                   opts, stream, raise_not_converged)

@@ -31,14 +31,39 @@ namespace {
 constexpr int kMaxDegAllowed = 1024;
 constexpr int kBatchWorkers = 8;  // host threads for the per-problem phases of a batched solve
 
-// Real problems: every matrix handed to the TMA product has an even leading
-// dimension (TMA strides are multiples of 16 bytes), so internal buffers pad
-// their rows to even; complex128 columns are already 16-byte multiples.
+// Scalar types of the solver: complex128 and float64 (the default), complex64
+// and float32 (the single-precision entry points; Sec. 5.1 templates the
+// library on both the field and the precision).
 template <class T>
-constexpr bool is_cplx = std::is_same<T, chase_c64>::value;
+constexpr bool is_cplx = std::is_same<T, chase_c64>::value || std::is_same<T, chase_c32>::value;
+template <class T>
+constexpr bool is_single = std::is_same<T, chase_c32>::value || std::is_same<T, float>::value;
+
+// Rounding unit, Cholesky pivot threshold (double precision: the single-
+// precision solver orthogonalises in double) and Lanczos breakdown threshold.
+template <class T>
+struct Prec {
+  static constexpr double u = 1.1102230246251565e-16;
+  static constexpr double chol_tol = 1e-12;
+  static constexpr double lanczos_tiny = 1e-13;
+};
+template <>
+struct Prec<chase_c32> {
+  static constexpr double lanczos_tiny = 1e-6;
+};
+template <>
+struct Prec<float> {
+  static constexpr double lanczos_tiny = 1e-6;
+};
+
+// Real float64 problems: every matrix handed to the TMA product has an even
+// leading dimension (TMA strides are multiples of 16 bytes), so internal
+// buffers pad their rows to even; complex128 columns are already 16-byte
+// multiples, and the single-precision products do not use TMA.
 template <class T>
 int64_t ld_pad(int64_t n) {
-  return is_cplx<T> ? std::max<int64_t>(n, 1) : std::max<int64_t>((n + 1) / 2 * 2, 2);
+  return std::is_same<T, double>::value ? std::max<int64_t>((n + 1) / 2 * 2, 2)
+                                        : std::max<int64_t>(n, 1);
 }
 template <class T>
 T from_real(double v);
@@ -49,6 +74,14 @@ chase_c64 from_real<chase_c64>(double v) {
 template <>
 double from_real<double>(double v) {
   return v;
+}
+template <>
+chase_c32 from_real<chase_c32>(double v) {
+  return chase_c32{static_cast<float>(v), 0.f};
+}
+template <>
+float from_real<float>(double v) {
+  return static_cast<float>(v);
 }
 
 // Events bracketing the phases of one call, accumulated into seconds.
@@ -88,7 +121,9 @@ template <class T>
 int filter_product(Dev& d, const T* H, int64_t N, int64_t ldh, const SplitH* sh, SplitX* sx,
                    const T* X, int64_t ldx, int b, T* Y, int64_t ldy, int j0,
                    double alpha, double beta, double shift) {
-  if (sh) return zgemm_split(d, *sh, *sx, X, ldx, j0, b, Y, ldy, alpha, beta, shift);
+  if constexpr (!is_single<T>) {
+    if (sh) return zgemm_split(d, *sh, *sx, X, ldx, j0, b, Y, ldy, alpha, beta, shift);
+  }
   return gemm(d, N, N, H, ldh, X, ldx, b, Y, ldy, j0, b, alpha, beta, shift);
 }
 
@@ -169,7 +204,7 @@ int cholqr_pass(Dev& d, int64_t N, const T* Y, int64_t ldy, int nconv, T* V,
     *flops += (is_cplx<T> ? 16.0 : 4.0) * N * nconv * b;
   }
   CHASE_TRY(gram(d, N, V, ldv, b, V, ldv, b, w.G, ldg));
-  CHASE_TRY(cholesky_blocked(d, w.G, ldg, b, 1e-12, shift, w.nrm, w.Rinv));
+  CHASE_TRY(cholesky_blocked(d, w.G, ldg, b, Prec<T>::chol_tol, shift, w.nrm, w.Rinv));
   int st = d.sync_check("cholesky");
   if (st != CHASE_OK) {
     cudaMemsetAsync(d.err, 0, sizeof(int), d.st);
@@ -192,7 +227,7 @@ int orth_core(Dev& d, int64_t N, const T* Y, int64_t ldy, int nconv, T* V,
   int st = cholqr_pass(d, N, Y, ldy, nconv, V, ldv, b, w, 0.0, flops);
   if (st == CHASE_QR_BREAKDOWN) {
     // Shifted Cholesky QR: ||G||_2 <= trace(G) <= b for columns of norm <= 1.
-    const double u = 1.1102230246251565e-16;
+    const double u = Prec<T>::u;
     const double shift = 11.0 * (static_cast<double>(N) * b + static_cast<double>(b) * (b + 1)) * u * b;
     CHASE_TRY(launch_col_norms(d, V, ldv, N, b, w.nrm));
     CHASE_TRY(launch_col_inv_scale(d, V, ldv, N, b, w.nrm));
@@ -208,6 +243,37 @@ int orth_core(Dev& d, int64_t N, const T* Y, int64_t ldy, int nconv, T* V,
   st = cholqr_pass(d, N, Y, ldy, nconv, V, ldv, b, w, 0.0, flops);
   if (st == CHASE_QR_BREAKDOWN) set_error("orthonormalisation: Cholesky QR broke down");
   return st;
+}
+
+// Single precision: the orthogonalisation runs in double on widened copies
+// (Cholesky QR squares the condition number of a filtered block, which FP32
+// would not hold), then the block is rounded back.
+template <class T>
+int orth_widened(Dev& d, int64_t N, const T* Y, int64_t ldy, int nconv, T* V, int64_t ldv, int b,
+                 double* flops) {
+  using D = typename std::conditional<std::is_same<T, chase_c32>::value, chase_c64, double>::type;
+  if (b == 0) return CHASE_OK;
+  const int64_t lD = ld_pad<D>(N);
+  D *Yd = nullptr, *Vd = nullptr;
+  if (nconv > 0) {
+    CHASE_TRY(d.alloc(&Yd, static_cast<size_t>(lD) * nconv));
+    CHASE_TRY(launch_convert(d, Y, ldy, Yd, lD, N, nconv));
+  }
+  CHASE_TRY(d.alloc(&Vd, static_cast<size_t>(lD) * b));
+  CHASE_TRY(launch_convert(d, V, ldv, Vd, lD, N, b));
+  OrthWork<D> w;
+  CHASE_TRY(orth_alloc(d, N, nconv, b, w));
+  CHASE_TRY(orth_core(d, N, Yd, lD, nconv, Vd, lD, b, w, flops));
+  return launch_convert(d, Vd, lD, V, ldv, N, b);
+}
+
+template <class T>
+int orth_any(Dev& d, int64_t N, const T* Y, int64_t ldy, int nconv, T* V, int64_t ldv, int b,
+             OrthWork<T>& w, double* flops) {
+  if constexpr (is_single<T>)
+    return orth_widened(d, N, Y, ldy, nconv, V, ldv, b, flops);
+  else
+    return orth_core(d, N, Y, ldy, nconv, V, ldv, b, w, flops);
 }
 
 // ---------------------------------------------------------------------------
@@ -239,10 +305,14 @@ int rr_core(Dev& d, const T* H, int64_t N, int64_t ldh, T* Q, int64_t ldq, int b
   const int64_t lN = ld_pad<T>(N), lg = ld_pad<T>(b);
   PhaseTimer tq(d.st);
   if (t_hq) tq.begin(t_hq);
-  if (sh)  // H Q on the split product (CHASE_SPLIT_BF16_RR)
-    CHASE_TRY(zgemm_split(d, *sh, *sx, Q, ldq, 0, b, w.HQ, lN, 1.0, 0.0, 0.0));
-  else
-    CHASE_TRY(gemm(d, N, N, H, ldh, Q, ldq, b, w.HQ, lN, 0, b, 1.0, 0.0, 0.0));  // H Q
+  bool on_split = false;
+  if constexpr (!is_single<T>) {
+    if (sh) {  // H Q on the split product (CHASE_SPLIT_BF16_RR)
+      CHASE_TRY(zgemm_split(d, *sh, *sx, Q, ldq, 0, b, w.HQ, lN, 1.0, 0.0, 0.0));
+      on_split = true;
+    }
+  }
+  if (!on_split) CHASE_TRY(gemm(d, N, N, H, ldh, Q, ldq, b, w.HQ, lN, 0, b, 1.0, 0.0, 0.0));
   if (t_hq) tq.end();
   CHASE_TRY(gram(d, N, Q, ldq, b, w.HQ, lN, b, w.G, lg));                       // G = Q^H H Q
   CHASE_TRY(launch_hermitize(d, w.G, lg, b));
@@ -293,7 +363,8 @@ int lanczos_core(Dev& d, const T* H, int64_t N, int64_t ldh, int k, int nvec, bo
     const T* Vp = j > 0 ? U + static_cast<size_t>(j - 1) * r * lN : nullptr;
     T* Vn = j + 1 < k ? U + static_cast<size_t>(j + 1) * r * lN : nullptr;
     CHASE_TRY(gemm(d, N, N, H, ldh, Vj, lN, r, Wt, lN, 0, r, 1.0, 0.0, 0.0));  // A v_j
-    CHASE_TRY(launch_lanczos_step(d, N, lN, r, j, Vj, Vp, Wt, Vn, alpha, beta));
+    CHASE_TRY(launch_lanczos_step(d, N, lN, r, j, Vj, Vp, Wt, Vn, alpha, beta,
+                                  Prec<T>::lanczos_tiny));
   }
   std::vector<double> ha(static_cast<size_t>(k) * r), hb(static_cast<size_t>(k) * r);
   CHASE_CUDA(cudaMemcpyAsync(ha.data(), alpha, ha.size() * sizeof(double), cudaMemcpyDeviceToHost, d.st));
@@ -311,7 +382,7 @@ int lanczos_core(Dev& d, const T* H, int64_t N, int64_t ldh, int k, int nvec, bo
     for (int j = 0; j < k; ++j) {
       const double a = ha[static_cast<size_t>(j) * r + c], bj = hb[static_cast<size_t>(j) * r + c];
       scale = std::max(scale, std::max(std::fabs(a), bj));
-      if (!(bj > 1e-13 * scale)) {
+      if (!(bj > Prec<T>::lanczos_tiny * scale)) {
         st = j + 1;
         break;
       }
@@ -415,7 +486,7 @@ int lanczos_core(Dev& d, const T* H, int64_t N, int64_t ldh, int k, int nvec, bo
 // products need even leading dimensions).
 template <class T>
 bool needs_stage(bool on_dev, int64_t ld) {
-  return !on_dev || (!is_cplx<T> && (ld & 1));
+  return !on_dev || (std::is_same<T, double>::value && (ld & 1));
 }
 
 template <class T>
@@ -504,13 +575,16 @@ struct Solver {
     CHASE_TRY(d.alloc(&Wk, static_cast<size_t>(lw) * nx));  // filter double buffer / permutation scratch
     CHASE_TRY(orth_alloc(d, N, nx, nx, ow));
     CHASE_TRY(rr_alloc(d, N, nx, rw));
-    split = o.precision == CHASE_SPLIT_BF16 || o.precision == CHASE_SPLIT_BF16_RR;
-    split_rr = o.precision == CHASE_SPLIT_BF16_RR;
-    if (split && !grouped_split) {  // slices of H once per solve, slice workspace for the block
-      CHASE_TRY(split_prepare_h(d, dH, N, lh, sh));
-      CHASE_TRY(split_alloc_x(d, N, nx, sx, is_cplx<T>));
-      rr_slices = &sh;
-      rr_sx = &sx;
+    // single-precision solves compute every product natively in FP32
+    split = !is_single<T> && (o.precision == CHASE_SPLIT_BF16 || o.precision == CHASE_SPLIT_BF16_RR);
+    split_rr = !is_single<T> && o.precision == CHASE_SPLIT_BF16_RR;
+    if constexpr (!is_single<T>) {
+      if (split && !grouped_split) {  // slices of H once per solve, slice workspace for the block
+        CHASE_TRY(split_prepare_h(d, dH, N, lh, sh));
+        CHASE_TRY(split_alloc_x(d, N, nx, sx, is_cplx<T>));
+        rr_slices = &sh;
+        rr_sx = &sx;
+      }
     }
     CHASE_TRY(d.alloc(&dw, nx));
     CHASE_TRY(d.alloc(&dres, nx));
@@ -613,7 +687,7 @@ struct Solver {
     T* va = Va();
     // lines 5-6: orthonormalise the active block against the locked one
     tm.begin(&S.t_qr);
-    CHASE_TRY(orth_core(d, N, dV, lv, nconv, va, lv, nb, ow, &S.flops_total));
+    CHASE_TRY(orth_any(d, N, dV, lv, nconv, va, lv, nb, ow, &S.flops_total));
     tm.end();
     // lines 7-8: Rayleigh-Ritz on the active block, residuals
     tm.begin(&S.t_rr);
@@ -856,6 +930,7 @@ namespace {
 template <class T>
 int filter_impl(const T* H, int64_t N, int64_t ldh, T* V, int64_t ldv, int b, const int* degrees,
                 double b_sup, double mu1, double mu_nevnex, int precision, T* work, void* stream) {
+  if constexpr (is_single<T>) precision = CHASE_FP64;  // native FP32 products
   if (precision != CHASE_FP64 && precision != CHASE_SPLIT_BF16) {
     set_error("chase_filter: unknown precision %d", precision);
     return CHASE_INVALID_ARG;
@@ -907,9 +982,11 @@ int filter_impl(const T* H, int64_t N, int64_t ldh, T* V, int64_t ldv, int b, co
   CHASE_TRY(d.sync_check("chase_filter plan"));
   SplitH sh;
   SplitX sx;
-  if (precision == CHASE_SPLIT_BF16) {
-    CHASE_TRY(split_prepare_h(d, dH, N, lh, sh));
-    CHASE_TRY(split_alloc_x(d, N, b, sx, is_cplx<T>));
+  if constexpr (!is_single<T>) {
+    if (precision == CHASE_SPLIT_BF16) {
+      CHASE_TRY(split_prepare_h(d, dH, N, lh, sh));
+      CHASE_TRY(split_alloc_x(d, N, b, sx, is_cplx<T>));
+    }
   }
   // sorted copy into the workspace; V becomes the second buffer
   CHASE_TRY(launch_permute_cols(d, dV, lv, wk, lw, N, b, dperm, false));
@@ -934,6 +1011,18 @@ extern "C" int chase_filter_real(const double* H, int64_t N, int64_t ldh, double
                                  int b, const int* degrees, double b_sup, double mu1,
                                  double mu_nevnex, int precision, double* work, void* stream) {
   return filter_impl(H, N, ldh, V, ldv, b, degrees, b_sup, mu1, mu_nevnex, precision, work, stream);
+}
+
+extern "C" int chase_filter_c32(const chase_c32* H, int64_t N, int64_t ldh, chase_c32* V,
+                                int64_t ldv, int b, const int* degrees, double b_sup, double mu1,
+                                double mu_nevnex, chase_c32* work, void* stream) {
+  return filter_impl(H, N, ldh, V, ldv, b, degrees, b_sup, mu1, mu_nevnex, CHASE_FP64, work, stream);
+}
+
+extern "C" int chase_filter_f32(const float* H, int64_t N, int64_t ldh, float* V, int64_t ldv,
+                                int b, const int* degrees, double b_sup, double mu1,
+                                double mu_nevnex, float* work, void* stream) {
+  return filter_impl(H, N, ldh, V, ldv, b, degrees, b_sup, mu1, mu_nevnex, CHASE_FP64, work, stream);
 }
 
 
@@ -1082,6 +1171,18 @@ extern "C" int chase_residuals_real(const double* H, int64_t N, int64_t ldh, con
   return residuals_impl(H, N, ldh, V, ldv, b, lambda, resid, stream);
 }
 
+extern "C" int chase_residuals_c32(const chase_c32* H, int64_t N, int64_t ldh, const chase_c32* V,
+                                   int64_t ldv, int b, const double* lambda, double* resid,
+                                   void* stream) {
+  return residuals_impl(H, N, ldh, V, ldv, b, lambda, resid, stream);
+}
+
+extern "C" int chase_residuals_f32(const float* H, int64_t N, int64_t ldh, const float* V,
+                                   int64_t ldv, int b, const double* lambda, double* resid,
+                                   void* stream) {
+  return residuals_impl(H, N, ldh, V, ldv, b, lambda, resid, stream);
+}
+
 namespace chase {
 namespace {
 template <class T>
@@ -1149,6 +1250,22 @@ extern "C" int chase_solve_real(const double* H, int64_t N, int64_t ldh, int nev
                                 double tol, double* V, int64_t ldv, double* Lambda, double* resid,
                                 const double* lanczos_starts, const chase_opts* opts_in,
                                 chase_stats* stats, void* stream) {
+  return solve_impl(H, N, ldh, nev, nex, tol, V, ldv, Lambda, resid, lanczos_starts, opts_in, stats,
+                    stream);
+}
+
+extern "C" int chase_solve_c32(const chase_c32* H, int64_t N, int64_t ldh, int nev, int nex,
+                               double tol, chase_c32* V, int64_t ldv, double* Lambda,
+                               double* resid, const chase_c32* lanczos_starts,
+                               const chase_opts* opts_in, chase_stats* stats, void* stream) {
+  return solve_impl(H, N, ldh, nev, nex, tol, V, ldv, Lambda, resid, lanczos_starts, opts_in, stats,
+                    stream);
+}
+
+extern "C" int chase_solve_f32(const float* H, int64_t N, int64_t ldh, int nev, int nex, double tol,
+                               float* V, int64_t ldv, double* Lambda, double* resid,
+                               const float* lanczos_starts, const chase_opts* opts_in,
+                               chase_stats* stats, void* stream) {
   return solve_impl(H, N, ldh, nev, nex, tol, V, ldv, Lambda, resid, lanczos_starts, opts_in, stats,
                     stream);
 }

@@ -159,6 +159,24 @@ inline int gemm(Dev& d, int64_t M, int64_t K, const double* A, int64_t lda, cons
   return dgemm(d, M, K, A, lda, B, ldb, ncols_b, C, ldc, j0, j1, alpha, beta, shift);
 }
 
+// Single precision (complex64 / float32) on the CUDA cores, same contract.
+int cgemm(Dev& d, int64_t M, int64_t K, const chase_c32* A, int64_t lda, const chase_c32* B,
+          int64_t ldb, int64_t ncols_b, chase_c32* C, int64_t ldc, int j0, int j1, double alpha,
+          double beta, double shift);
+int sgemm(Dev& d, int64_t M, int64_t K, const float* A, int64_t lda, const float* B, int64_t ldb,
+          int64_t ncols_b, float* C, int64_t ldc, int j0, int j1, double alpha, double beta,
+          double shift);
+inline int gemm(Dev& d, int64_t M, int64_t K, const chase_c32* A, int64_t lda, const chase_c32* B,
+                int64_t ldb, int64_t ncols_b, chase_c32* C, int64_t ldc, int j0, int j1,
+                double alpha, double beta, double shift) {
+  return cgemm(d, M, K, A, lda, B, ldb, ncols_b, C, ldc, j0, j1, alpha, beta, shift);
+}
+inline int gemm(Dev& d, int64_t M, int64_t K, const float* A, int64_t lda, const float* B,
+                int64_t ldb, int64_t ncols_b, float* C, int64_t ldc, int j0, int j1, double alpha,
+                double beta, double shift) {
+  return sgemm(d, M, K, A, lda, B, ldb, ncols_b, C, ldc, j0, j1, alpha, beta, shift);
+}
+
 // C (p x q, ldc) = X^H Y with X: N x p (ldx), Y: N x q (ldy).
 int zgram(Dev& d, int64_t N, const chase_c64* X, int64_t ldx, int p, const chase_c64* Y,
           int64_t ldy, int q, chase_c64* C, int64_t ldc);

@@ -39,6 +39,10 @@ int copy_block(Dev& d, chase_c64* dst, int64_t ldd, const chase_c64* src, int64_
                int64_t cols, cudaMemcpyKind kind);
 int copy_block(Dev& d, double* dst, int64_t ldd, const double* src, int64_t lds, int64_t rows,
                int64_t cols, cudaMemcpyKind kind);
+int copy_block(Dev& d, chase_c32* dst, int64_t ldd, const chase_c32* src, int64_t lds, int64_t rows,
+               int64_t cols, cudaMemcpyKind kind);
+int copy_block(Dev& d, float* dst, int64_t ldd, const float* src, int64_t lds, int64_t rows,
+               int64_t cols, cudaMemcpyKind kind);
 
 // ---- kernels.cu ------------------------------------------------------------
 // Element launchers are templates over the scalar T: chase_c64 (Hermitian
@@ -81,11 +85,11 @@ int trsm_right_lh(Dev& d, T* X, int64_t ldx, int64_t N, const T* L, int64_t ldl,
 // One Lanczos three-term step on r independent runs (one CTA per run, run c
 // in column c of each N x r block, leading dimension ld):
 // alpha = Re(v^H w); w -= alpha v + beta_prev v_prev; beta = ||w||;
-// v_next = w / beta (zero when beta is rounding noise).  alpha/beta arrays
-// are indexed [step * r + run].
+// v_next = w / beta (zero when beta <= tiny * the run's largest coefficient,
+// i.e. rounding noise).  alpha/beta arrays are indexed [step * r + run].
 template <class T>
 int launch_lanczos_step(Dev& d, int64_t N, int64_t ld, int r, int step, const T* Vj,
-                        const T* Vprev, T* W, T* Vnext, double* alpha, double* beta);
+                        const T* Vprev, T* W, T* Vnext, double* alpha, double* beta, double tiny);
 // Normalise r columns in place (Lanczos start vectors).
 template <class T>
 int launch_normalize_cols(Dev& d, T* X, int64_t ldx, int64_t N, int r);
@@ -93,6 +97,15 @@ int launch_normalize_cols(Dev& d, T* X, int64_t ldx, int64_t N, int r);
 // triangle, diagonal included, is that of L; L's strict upper part is not read.
 template <class T>
 int launch_hermitian_from_lower(Dev& d, const T* L, int64_t ldl, T* F, int64_t ldf, int64_t n);
+// dst (rows x cols, ldd) = src rounded to / widened from single precision.
+int launch_convert(Dev& d, const chase_c32* src, int64_t lds, chase_c64* dst, int64_t ldd,
+                   int64_t rows, int64_t cols);
+int launch_convert(Dev& d, const chase_c64* src, int64_t lds, chase_c32* dst, int64_t ldd,
+                   int64_t rows, int64_t cols);
+int launch_convert(Dev& d, const float* src, int64_t lds, double* dst, int64_t ldd, int64_t rows,
+                   int64_t cols);
+int launch_convert(Dev& d, const double* src, int64_t lds, float* dst, int64_t ldd, int64_t rows,
+                   int64_t cols);
 // Fill the strict lower (lower=true) or upper part of a p x p matrix with zero.
 template <class T>
 int launch_zero_triangle(Dev& d, T* A, int64_t lda, int p, bool lower);
@@ -106,6 +119,18 @@ inline int gram(Dev& d, int64_t N, const chase_c64* X, int64_t ldx, int p, const
 inline int gram(Dev& d, int64_t N, const double* X, int64_t ldx, int p, const double* Y,
                 int64_t ldy, int q, double* C, int64_t ldc) {
   return dgram(d, N, X, ldx, p, Y, ldy, q, C, ldc);
+}
+int cgram(Dev& d, int64_t N, const chase_c32* X, int64_t ldx, int p, const chase_c32* Y,
+          int64_t ldy, int q, chase_c32* C, int64_t ldc);
+int sgram(Dev& d, int64_t N, const float* X, int64_t ldx, int p, const float* Y, int64_t ldy,
+          int q, float* C, int64_t ldc);
+inline int gram(Dev& d, int64_t N, const chase_c32* X, int64_t ldx, int p, const chase_c32* Y,
+                int64_t ldy, int q, chase_c32* C, int64_t ldc) {
+  return cgram(d, N, X, ldx, p, Y, ldy, q, C, ldc);
+}
+inline int gram(Dev& d, int64_t N, const float* X, int64_t ldx, int p, const float* Y,
+                int64_t ldy, int q, float* C, int64_t ldc) {
+  return sgram(d, N, X, ldx, p, Y, ldy, q, C, ldc);
 }
 
 // ---- zgemm_split.cu: split-BF16 filter product on the tensor cores --------
@@ -247,6 +272,9 @@ int launch_grouped_permute(Dev& d, const GroupedPermute* probs, int P, int total
 // ---- eigh (cuSOLVER, the small projected eigensolve of Alg. 2 line 3) -----
 int eigh_device(Dev& d, chase_c64* G, int64_t ldg, int p, double* w_dev);
 int eigh_device(Dev& d, double* G, int64_t ldg, int p, double* w_dev);
+// Single precision (cheevd / ssyevd); eigenvalues returned in double.
+int eigh_device(Dev& d, chase_c32* G, int64_t ldg, int p, double* w_dev);
+int eigh_device(Dev& d, float* G, int64_t ldg, int p, double* w_dev);
 // Destroy the calling thread's cuSOLVER handle (worker threads, before they end).
 void release_thread_solver();
 

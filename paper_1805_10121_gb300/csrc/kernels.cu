@@ -109,9 +109,79 @@ struct Sc<double> {
   static __device__ __forceinline__ void hermitize_diag(double&) {}
 };
 
+// Single precision: values in FP32, norms and dot products accumulated in
+// double by the reductions that call abs2 / re_dot.
+template <>
+struct Sc<float2> {
+  static __device__ __forceinline__ float2 zero() { return make_float2(0.f, 0.f); }
+  static __device__ __forceinline__ float2 real(double r) { return make_float2((float)r, 0.f); }
+  static __device__ __forceinline__ double re(float2 a) { return a.x; }
+  static __device__ __forceinline__ double abs2(float2 a) {
+    return (double)a.x * a.x + (double)a.y * a.y;
+  }
+  static __device__ __forceinline__ float2 scale(float2 a, double f) {
+    return make_float2((float)(a.x * f), (float)(a.y * f));
+  }
+  static __device__ __forceinline__ float2 conj(float2 a) { return make_float2(a.x, -a.y); }
+  static __device__ __forceinline__ float2 sub_mul_conj(float2 acc, float2 a, float2 b) {
+    acc.x -= a.x * b.x + a.y * b.y;
+    acc.y -= a.y * b.x - a.x * b.y;
+    return acc;
+  }
+  static __device__ __forceinline__ double re_dot(float2 a, float2 b) {
+    return (double)a.x * b.x + (double)a.y * b.y;
+  }
+  static __device__ __forceinline__ float2 sub_scaled(float2 a, double f, float2 b) {
+    return make_float2((float)(a.x - f * b.x), (float)(a.y - f * b.y));
+  }
+  static __device__ __forceinline__ void add_re(float2& a, double v) { a.x = (float)(a.x + v); }
+  static __device__ __forceinline__ float2 add(float2 a, float2 b) {
+    return make_float2(a.x + b.x, a.y + b.y);
+  }
+  static __device__ __forceinline__ void hermitize_pair(float2& a, float2& b) {
+    const float2 x = a, y = b;
+    const float re = 0.5f * (x.x + y.x), im = 0.5f * (x.y - y.y);
+    a = make_float2(re, im);
+    b = make_float2(re, -im);
+  }
+  static __device__ __forceinline__ void hermitize_diag(float2& a) { a.y = 0.f; }
+};
+template <>
+struct Sc<float> {
+  static __device__ __forceinline__ float zero() { return 0.f; }
+  static __device__ __forceinline__ float real(double r) { return (float)r; }
+  static __device__ __forceinline__ double re(float a) { return a; }
+  static __device__ __forceinline__ double abs2(float a) { return (double)a * a; }
+  static __device__ __forceinline__ float scale(float a, double f) { return (float)(a * f); }
+  static __device__ __forceinline__ float conj(float a) { return a; }
+  static __device__ __forceinline__ float sub_mul_conj(float acc, float a, float b) {
+    return acc - a * b;
+  }
+  static __device__ __forceinline__ double re_dot(float a, float b) { return (double)a * b; }
+  static __device__ __forceinline__ float sub_scaled(float a, double f, float b) {
+    return (float)(a - f * b);
+  }
+  static __device__ __forceinline__ void add_re(float& a, double v) { a = (float)(a + v); }
+  static __device__ __forceinline__ float add(float a, float b) { return a + b; }
+  static __device__ __forceinline__ void hermitize_pair(float& a, float& b) {
+    const float m = 0.5f * (a + b);
+    a = m;
+    b = m;
+  }
+  static __device__ __forceinline__ void hermitize_diag(float&) {}
+};
+
 // Device element type of a host scalar type.
 template <class T>
 struct Dv;
+template <>
+struct Dv<chase_c32> {
+  using type = float2;
+};
+template <>
+struct Dv<float> {
+  using type = float;
+};
 template <>
 struct Dv<chase_c64> {
   using type = double2;
@@ -553,7 +623,7 @@ template <class T>
 __global__ void __launch_bounds__(kRed)
     lanczos_step_kernel(long long N, long long ld, int r, int step, const T* __restrict__ Vj,
                         const T* __restrict__ Vprev, T* __restrict__ W, T* __restrict__ Vnext,
-                        double* __restrict__ alpha, double* __restrict__ beta) {
+                        double* __restrict__ alpha, double* __restrict__ beta, double tiny) {
   __shared__ double scratch[33];
   const int c = blockIdx.x;
   const T* v = Vj + (long long)c * ld;
@@ -575,7 +645,7 @@ __global__ void __launch_bounds__(kRed)
   // beta is rounding noise once the Krylov space is invariant: stop the run
   double scale = fabs(al);
   for (int k = 0; k < step; ++k) scale = fmax(scale, fmax(fabs(alpha[k * r + c]), beta[k * r + c]));
-  const bool stop = !(be > 1e-13 * fmax(scale, be));
+  const bool stop = !(be > tiny * fmax(scale, be));
   if (threadIdx.x == 0) {
     alpha[step * r + c] = al;
     beta[step * r + c] = be;
@@ -744,6 +814,70 @@ int launch_hermitize(Dev& d, T* G, int64_t ldg, int p) {
   return CHASE_OK;
 }
 
+namespace {
+template <class S, class D>
+__global__ void convert_kernel(const S* __restrict__ src, long long lds, D* __restrict__ dst,
+                               long long ldd, long long rows, long long cols) {
+  const long long total = rows * cols;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e % rows, c = e / rows;
+    const S v = src[c * lds + r];
+    D o;
+    o.x = v.x;
+    o.y = v.y;
+    dst[c * ldd + r] = o;
+  }
+}
+template <class S, class D>
+__global__ void convert_real_kernel(const S* __restrict__ src, long long lds, D* __restrict__ dst,
+                                    long long ldd, long long rows, long long cols) {
+  const long long total = rows * cols;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e % rows, c = e / rows;
+    dst[c * ldd + r] = static_cast<D>(src[c * lds + r]);
+  }
+}
+}  // namespace
+
+int launch_convert(Dev& d, const chase_c32* src, int64_t lds, chase_c64* dst, int64_t ldd,
+                   int64_t rows, int64_t cols) {
+  if (rows * cols == 0) return CHASE_OK;
+  convert_kernel<<<grid_for(rows * cols, 256, 152 * 16), 256, 0, d.st>>>(dp(src), lds, dp(dst), ldd,
+                                                                         rows, cols);
+  note_launch();
+  CHASE_CUDA(cudaGetLastError());
+  return CHASE_OK;
+}
+int launch_convert(Dev& d, const chase_c64* src, int64_t lds, chase_c32* dst, int64_t ldd,
+                   int64_t rows, int64_t cols) {
+  if (rows * cols == 0) return CHASE_OK;
+  convert_kernel<<<grid_for(rows * cols, 256, 152 * 16), 256, 0, d.st>>>(dp(src), lds, dp(dst), ldd,
+                                                                         rows, cols);
+  note_launch();
+  CHASE_CUDA(cudaGetLastError());
+  return CHASE_OK;
+}
+int launch_convert(Dev& d, const float* src, int64_t lds, double* dst, int64_t ldd, int64_t rows,
+                   int64_t cols) {
+  if (rows * cols == 0) return CHASE_OK;
+  convert_real_kernel<<<grid_for(rows * cols, 256, 152 * 16), 256, 0, d.st>>>(src, lds, dst, ldd,
+                                                                              rows, cols);
+  note_launch();
+  CHASE_CUDA(cudaGetLastError());
+  return CHASE_OK;
+}
+int launch_convert(Dev& d, const double* src, int64_t lds, float* dst, int64_t ldd, int64_t rows,
+                   int64_t cols) {
+  if (rows * cols == 0) return CHASE_OK;
+  convert_real_kernel<<<grid_for(rows * cols, 256, 152 * 16), 256, 0, d.st>>>(src, lds, dst, ldd,
+                                                                              rows, cols);
+  note_launch();
+  CHASE_CUDA(cudaGetLastError());
+  return CHASE_OK;
+}
+
 template <class T>
 int launch_hermitian_from_lower(Dev& d, const T* L, int64_t ldl, T* F, int64_t ldf, int64_t n) {
   if (n == 0) return CHASE_OK;
@@ -855,9 +989,9 @@ int trsm_right_lh(Dev& d, T* X, int64_t ldx, int64_t N, const T* L, int64_t ldl,
 
 template <class T>
 int launch_lanczos_step(Dev& d, int64_t N, int64_t ld, int r, int step, const T* Vj,
-                        const T* Vprev, T* W, T* Vnext, double* alpha, double* beta) {
+                        const T* Vprev, T* W, T* Vnext, double* alpha, double* beta, double tiny) {
   lanczos_step_kernel<<<r, kRed, 0, d.st>>>(N, ld, r, step, dp(Vj), dp(Vprev), dp(W), dp(Vnext),
-                                            alpha, beta);
+                                            alpha, beta, tiny);
   note_launch();
   CHASE_CUDA(cudaGetLastError());
   return CHASE_OK;
@@ -886,10 +1020,12 @@ int launch_normalize_cols(Dev& d, T* X, int64_t ldx, int64_t N, int r) {
   template int cholesky_blocked<T>(Dev&, T*, int64_t, int, double, double, double*, T*);           \
   template int trsm_right_lh<T>(Dev&, T*, int64_t, int64_t, const T*, int64_t, int, T*);           \
   template int launch_lanczos_step<T>(Dev&, int64_t, int64_t, int, int, const T*, const T*, T*,    \
-                                      T*, double*, double*);                                       \
+                                      T*, double*, double*, double);                               \
   template int launch_normalize_cols<T>(Dev&, T*, int64_t, int64_t, int);
 CHASE_INSTANTIATE_ELEMENT_LAUNCHERS(chase_c64)
 CHASE_INSTANTIATE_ELEMENT_LAUNCHERS(double)
+CHASE_INSTANTIATE_ELEMENT_LAUNCHERS(chase_c32)
+CHASE_INSTANTIATE_ELEMENT_LAUNCHERS(float)
 #undef CHASE_INSTANTIATE_ELEMENT_LAUNCHERS
 
 // ---------------------------------------------------------------------------
@@ -954,6 +1090,69 @@ int eigh_device(Dev& d, double* G, int64_t ldg, int p, double* w_dev) {
     return CHASE_EIGENSOLVER_ERROR;
   }
   return eigh_info(d, info, "dsyevd");
+}
+
+namespace {
+__global__ void widen_kernel(const float* __restrict__ w, int p, double* __restrict__ out) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < p; j += gridDim.x * blockDim.x)
+    out[j] = w[j];
+}
+}  // namespace
+
+// Single-precision projected eigenproblems: cuSOLVER cheevd / ssyevd, the
+// eigenvalues widened to double for the host decisions.
+int eigh_device(Dev& d, chase_c32* G, int64_t ldg, int p, double* w_dev) {
+  if (p == 0) return CHASE_OK;
+  CHASE_TRY(solver_handle(d));
+  float* wf = nullptr;
+  CHASE_TRY(d.alloc(&wf, static_cast<size_t>(p)));
+  int lwork = 0;
+  if (cusolverDnCheevd_bufferSize(t_solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, p,
+                                  reinterpret_cast<cuComplex*>(G), static_cast<int>(ldg), wf,
+                                  &lwork) != CUSOLVER_STATUS_SUCCESS) {
+    set_error("cusolverDnCheevd_bufferSize failed");
+    return CHASE_EIGENSOLVER_ERROR;
+  }
+  cuComplex* work = nullptr;
+  int* info = nullptr;
+  CHASE_TRY(d.alloc(&work, static_cast<size_t>(std::max(lwork, 1))));
+  CHASE_TRY(d.alloc(&info, 1));
+  if (cusolverDnCheevd(t_solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, p,
+                       reinterpret_cast<cuComplex*>(G), static_cast<int>(ldg), wf, work, lwork,
+                       info) != CUSOLVER_STATUS_SUCCESS) {
+    set_error("cusolverDnCheevd failed to launch");
+    return CHASE_EIGENSOLVER_ERROR;
+  }
+  widen_kernel<<<grid_for(p, 256, 64), 256, 0, d.st>>>(wf, p, w_dev);
+  note_launch();
+  CHASE_CUDA(cudaGetLastError());
+  return eigh_info(d, info, "cheevd");
+}
+
+int eigh_device(Dev& d, float* G, int64_t ldg, int p, double* w_dev) {
+  if (p == 0) return CHASE_OK;
+  CHASE_TRY(solver_handle(d));
+  float* wf = nullptr;
+  CHASE_TRY(d.alloc(&wf, static_cast<size_t>(p)));
+  int lwork = 0;
+  if (cusolverDnSsyevd_bufferSize(t_solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, p, G,
+                                  static_cast<int>(ldg), wf, &lwork) != CUSOLVER_STATUS_SUCCESS) {
+    set_error("cusolverDnSsyevd_bufferSize failed");
+    return CHASE_EIGENSOLVER_ERROR;
+  }
+  float* work = nullptr;
+  int* info = nullptr;
+  CHASE_TRY(d.alloc(&work, static_cast<size_t>(std::max(lwork, 1))));
+  CHASE_TRY(d.alloc(&info, 1));
+  if (cusolverDnSsyevd(t_solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, p, G,
+                       static_cast<int>(ldg), wf, work, lwork, info) != CUSOLVER_STATUS_SUCCESS) {
+    set_error("cusolverDnSsyevd failed to launch");
+    return CHASE_EIGENSOLVER_ERROR;
+  }
+  widen_kernel<<<grid_for(p, 256, 64), 256, 0, d.st>>>(wf, p, w_dev);
+  note_launch();
+  CHASE_CUDA(cudaGetLastError());
+  return eigh_info(d, info, "ssyevd");
 }
 
 int eigh_device(Dev& d, chase_c64* G, int64_t ldg, int p, double* w_dev) {

@@ -214,6 +214,16 @@ int copy_block(Dev& d, double* dst, int64_t ldd, const double* src, int64_t lds,
   return copy_block_bytes(d, dst, ldd, src, lds, rows, cols, sizeof(double), kind);
 }
 
+int copy_block(Dev& d, chase_c32* dst, int64_t ldd, const chase_c32* src, int64_t lds, int64_t rows,
+               int64_t cols, cudaMemcpyKind kind) {
+  return copy_block_bytes(d, dst, ldd, src, lds, rows, cols, sizeof(chase_c32), kind);
+}
+
+int copy_block(Dev& d, float* dst, int64_t ldd, const float* src, int64_t lds, int64_t rows,
+               int64_t cols, cudaMemcpyKind kind) {
+  return copy_block_bytes(d, dst, ldd, src, lds, rows, cols, sizeof(float), kind);
+}
+
 }  // namespace chase
 
 extern "C" const char* chase_last_error(void) { return chase::g_err; }
