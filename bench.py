@@ -77,6 +77,18 @@ def parse():
     return p.parse_args()
 
 
+def combine_over_ranks(elapsed, flops, device):
+    """Whole-job figures of replicas: the slowest rank's time and the FLOPs of
+    all ranks (the identity without a process group)."""
+    t = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+    f = torch.tensor([float(flops)], dtype=torch.float64, device=device)
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(f, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(f.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -899,15 +911,7 @@ def main():
         torch.distributed.barrier()
     launches = chase.chase_kernel_launches() - launches0
     elapsed = e0.elapsed_time(e1) / 1e3
-    t_local = torch.tensor([elapsed], device=dev, dtype=torch.float64)
-    fl_local = torch.tensor([sum(s["flops_total"] for s in stats_t)], device=dev,
-                            dtype=torch.float64)
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-        dist.all_reduce(fl_local, op=dist.ReduceOp.SUM)
-    t_max = float(t_local.item())
-    total_flops = float(fl_local.item())
+    t_max, total_flops = combine_over_ranks(elapsed, sum(s["flops_total"] for s in stats_t), dev)
     value = total_flops / t_max / 1e12
 
     # ---------------- the same problem on the FP64 path ----------------
