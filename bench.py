@@ -50,7 +50,8 @@ def parse():
     p.add_argument("--nex", type=int, default=80)
     p.add_argument("--tol", type=float, default=1e-10)
     p.add_argument("--seed", type=int, default=2024)
-    p.add_argument("--precision", default="split", choices=["split", "split_rr", "fp64"],
+    p.add_argument("--precision", default="split",
+                   choices=["split", "split_rr", "split_adapt", "fp64"],
                    help="split: split-BF16 filter; split_rr: also Rayleigh-Ritz's H Q on the "
                         "split product; fp64: FP64 throughout")
     p.add_argument("--workload", default="sequence",
@@ -182,7 +183,7 @@ def make_sequence(n, count, seed, device):
 def prec_code(name):
     from paper_1805_10121_gb300 import chase
     return {"split": chase.CHASE_SPLIT_BF16, "split_rr": chase.CHASE_SPLIT_BF16_RR,
-            "fp64": chase.CHASE_FP64}[name]
+            "split_adapt": chase.CHASE_SPLIT_BF16_ADAPT, "fp64": chase.CHASE_FP64}[name]
 
 
 # Slice-pair products the split-BF16 kernel executes per FP64-equivalent

@@ -75,6 +75,19 @@ typedef struct {
  * FP64.  chase_solve and chase_solve_batched only (the filter entry points
  * take CHASE_FP64 or CHASE_SPLIT_BF16). */
 #define CHASE_SPLIT_BF16_RR 2
+/* Split-BF16 filter whose accuracy follows the residuals (chase_solve only):
+ * while every active residual exceeds 1e-3 h (h = largest |Ritz value|) the
+ * filter products keep the leading 3 slices of each operand (about 2^-21
+ * relative), above 1e-6 h 4 slices (2^-28), then all 7 (2^-49).  Rayleigh-
+ * Ritz, QR and residuals stay FP64, so the converged pairs meet the same
+ * tolerance; a low-precision iteration only limits how far that iteration
+ * can reduce the residuals. */
+#define CHASE_SPLIT_BF16_ADAPT 3
+/* chase_filter only: split-BF16 products with the leading 4 or 3 slices of
+ * each operand (about 2^-28 or 2^-21 relative per product), the reduced
+ * precisions CHASE_SPLIT_BF16_ADAPT switches between. */
+#define CHASE_SPLIT_BF16_4 4
+#define CHASE_SPLIT_BF16_3 5
 
 /* ---- which part of H the solver reads (chase_solve*, via chase_opts) ---- */
 #define CHASE_STORAGE_FULL 0  /* both triangles hold H */
@@ -99,7 +112,7 @@ typedef struct {
   int approx;       /* 1: V and Lambda hold an approximate solution (Sec. 3.3) */
   double dos_sigma; /* Gaussian width of Eq. 10 in the variable mapped to [-1, 1] (Sec. 4.2: 0.25) */
   int conv_mode;    /* CHASE_CONV_ABS or CHASE_CONV_REL */
-  int precision;    /* CHASE_FP64, CHASE_SPLIT_BF16 or CHASE_SPLIT_BF16_RR */
+  int precision;    /* CHASE_FP64, CHASE_SPLIT_BF16, _RR or _ADAPT */
   int storage;      /* CHASE_STORAGE_FULL or CHASE_STORAGE_LOWER */
 } chase_opts;
 
@@ -116,6 +129,7 @@ typedef struct {
   double t_total, t_lanczos, t_filter, t_qr, t_rr, t_eigh, t_resid, t_host; /* seconds */
   double t_rr_product;     /* seconds of Rayleigh-Ritz's H Q products (inside t_rr) */
   double flops_rr_product; /* their algorithmic FLOPs (8 N^2 b complex, 2 N^2 b real) */
+  int filter_slices_low;   /* iterations whose filter kept fewer than 7 slices (ADAPT) */
 } chase_stats;
 
 /* Tile choice of the grouped FP64 filter: time the candidates on the first
@@ -168,7 +182,7 @@ long long chase_kernel_launches(void);
  *          (Sec. 4.1.3, Alg. 5 line 6).  Internally the columns are sorted by
  *          degree so that every product acts on a contiguous suffix; a column
  *          leaves the products once it reaches its degree (Alg. 4 lines 12-14).
- * precision  CHASE_FP64 or CHASE_SPLIT_BF16.
+ * precision  CHASE_FP64, CHASE_SPLIT_BF16, CHASE_SPLIT_BF16_4 or CHASE_SPLIT_BF16_3.
  * work     N x b device workspace with leading dimension N, or NULL (the
  *          library allocates it); ignored for host V.
  * Requires mu1 < mu_nevnex < b_sup.  b == 0 or N == 0 is a no-op.

@@ -25,7 +25,8 @@ __all__ = [
     "CHASE_OK", "CHASE_INVALID_ARG", "CHASE_NOT_CONVERGED", "CHASE_QR_BREAKDOWN",
     "CHASE_BOUND_VIOLATION", "CHASE_CUDA_ERROR", "CHASE_OUT_OF_MEMORY", "CHASE_TIMEOUT",
     "CHASE_EIGENSOLVER_ERROR", "CHASE_CONV_ABS", "CHASE_CONV_REL", "CHASE_FP64",
-    "CHASE_SPLIT_BF16", "CHASE_SPLIT_BF16_RR", "CHASE_TILE_AUTO", "CHASE_STORAGE_FULL",
+    "CHASE_SPLIT_BF16", "CHASE_SPLIT_BF16_RR", "CHASE_SPLIT_BF16_ADAPT",
+    "CHASE_SPLIT_BF16_4", "CHASE_SPLIT_BF16_3", "CHASE_TILE_AUTO", "CHASE_STORAGE_FULL",
     "CHASE_STORAGE_LOWER", "ChaseBatchStats", "chase_filter_batched",
     "chase_solve_batched", "chase_filter_real", "chase_residuals_real", "chase_solve_real",
     "chase_filter_c32", "chase_filter_f32", "chase_residuals_c32", "chase_residuals_f32",
@@ -47,6 +48,9 @@ CHASE_EIGENSOLVER_ERROR = 8
 CHASE_FP64 = 0
 CHASE_SPLIT_BF16 = 1
 CHASE_SPLIT_BF16_RR = 2
+CHASE_SPLIT_BF16_ADAPT = 3
+CHASE_SPLIT_BF16_4 = 4
+CHASE_SPLIT_BF16_3 = 5
 CHASE_CONV_ABS = 0
 CHASE_CONV_REL = 1
 CHASE_TILE_AUTO = -1
@@ -79,7 +83,7 @@ class ChaseStats(ctypes.Structure):
         ("t_lanczos", ctypes.c_double), ("t_filter", ctypes.c_double), ("t_qr", ctypes.c_double),
         ("t_rr", ctypes.c_double), ("t_eigh", ctypes.c_double), ("t_resid", ctypes.c_double),
         ("t_host", ctypes.c_double), ("t_rr_product", ctypes.c_double),
-        ("flops_rr_product", ctypes.c_double),
+        ("flops_rr_product", ctypes.c_double), ("filter_slices_low", ctypes.c_int),
     ]
 
     def as_dict(self):

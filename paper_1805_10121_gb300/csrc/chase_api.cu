@@ -120,9 +120,9 @@ struct PhaseTimer {
 template <class T>
 int filter_product(Dev& d, const T* H, int64_t N, int64_t ldh, const SplitH* sh, SplitX* sx,
                    const T* X, int64_t ldx, int b, T* Y, int64_t ldy, int j0,
-                   double alpha, double beta, double shift) {
+                   double alpha, double beta, double shift, int nslices = 7) {
   if constexpr (!is_single<T>) {
-    if (sh) return zgemm_split(d, *sh, *sx, X, ldx, j0, b, Y, ldy, alpha, beta, shift);
+    if (sh) return zgemm_split(d, *sh, *sx, X, ldx, j0, b, Y, ldy, alpha, beta, shift, nslices);
   }
   return gemm(d, N, N, H, ldh, X, ldx, b, Y, ldy, j0, b, alpha, beta, shift);
 }
@@ -131,12 +131,13 @@ template <class T>
 int filter_sorted(Dev& d, const T* H, int64_t N, int64_t ldh, T* X, int64_t ldx,
                   T* Wk, int64_t ldw, int b, const int* start, int maxdeg, double b_sup,
                   double mu1, double mu_nn, long long* matvecs, const SplitH* sh = nullptr,
-                  SplitX* sx = nullptr) {
+                  SplitX* sx = nullptr, int nslices = 7) {
   const double c = 0.5 * (b_sup + mu_nn);  // Alg. 4 line 2
   const double e = 0.5 * (b_sup - mu_nn);
   const double sigma1 = e / (mu1 - c);     // line 3
   // line 4: W = (sigma_1 / e) (H - c I) V
-  CHASE_TRY(filter_product(d, H, N, ldh, sh, sx, X, ldx, b, Wk, ldw, 0, sigma1 / e, 0.0, c));
+  CHASE_TRY(filter_product(d, H, N, ldh, sh, sx, X, ldx, b, Wk, ldw, 0, sigma1 / e, 0.0, c,
+                           nslices));
   long long mv = b;
   double sigma = sigma1;  // line 5
   T* Vb = X;
@@ -147,7 +148,7 @@ int filter_sorted(Dev& d, const T* H, int64_t N, int64_t ldh, T* X, int64_t ldx,
     const int s = start[i];  // lines 12-14: columns with degree < i are done
     // line 9: V[:, s:] = 2 (tau / e) (H - c I) W[:, s:] - tau sigma V[:, s:]
     CHASE_TRY(filter_product(d, H, N, ldh, sh, sx, Wb, ldW, b, Vb, ldV, s, 2.0 * tau / e,
-                             -tau * sigma, c));
+                             -tau * sigma, c, nslices));
     mv += b - s;
     std::swap(Vb, Wb);  // line 10
     std::swap(ldV, ldW);
@@ -576,7 +577,8 @@ struct Solver {
     CHASE_TRY(orth_alloc(d, N, nx, nx, ow));
     CHASE_TRY(rr_alloc(d, N, nx, rw));
     // single-precision solves compute every product natively in FP32
-    split = !is_single<T> && (o.precision == CHASE_SPLIT_BF16 || o.precision == CHASE_SPLIT_BF16_RR);
+    split = !is_single<T> && (o.precision == CHASE_SPLIT_BF16 || o.precision == CHASE_SPLIT_BF16_RR ||
+                              o.precision == CHASE_SPLIT_BF16_ADAPT);
     split_rr = !is_single<T> && o.precision == CHASE_SPLIT_BF16_RR;
     if constexpr (!is_single<T>) {
       if (split && !grouped_split) {  // slices of H once per solve, slice workspace for the block
@@ -636,13 +638,29 @@ struct Solver {
     return true;
   }
 
+  // Slices of the split product for this iteration's filter.  With
+  // CHASE_SPLIT_BF16_ADAPT the precision follows the residuals (Sec. 3.2:
+  // the filter only has to beat the residuals it is asked to reduce): while
+  // every active residual is above 1e-3 h the product keeps 3 slices (about
+  // 2^-21 relative), above 1e-6 h 4 slices (2^-28), else all 7.
+  int slices_for_iteration() const {
+    if (o.precision != CHASE_SPLIT_BF16_ADAPT) return 7;
+    double rmin = HUGE_VAL;
+    for (int a = nconv; a < nx; ++a) rmin = std::min(rmin, res[a]);
+    if (rmin > 1e-3 * h) return 3;
+    if (rmin > 1e-6 * h) return 4;
+    return 7;
+  }
+
   // The filter of this solve alone (line 4).
   int filter(Dev& d) {
     PhaseTimer tm(d.st);
     long long fm = 0;
+    const int ns = slices_for_iteration();
+    S.filter_slices_low += ns < 7 ? 1 : 0;
     tm.begin(&S.t_filter);
     CHASE_TRY(filter_sorted(d, dH, N, lh, Va(), lv, Wk, lw, b(), start.data(), maxdeg, b_sup, mu1,
-                            mu_nn, &fm, split ? &sh : nullptr, &sx));
+                            mu_nn, &fm, split ? &sh : nullptr, &sx, ns));
     tm.end();
     count_filter(fm);
     return CHASE_OK;
@@ -895,7 +913,7 @@ bool solve_args_ok(int64_t N, int64_t ldh, int nev, int nex, double tol, int64_t
            o.deg_extra < 0 || o.max_iter < 0 || o.lanczos_iter < 1 || o.lanczos_iter > N ||
            (!o.approx && o.num_lanczos < 1) ||
            (o.precision != CHASE_FP64 && o.precision != CHASE_SPLIT_BF16 &&
-            o.precision != CHASE_SPLIT_BF16_RR) ||
+            o.precision != CHASE_SPLIT_BF16_RR && o.precision != CHASE_SPLIT_BF16_ADAPT) ||
            (o.conv_mode != CHASE_CONV_ABS && o.conv_mode != CHASE_CONV_REL) ||
            (o.storage != CHASE_STORAGE_FULL && o.storage != CHASE_STORAGE_LOWER));
 }
@@ -931,7 +949,8 @@ template <class T>
 int filter_impl(const T* H, int64_t N, int64_t ldh, T* V, int64_t ldv, int b, const int* degrees,
                 double b_sup, double mu1, double mu_nevnex, int precision, T* work, void* stream) {
   if constexpr (is_single<T>) precision = CHASE_FP64;  // native FP32 products
-  if (precision != CHASE_FP64 && precision != CHASE_SPLIT_BF16) {
+  if (precision != CHASE_FP64 && precision != CHASE_SPLIT_BF16 &&
+      precision != CHASE_SPLIT_BF16_4 && precision != CHASE_SPLIT_BF16_3) {
     set_error("chase_filter: unknown precision %d", precision);
     return CHASE_INVALID_ARG;
   }
@@ -982,8 +1001,10 @@ int filter_impl(const T* H, int64_t N, int64_t ldh, T* V, int64_t ldv, int b, co
   CHASE_TRY(d.sync_check("chase_filter plan"));
   SplitH sh;
   SplitX sx;
+  const bool split = precision != CHASE_FP64;
+  const int nslices = precision == CHASE_SPLIT_BF16_4 ? 4 : precision == CHASE_SPLIT_BF16_3 ? 3 : 7;
   if constexpr (!is_single<T>) {
-    if (precision == CHASE_SPLIT_BF16) {
+    if (split) {
       CHASE_TRY(split_prepare_h(d, dH, N, lh, sh));
       CHASE_TRY(split_alloc_x(d, N, b, sx, is_cplx<T>));
     }
@@ -991,7 +1012,7 @@ int filter_impl(const T* H, int64_t N, int64_t ldh, T* V, int64_t ldv, int b, co
   // sorted copy into the workspace; V becomes the second buffer
   CHASE_TRY(launch_permute_cols(d, dV, lv, wk, lw, N, b, dperm, false));
   CHASE_TRY(filter_sorted(d, dH, N, lh, wk, lw, dV, lv, b, start.data(), maxdeg, b_sup, mu1,
-                          mu_nevnex, nullptr, precision == CHASE_SPLIT_BF16 ? &sh : nullptr, &sx));
+                          mu_nevnex, nullptr, split ? &sh : nullptr, &sx, nslices));
   CHASE_TRY(launch_permute_cols(d, wk, lw, dV, lv, N, b, dperm, true));
   if (dV != V)
     CHASE_TRY(copy_block(d, V, ldv, dV, lv, N, b,

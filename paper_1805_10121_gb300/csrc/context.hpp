@@ -156,10 +156,13 @@ int split_prepare_h(Dev& d, const chase_c64* H, int64_t N, int64_t ldh, SplitH& 
 int split_prepare_h(Dev& d, const double* H, int64_t N, int64_t ldh, SplitH& out);
 int split_alloc_x(Dev& d, int64_t N, int max_cols, SplitX& out, bool cplx = true);
 // C[:, j0:j1] = alpha (H X[:, j0:j1] - shift X[:, j0:j1]) + beta C[:, j0:j1]
+// with the leading `nslices` slices of each operand (7: full accuracy, about
+// 2^-49 relative; 4: about 2^-28; 3: about 2^-21).
 int zgemm_split(Dev& d, const SplitH& h, SplitX& x, const chase_c64* X, int64_t ldx, int j0, int j1,
-                chase_c64* C, int64_t ldc, double alpha, double beta, double shift);
+                chase_c64* C, int64_t ldc, double alpha, double beta, double shift,
+                int nslices = 7);
 int zgemm_split(Dev& d, const SplitH& h, SplitX& x, const double* X, int64_t ldx, int j0, int j1,
-                double* C, int64_t ldc, double alpha, double beta, double shift);
+                double* C, int64_t ldc, double alpha, double beta, double shift, int nslices = 7);
 
 // ---- grouped filter: many independent problems per launch ----------------
 // One problem of a grouped filter, in device memory.  buf0 holds the block

@@ -61,7 +61,7 @@
 
 namespace chase {
 namespace split {
-constexpr int S = 7;                 // 7-bit slices per operand
+constexpr int S = 7;                 // 7-bit slices per operand (full accuracy)
 constexpr int BM = 128;              // rows per CTA (TMEM lanes)
 constexpr int BN = 64;               // real columns of the product per CTA (32 complex)
 constexpr int BK = 16;               // K per MMA (a K block)
@@ -79,6 +79,23 @@ constexpr int TMEM_COLS = 512;
 constexpr int kFlushWarps = 8;       // two per TMEM lane quarter, 32 columns each
 constexpr int kThreads = (2 + kFlushWarps) * 32;
 constexpr int SMEM = 1024 + NSTAGE * STAGE_BYTES + 256;
+
+// A product that keeps only the leading NS slices of each operand (pairs
+// s + t < NS): the truncation error becomes about 2^-(7 NS) of the scales
+// instead of 2^-49, for (NS (NS + 1) / 2) / 28 of the tensor work.  The stage
+// ring and the TMEM allocation shrink with NS.
+template <int NS>
+struct Slices {
+  static constexpr int S = NS;
+  static constexpr int NEXACT = NS < 3 ? NS : 3;
+  static constexpr int STAGE_A = NS * A_TILE;
+  static constexpr int STAGE_B = NS * B_TILE;
+  static constexpr int STAGE_BYTES = STAGE_A + STAGE_B;
+  static constexpr int NSTAGE = NS <= 4 ? 4 : 2;
+  static constexpr int TMEM_COLS = NS * BN <= 256 ? 256 : 512;
+  static constexpr int SMEM = 1024 + NSTAGE * STAGE_BYTES + 256;
+  static_assert(SMEM <= 232448, "shared memory per CTA");
+};
 
 // K-major operand with 64-byte swizzled rows: 8-row atoms of 512 B stacked
 // along M (SBO); the second K block of a row starts 32 bytes in.
@@ -179,7 +196,17 @@ __device__ __forceinline__ void acquire_tmap(const CUtensorMap* map) {
                : "memory");
 }
 
+template <int NS>
 __device__ __forceinline__ void split_tile_body(const SplitTile& T, int* __restrict__ err) {
+  static_assert(NS >= 3 && NS <= 7, "3 to 7 slices");
+  using C = Slices<NS>;
+  constexpr int S = C::S;
+  constexpr int NEXACT = C::NEXACT;
+  constexpr int NSTAGE = C::NSTAGE;
+  constexpr int STAGE_A = C::STAGE_A;
+  constexpr int STAGE_B = C::STAGE_B;
+  constexpr int STAGE_BYTES = C::STAGE_BYTES;
+  constexpr int TMEM_COLS = C::TMEM_COLS;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -349,20 +376,22 @@ __device__ __forceinline__ void split_tile_body(const SplitTile& T, int* __restr
 #pragma unroll
       for (int c0 = 0; c0 < 32; c0 += 8) {
         float t[8];
-        {
+        if constexpr (S > NEXACT) {
           uint32_t r[8];
           TMEM_LD8(tbase + (S - 1) * BN + c0, r);
           asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
           for (int j = 0; j < 8; ++j) t[j] = __uint_as_float(r[j]);
-        }
 #pragma unroll 1
-        for (int d = S - 2; d >= NEXACT; --d) {
-          uint32_t r[8];
-          TMEM_LD8(tbase + d * BN + c0, r);
-          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+          for (int d = S - 2; d >= NEXACT; --d) {
+            TMEM_LD8(tbase + d * BN + c0, r);
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-          for (int j = 0; j < 8; ++j) t[j] = fmaf(t[j], 0.0078125f, __uint_as_float(r[j]));
+            for (int j = 0; j < 8; ++j) t[j] = fmaf(t[j], 0.0078125f, __uint_as_float(r[j]));
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) t[j] = 0.f;  // no tail levels
         }
         if (in_rows && T.cplx) {
 #pragma unroll
@@ -436,6 +465,7 @@ __device__ __forceinline__ void split_tile_body(const SplitTile& T, int* __restr
 }
 
 // One problem: grid (column tiles, row tiles), B map over the active block.
+template <int NS>
 __global__ void __launch_bounds__(kThreads, 1)
     zgemm_split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                        const int* __restrict__ Erow, const int* __restrict__ Fcol,
@@ -467,7 +497,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   T.shift = shift;
   T.P = P;
   T.ldp = ldp;
-  split_tile_body(T, err);
+  split_tile_body<NS>(T, err);
 }
 
 // Problem of CTA `bid` in a grouped step list: the last entry with
@@ -520,7 +550,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   T.shift = stp.shift;
   T.P = nullptr;
   T.ldp = 0;
-  split_tile_body(T, err);
+  split_tile_body<S>(T, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -869,10 +899,12 @@ int segments_for(int64_t nkb, int64_t tiles) {
   return nseg;
 }
 
-// The split product for complex (E = double2) or real (E = double) operands.
-template <class E>
-int split_product(Dev& d, const SplitH& h, SplitX& x, const E* X, int64_t ldx, int j0, int j1, E* C,
-                  int64_t ldc, double alpha, double beta, double shift) {
+// The split product for complex (E = double2) or real (E = double) operands
+// with the leading NS slices of each operand.
+template <int NS, class E>
+int split_product_ns(Dev& d, const SplitH& h, SplitX& x, const E* X, int64_t ldx, int j0, int j1,
+                     E* C, int64_t ldc, double alpha, double beta, double shift) {
+  using SC = split::Slices<NS>;
   constexpr bool cplx = sizeof(E) == 16;
   const int ncols = j1 - j0;
   if (ncols <= 0) return CHASE_OK;
@@ -894,14 +926,15 @@ int split_product(Dev& d, const SplitH& h, SplitX& x, const E* X, int64_t ldx, i
   note_launch();
   CHASE_CUDA(cudaGetLastError());
   CUtensorMap tmA, tmB;
+  // the maps read the leading NS slice planes
   CHASE_TRY(make_tmap_bf16_3d(&tmA, h.A, K, N, split::S, Kp * 2, Kp * 2 * N, split::BX, split::BM,
-                              split::S));
+                              NS));
   CHASE_TRY(make_tmap_bf16_3d(&tmB, x.B, K, brows, split::S, Kp * 2, Kp * 2 * rows_cap, split::BX,
-                              split::BN, split::S));
-  static bool attr_done = false;
+                              split::BN, NS));
+  static bool attr_done = false;  // per instantiation
   if (!attr_done) {
-    CHASE_CUDA(cudaFuncSetAttribute(split::zgemm_split_kernel,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, split::SMEM));
+    CHASE_CUDA(cudaFuncSetAttribute(split::zgemm_split_kernel<NS>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, SC::SMEM));
     attr_done = true;
   }
   const int64_t ctiles = (brows + split::BN - 1) / split::BN;
@@ -912,7 +945,7 @@ int split_product(Dev& d, const SplitH& h, SplitX& x, const E* X, int64_t ldx, i
   const double2* Xd = reinterpret_cast<const double2*>(X);
   double2* Cd = reinterpret_cast<double2*>(C);
   if (nseg == 1) {
-    split::zgemm_split_kernel<<<grid, split::kThreads, split::SMEM, d.st>>>(
+    split::zgemm_split_kernel<NS><<<grid, split::kThreads, SC::SMEM, d.st>>>(
         tmA, tmB, h.E, x.F, h.Dg, static_cast<int>(N), 0, nkb, ncols, j0, Xd, ldx, Cd, ldc, alpha,
         beta, shift, nullptr, 0, cplx ? 1 : 0, d.err);
     note_launch();
@@ -936,7 +969,7 @@ int split_product(Dev& d, const SplitH& h, SplitX& x, const E* X, int64_t ldx, i
     const int kb0 = g * per;
     const int cnt = std::min(per, nkb - kb0);
     if (cnt <= 0) break;
-    split::zgemm_split_kernel<<<grid, split::kThreads, split::SMEM, d.st>>>(
+    split::zgemm_split_kernel<NS><<<grid, split::kThreads, SC::SMEM, d.st>>>(
         tmA, tmB, h.E, x.F, h.Dg, static_cast<int>(N), kb0, cnt, ncols, j0, Xd, ldx, Cd, ldc,
         alpha, beta, shift, reinterpret_cast<double2*>(P + g * pstride), N, cplx ? 1 : 0, d.err);
     note_launch();
@@ -951,17 +984,33 @@ int split_product(Dev& d, const SplitH& h, SplitX& x, const E* X, int64_t ldx, i
   CHASE_CUDA(cudaGetLastError());
   return CHASE_OK;
 }
+
+template <class E>
+int split_product(Dev& d, const SplitH& h, SplitX& x, const E* X, int64_t ldx, int j0, int j1, E* C,
+                  int64_t ldc, double alpha, double beta, double shift, int nslices) {
+  switch (nslices) {
+    case 3:
+      return split_product_ns<3>(d, h, x, X, ldx, j0, j1, C, ldc, alpha, beta, shift);
+    case 4:
+      return split_product_ns<4>(d, h, x, X, ldx, j0, j1, C, ldc, alpha, beta, shift);
+    case 7:
+      return split_product_ns<7>(d, h, x, X, ldx, j0, j1, C, ldc, alpha, beta, shift);
+    default:
+      set_error("split product: %d slices (3, 4 or 7 supported)", nslices);
+      return CHASE_INVALID_ARG;
+  }
+}
 }  // namespace
 
 int zgemm_split(Dev& d, const SplitH& h, SplitX& x, const chase_c64* X, int64_t ldx, int j0, int j1,
-                chase_c64* C, int64_t ldc, double alpha, double beta, double shift) {
+                chase_c64* C, int64_t ldc, double alpha, double beta, double shift, int nslices) {
   return split_product(d, h, x, reinterpret_cast<const double2*>(X), ldx, j0, j1,
-                       reinterpret_cast<double2*>(C), ldc, alpha, beta, shift);
+                       reinterpret_cast<double2*>(C), ldc, alpha, beta, shift, nslices);
 }
 
 int zgemm_split(Dev& d, const SplitH& h, SplitX& x, const double* X, int64_t ldx, int j0, int j1,
-                double* C, int64_t ldc, double alpha, double beta, double shift) {
-  return split_product(d, h, x, X, ldx, j0, j1, C, ldc, alpha, beta, shift);
+                double* C, int64_t ldc, double alpha, double beta, double shift, int nslices) {
+  return split_product(d, h, x, X, ldx, j0, j1, C, ldc, alpha, beta, shift, nslices);
 }
 
 int split_grouped_prepare_h(Dev& d, const GroupedSliceH* probs, int P, int total_rows) {

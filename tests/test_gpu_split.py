@@ -213,3 +213,47 @@ def test_split_rr_batched_solve():
     for k, (n, nev, nex) in enumerate(shapes):
         check_solution(Hs[k].cpu().numpy(), lams[k], ritz[k], res[k], Vs[k].cpu().numpy(), nev,
                        tol)
+
+
+# Per filtered column the error is a few hundred times the per-product
+# truncation 2^-(7 S) over degrees up to 20 (measured: 2e-6 with 4 slices,
+# 2e-4 with 3, 1e-12 with 7); the bound allows 4000 x 2^-(7 S).
+@pytest.mark.parametrize("precision,rtol", [(chase.CHASE_SPLIT_BF16_4, 4000 * 2.0 ** -28),
+                                            (chase.CHASE_SPLIT_BF16_3, 4000 * 2.0 ** -21)])
+@pytest.mark.parametrize("n,b", [(300, 37), (1000, 33)])
+def test_reduced_slice_filter_accuracy(precision, rtol, n, b):
+    # the leading 4 (3) slices: about 2^-28 (2^-21) relative per product;
+    # the FP64 diagonal term is unchanged
+    H, lam = known_h(n, 291 + n)
+    V = synth.gaussian_block(n, b, 292 + b)
+    rng = np.random.default_rng(n + 11 * b)
+    deg = (2 * rng.integers(1, 11, size=b)).astype(np.int32)
+    l = lam.numpy()
+    b_sup, mu1, mu_nn = 1.02, float(l[0]), float(l[min(n - 1, max(1, n // 8))])
+    ref = oracle_filter_any_order(H.numpy(), V.numpy(), deg, b_sup, mu1, mu_nn)
+    Vd = dcol(V)
+    chase.chase_filter(dcol(H), Vd, deg, b_sup, mu1, mu_nn, precision=precision)
+    err = col_rel_err(Vd.cpu().numpy(), ref)
+    assert err <= rtol
+    # and it is a genuinely reduced precision: well above the 7-slice error
+    assert err >= 1e-12
+
+
+@pytest.mark.parametrize("n,nev,nex", [(1000, 50, 20), (700, 35, 14)])
+def test_adaptive_slices_solve_matches_fp64(n, nev, nex):
+    tol = 1e-10
+    H, lam = known_h(n, 301 + n, n_cluster=60)
+    V0 = synth.gaussian_block(n, nev + nex, 302)
+    S = synth.gaussian_block(n, 5, 303)
+    out = {}
+    for prec in (chase.CHASE_SPLIT_BF16, chase.CHASE_SPLIT_BF16_ADAPT):
+        Vd = dcol(V0)
+        o = chase.chase_opts_default(precision=prec)
+        st, ritz, resid, stats = chase.chase_solve(dcol(H), nev, nex, tol, Vd, dcol(S), opts=o)
+        assert st == chase.CHASE_OK
+        check_solution(H.numpy(), lam.numpy(), ritz, resid, Vd.cpu().numpy(), nev, tol)
+        out[prec] = (ritz, stats)
+    assert out[chase.CHASE_SPLIT_BF16_ADAPT][1]["filter_slices_low"] >= 1
+    hn = float(lam.abs().max())
+    assert np.max(np.abs(out[chase.CHASE_SPLIT_BF16][0][:nev] -
+                         out[chase.CHASE_SPLIT_BF16_ADAPT][0][:nev])) <= EIG_RTOL * hn
