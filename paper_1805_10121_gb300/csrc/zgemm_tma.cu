@@ -26,6 +26,11 @@
 //  * the shift, scale and axpby of the recurrence are applied while the
 //    accumulators are still in registers, so the filter makes one pass over
 //    its output per degree step;
+//  * the tile shape (64 x 32, 128 x 16, 64 x 16 or 64 x 8 outputs) is the one
+//    with the least work on the busiest SM: one CTA already keeps an SM's
+//    FP64 pipe busy, so narrow blocks want narrow tiles on more SMs
+//    (measured, N = 8000: one column 14.4 ms with 64 x 32, 4.0 ms with
+//    64 x 8; 100 columns 56.7 ms and 40.5 ms);
 //  * every mbarrier wait is bounded; a wait that gives up records an error
 //    flag that the host turns into CHASE_TIMEOUT, and the producer drains
 //    its own copies in flight before the CTA exits.
@@ -500,6 +505,31 @@ int launch_grouped(Dev& d, const GroupedProblem* probs, const GroupedStep* steps
   return CHASE_OK;
 }
 
+int sm_count() {
+  static int v = 0;
+  if (v == 0) {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+      n = 152;
+    cudaGetLastError();
+    v = n;
+  }
+  return v;
+}
+
+// Predicted time of an M x w product with tile shape C, in units of
+// output-tile area: one CTA of four DMMA warps already keeps an SM's FP64
+// pipe busy (measured: two to six co-resident CTAs run no faster per
+// output), so the product takes as long as the busiest SM's tiles, i.e.
+// ceil(tiles / SMs) x tile area.  Fits the measured times of all four
+// shapes at N = 1200 - 8000 and 1 - 480 columns to within a few percent.
+template <class C>
+double tile_cost(int64_t M, int w) {
+  const int64_t tiles = ((M + C::BM - 1) / C::BM) * ((w + C::BN - 1) / C::BN);
+  const int64_t per_sm = (tiles + sm_count() - 1) / sm_count();
+  return static_cast<double>(per_sm) * C::BM * C::BN;
+}
 }  // namespace
 
 // Candidate tile shapes of the grouped FP64 filter, in autotuning order.
@@ -545,9 +575,17 @@ int zgemm(Dev& d, int64_t M, int64_t K, const chase_c64* A, int64_t lda, const c
     return CHASE_INVALID_ARG;
   }
   const int w = j1 - j0;
-  if (w <= 8) return launch_cfg<CfgNarrow>(d, M, K, A, lda, B, ldb, ncols_b, Cm, ldc, j0, j1, alpha, beta, shift);
-  if (w <= 16) return launch_cfg<CfgMid>(d, M, K, A, lda, B, ldb, ncols_b, Cm, ldc, j0, j1, alpha, beta, shift);
-  return launch_cfg<CfgWide>(d, M, K, A, lda, B, ldb, ncols_b, Cm, ldc, j0, j1, alpha, beta, shift);
+  // the tile shape with the least work on the busiest SM (ties: the wider
+  // tile, which re-reads A fewer times)
+  const double cost[4] = {tile_cost<CfgWide>(M, w), tile_cost<CfgTall>(M, w),
+                          tile_cost<CfgMid>(M, w), tile_cost<CfgNarrow>(M, w)};
+  int best = 0;
+  for (int c = 1; c < 4; ++c)
+    if (cost[c] < 0.97 * cost[best]) best = c;
+  if (best == 0) return launch_cfg<CfgWide>(d, M, K, A, lda, B, ldb, ncols_b, Cm, ldc, j0, j1, alpha, beta, shift);
+  if (best == 1) return launch_cfg<CfgTall>(d, M, K, A, lda, B, ldb, ncols_b, Cm, ldc, j0, j1, alpha, beta, shift);
+  if (best == 2) return launch_cfg<CfgMid>(d, M, K, A, lda, B, ldb, ncols_b, Cm, ldc, j0, j1, alpha, beta, shift);
+  return launch_cfg<CfgNarrow>(d, M, K, A, lda, B, ldb, ncols_b, Cm, ldc, j0, j1, alpha, beta, shift);
 }
 
 int dgemm(Dev& d, int64_t M, int64_t K, const double* A, int64_t lda, const double* B, int64_t ldb,
@@ -563,10 +601,16 @@ int dgemm(Dev& d, int64_t M, int64_t K, const double* A, int64_t lda, const doub
     return CHASE_INVALID_ARG;
   }
   const int w = j1 - j0;
-  if (w <= 8)
+  // as for complex: the least work on the busiest SM, ties to the wider tile
+  const double cost[3] = {tile_cost<RCfgWide>(M, w), tile_cost<RCfgMid>(M, w),
+                          tile_cost<RCfgNarrow>(M, w)};
+  int best = 0;
+  for (int c = 1; c < 3; ++c)
+    if (cost[c] < 0.97 * cost[best]) best = c;
+  if (best == 2)
     return launch_cfg_real<RCfgNarrow>(d, M, K, A, lda, B, ldb, ncols_b, Cm, ldc, j0, j1, alpha,
                                        beta, shift);
-  if (w <= 16)
+  if (best == 1)
     return launch_cfg_real<RCfgMid>(d, M, K, A, lda, B, ldb, ncols_b, Cm, ldc, j0, j1, alpha, beta,
                                     shift);
   return launch_cfg_real<RCfgWide>(d, M, K, A, lda, B, ldb, ncols_b, Cm, ldc, j0, j1, alpha, beta,
