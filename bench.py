@@ -56,7 +56,7 @@ def parse():
                         "split product; fp64: FP64 throughout")
     p.add_argument("--workload", default="sequence",
                    choices=["sequence", "filter", "serve", "batched", "batched-solve",
-                            "degree-sweep"],
+                            "degree-sweep", "side"],
                    help="sequence: timed solves of the correlated sequence (default); "
                         "filter: timed degree-m filter calls on one problem, split vs FP64")
     p.add_argument("--filter-degree", type=int, default=20)
@@ -272,6 +272,36 @@ def roofline_entry(stats_list, pk, src, precision):
     if rr_t >= sum(s["t_filter"] for s in stats_list):
         return rr, filt
     return filt, rr
+
+
+def lanczos_entry(stats_list, n, pk, src):
+    """Rate of the Lanczos phase (Alg. 6): its matvecs run on the few-column
+    product (one vector per step after a warm start), which reads H once per
+    step and is bound by the FP64 FMA pipe (2 FLOP/byte against a machine
+    balance of 0.15)."""
+    mv = sum(s.get("lanczos_matvecs", 0) for s in stats_list)
+    t = sum(s["t_lanczos"] for s in stats_list)
+    if mv <= 0 or t <= 0:
+        return None
+    flops = 8.0 * n * n * mv
+    hbm_bytes = 16.0 * n * n * mv  # warm-started solves: one vector per step
+    peak = pk.get("bf16_tflops", 1900.0) * NOMINAL_FP64_OVER_BF16
+    tf = flops / t / 1e12
+    return {
+        "kernel": "fewcol_kernel (FP64 FMA on the CUDA cores): the Lanczos matvecs",
+        "bound": "fp64",
+        "matvecs": int(mv),
+        "seconds": round(t, 4),
+        "achieved": round(tf, 4),
+        "peak": round(peak, 4),
+        "unit": "TFLOP/s",
+        "frac": round(tf / peak, 4),
+        "hbm_gbs": round(hbm_bytes / t / 1e9, 1),
+        "hbm_frac": round(hbm_bytes / t / 1e9 / pk.get("hbm_gbs", 6800.0), 4),
+        "timing": "whole Lanczos phase (matvecs, three-term steps, host tridiagonal "
+                  "eigensolves), CUDA events on the solve's stream",
+        "peak_source": f"{src} bf16_tflops x nominal FP64/BF16 ratio (1.25/2250)",
+    }
 
 
 def workload_config(args, world):
@@ -767,6 +797,92 @@ def run_degree_sweep(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def run_side_workload(args, rank, world, local):
+    """The steps beside the filter, one C-ABI call each on problem 1 of the
+    sequence workload: the Lanczos bound estimate of a warm start (Alg. 6,
+    one vector, k = 25 matvecs), the full Lanczos of a cold start (1 + n_vec
+    = 5 vectors as one block) and the residual norms of the nev + nex block
+    (one product with H plus the fused norm kernel).  All are FP64; on this
+    GPU the FP64 pipe, not HBM, bounds each of them (the one-vector matvec
+    has 2 FLOP/byte against a machine balance of 0.15), so each line gives
+    the FP64 rate and the HBM rate the pass over H achieved."""
+    from paper_1805_10121_gb300 import build, chase, synth
+    build.build()
+    chase.lib()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n, nev, nex = args.n, args.nev, args.nex
+    nx = nev + nex
+    seed = args.seed + 1000 * rank
+    seq, lam, hnorm = make_sequence(n, 1, seed, dev)
+    H = seq[0]
+    S = synth.gaussian_block(n, 5, seed + 8, device=dev)
+    V = synth.gaussian_block(n, nx, seed + 7, device=dev)
+    w = np.linspace(float(lam.min()), float(lam.max()), nx)
+    stream = torch.cuda.current_stream(dev)
+    k = 25
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3 / args.steps
+
+    launches0 = chase.chase_kernel_launches()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_warm = timed(lambda: chase.chase_lanczos(H, k, 4, 1, nev, nex, S[:, :1]))
+    t_cold = timed(lambda: chase.chase_lanczos(H, k, 4, 0, nev, nex, S))
+    t_res = timed(lambda: chase.chase_residuals(H, V, w))
+    clk = clocks.stop()
+    launches = chase.chase_kernel_launches() - launches0
+    pk, src = peaks()
+    fp64_peak = pk.get("bf16_tflops", 1900.0) * NOMINAL_FP64_OVER_BF16
+    hbm = pk.get("hbm_gbs", 6800.0)
+
+    def entry(what, secs, flops, hbm_bytes, kernel):
+        tf = flops / secs / 1e12
+        gbs = hbm_bytes / secs / 1e9
+        return {"step": what, "kernel": kernel, "seconds": round(secs, 5),
+                "tflops": round(tf, 4), "fp64_frac": round(tf / fp64_peak, 4),
+                "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4)}
+
+    h_bytes = 16.0 * n * n
+    rows = [
+        entry("Lanczos bound, warm start (1 vector, 25 steps)", t_warm, 8.0 * n * n * k,
+              h_bytes * k, "fewcol_kernel<1> + lanczos_step_kernel"),
+        entry("Lanczos with DoS, cold start (5 vectors, 25 steps)", t_cold, 8.0 * n * n * k * 5,
+              h_bytes * k, "fewcol_kernel<5> + lanczos_step_kernel"),
+        entry(f"residual norms of {nx} columns", t_res, 8.0 * n * n * nx,
+              h_bytes + 3 * 16.0 * n * nx, "zgemm_tma_kernel + resid_norms_kernel"),
+    ]
+    cfg = workload_config(args, world)
+    cfg["workload"] = (f"steps beside the filter on problem 1 of the sequence workload, N={n}, "
+                       f"nev={nev}, nex={nex}: Lanczos (warm and cold) and residual norms; "
+                       f"step = one call of each")
+    line = {
+        "metric": METRIC, "value": rows[0]["tflops"], "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * (t_warm + t_cold + t_res), 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": cfg, "side_steps": rows,
+        "roofline": {"bound": "tensor", "kernel": "fewcol_kernel (FP64 FMA): Lanczos matvec",
+                     "achieved": rows[0]["tflops"], "peak": round(fp64_peak, 4),
+                     "unit": "TFLOP/s", "frac": rows[0]["fp64_frac"], "traffic": None,
+                     "peak_source": f"{src} bf16_tflops x nominal FP64/BF16 ratio (1.25/2250)"},
+        "gpu_launches": int(launches), "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_serve_workload(args, rank, world, local):
     """Replay a seeded Poisson trace of sequence-solve requests through the
     continuous-batching server; report throughput and p50/p99 latency."""
@@ -846,6 +962,9 @@ def main():
         return
     if args.workload == "batched-solve":
         run_batched_solve_workload(args, rank, world, local)
+        return
+    if args.workload == "side":
+        run_side_workload(args, rank, world, local)
         return
     if args.workload == "degree-sweep":
         run_degree_sweep(args, rank, world, local)
@@ -1016,6 +1135,7 @@ def main():
         "warmup_iterations": [s["iterations"] for _, s in stats_w],
         "roofline": roof_main,
         "roofline_other_kernel": roof_other,
+        "lanczos": lanczos_entry(stats_t, n, pk, src),
         "fp64_same_problem": fp64,
         "split_rr_same_problem": split_rr,
         "cpu_baseline": cb,

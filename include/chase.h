@@ -130,6 +130,7 @@ typedef struct {
   double t_rr_product;     /* seconds of Rayleigh-Ritz's H Q products (inside t_rr) */
   double flops_rr_product; /* their algorithmic FLOPs (8 N^2 b complex, 2 N^2 b real) */
   int filter_slices_low;   /* iterations whose filter kept fewer than 7 slices (ADAPT) */
+  long long lanczos_matvecs; /* column products with H inside Alg. 6 (k per run) */
 } chase_stats;
 
 /* Tile choice of the grouped FP64 filter: time the candidates on the first

@@ -84,6 +84,7 @@ class ChaseStats(ctypes.Structure):
         ("t_rr", ctypes.c_double), ("t_eigh", ctypes.c_double), ("t_resid", ctypes.c_double),
         ("t_host", ctypes.c_double), ("t_rr_product", ctypes.c_double),
         ("flops_rr_product", ctypes.c_double), ("filter_slices_low", ctypes.c_int),
+        ("lanczos_matvecs", ctypes.c_longlong),
     ]
 
     def as_dict(self):

@@ -603,6 +603,7 @@ struct Solver {
                            lz));
     tm.end();
     S.matvecs += lz.matvecs;
+    S.lanczos_matvecs += lz.matvecs;
     S.flops_total += kMv * N2 * lz.matvecs;
     b_sup = lz.b_sup;
     if (o.approx) {

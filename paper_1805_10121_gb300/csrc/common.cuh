@@ -177,6 +177,23 @@ inline int gemm(Dev& d, int64_t M, int64_t K, const float* A, int64_t lda, const
   return sgemm(d, M, K, A, lda, B, ldb, ncols_b, C, ldc, j0, j1, alpha, beta, shift);
 }
 
+// Products with at most kFewColMax columns (fewcol.cu), same contract as the
+// gemm overloads above; they run on the CUDA cores' FMA pipe without
+// workspace, and the gemm overloads route every such product here.
+constexpr int kFewColMax = 6;
+int fewcol_gemm(Dev& d, int64_t M, int64_t K, const chase_c64* A, int64_t lda, const chase_c64* B,
+                int64_t ldb, chase_c64* C, int64_t ldc, int j0, int j1, double alpha, double beta,
+                double shift);
+int fewcol_gemm(Dev& d, int64_t M, int64_t K, const double* A, int64_t lda, const double* B,
+                int64_t ldb, double* C, int64_t ldc, int j0, int j1, double alpha, double beta,
+                double shift);
+int fewcol_gemm(Dev& d, int64_t M, int64_t K, const chase_c32* A, int64_t lda, const chase_c32* B,
+                int64_t ldb, chase_c32* C, int64_t ldc, int j0, int j1, double alpha, double beta,
+                double shift);
+int fewcol_gemm(Dev& d, int64_t M, int64_t K, const float* A, int64_t lda, const float* B,
+                int64_t ldb, float* C, int64_t ldc, int j0, int j1, double alpha, double beta,
+                double shift);
+
 // C (p x q, ldc) = X^H Y with X: N x p (ldx), Y: N x q (ldy).
 int zgram(Dev& d, int64_t N, const chase_c64* X, int64_t ldx, int p, const chase_c64* Y,
           int64_t ldy, int q, chase_c64* C, int64_t ldc);

@@ -191,6 +191,8 @@ int gemm_impl(Dev& d, int64_t M, int64_t K, const T* A, int64_t lda, const T* B,
     set_error("single-precision gemm: the shifted product needs a square A");
     return CHASE_INVALID_ARG;
   }
+  if (j1 - j0 <= kFewColMax)
+    return fewcol_gemm(d, M, K, A, lda, B, ldb, Cm, ldc, j0, j1, alpha, beta, shift);
   using E = elem<T>;
   dim3 grid(static_cast<unsigned>((M + TM - 1) / TM), static_cast<unsigned>((j1 - j0 + TN - 1) / TN));
   f32_gemm_kernel<E, false><<<grid, NT, 0, d.st>>>(

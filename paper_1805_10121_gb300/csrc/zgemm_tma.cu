@@ -30,7 +30,8 @@
 //    with the least work on the busiest SM: one CTA already keeps an SM's
 //    FP64 pipe busy, so narrow blocks want narrow tiles on more SMs
 //    (measured, N = 8000: one column 14.4 ms with 64 x 32, 4.0 ms with
-//    64 x 8; 100 columns 56.7 ms and 40.5 ms);
+//    64 x 8; 100 columns 56.7 ms and 40.5 ms); products of at most six
+//    columns skip the tensor pipe altogether (fewcol.cu);
 //  * every mbarrier wait is bounded; a wait that gives up records an error
 //    flag that the host turns into CHASE_TIMEOUT, and the producer drains
 //    its own copies in flight before the CTA exits.
@@ -575,6 +576,8 @@ int zgemm(Dev& d, int64_t M, int64_t K, const chase_c64* A, int64_t lda, const c
     return CHASE_INVALID_ARG;
   }
   const int w = j1 - j0;
+  if (w <= kFewColMax)
+    return fewcol_gemm(d, M, K, A, lda, B, ldb, Cm, ldc, j0, j1, alpha, beta, shift);
   // the tile shape with the least work on the busiest SM (ties: the wider
   // tile, which re-reads A fewer times)
   const double cost[4] = {tile_cost<CfgWide>(M, w), tile_cost<CfgTall>(M, w),
@@ -601,6 +604,8 @@ int dgemm(Dev& d, int64_t M, int64_t K, const double* A, int64_t lda, const doub
     return CHASE_INVALID_ARG;
   }
   const int w = j1 - j0;
+  if (w <= kFewColMax)
+    return fewcol_gemm(d, M, K, A, lda, B, ldb, Cm, ldc, j0, j1, alpha, beta, shift);
   // as for complex: the least work on the busiest SM, ties to the wider tile
   const double cost[3] = {tile_cost<RCfgWide>(M, w), tile_cost<RCfgMid>(M, w),
                           tile_cost<RCfgNarrow>(M, w)};
