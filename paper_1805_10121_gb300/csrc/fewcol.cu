@@ -12,10 +12,16 @@
 //
 // Layout of the work: a warp owns RW consecutive rows of A and splits K over
 // KL = 32 / RW lanes (lane = kphase * RW + row), so each load instruction
-// reads KL column segments of RW * sizeof(E) contiguous bytes (a whole
-// number of 32-byte sectors).  The KL partial sums of a row are combined by
-// a fixed butterfly of shuffles, so the result does not depend on timing.
-// No workspace is needed: the products run inside allocation-free callers.
+// reads KL column segments of RW * sizeof(E) = 32 contiguous bytes (one
+// sector each).  The KL partial sums of a row are combined by a fixed
+// butterfly of shuffles, so the result does not depend on timing.  No
+// workspace is needed: the products run inside allocation-free callers.
+//
+// With one or two columns the FP64 pipe needs A at about 2 TB/s (N = 4000),
+// which takes tens of KB of loads in flight per SM: narrow row groups give
+// many warps, and each lane keeps kUnroll independent loads of A in flight
+// (measured with 4 rows per warp and 4 loads: 34 % FP64 pipe, stalled on
+// memory latency).
 #include "common.cuh"
 #include "context.hpp"
 
@@ -23,7 +29,10 @@ namespace chase {
 namespace {
 
 constexpr int kThreads = 128;  // 4 warps
-constexpr int kUnroll = 4;     // independent loads of A in flight per lane
+// independent loads of A in flight per lane: more where the FP64 work per
+// loaded element is small
+template <int R>
+constexpr int kUnroll = R <= 2 ? 8 : 4;
 
 template <class E>
 struct FC;
@@ -31,7 +40,7 @@ struct FC;
 template <>
 struct FC<double2> {
   using S = double;
-  static constexpr int KL = 8;  // 4 rows x 16 B = 64 B per column segment
+  static constexpr int KL = 16;  // 2 rows x 16 B per column segment
   static __device__ __forceinline__ double2 zero() { return make_double2(0.0, 0.0); }
   static __device__ __forceinline__ void fma(double2& c, double2 a, double2 b) {
     c.x = ::fma(a.x, b.x, c.x);
@@ -58,7 +67,7 @@ struct FC<double2> {
 template <>
 struct FC<double> {
   using S = double;
-  static constexpr int KL = 8;  // 4 rows x 8 B = one 32 B sector per column segment
+  static constexpr int KL = 8;  // 4 rows x 8 B per column segment
   static __device__ __forceinline__ double zero() { return 0.0; }
   static __device__ __forceinline__ void fma(double& c, double a, double b) { c = ::fma(a, b, c); }
   static __device__ __forceinline__ double shfl_add(double v, int m) {
@@ -75,7 +84,7 @@ struct FC<double> {
 template <>
 struct FC<float2> {
   using S = float;
-  static constexpr int KL = 4;  // 8 rows x 8 B = 64 B
+  static constexpr int KL = 8;  // 4 rows x 8 B
   static __device__ __forceinline__ float2 zero() { return make_float2(0.f, 0.f); }
   static __device__ __forceinline__ void fma(float2& c, float2 a, float2 b) {
     c.x = fmaf(a.x, b.x, c.x);
@@ -102,7 +111,7 @@ struct FC<float2> {
 template <>
 struct FC<float> {
   using S = float;
-  static constexpr int KL = 2;  // 16 rows x 4 B = 64 B
+  static constexpr int KL = 4;  // 8 rows x 4 B
   static __device__ __forceinline__ float zero() { return 0.f; }
   static __device__ __forceinline__ void fma(float& c, float a, float b) { c = fmaf(a, b, c); }
   static __device__ __forceinline__ float shfl_add(float v, int m) {
@@ -135,13 +144,14 @@ __global__ void __launch_bounds__(kThreads)
 
   const E* Ar = A + (live ? r : 0);
   const E* Bj = B + static_cast<long long>(j0) * ldb;
+  constexpr int U = kUnroll<R>;
   long long k = kp;
-  for (; k + (kUnroll - 1) * KL < K; k += kUnroll * KL) {
-    E h[kUnroll];
+  for (; k + (U - 1) * KL < K; k += U * KL) {
+    E h[U];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) h[u] = live ? __ldg(Ar + (k + u * KL) * lda) : F::zero();
+    for (int u = 0; u < U; ++u) h[u] = live ? __ldg(Ar + (k + u * KL) * lda) : F::zero();
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u)
+    for (int u = 0; u < U; ++u)
 #pragma unroll
       for (int j = 0; j < R; ++j) F::fma(acc[j], h[u], __ldg(Bj + j * ldb + k + u * KL));
   }

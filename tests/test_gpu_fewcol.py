@@ -2,8 +2,8 @@
 Lanczos matvecs and the last degree steps of the filter) in all four scalar
 kinds, through chase_filter* and chase_residuals* against the oracle.
 Seven columns take the tensor-core tile path and are checked beside them.
-n = 517 leaves a ragged tail in rows (16, 32 or 64 rows per block) and in
-K (8, 4 or 2 K lanes times an unroll of 4)."""
+n = 517 leaves a ragged tail in rows (8, 16 or 32 rows per block) and in
+K (16, 8 or 4 K lanes times an unroll of 8 or 4)."""
 
 import numpy as np
 import pytest
