@@ -20,8 +20,9 @@
 // With one or two columns the FP64 pipe needs A at about 2 TB/s (N = 4000),
 // which takes tens of KB of loads in flight per SM: narrow row groups give
 // many warps, and each lane keeps kUnroll independent loads of A in flight
-// (measured with 4 rows per warp and 4 loads: 34 % FP64 pipe, stalled on
-// memory latency).
+// (measured at N = 4000 with one column: 4 rows per warp and 4 loads,
+// 310 us and the FP64 pipe 34 % busy, stalled on memory latency; 2 rows and
+// 8 loads, 179 us; 16 loads, another 18 % off the Lanczos phase).
 #include "common.cuh"
 #include "context.hpp"
 
@@ -32,7 +33,7 @@ constexpr int kThreads = 128;  // 4 warps
 // independent loads of A in flight per lane: more where the FP64 work per
 // loaded element is small
 template <int R>
-constexpr int kUnroll = R <= 2 ? 8 : 4;
+constexpr int kUnroll = R == 1 ? 16 : R <= 2 ? 8 : 4;
 
 template <class E>
 struct FC;
