@@ -197,9 +197,10 @@ SPLIT_PAIRS = 28
 NCU_TRAFFIC = {
     "zgemm_split_kernel": {"case": "N=4000, 480 real columns, full-width degree step",
                            "dram_bytes": 588.6e6 + 41.9e6, "algorithmic_bytes": 548e6},
-    "zgemm_tma_kernel": {"case": "N=4000, 240 columns, FP64 filter step (same tile as the "
-                                 "Rayleigh-Ritz H Q)",
-                         "dram_bytes": 647.2e6 + 18.4e6, "algorithmic_bytes": 301e6},
+    "zgemm_tma_kernel": {"case": "N=4000, 240 columns, FP64 filter step on the 64 x 8 tile that "
+                                 "the host picks there (the N=8000 Rayleigh-Ritz H Q of 480 "
+                                 "columns takes 64 x 16)",
+                         "dram_bytes": 2989.5e6 + 18.1e6, "algorithmic_bytes": 301e6},
 }
 
 
