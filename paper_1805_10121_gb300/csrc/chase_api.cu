@@ -204,7 +204,7 @@ int cholqr_pass(Dev& d, int64_t N, const T* Y, int64_t ldy, int nconv, T* V,
     CHASE_TRY(gemm(d, N, nconv, Y, ldy, w.P, ldp, b, V, ldv, 0, b, -1.0, 1.0, 0.0));
     *flops += (is_cplx<T> ? 16.0 : 4.0) * N * nconv * b;
   }
-  CHASE_TRY(gram(d, N, V, ldv, b, V, ldv, b, w.G, ldg));
+  CHASE_TRY(gram(d, N, V, ldv, b, V, ldv, b, w.G, ldg, /*lower=*/true));  // the factor reads only it
   CHASE_TRY(cholesky_blocked(d, w.G, ldg, b, Prec<T>::chol_tol, shift, w.nrm, w.Rinv));
   int st = d.sync_check("cholesky");
   if (st != CHASE_OK) {
@@ -315,8 +315,10 @@ int rr_core(Dev& d, const T* H, int64_t N, int64_t ldh, T* Q, int64_t ldq, int b
   }
   if (!on_split) CHASE_TRY(gemm(d, N, N, H, ldh, Q, ldq, b, w.HQ, lN, 0, b, 1.0, 0.0, 0.0));
   if (t_hq) tq.end();
-  CHASE_TRY(gram(d, N, Q, ldq, b, w.HQ, lN, b, w.G, lg));                       // G = Q^H H Q
-  CHASE_TRY(launch_hermitize(d, w.G, lg, b));
+  // G = Q^H H Q is Hermitian up to rounding: form its lower triangle (the one
+  // the eigensolver reads) and take the upper one from it
+  CHASE_TRY(gram(d, N, Q, ldq, b, w.HQ, lN, b, w.G, lg, /*lower=*/true));
+  CHASE_TRY(launch_fill_upper_hermitian(d, w.G, lg, b));
   PhaseTimer tm(d.st);
   tm.begin(t_eigh);
   CHASE_TRY(eigh_device(d, w.G, lg, b, w_dev));  // (W, Lambda) = TSOLVE(G)

@@ -194,8 +194,10 @@ int fewcol_gemm(Dev& d, int64_t M, int64_t K, const float* A, int64_t lda, const
                 int64_t ldb, float* C, int64_t ldc, int j0, int j1, double alpha, double beta,
                 double shift);
 
-// C (p x q, ldc) = X^H Y with X: N x p (ldx), Y: N x q (ldy).
+// C (p x q, ldc) = X^H Y with X: N x p (ldx), Y: N x q (ldy).  lower: only
+// the entries on and below the diagonal are formed (the rest of C is left as
+// it was), for Hermitian results of which only the lower triangle is read.
 int zgram(Dev& d, int64_t N, const chase_c64* X, int64_t ldx, int p, const chase_c64* Y,
-          int64_t ldy, int q, chase_c64* C, int64_t ldc);
+          int64_t ldy, int q, chase_c64* C, int64_t ldc, bool lower = false);
 
 }  // namespace chase

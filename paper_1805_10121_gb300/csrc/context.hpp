@@ -66,9 +66,10 @@ int launch_col_inv_scale(Dev& d, T* X, int64_t ldx, int64_t N, int b, const doub
 template <class T>
 int launch_resid_norms(Dev& d, const T* HV, int64_t ldhv, const T* V, int64_t ldv, int64_t N, int b,
                        const double* lam, double* res);
-// G <- (G + G^H) / 2 for a p x p matrix
+// Upper triangle of the p x p matrix G <- conjugate of its lower triangle,
+// diagonal made real: the Hermitian matrix that G's lower triangle defines.
 template <class T>
-int launch_hermitize(Dev& d, T* G, int64_t ldg, int p);
+int launch_fill_upper_hermitian(Dev& d, T* G, int64_t ldg, int p);
 // In-place lower Cholesky G = L L^H (one CTA); sets KERR_CHOL_BREAKDOWN when a
 // pivot is not above rel_tol * G_jj.  `shift` is added to the diagonal first.
 template <class T>
@@ -111,26 +112,26 @@ template <class T>
 int launch_zero_triangle(Dev& d, T* A, int64_t lda, int p, bool lower);
 // Real Gram product C = X^T Y (X N x p, Y N x q) on the FP64 tensor pipe.
 int dgram(Dev& d, int64_t N, const double* X, int64_t ldx, int p, const double* Y, int64_t ldy,
-          int q, double* C, int64_t ldc);
+          int q, double* C, int64_t ldc, bool lower = false);
 inline int gram(Dev& d, int64_t N, const chase_c64* X, int64_t ldx, int p, const chase_c64* Y,
-                int64_t ldy, int q, chase_c64* C, int64_t ldc) {
-  return zgram(d, N, X, ldx, p, Y, ldy, q, C, ldc);
+                int64_t ldy, int q, chase_c64* C, int64_t ldc, bool lower = false) {
+  return zgram(d, N, X, ldx, p, Y, ldy, q, C, ldc, lower);
 }
 inline int gram(Dev& d, int64_t N, const double* X, int64_t ldx, int p, const double* Y,
-                int64_t ldy, int q, double* C, int64_t ldc) {
-  return dgram(d, N, X, ldx, p, Y, ldy, q, C, ldc);
+                int64_t ldy, int q, double* C, int64_t ldc, bool lower = false) {
+  return dgram(d, N, X, ldx, p, Y, ldy, q, C, ldc, lower);
 }
 int cgram(Dev& d, int64_t N, const chase_c32* X, int64_t ldx, int p, const chase_c32* Y,
-          int64_t ldy, int q, chase_c32* C, int64_t ldc);
+          int64_t ldy, int q, chase_c32* C, int64_t ldc, bool lower = false);
 int sgram(Dev& d, int64_t N, const float* X, int64_t ldx, int p, const float* Y, int64_t ldy,
-          int q, float* C, int64_t ldc);
+          int q, float* C, int64_t ldc, bool lower = false);
 inline int gram(Dev& d, int64_t N, const chase_c32* X, int64_t ldx, int p, const chase_c32* Y,
-                int64_t ldy, int q, chase_c32* C, int64_t ldc) {
-  return cgram(d, N, X, ldx, p, Y, ldy, q, C, ldc);
+                int64_t ldy, int q, chase_c32* C, int64_t ldc, bool lower = false) {
+  return cgram(d, N, X, ldx, p, Y, ldy, q, C, ldc, lower);
 }
 inline int gram(Dev& d, int64_t N, const float* X, int64_t ldx, int p, const float* Y,
-                int64_t ldy, int q, float* C, int64_t ldc) {
-  return sgram(d, N, X, ldx, p, Y, ldy, q, C, ldc);
+                int64_t ldy, int q, float* C, int64_t ldc, bool lower = false) {
+  return sgram(d, N, X, ldx, p, Y, ldy, q, C, ldc, lower);
 }
 
 // ---- zgemm_split.cu: split-BF16 filter product on the tensor cores --------

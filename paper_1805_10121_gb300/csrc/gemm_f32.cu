@@ -62,7 +62,10 @@ template <class E, bool GRAM>
 __global__ void __launch_bounds__(NT)
     f32_gemm_kernel(const E* __restrict__ A, long long lda, const E* __restrict__ B, long long ldb,
                     E* __restrict__ C, long long ldc, int M, long long K, int j0, int j1,
-                    float alpha, float beta, float shift, long long kchunk, long long pstride) {
+                    float alpha, float beta, float shift, long long kchunk, long long pstride,
+                    int lower) {
+  // Gram with lower: tiles strictly above the diagonal are not wanted
+  if (GRAM && lower && blockIdx.x < blockIdx.y) return;
   __shared__ E As[TK][TM + 1];
   __shared__ E Bs[TK][TN + 1];
   const int tid = threadIdx.x;
@@ -157,11 +160,13 @@ __global__ void __launch_bounds__(NT)
 
 template <class E>
 __global__ void f32_sum_partials_kernel(const E* __restrict__ P, int p, int q, int nsplit,
-                                        long long pstride, E* __restrict__ C, long long ldc) {
+                                        long long pstride, E* __restrict__ C, long long ldc,
+                                        int lower) {
   const long long n = (long long)p * q;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
     const long long r = e % p, c = e / p;
+    if (lower && r < c) continue;
     E s = P[e];
     for (int z = 1; z < nsplit; ++z) {
       const E v = P[z * pstride + e];
@@ -198,7 +203,7 @@ int gemm_impl(Dev& d, int64_t M, int64_t K, const T* A, int64_t lda, const T* B,
   f32_gemm_kernel<E, false><<<grid, NT, 0, d.st>>>(
       reinterpret_cast<const E*>(A), lda, reinterpret_cast<const E*>(B), ldb,
       reinterpret_cast<E*>(Cm), ldc, static_cast<int>(M), K, j0, j1, static_cast<float>(alpha),
-      static_cast<float>(beta), static_cast<float>(shift), 0, 0);
+      static_cast<float>(beta), static_cast<float>(shift), 0, 0, 0);
   note_launch();
   CHASE_CUDA(cudaGetLastError());
   return CHASE_OK;
@@ -206,7 +211,7 @@ int gemm_impl(Dev& d, int64_t M, int64_t K, const T* A, int64_t lda, const T* B,
 
 template <class T>
 int gram_impl(Dev& d, int64_t N, const T* X, int64_t ldx, int p, const T* Y, int64_t ldy, int q,
-              T* Cm, int64_t ldc) {
+              T* Cm, int64_t ldc, bool lower) {
   if (p == 0 || q == 0) return CHASE_OK;
   using E = elem<T>;
   const int tp = (p + TM - 1) / TM, tq = (q + TN - 1) / TN;
@@ -221,12 +226,13 @@ int gram_impl(Dev& d, int64_t N, const T* X, int64_t ldx, int p, const T* Y, int
   dim3 grid(static_cast<unsigned>(tp), static_cast<unsigned>(tq), static_cast<unsigned>(ns));
   f32_gemm_kernel<E, true><<<grid, NT, 0, d.st>>>(
       reinterpret_cast<const E*>(X), ldx, reinterpret_cast<const E*>(Y), ldy, P, p, p, N, 0, q,
-      1.f, 0.f, 0.f, kc, pstride);
+      1.f, 0.f, 0.f, kc, pstride, lower ? 1 : 0);
   note_launch();
   CHASE_CUDA(cudaGetLastError());
   const unsigned blocks = static_cast<unsigned>(std::min<long long>((pstride + 255) / 256, 4096));
   f32_sum_partials_kernel<E><<<blocks, 256, 0, d.st>>>(P, p, q, static_cast<int>(ns), pstride,
-                                                       reinterpret_cast<E*>(Cm), ldc);
+                                                       reinterpret_cast<E*>(Cm), ldc,
+                                                       lower ? 1 : 0);
   note_launch();
   CHASE_CUDA(cudaGetLastError());
   return CHASE_OK;
@@ -247,13 +253,13 @@ int sgemm(Dev& d, int64_t M, int64_t K, const float* A, int64_t lda, const float
 }
 
 int cgram(Dev& d, int64_t N, const chase_c32* X, int64_t ldx, int p, const chase_c32* Y,
-          int64_t ldy, int q, chase_c32* C, int64_t ldc) {
-  return gram_impl(d, N, X, ldx, p, Y, ldy, q, C, ldc);
+          int64_t ldy, int q, chase_c32* C, int64_t ldc, bool lower) {
+  return gram_impl(d, N, X, ldx, p, Y, ldy, q, C, ldc, lower);
 }
 
 int sgram(Dev& d, int64_t N, const float* X, int64_t ldx, int p, const float* Y, int64_t ldy,
-          int q, float* C, int64_t ldc) {
-  return gram_impl(d, N, X, ldx, p, Y, ldy, q, C, ldc);
+          int q, float* C, int64_t ldc, bool lower) {
+  return gram_impl(d, N, X, ldx, p, Y, ldy, q, C, ldc, lower);
 }
 
 }  // namespace chase

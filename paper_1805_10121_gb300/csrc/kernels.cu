@@ -76,12 +76,6 @@ struct Sc<double2> {
     return make_double2(a.x + b.x, a.y + b.y);
   }
   // (a, b) <- ((a + conj(b)) / 2, conj of that): entries (r, c) and (c, r)
-  static __device__ __forceinline__ void hermitize_pair(double2& a, double2& b) {
-    const double2 x = a, y = b;
-    const double re = 0.5 * (x.x + y.x), im = 0.5 * (x.y - y.y);
-    a = make_double2(re, im);
-    b = make_double2(re, -im);
-  }
   static __device__ __forceinline__ void hermitize_diag(double2& a) { a.y = 0.0; }
 };
 template <>
@@ -101,11 +95,6 @@ struct Sc<double> {
   }
   static __device__ __forceinline__ void add_re(double& a, double v) { a += v; }
   static __device__ __forceinline__ double add(double a, double b) { return a + b; }
-  static __device__ __forceinline__ void hermitize_pair(double& a, double& b) {
-    const double m = 0.5 * (a + b);
-    a = m;
-    b = m;
-  }
   static __device__ __forceinline__ void hermitize_diag(double&) {}
 };
 
@@ -138,12 +127,6 @@ struct Sc<float2> {
   static __device__ __forceinline__ float2 add(float2 a, float2 b) {
     return make_float2(a.x + b.x, a.y + b.y);
   }
-  static __device__ __forceinline__ void hermitize_pair(float2& a, float2& b) {
-    const float2 x = a, y = b;
-    const float re = 0.5f * (x.x + y.x), im = 0.5f * (x.y - y.y);
-    a = make_float2(re, im);
-    b = make_float2(re, -im);
-  }
   static __device__ __forceinline__ void hermitize_diag(float2& a) { a.y = 0.f; }
 };
 template <>
@@ -163,11 +146,6 @@ struct Sc<float> {
   }
   static __device__ __forceinline__ void add_re(float& a, double v) { a = (float)(a + v); }
   static __device__ __forceinline__ float add(float a, float b) { return a + b; }
-  static __device__ __forceinline__ void hermitize_pair(float& a, float& b) {
-    const float m = 0.5f * (a + b);
-    a = m;
-    b = m;
-  }
   static __device__ __forceinline__ void hermitize_diag(float&) {}
 };
 
@@ -210,7 +188,9 @@ constexpr int GK = 16;  // K per shared-memory tile
 __global__ void __launch_bounds__(128)
     gram_kernel(const double2* __restrict__ X, long long ldx, int p, const double2* __restrict__ Y,
                 long long ldy, int q, long long N, long long kchunk, double2* __restrict__ P,
-                long long ldp, long long pstride) {
+                long long ldp, long long pstride, int lower) {
+  // lower: only entries r >= c are wanted; tiles strictly above the diagonal exit
+  if (lower && blockIdx.x < blockIdx.y) return;
   __shared__ double2 sX[GT][GK];
   __shared__ double2 sY[GT][GK];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -281,7 +261,8 @@ __global__ void __launch_bounds__(128)
 __global__ void __launch_bounds__(128)
     gram_real_kernel(const double* __restrict__ X, long long ldx, int p, const double* __restrict__ Y,
                      long long ldy, int q, long long N, long long kchunk, double* __restrict__ P,
-                     long long ldp, long long pstride) {
+                     long long ldp, long long pstride, int lower) {
+  if (lower && blockIdx.x < blockIdx.y) return;
   __shared__ double sX[GT][GK + 1];
   __shared__ double sY[GT][GK + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -333,13 +314,15 @@ __global__ void __launch_bounds__(128)
 
 template <class T>
 __global__ void sum_partials_kernel(const T* __restrict__ P, int p, int q, int nsplit,
-                                    long long pstride, T* __restrict__ C, long long ldc) {
+                                    long long pstride, T* __restrict__ C, long long ldc,
+                                    int lower) {
   const long long n = (long long)p * q;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e % p, c = e / p;
+    if (lower && r < c) continue;
     T acc = Sc<T>::zero();
     for (int z = 0; z < nsplit; ++z) acc = Sc<T>::add(acc, P[z * pstride + e]);
-    const long long r = e % p, c = e / p;
     C[c * ldc + r] = acc;
   }
 }
@@ -480,18 +463,17 @@ __global__ void __launch_bounds__(kRed)
 }
 
 template <class T>
-__global__ void hermitize_kernel(T* __restrict__ G, long long ldg, int p) {
+__global__ void fill_upper_hermitian_kernel(T* __restrict__ G, long long ldg, int p) {
   const long long n = (long long)p * p;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(e % p), c = (int)(e / p);
-    if (r > c) continue;
+    if (r > c) continue;  // the lower triangle is only read
     T* a = G + (long long)c * ldg + r;  // (r, c), upper
-    T* b = G + (long long)r * ldg + c;  // (c, r), lower
     if (r == c)
       Sc<T>::hermitize_diag(*a);
     else
-      Sc<T>::hermitize_pair(*a, *b);
+      *a = Sc<T>::conj(G[(long long)r * ldg + c]);  // conj of (c, r)
   }
 }
 
@@ -682,9 +664,14 @@ unsigned grid_for(long long n, int threads, unsigned cap = 65535u) {
 // ---------------------------------------------------------------------------
 namespace {
 // Gram launch shape: split K so that the grid covers the 152 SMs about four times.
-void gram_shape(int64_t N, int p, int q, dim3* grid, long long* kchunk, long long* nsplit) {
+void gram_shape(int64_t N, int p, int q, bool lower, dim3* grid, long long* kchunk,
+                long long* nsplit) {
   const int tp = (p + GT - 1) / GT, tq = (q + GT - 1) / GT;
-  long long ns = std::max<long long>(1, (4 * 152) / std::max(1, tp * tq));
+  // tiles that do work: all, or those on and below the diagonal
+  const long long tiles = lower ? static_cast<long long>(std::min(tp, tq)) * (std::min(tp, tq) + 1) / 2 +
+                                      static_cast<long long>(std::max(0, tp - tq)) * tq
+                                : static_cast<long long>(tp) * tq;
+  long long ns = std::max<long long>(1, (4 * 152) / std::max<long long>(1, tiles));
   ns = std::min<long long>(ns, std::max<long long>(1, N / 256));
   long long kc = (N + ns - 1) / ns;
   kc = ((kc + GK - 1) / GK) * GK;
@@ -697,12 +684,12 @@ void gram_shape(int64_t N, int p, int q, dim3* grid, long long* kchunk, long lon
 
 template <class T>
 int gram_impl(Dev& d, int64_t N, const T* X, int64_t ldx, int p, const T* Y, int64_t ldy, int q,
-              T* C, int64_t ldc) {
+              T* C, int64_t ldc, bool lower) {
   if (p == 0 || q == 0) return CHASE_OK;
   using D = elem_t<T>;
   dim3 grid;
   long long kchunk = 0, nsplit = 1;
-  gram_shape(N, p, q, &grid, &kchunk, &nsplit);
+  gram_shape(N, p, q, lower, &grid, &kchunk, &nsplit);
   D* out = dp(C);
   long long ldo = ldc, pstride = 0;
   D* P = nullptr;
@@ -713,15 +700,16 @@ int gram_impl(Dev& d, int64_t N, const T* X, int64_t ldx, int p, const T* Y, int
     ldo = p;
   }
   if constexpr (sizeof(D) == 16)
-    gram_kernel<<<grid, 128, 0, d.st>>>(dp(X), ldx, p, dp(Y), ldy, q, N, kchunk, out, ldo, pstride);
+    gram_kernel<<<grid, 128, 0, d.st>>>(dp(X), ldx, p, dp(Y), ldy, q, N, kchunk, out, ldo, pstride,
+                                        lower ? 1 : 0);
   else
     gram_real_kernel<<<grid, 128, 0, d.st>>>(dp(X), ldx, p, dp(Y), ldy, q, N, kchunk, out, ldo,
-                                             pstride);
+                                             pstride, lower ? 1 : 0);
   note_launch();
   CHASE_CUDA(cudaGetLastError());
   if (nsplit > 1) {
     sum_partials_kernel<D><<<grid_for(pstride, 256, 4096), 256, 0, d.st>>>(
-        P, p, q, static_cast<int>(nsplit), pstride, dp(C), ldc);
+        P, p, q, static_cast<int>(nsplit), pstride, dp(C), ldc, lower ? 1 : 0);
     note_launch();
     CHASE_CUDA(cudaGetLastError());
   }
@@ -730,13 +718,13 @@ int gram_impl(Dev& d, int64_t N, const T* X, int64_t ldx, int p, const T* Y, int
 }  // namespace
 
 int zgram(Dev& d, int64_t N, const chase_c64* X, int64_t ldx, int p, const chase_c64* Y,
-          int64_t ldy, int q, chase_c64* C, int64_t ldc) {
-  return gram_impl(d, N, X, ldx, p, Y, ldy, q, C, ldc);
+          int64_t ldy, int q, chase_c64* C, int64_t ldc, bool lower) {
+  return gram_impl(d, N, X, ldx, p, Y, ldy, q, C, ldc, lower);
 }
 
 int dgram(Dev& d, int64_t N, const double* X, int64_t ldx, int p, const double* Y, int64_t ldy,
-          int q, double* C, int64_t ldc) {
-  return gram_impl(d, N, X, ldx, p, Y, ldy, q, C, ldc);
+          int q, double* C, int64_t ldc, bool lower) {
+  return gram_impl(d, N, X, ldx, p, Y, ldy, q, C, ldc, lower);
 }
 
 int launch_filter_plan(Dev& d, const int* deg, int b, int max_allowed, int* perm, int* start,
@@ -806,9 +794,10 @@ int launch_resid_norms(Dev& d, const T* HV, int64_t ldhv, const T* V, int64_t ld
 }
 
 template <class T>
-int launch_hermitize(Dev& d, T* G, int64_t ldg, int p) {
+int launch_fill_upper_hermitian(Dev& d, T* G, int64_t ldg, int p) {
   if (p == 0) return CHASE_OK;
-  hermitize_kernel<<<grid_for((long long)p * p, 256, 4096), 256, 0, d.st>>>(dp(G), ldg, p);
+  fill_upper_hermitian_kernel<<<grid_for((long long)p * p, 256, 4096), 256, 0, d.st>>>(dp(G), ldg,
+                                                                                       p);
   note_launch();
   CHASE_CUDA(cudaGetLastError());
   return CHASE_OK;
@@ -1013,7 +1002,7 @@ int launch_normalize_cols(Dev& d, T* X, int64_t ldx, int64_t N, int r) {
   template int launch_col_inv_scale<T>(Dev&, T*, int64_t, int64_t, int, const double*);            \
   template int launch_resid_norms<T>(Dev&, const T*, int64_t, const T*, int64_t, int64_t, int,     \
                                      const double*, double*);                                      \
-  template int launch_hermitize<T>(Dev&, T*, int64_t, int);                                        \
+  template int launch_fill_upper_hermitian<T>(Dev&, T*, int64_t, int);                             \
   template int launch_zero_triangle<T>(Dev&, T*, int64_t, int, bool);                              \
   template int launch_hermitian_from_lower<T>(Dev&, const T*, int64_t, T*, int64_t, int64_t);      \
   template int launch_cholesky<T>(Dev&, T*, int64_t, int, double, double);                         \
