@@ -7,6 +7,7 @@
 // 10-11) and the degree rule (Alg. 5) run; the resulting column permutation
 // goes back to the device as one gather.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -846,12 +847,14 @@ class WorkerPool {
     for (auto s : streams_) cudaStreamDestroy(s);
   }
 
-  // fn(worker context, item) for every item, round robin over the workers.
+  // fn(worker context, item) for every item; each worker takes the next
+  // item in list order as soon as it is free (list the costly items first).
   int run(const std::vector<int>& items, std::function<int(Dev&, int)> fn) {
     std::unique_lock<std::mutex> lk(mu_);
     items_ = &items;
     job_ = std::move(fn);
     finished_ = 0;
+    next_.store(0);
     ++generation_;
     cv_.notify_all();
     done_.wait(lk, [&] { return finished_ == nw_; });
@@ -866,7 +869,6 @@ class WorkerPool {
  private:
   void loop(int w) {
     int seen = 0;
-    const size_t nw = static_cast<size_t>(nw_);
     for (;;) {
       std::unique_lock<std::mutex> lk(mu_);
       cv_.wait(lk, [&] { return stop_ || generation_ != seen; });
@@ -876,7 +878,7 @@ class WorkerPool {
       lk.unlock();
       int r = CHASE_OK;
       std::string m;
-      for (size_t i = static_cast<size_t>(w); i < items->size(); i += nw) {
+      for (size_t i = next_.fetch_add(1); i < items->size(); i = next_.fetch_add(1)) {
         r = job_(*devs_[w], (*items)[i]);
         if (r != CHASE_OK) {
           m = chase_last_error();
@@ -900,6 +902,7 @@ class WorkerPool {
   std::function<int(Dev&, int)> job_;
   const std::vector<int>* items_ = nullptr;
   int nw_ = 0, generation_ = 0, finished_ = 0;
+  std::atomic<size_t> next_{0};
   bool stop_ = false;
   std::vector<int> rc_;
   std::vector<std::string> msg_;
@@ -1348,8 +1351,12 @@ extern "C" int chase_solve_batched(int P, const chase_c64* const* H, const int64
   }
   WorkerPool pool(d.st);
   CHASE_TRY(pool.init(std::min(P, kBatchWorkers)));
-  std::vector<int> all(P);
+  std::vector<int> all(P);  // largest problems first (see WorkerPool::run)
   std::iota(all.begin(), all.end(), 0);
+  std::stable_sort(all.begin(), all.end(),
+                   [&](int a, int b) {
+                     return sv[a].N * (sv[a].nev + sv[a].nex) > sv[b].N * (sv[b].nev + sv[b].nex);
+                   });
   // Alg. 1 lines 1-2 of every problem
   CHASE_TRY(pool.run(all, [&](Dev& w, int p) { return sv[p].setup(w, true); }));
   std::vector<GroupedFilterInput> slices(P);  // split: slices of every H, made once
@@ -1414,7 +1421,11 @@ extern "C" int chase_solve_batched(int P, const chase_c64* const* H, const int64
       // the grouped filter's time, shared out by each problem's FLOPs
       if (tt.flops > 0) s.S.t_filter += tt.t_steps * 8.0 * s.N2 * fm / tt.flops;
     }
-    CHASE_TRY(pool.run(act, [&](Dev& w, int p) { return sv[p].after_filter(w); }));  // lines 5-15
+    // lines 5-15 per problem, largest first so that the workers finish together
+    std::stable_sort(act.begin(), act.end(), [&](int a, int b) {  // cost ~ N^2 (active columns)
+      return sv[a].N * sv[a].N * sv[a].b() > sv[b].N * sv[b].N * sv[b].b();
+    });
+    CHASE_TRY(pool.run(act, [&](Dev& w, int p) { return sv[p].after_filter(w); }));
   }
   int worst = CHASE_OK;
   const double t_total =
