@@ -699,6 +699,11 @@ def run_batched_solve_workload(args, rank, world, local):
                           "grouped_steps": bst["steps"],
                           "qr_seconds_sum": round(sum(s["t_qr"] for s in stats), 3),
                           "rr_seconds_sum": round(sum(s["t_rr"] for s in stats), 3),
+                          "rr_hq_seconds_sum": round(sum(s["t_rr_product"] for s in stats), 3),
+                          "eigh_seconds_sum": round(sum(s["t_eigh"] for s in stats), 3),
+                          "lanczos_seconds_sum": round(sum(s["t_lanczos"] for s in stats), 3),
+                          "per_problem_phases_note": "sums over problems of per-problem phase "
+                                                     "times; eight worker threads overlap them",
                           "first32_one_by_one_seconds": round(t_seq, 3),
                           "first32_batched_seconds": round(t_b32, 3),
                           "first32_speedup": round(t_seq / t_b32, 2)},
