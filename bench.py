@@ -56,7 +56,7 @@ def parse():
                         "split product; fp64: FP64 throughout")
     p.add_argument("--workload", default="sequence",
                    choices=["sequence", "filter", "serve", "batched", "batched-solve",
-                            "degree-sweep", "side"],
+                            "degree-sweep", "side", "variants"],
                    help="sequence: timed solves of the correlated sequence (default); "
                         "filter: timed degree-m filter calls on one problem, split vs FP64")
     p.add_argument("--filter-degree", type=int, default=20)
@@ -889,6 +889,100 @@ def run_side_workload(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def run_variants_workload(args, rank, world, local):
+    """The real symmetric and single-precision solvers on the sequence law:
+    a correlated sequence H_{k+1} = H_k + 1e-3 ||H_1|| E_k with the
+    spectrum of the sequence workload, built as a real symmetric matrix
+    (Q orthogonal, E symmetric) for float64 and float32 and as a Hermitian
+    one for complex64; warm-started solves as in the default workload.
+    Single precision uses tol = max(--tol, 1e-5) (Table 1's single-precision
+    column).  Each variant's line gives seconds per solve, iterations, the
+    largest residual and its algorithmic TFLOP/s."""
+    from paper_1805_10121_gb300 import build, chase, synth
+    build.build()
+    chase.lib()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n, nev, nex = args.n, args.nev, args.nex
+    nx = nev + nex
+    W, K = args.warmup, args.steps
+    seed = args.seed + 1000 * rank
+    prec = prec_code(args.precision)
+    stream = torch.cuda.current_stream(dev)
+
+    def sequence(real, dtype):
+        lam = synth.spectrum_dft(n, seed, device=dev)
+        hnorm = float(lam.abs().max())
+        if real:
+            H = synth.symmetric_from(synth.orthogonal_qr(n, seed + 1, device=dev), lam)
+        else:
+            H = synth.hermitian_from(synth.unitary_dft(n, seed + 1, device=dev), lam)
+        seq = []
+        for k in range(W + K):
+            if k > 0:
+                E = (synth.symmetric_noise if real else synth.hermitian_noise)(
+                    n, seed + 100 + k, device=dev)
+                H = (H + (1e-3 * hnorm) * E).t().contiguous().t()
+                del E
+            seq.append(H.to(dtype).t().contiguous().t())
+        del H
+        return seq, hnorm
+
+    rows = []
+    launches0 = chase.chase_kernel_launches()
+    clocks = ClockSampler(local)
+    clocks.start()
+    for name, real, dtype, entry, precision, tol in (
+            ("float64 real symmetric", True, torch.float64, chase.chase_solve_real, prec, args.tol),
+            ("complex64", False, torch.complex64, chase.chase_solve_c32, None, max(args.tol, 1e-5)),
+            ("float32 real symmetric", True, torch.float32, chase.chase_solve_f32, None,
+             max(args.tol, 1e-5))):
+        seq, hnorm = sequence(real, dtype)
+        blk = synth.gaussian_block_real if real else synth.gaussian_block
+        V = blk(n, nx, seed + 7, device=dev).to(dtype)
+        S = blk(n, 5, seed + 8, device=dev).to(dtype).t().contiguous().t()
+        Lam = None
+        times, its, res_max, flops = [], [], 0.0, 0.0
+        for k in range(W + K):
+            kw = {} if precision is None else {"precision": precision}
+            o = chase.chase_opts_default(approx=0 if k == 0 else 1, **kw)
+            Sk = S if k == 0 else S[:, :1].contiguous()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st, Lam, res, s = entry(seq[k], nev, nex, tol, V, Sk, Lambda=Lam, opts=o)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if k >= W:
+                times.append(a.elapsed_time(b) / 1e3)
+                its.append(s["iterations"])
+                res_max = max(res_max, float(np.max(res[:nev])) / hnorm)
+                flops += s["flops_total"]
+                if st != 0:
+                    raise RuntimeError(f"{name}: solve {k} returned status {st}")
+        rows.append({"variant": name, "tol": tol,
+                     "precision": args.precision if precision is not None else "fp32",
+                     "s_per_solve": round(float(np.mean(times)), 3), "iterations": its,
+                     "resid_max_over_norm": res_max,
+                     "tflops": round(flops / sum(times) / 1e12, 3)})
+        del seq, V, S
+        torch.cuda.empty_cache()
+    clk = clocks.stop()
+    cfg = workload_config(args, world)
+    cfg["workload"] = (f"real symmetric and single-precision solves of the sequence law, N={n}, "
+                       f"nev={nev}, nex={nex}, warm start; step = one solve of each variant")
+    line = {
+        "metric": METRIC, "value": rows[0]["tflops"], "unit": "TFLOP/s", "n_gpus": world,
+        "steps": K, "warmup": W, "ms_per_step": round(1e3 * sum(r["s_per_solve"] for r in rows), 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64/c32/f32", "data": "synthetic", "config": cfg, "variants": rows,
+        "gpu_launches": int(chase.chase_kernel_launches() - launches0), "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_serve_workload(args, rank, world, local):
     """Replay a seeded Poisson trace of sequence-solve requests through the
     continuous-batching server; report throughput and p50/p99 latency."""
@@ -968,6 +1062,9 @@ def main():
         return
     if args.workload == "batched-solve":
         run_batched_solve_workload(args, rank, world, local)
+        return
+    if args.workload == "variants":
+        run_variants_workload(args, rank, world, local)
         return
     if args.workload == "side":
         run_side_workload(args, rank, world, local)

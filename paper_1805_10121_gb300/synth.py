@@ -173,6 +173,16 @@ def symmetric_from(q: torch.Tensor, lam: torch.Tensor) -> torch.Tensor:
     return h.t().contiguous().t()
 
 
+def symmetric_noise(n: int, seed: int, device="cpu") -> torch.Tensor:
+    """``E = (G + G^T) / (2 sqrt(2n))`` with G i.i.d. real Gaussian: the real
+    counterpart of ``hermitian_noise`` (off-diagonal variance 1/(4n), so
+    ``||E||_2`` is close to 1)."""
+    g = generator(seed, device)
+    z = torch.randn(n, n, dtype=torch.float64, device=device, generator=g)
+    e = (z + z.t()) * (1.0 / (2.0 * math.sqrt(2.0 * n)))
+    return e.t().contiguous().t()
+
+
 def gaussian_block_real(n: int, b: int, seed: int, device="cpu") -> torch.Tensor:
     """n x b real Gaussian block, column-major."""
     g = generator(seed, device)
