@@ -931,12 +931,10 @@ int split_product_ns(Dev& d, const SplitH& h, SplitX& x, const E* X, int64_t ldx
                               NS));
   CHASE_TRY(make_tmap_bf16_3d(&tmB, x.B, K, brows, split::S, Kp * 2, Kp * 2 * rows_cap, split::BX,
                               split::BN, NS));
-  static bool attr_done = false;  // per instantiation
-  if (!attr_done) {
-    CHASE_CUDA(cudaFuncSetAttribute(split::zgemm_split_kernel<NS>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, SC::SMEM));
-    attr_done = true;
-  }
+  // once per instantiation; function-local static initialisation is thread safe
+  static const cudaError_t attr_rc = cudaFuncSetAttribute(
+      split::zgemm_split_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, SC::SMEM);
+  CHASE_CUDA(attr_rc);
   const int64_t ctiles = (brows + split::BN - 1) / split::BN;
   const int64_t rtiles = (N + split::BM - 1) / split::BM;
   dim3 grid(static_cast<unsigned>(ctiles), static_cast<unsigned>(rtiles));
@@ -1032,12 +1030,10 @@ int split_grouped_slice_x(Dev& d, const GroupedProblem* probs, const GroupedStep
 }
 
 int zgemm_split_grouped_prepare() {
-  static bool attr_done = false;
-  if (!attr_done) {
-    CHASE_CUDA(cudaFuncSetAttribute(split::zgemm_split_grouped_kernel,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, split::SMEM));
-    attr_done = true;
-  }
+  // once per instantiation; function-local static initialisation is thread safe
+  static const cudaError_t attr_rc = cudaFuncSetAttribute(
+      split::zgemm_split_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, split::SMEM);
+  CHASE_CUDA(attr_rc);
   return CHASE_OK;
 }
 

@@ -436,12 +436,10 @@ int launch_cfg(Dev& d, int64_t M, int64_t K, const chase_c64* A, int64_t lda, co
   CUtensorMap tmA, tmB;
   CHASE_TRY(make_tmap_c64(&tmA, A, M, K, lda, C::BM, C::BK));
   CHASE_TRY(make_tmap_c64(&tmB, B, K, ncols_b, ldb, C::BK, C::BN));
-  static bool attr_done = false;  // per instantiation
-  if (!attr_done) {
-    CHASE_CUDA(cudaFuncSetAttribute(zgemm_tma_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    C::SMEM));
-    attr_done = true;
-  }
+  // once per instantiation; function-local static initialisation is thread safe
+  static const cudaError_t attr_rc = cudaFuncSetAttribute(
+      zgemm_tma_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+  CHASE_CUDA(attr_rc);
   dim3 grid(static_cast<unsigned>((M + C::BM - 1) / C::BM),
             static_cast<unsigned>((j1 - j0 + C::BN - 1) / C::BN));
   zgemm_tma_kernel<C><<<grid, C::kThreads, C::SMEM, d.st>>>(
@@ -460,12 +458,10 @@ int launch_cfg_real(Dev& d, int64_t M, int64_t K, const double* A, int64_t lda, 
   CUtensorMap tmA, tmB;
   CHASE_TRY(make_tmap_f64(&tmA, A, M, K, lda, C::BM, C::BK));
   CHASE_TRY(make_tmap_f64(&tmB, B, K, ncols_b, ldb, C::BK, C::BN));
-  static bool attr_done = false;  // per instantiation
-  if (!attr_done) {
-    CHASE_CUDA(cudaFuncSetAttribute(dgemm_tma_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    C::SMEM));
-    attr_done = true;
-  }
+  // once per instantiation; function-local static initialisation is thread safe
+  static const cudaError_t attr_rc = cudaFuncSetAttribute(
+      dgemm_tma_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+  CHASE_CUDA(attr_rc);
   dim3 grid(static_cast<unsigned>((M + C::BM - 1) / C::BM),
             static_cast<unsigned>((j1 - j0 + C::BN - 1) / C::BN));
   dgemm_tma_kernel<C><<<grid, C::kThreads, C::SMEM, d.st>>>(
@@ -486,12 +482,10 @@ using RCfgNarrow = Cfg<64, 8, 16, 3, 4, 8>;
 
 template <class C>
 int grouped_attr() {
-  static bool attr_done = false;  // per instantiation
-  if (!attr_done) {
-    CHASE_CUDA(cudaFuncSetAttribute(zgemm_grouped_kernel<C>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-    attr_done = true;
-  }
+  // once per instantiation; function-local static initialisation is thread safe
+  static const cudaError_t attr_rc = cudaFuncSetAttribute(
+      zgemm_grouped_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+  CHASE_CUDA(attr_rc);
   return CHASE_OK;
 }
 
