@@ -501,15 +501,14 @@ int launch_grouped(Dev& d, const GroupedProblem* probs, const GroupedStep* steps
 }
 
 int sm_count() {
-  static int v = 0;
-  if (v == 0) {
+  static const int v = [] {  // thread-safe one-time initialisation
     int dev = 0, n = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
       n = 152;
     cudaGetLastError();
-    v = n;
-  }
+    return n;
+  }();
   return v;
 }
 
