@@ -932,17 +932,22 @@ def run_variants_workload(args, rank, world, local):
     launches0 = chase.chase_kernel_launches()
     clocks = ClockSampler(local)
     clocks.start()
+    stol = max(args.tol, 1e-5)
+    split = chase.CHASE_SPLIT_BF16
     for name, real, dtype, entry, precision, tol in (
             ("float64 real symmetric", True, torch.float64, chase.chase_solve_real, prec, args.tol),
-            ("complex64", False, torch.complex64, chase.chase_solve_c32, None, max(args.tol, 1e-5)),
-            ("float32 real symmetric", True, torch.float32, chase.chase_solve_f32, None,
-             max(args.tol, 1e-5))):
+            ("complex64", False, torch.complex64, chase.chase_solve_c32, None, stol),
+            ("complex64, filter on the 4-slice split product", False, torch.complex64,
+             chase.chase_solve_c32, split, stol),
+            ("float32 real symmetric", True, torch.float32, chase.chase_solve_f32, None, stol),
+            ("float32 real symmetric, filter on the 4-slice split product", True, torch.float32,
+             chase.chase_solve_f32, split, stol)):
         seq, hnorm = sequence(real, dtype)
         blk = synth.gaussian_block_real if real else synth.gaussian_block
         V = blk(n, nx, seed + 7, device=dev).to(dtype)
         S = blk(n, 5, seed + 8, device=dev).to(dtype).t().contiguous().t()
         Lam = None
-        times, its, res_max, flops = [], [], 0.0, 0.0
+        times, its, res_max, flops, t_filt = [], [], 0.0, 0.0, 0.0
         for k in range(W + K):
             kw = {} if precision is None else {"precision": precision}
             o = chase.chase_opts_default(approx=0 if k == 0 else 1, **kw)
@@ -959,11 +964,14 @@ def run_variants_workload(args, rank, world, local):
                 its.append(s["iterations"])
                 res_max = max(res_max, float(np.max(res[:nev])) / hnorm)
                 flops += s["flops_total"]
+                t_filt += s["t_filter"]
                 if st != 0:
                     raise RuntimeError(f"{name}: solve {k} returned status {st}")
-        rows.append({"variant": name, "tol": tol,
-                     "precision": args.precision if precision is not None else "fp32",
+        label = "fp32" if precision is None else (
+            "split4" if dtype in (torch.complex64, torch.float32) else args.precision)
+        rows.append({"variant": name, "tol": tol, "precision": label,
                      "s_per_solve": round(float(np.mean(times)), 3), "iterations": its,
+                     "filter_s_per_solve": round(t_filt / len(times), 3),
                      "resid_max_over_norm": res_max,
                      "tflops": round(flops / sum(times) / 1e12, 3)})
         del seq, V, S

@@ -318,7 +318,11 @@ int chase_solve_real(const double* H, int64_t N, int64_t ldh, int nev, int nex, 
  * hold) and rounds back.  Eigenvalues, residuals, bounds and tolerances are
  * doubles.  Single precision reaches residuals of about 1e-6 ||H||, so tol
  * should be 1e-5 or larger (Table 1's single-precision column).
- * opts->precision is ignored. */
+ * opts->precision: CHASE_FP64 (the default) keeps the FP32 products; any
+ * split value runs the solve's filter on the split-BF16 tensor-core product
+ * with the leading 4 slices of each operand (about 2^-28 relative per
+ * product entry, finer than FP32 rounding) on widened copies of the active
+ * block, rounded back to single precision after the filter. */
 int chase_filter_c32(const chase_c32* H, int64_t N, int64_t ldh, chase_c32* V, int64_t ldv, int b,
                      const int* degrees, double b_sup, double mu1, double mu_nevnex,
                      chase_c32* work, void* stream);

@@ -536,6 +536,11 @@ struct Solver {
   RRWork<T> rw;
   SplitH sh;
   SplitX sx;
+  // single precision with CHASE_SPLIT_BF16: the filter runs on widened FP64
+  // copies of the active block (Dv, Dw), the product with 4 slices
+  using Wide = typename std::conditional<is_cplx<T>, chase_c64, double>::type;
+  Wide *Dv = nullptr, *Dw = nullptr;
+  int64_t lD = 0;
   bool split = false;
   bool split_rr = false;            // H Q of Rayleigh-Ritz on the split product too
   const SplitH* rr_slices = nullptr;  // the slices of H used there
@@ -579,16 +584,22 @@ struct Solver {
     CHASE_TRY(d.alloc(&Wk, static_cast<size_t>(lw) * nx));  // filter double buffer / permutation scratch
     CHASE_TRY(orth_alloc(d, N, nx, nx, ow));
     CHASE_TRY(rr_alloc(d, N, nx, rw));
-    // single-precision solves compute every product natively in FP32
-    split = !is_single<T> && (o.precision == CHASE_SPLIT_BF16 || o.precision == CHASE_SPLIT_BF16_RR ||
-                              o.precision == CHASE_SPLIT_BF16_ADAPT);
+    // single precision: every product in FP32 on the CUDA cores, or with
+    // CHASE_SPLIT_BF16 the filter's products on the split tensor-core
+    // product (4 slices, about 2^-28 relative: finer than FP32 rounding)
+    split = is_single<T> ? o.precision != CHASE_FP64
+                         : (o.precision == CHASE_SPLIT_BF16 || o.precision == CHASE_SPLIT_BF16_RR ||
+                            o.precision == CHASE_SPLIT_BF16_ADAPT);
     split_rr = !is_single<T> && o.precision == CHASE_SPLIT_BF16_RR;
-    if constexpr (!is_single<T>) {
-      if (split && !grouped_split) {  // slices of H once per solve, slice workspace for the block
-        CHASE_TRY(split_prepare_h(d, dH, N, lh, sh));
-        CHASE_TRY(split_alloc_x(d, N, nx, sx, is_cplx<T>));
-        rr_slices = &sh;
-        rr_sx = &sx;
+    if (split && !grouped_split) {  // slices of H once per solve, slice workspace for the block
+      CHASE_TRY(split_prepare_h(d, dH, N, lh, sh));
+      CHASE_TRY(split_alloc_x(d, N, nx, sx, is_cplx<T>));
+      rr_slices = &sh;
+      rr_sx = &sx;
+      if constexpr (is_single<T>) {
+        lD = ld_pad<Wide>(N);
+        CHASE_TRY(d.alloc(&Dv, static_cast<size_t>(lD) * nx));
+        CHASE_TRY(d.alloc(&Dw, static_cast<size_t>(lD) * nx));
       }
     }
     CHASE_TRY(d.alloc(&dw, nx));
@@ -648,6 +659,7 @@ struct Solver {
   // every active residual is above 1e-3 h the product keeps 3 slices (about
   // 2^-21 relative), above 1e-6 h 4 slices (2^-28), else all 7.
   int slices_for_iteration() const {
+    if constexpr (is_single<T>) return 4;
     if (o.precision != CHASE_SPLIT_BF16_ADAPT) return 7;
     double rmin = HUGE_VAL;
     for (int a = nconv; a < nx; ++a) rmin = std::min(rmin, res[a]);
@@ -663,8 +675,20 @@ struct Solver {
     const int ns = slices_for_iteration();
     S.filter_slices_low += ns < 7 ? 1 : 0;
     tm.begin(&S.t_filter);
-    CHASE_TRY(filter_sorted(d, dH, N, lh, Va(), lv, Wk, lw, b(), start.data(), maxdeg, b_sup, mu1,
-                            mu_nn, &fm, split ? &sh : nullptr, &sx, ns));
+    if constexpr (is_single<T>) {
+      if (split) {  // widen, filter on the split product, round back
+        CHASE_TRY(launch_convert(d, Va(), lv, Dv, lD, N, b()));
+        CHASE_TRY(filter_sorted(d, static_cast<const Wide*>(nullptr), N, lD, Dv, lD, Dw, lD, b(),
+                                start.data(), maxdeg, b_sup, mu1, mu_nn, &fm, &sh, &sx, ns));
+        CHASE_TRY(launch_convert(d, Dv, lD, Va(), lv, N, b()));
+      } else {
+        CHASE_TRY(filter_sorted(d, dH, N, lh, Va(), lv, Wk, lw, b(), start.data(), maxdeg, b_sup,
+                                mu1, mu_nn, &fm, nullptr, &sx, ns));
+      }
+    } else {
+      CHASE_TRY(filter_sorted(d, dH, N, lh, Va(), lv, Wk, lw, b(), start.data(), maxdeg, b_sup,
+                              mu1, mu_nn, &fm, split ? &sh : nullptr, &sx, ns));
+    }
     tm.end();
     count_filter(fm);
     return CHASE_OK;

@@ -155,6 +155,9 @@ struct SplitX {
 };
 int split_prepare_h(Dev& d, const chase_c64* H, int64_t N, int64_t ldh, SplitH& out);
 int split_prepare_h(Dev& d, const double* H, int64_t N, int64_t ldh, SplitH& out);
+// The same slices from a complex64 / float32 H (entries widened exactly).
+int split_prepare_h(Dev& d, const chase_c32* H, int64_t N, int64_t ldh, SplitH& out);
+int split_prepare_h(Dev& d, const float* H, int64_t N, int64_t ldh, SplitH& out);
 int split_alloc_x(Dev& d, int64_t N, int max_cols, SplitX& out, bool cplx = true);
 // C[:, j0:j1] = alpha (H X[:, j0:j1] - shift X[:, j0:j1]) + beta C[:, j0:j1]
 // with the leading `nslices` slices of each operand (7: full accuracy, about

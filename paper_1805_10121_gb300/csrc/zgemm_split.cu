@@ -614,16 +614,23 @@ __device__ unsigned long long block_max_u64(unsigned long long v, unsigned long 
   return scratch[32];
 }
 
-// Row r of Ht from column r of the Hermitian H: Re H[r, k] = Re H[k, r],
-// Im H[r, k] = -Im H[k, r].  A: [S][N][Kp] bf16, E: [N].
-__device__ __forceinline__ void slice_h_row(const double2* __restrict__ col, int r, int N,
+// Entries of H widened to FP64 (exact for complex64 input).
+__device__ __forceinline__ double2 widen2(double2 v) { return v; }
+__device__ __forceinline__ double2 widen2(float2 v) {
+  return make_double2(static_cast<double>(v.x), static_cast<double>(v.y));
+}
+
+// Row r of Ht from column r of the Hermitian H (complex128 or complex64):
+// Re H[r, k] = Re H[k, r], Im H[r, k] = -Im H[k, r].  A: [S][N][Kp] bf16, E: [N].
+template <class C2>
+__device__ __forceinline__ void slice_h_row(const C2* __restrict__ col, int r, int N,
                                             __nv_bfloat16* __restrict__ A, long long Kp,
                                             int* __restrict__ E, double* __restrict__ Dg,
                                             unsigned long long* scratch) {
   unsigned long long mb = 0;
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
     if (k == r) continue;  // the diagonal is applied in FP64 by the epilogue
-    const double2 v = col[k];
+    const double2 v = widen2(col[k]);
     const unsigned long long x = abs_bits(v.x), y = abs_bits(v.y);
     mb = x > mb ? x : mb;
     mb = y > mb ? y : mb;
@@ -632,12 +639,12 @@ __device__ __forceinline__ void slice_h_row(const double2* __restrict__ col, int
   const int er = exponent_above_bits(mb);
   if (threadIdx.x == 0) {
     E[r] = er;
-    Dg[r] = col[r].x;
+    Dg[r] = widen2(col[r]).x;
   }
   const long long plane = static_cast<long long>(N) * Kp;
   __nv_bfloat16* row = A + static_cast<long long>(r) * Kp;
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
-    const double2 v = k == r ? make_double2(0.0, 0.0) : col[k];
+    const double2 v = k == r ? make_double2(0.0, 0.0) : widen2(col[k]);
     float ar[S], ai[S];
     slice7_bits(v.x, er, ar);
     slice7_bits(-v.y, er, ai);
@@ -649,7 +656,8 @@ __device__ __forceinline__ void slice_h_row(const double2* __restrict__ col, int
   }
 }
 
-__global__ void __launch_bounds__(256) slice_h_kernel(const double2* __restrict__ H, long long ldh,
+template <class C2>
+__global__ void __launch_bounds__(256) slice_h_kernel(const C2* __restrict__ H, long long ldh,
                                                       int N, __nv_bfloat16* __restrict__ A,
                                                       long long Kp, int* __restrict__ E,
                                                       double* __restrict__ Dg) {
@@ -736,31 +744,33 @@ __global__ void __launch_bounds__(256) slice_x_grouped_kernel(const GroupedProbl
               pr.Kp, 2LL * pr.bcap * pr.Kp, pr.F + c, scratch);
 }
 
-// Real operands: row r of H from its column r (H symmetric), K = N.
-__global__ void __launch_bounds__(256) slice_h_real_kernel(const double* __restrict__ H, long long ldh,
+// Real operands (float64 or float32 H): row r of H from its column r (H
+// symmetric), K = N.
+template <class R>
+__global__ void __launch_bounds__(256) slice_h_real_kernel(const R* __restrict__ H, long long ldh,
                                                            int N, __nv_bfloat16* __restrict__ A,
                                                            long long Kp, int* __restrict__ E,
                                                            double* __restrict__ Dg) {
   __shared__ unsigned long long scratch[33];
   const int r = blockIdx.x;
-  const double* col = H + static_cast<long long>(r) * ldh;
+  const R* col = H + static_cast<long long>(r) * ldh;
   unsigned long long mb = 0;
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
     if (k == r) continue;
-    const unsigned long long x = abs_bits(col[k]);
+    const unsigned long long x = abs_bits(static_cast<double>(col[k]));
     mb = x > mb ? x : mb;
   }
   mb = block_max_u64(mb, scratch);
   const int er = exponent_above_bits(mb);
   if (threadIdx.x == 0) {
     E[r] = er;
-    Dg[r] = col[r];
+    Dg[r] = static_cast<double>(col[r]);
   }
   const long long plane = static_cast<long long>(N) * Kp;
   __nv_bfloat16* row = A + static_cast<long long>(r) * Kp;
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
     float a[S];
-    slice7_bits(k == r ? 0.0 : col[k], er, a);
+    slice7_bits(k == r ? 0.0 : static_cast<double>(col[k]), er, a);
 #pragma unroll
     for (int s = 0; s < S; ++s) row[s * plane + k] = __float2bfloat16_rn(a[s]);
   }
@@ -844,33 +854,52 @@ namespace {
 int64_t k_padded_real(int64_t N) { return ((N + split::BK - 1) / split::BK) * split::BK; }
 }  // namespace
 
-int split_prepare_h(Dev& d, const chase_c64* H, int64_t N, int64_t ldh, SplitH& out) {
+namespace {
+template <class C2>
+int prepare_h_complex(Dev& d, const C2* H, int64_t N, int64_t ldh, SplitH& out) {
   out.N = N;
   out.Kp = k_padded(N);
   out.cplx = 1;
   CHASE_TRY(d.alloc_bytes(&out.A, static_cast<size_t>(split::S) * N * out.Kp * 2));
   CHASE_TRY(d.alloc(&out.E, static_cast<size_t>(N)));
   CHASE_TRY(d.alloc(&out.Dg, static_cast<size_t>(N)));
-  split::slice_h_kernel<<<static_cast<unsigned>(N), 256, 0, d.st>>>(
-      reinterpret_cast<const double2*>(H), ldh, static_cast<int>(N),
-      static_cast<__nv_bfloat16*>(out.A), out.Kp, out.E, out.Dg);
+  split::slice_h_kernel<C2><<<static_cast<unsigned>(N), 256, 0, d.st>>>(
+      H, ldh, static_cast<int>(N), static_cast<__nv_bfloat16*>(out.A), out.Kp, out.E, out.Dg);
   note_launch();
   CHASE_CUDA(cudaGetLastError());
   return CHASE_OK;
 }
 
-int split_prepare_h(Dev& d, const double* H, int64_t N, int64_t ldh, SplitH& out) {
+template <class R>
+int prepare_h_real(Dev& d, const R* H, int64_t N, int64_t ldh, SplitH& out) {
   out.N = N;
   out.Kp = k_padded_real(N);
   out.cplx = 0;
   CHASE_TRY(d.alloc_bytes(&out.A, static_cast<size_t>(split::S) * N * out.Kp * 2));
   CHASE_TRY(d.alloc(&out.E, static_cast<size_t>(N)));
   CHASE_TRY(d.alloc(&out.Dg, static_cast<size_t>(N)));
-  split::slice_h_real_kernel<<<static_cast<unsigned>(N), 256, 0, d.st>>>(
+  split::slice_h_real_kernel<R><<<static_cast<unsigned>(N), 256, 0, d.st>>>(
       H, ldh, static_cast<int>(N), static_cast<__nv_bfloat16*>(out.A), out.Kp, out.E, out.Dg);
   note_launch();
   CHASE_CUDA(cudaGetLastError());
   return CHASE_OK;
+}
+}  // namespace
+
+int split_prepare_h(Dev& d, const chase_c64* H, int64_t N, int64_t ldh, SplitH& out) {
+  return prepare_h_complex(d, reinterpret_cast<const double2*>(H), N, ldh, out);
+}
+
+int split_prepare_h(Dev& d, const chase_c32* H, int64_t N, int64_t ldh, SplitH& out) {
+  return prepare_h_complex(d, reinterpret_cast<const float2*>(H), N, ldh, out);
+}
+
+int split_prepare_h(Dev& d, const double* H, int64_t N, int64_t ldh, SplitH& out) {
+  return prepare_h_real(d, H, N, ldh, out);
+}
+
+int split_prepare_h(Dev& d, const float* H, int64_t N, int64_t ldh, SplitH& out) {
+  return prepare_h_real(d, H, N, ldh, out);
 }
 
 int split_alloc_x(Dev& d, int64_t N, int max_cols, SplitX& out, bool cplx) {

@@ -92,9 +92,12 @@ def test_single_residuals(real):
     assert np.max(np.abs(got - ref) / ref) <= 1e-5
 
 
+@pytest.mark.parametrize("precision", [chase.CHASE_FP64, chase.CHASE_SPLIT_BF16])
 @pytest.mark.parametrize("real", [False, True])
 @pytest.mark.parametrize("n,nev,nex", [(1000, 50, 20), (601, 30, 11)])
-def test_single_solve_known_spectrum(real, n, nev, nex):
+def test_single_solve_known_spectrum(real, n, nev, nex, precision):
+    """FP32 products throughout, or (CHASE_SPLIT_BF16) the filter on the
+    four-slice split product over widened copies of the block."""
     tol = 1e-5
     H, lam = problem(n, 441 + n, real, n_cluster=60)
     V0 = block(n, nev + nex, 442, real)
@@ -102,8 +105,11 @@ def test_single_solve_known_spectrum(real, n, nev, nex):
     dt = torch.float32 if real else torch.complex64
     Vd = dcol(V0.to(dt))
     solve = chase.chase_solve_f32 if real else chase.chase_solve_c32
-    st, ritz, resid, stats = solve(dcol(H.to(dt)), nev, nex, tol, Vd, dcol(S.to(dt)))
+    st, ritz, resid, stats = solve(dcol(H.to(dt)), nev, nex, tol, Vd, dcol(S.to(dt)),
+                                   opts=chase.chase_opts_default(precision=precision))
     assert st == chase.CHASE_OK
+    if precision != chase.CHASE_FP64:
+        assert stats["filter_slices_low"] == stats["iterations"]  # 4 slices every iteration
     l = lam.numpy()
     hn = float(np.abs(l).max())
     assert np.max(np.abs(ritz[:nev] - l[:nev])) <= EIG_RTOL * hn
