@@ -1379,7 +1379,8 @@ extern "C" int chase_solve_batched(int P, const chase_c64* const* H, const int64
   std::iota(all.begin(), all.end(), 0);
   std::stable_sort(all.begin(), all.end(),
                    [&](int a, int b) {
-                     return sv[a].N * (sv[a].nev + sv[a].nex) > sv[b].N * (sv[b].nev + sv[b].nex);
+                     return static_cast<double>(sv[a].N) * (sv[a].nev + sv[a].nex) >
+                            static_cast<double>(sv[b].N) * (sv[b].nev + sv[b].nex);
                    });
   // Alg. 1 lines 1-2 of every problem
   CHASE_TRY(pool.run(all, [&](Dev& w, int p) { return sv[p].setup(w, true); }));
@@ -1447,7 +1448,7 @@ extern "C" int chase_solve_batched(int P, const chase_c64* const* H, const int64
     }
     // lines 5-15 per problem, largest first so that the workers finish together
     std::stable_sort(act.begin(), act.end(), [&](int a, int b) {  // cost ~ N^2 (active columns)
-      return sv[a].N * sv[a].N * sv[a].b() > sv[b].N * sv[b].N * sv[b].b();
+      return sv[a].N2 * sv[a].b() > sv[b].N2 * sv[b].b();
     });
     CHASE_TRY(pool.run(act, [&](Dev& w, int p) { return sv[p].after_filter(w); }));
   }
