@@ -129,7 +129,8 @@ typedef struct {
   double t_total, t_lanczos, t_filter, t_qr, t_rr, t_eigh, t_resid, t_host; /* seconds */
   double t_rr_product;     /* seconds of Rayleigh-Ritz's H Q products (inside t_rr) */
   double flops_rr_product; /* their algorithmic FLOPs (8 N^2 b complex, 2 N^2 b real) */
-  int filter_slices_low;   /* iterations whose filter kept fewer than 7 slices (ADAPT) */
+  int filter_slices_low;   /* iterations whose split filter kept fewer than 7 slices
+                              (CHASE_SPLIT_BF16_ADAPT; single precision) */
   long long lanczos_matvecs; /* column products with H inside Alg. 6 (k per run) */
 } chase_stats;
 

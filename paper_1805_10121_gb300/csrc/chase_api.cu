@@ -673,7 +673,7 @@ struct Solver {
     PhaseTimer tm(d.st);
     long long fm = 0;
     const int ns = slices_for_iteration();
-    S.filter_slices_low += ns < 7 ? 1 : 0;
+    S.filter_slices_low += split && ns < 7 ? 1 : 0;
     tm.begin(&S.t_filter);
     if constexpr (is_single<T>) {
       if (split) {  // widen, filter on the split product, round back
