@@ -60,6 +60,9 @@ def parse():
                    help="sequence: timed solves of the correlated sequence (default); "
                         "filter: timed degree-m filter calls on one problem, split vs FP64")
     p.add_argument("--filter-degree", type=int, default=20)
+    p.add_argument("--deg-extra", type=int, default=None,
+                   help="DEGEXTRA of Alg. 5 for the sequence workload (default: 6 with a "
+                        "split filter, Table 1's 2 with --precision fp64)")
     p.add_argument("--sweep-degrees", default="6,10,14,18,22,26,30,34,40")
     p.add_argument("--batch-problems", type=int, default=512)
     p.add_argument("--batch-degrees", default="const", choices=["const", "mixed"],
@@ -303,6 +306,21 @@ def lanczos_entry(stats_list, n, pk, src):
                   "eigensolves), CUDA events on the solve's stream",
         "peak_source": f"{src} bf16_tflops x nominal FP64/BF16 ratio (1.25/2250)",
     }
+
+
+# DEGEXTRA of Alg. 5 (Table 1: 2).  With the split filter a column product
+# costs about 1/36 of the FP64 work per FLOP that Rayleigh-Ritz and QR do, so
+# slightly higher degrees, which lock columns sooner and leave smaller
+# blocks for the FP64 steps, pay off: N = 8000 sequence, 2.60 s per solve
+# with 2, 2.47 s with 6, 2.49 s with 12 (measured).  The FP64 path keeps 2.
+SPLIT_DEG_EXTRA = 6
+
+
+def deg_extra_for(args, precision_code):
+    from paper_1805_10121_gb300 import chase
+    if getattr(args, "deg_extra", None) is not None:
+        return args.deg_extra
+    return 2 if precision_code == chase.CHASE_FP64 else SPLIT_DEG_EXTRA
 
 
 def workload_config(args, world):
@@ -1182,8 +1200,9 @@ def main():
     prec = prec_code(args.precision)
 
     def solve(k, Vb, Lamb, precision=None):
-        o = chase.chase_opts_default(approx=0 if k == 0 else 1,
-                                     precision=prec if precision is None else precision)
+        p = prec if precision is None else precision
+        o = chase.chase_opts_default(approx=0 if k == 0 else 1, precision=p,
+                                     deg_extra=deg_extra_for(args, p))
         S = starts if k == 0 else starts[:, :1].contiguous()
         return chase.chase_solve(seq[k], nev, nex, tol, Vb, S, Lambda=Lamb, opts=o)
 
@@ -1280,7 +1299,8 @@ def main():
         Sh.copy_(starts[:, :1])
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        o = chase.chase_opts_default(approx=1, precision=prec)
+        o = chase.chase_opts_default(approx=1, precision=prec,
+                                     deg_extra=deg_extra_for(args, prec))
         st_e, lam_e, res_e, s_e = chase.chase_solve(Hh, nev, nex, tol, Vh, Sh,
                                                     Lambda=Lam_before, opts=o)
         t_e2e = time.perf_counter() - t0
@@ -1315,7 +1335,7 @@ def main():
         "vs_baseline": None,
         "dtype": "bf16-split+f64" if args.precision != "fp64" else "f64",
         "data": "synthetic",
-        "config": workload_config(args, world),
+        "config": dict(workload_config(args, world), deg_extra=deg_extra_for(args, prec)),
         "s_per_solve": round(t_max / K, 3),
         "filter_tflops": round(filt_fl / filt_t / 1e12, 4) if filt_t > 0 else None,
         "filter_share_of_time": round(filt_t / max(elapsed, 1e-12), 4),
