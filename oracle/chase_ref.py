@@ -47,6 +47,13 @@ design notes as well):
   rounded value is replaced by ``(G + G^H) / 2`` before the eigensolve.
 * Random numbers are inputs: the start block ``V`` and the Lanczos start
   vectors are passed in by the caller.
+
+Pins: ``tests/test_oracle_pins.py`` and ``tests/test_oracle_properties.py``
+check every function against closed forms, library routines on special
+cases, invariants or the paper's worked values, except one: the width
+safeguard of the density-of-states quantile (in ``lanczos_estimates``: the halving
+and the uniform fallback above) is pinned only by invariants
+(``mu_1 < mu_nev+nex < b_sup``); its value is **parity unpinned**.
 """
 
 from __future__ import annotations
