@@ -424,3 +424,47 @@ def test_solve_max_iter_returns_partial():
     assert out["iterations"] == 1
     assert not out["converged"]
     assert out["V"].shape == (n, nev + nex)
+
+
+# ------------------------------------------------------- small helpers ---
+
+def test_filter_bounds_hand_values():
+    # Alg. 4 lines 2-3 with b_sup = 3, mu_nev+nex = 1, mu_1 = -1:
+    # c = 2, e = 1, sigma_1 = e / (mu_1 - c) = -1/3
+    c, e, s1 = oracle.filter_bounds(3.0, -1.0, 1.0)
+    assert (c, e) == (2.0, 1.0)
+    assert s1 == pytest.approx(-1.0 / 3.0, abs=1e-15)
+
+
+def test_shifted_apply_is_h_minus_c_identity():
+    rng = np.random.default_rng(5)
+    n, b = 7, 3
+    H = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    X = rng.standard_normal((n, b)) + 1j * rng.standard_normal((n, b))
+    out = oracle.shifted_apply(H, X, 0.75)
+    assert np.allclose(out, (H - 0.75 * np.eye(n)) @ X, rtol=0, atol=1e-13)
+
+
+def test_degrees_is_degree_one_per_column():
+    rng = np.random.default_rng(9)
+    res = 10.0 ** rng.uniform(-12, 0, 20)
+    ritz = rng.uniform(-2.0, 0.4, 20)
+    c, e, tol = 0.5, 0.5, 1e-10
+    got = oracle.degrees(res, ritz, c, e, tol)
+    ref = [oracle.degree_one(tol, r, l, c, e, 2, 36) for r, l in zip(res, ritz)]
+    assert list(got) == ref
+    assert all(d % 2 == 0 and 2 <= d <= 36 for d in got)
+
+
+def test_dos_cdf_single_node_is_the_normal_cdf():
+    # one run, one Ritz value at 0 with unit weight: the integral of Eq. 10
+    # is the Gaussian CDF Phi(t / sigma)
+    nodes = [(np.array([0.0]), np.array([1.0]))]
+    for t, ref in ((0.0, 0.5), (0.25, 0.5 * (1 + math.erf(1.0 / math.sqrt(2)))),
+                   (-0.5, 0.5 * (1 + math.erf(-2.0 / math.sqrt(2))))):
+        assert oracle.dos_cdf(nodes, t, 0.25) == pytest.approx(ref, abs=1e-15)
+    # two runs are averaged; weights summing to one give a CDF from 0 to 1
+    nodes2 = [(np.array([-1.0, 1.0]), np.array([0.5, 0.5])), (np.array([0.0]), np.array([1.0]))]
+    assert oracle.dos_cdf(nodes2, -50.0, 0.1) == pytest.approx(0.0, abs=1e-15)
+    assert oracle.dos_cdf(nodes2, 50.0, 0.1) == pytest.approx(1.0, abs=1e-15)
+    assert oracle.dos_cdf(nodes2, 0.0, 0.1) == pytest.approx(0.5, abs=1e-12)
