@@ -69,13 +69,11 @@ constexpr int KPS = 2;               // K blocks per stage: 32 K, one 64-byte sw
 constexpr int BX = BK * KPS;         // K per stage
 constexpr int NSTAGE = 2;
 constexpr int CHUNK = 16;            // k-blocks per exact chunk (256 K)
-constexpr int NEXACT = 3;            // levels accumulated exactly
 constexpr int A_TILE = BM * BX * 2;  // 8192 B per slice
 constexpr int B_TILE = BN * BX * 2;  // 4096 B per slice
 constexpr int STAGE_A = S * A_TILE;
 constexpr int STAGE_B = S * B_TILE;
 constexpr int STAGE_BYTES = STAGE_A + STAGE_B;
-constexpr int TMEM_COLS = 512;
 constexpr int kFlushWarps = 8;       // two per TMEM lane quarter, 32 columns each
 constexpr int kThreads = (2 + kFlushWarps) * 32;
 constexpr int SMEM = 1024 + NSTAGE * STAGE_BYTES + 256;
