@@ -241,6 +241,29 @@ int chase_lock(int b, const double* ritz, const double* resid, double tol, int* 
  * Errors: CHASE_INVALID_ARG, CHASE_EIGENSOLVER_ERROR (no convergence). */
 int chase_tridiag_eigh(int k, const double* diag, const double* off, double* w, double* z);
 
+/* mu_nev+nex of Alg. 6 line 11 from Lanczos Ritz data, host arrays only:
+ * the value t at which the integral of the density estimate of Eq. 10
+ * (Sec. 4.2) reaches `target` (= (nev + nex) / N in the solver).
+ * nruns    number of density runs (n_vec), >= 1.
+ * steps    nruns run lengths (>= 1 each).
+ * theta    the Ritz values of run 0, then run 1, ... (sum of steps values).
+ * weights  the matching weights |Z_1i|^2 (first eigenvector components
+ *          squared), same layout; each run's weights sum to 1.
+ * The estimate is the average over the runs of sum_i w_i Phi((t -
+ * theta_i) / s), s = dos_sigma (b_sup - mu1) / 2 (dos_sigma itself when the
+ * interval has collapsed).  The paper leaves its safeguards unpublished;
+ * this library keeps the result strictly inside (mu1, b_sup) by a margin
+ * of 1e-6 (b_sup - mu1): it halves s, at most 40 times, and failing that
+ * returns mu1 + (b_sup - mu1) min(max(target, 1e-3), 0.5), the quantile of
+ * a uniform density.
+ * mu_out        out: the estimate.
+ * halvings_out  out (nullable): halvings taken, or -1 for the uniform fallback.
+ * Errors: CHASE_INVALID_ARG (NULL array, a run length < 1, target outside
+ * (0, 1), non-finite bounds, mu1 > b_sup, dos_sigma <= 0). */
+int chase_dos_estimate(int nruns, const int* steps, const double* theta, const double* weights,
+                       double target, double mu1, double b_sup, double dos_sigma, double* mu_out,
+                       int* halvings_out);
+
 /* Orthonormalise V against the locked block Y and within itself (Alg. 1
  * line 5, QR of [Y V], keeping Y): block Gram-Schmidt against Y followed by
  * Cholesky QR, twice; if a Cholesky pivot is not safely positive the first

@@ -50,10 +50,12 @@ design notes as well):
 
 Pins: ``tests/test_oracle_pins.py`` and ``tests/test_oracle_properties.py``
 check every function against closed forms, library routines on special
-cases, invariants or the paper's worked values, except one: the width
-safeguard of the density-of-states quantile (in ``lanczos_estimates``: the halving
-and the uniform fallback above) is pinned only by invariants
-(``mu_1 < mu_nev+nex < b_sup``); its value is **parity unpinned**.
+cases, invariants or the paper's worked values.  The width safeguard of the
+density-of-states quantile (``dos_estimate``: the halving and the uniform
+fallback above) is a reading of a part the paper does not publish; its
+arithmetic is pinned by hand-worked cases of each branch
+(``tests/golden/dos_safeguard.txt``), while the choice of that heuristic
+over the paper's own has nothing in the paper to be checked against.
 """
 
 from __future__ import annotations
@@ -76,6 +78,7 @@ __all__ = [
     "lanczos_run",
     "dos_cdf",
     "dos_quantile",
+    "dos_estimate",
     "lanczos_estimates",
     "solve",
 ]
@@ -360,6 +363,37 @@ def dos_quantile(nodes, target, sig):
     return 0.5 * (lo + hi)
 
 
+def dos_estimate(nodes, target, mu1, b_sup, sigma=0.25):
+    """``mu_nev+nex`` of Alg. 6 line 11: the ``target`` quantile of the
+    density estimate of Eq. 10 built from ``nodes`` (one (theta, w) pair of
+    arrays per density run), kept strictly inside ``(mu_1, b_sup)``.
+
+    The Gaussian width is ``sigma`` times the half-width of ``[mu_1,
+    b_sup]`` (``sigma`` itself when that interval has collapsed).  Sec. 4.2
+    leaves the safeguards unpublished.  Reading: when the quantile is not
+    inside the interval by a margin of ``1e-6 (b_sup - mu_1)``, halve the
+    width and take the quantile again, at most 40 times; failing that, take
+    the ``target`` quantile of a uniform density on ``[mu_1, b_sup]``, with
+    ``target`` clamped to ``[1e-3, 0.5]``.
+
+    Returns ``{"mu": value, "halvings": count, "fallback": bool}``.
+    """
+    half = (b_sup - mu1) / 2.0
+    # a collapsed interval (all Ritz values equal) falls back to sigma itself
+    sig = sigma * half if half > 1e-12 * max(1.0, abs(b_sup), abs(mu1)) else sigma
+    mu = dos_quantile(nodes, target, sig)
+    margin = 1e-6 * (b_sup - mu1)
+    halvings = 0
+    while not (mu1 + margin < mu < b_sup - margin) and halvings < 40:
+        sig *= 0.5
+        halvings += 1
+        mu = dos_quantile(nodes, target, sig)
+    if mu1 + margin < mu < b_sup - margin:
+        return {"mu": mu, "halvings": halvings, "fallback": False}
+    return {"mu": mu1 + (b_sup - mu1) * min(max(target, 1e-3), 0.5), "halvings": halvings,
+            "fallback": True}
+
+
 def lanczos_estimates(H, starts, k, nvec, approx, nev, nex, V=None, sigma=0.25):
     """Alg. 6: spectral bounds, and (when ``approx`` is false) the density
     estimate of Eq. 10 with ``mu_1``, ``mu_nev+nex`` and start vectors.
@@ -384,24 +418,9 @@ def lanczos_estimates(H, starts, k, nvec, approx, nev, nex, V=None, sigma=0.25):
         b_sup = max(b_sup, f + float(theta.max()))
         absmax = max(absmax, float(np.abs(theta).max()))
     mu1 = min(float(theta.min()) for theta, _, _, _ in runs)             # line 12
-    half = (b_sup - mu1) / 2.0
-    # a collapsed interval (all Ritz values equal) falls back to sigma itself
-    sig = sigma * half if half > 1e-12 * max(1.0, abs(b_sup), abs(mu1)) else sigma
     target = (nev + nex) / n                                 # line 11
     nodes = [(theta, np.abs(Z[0, :]) ** 2) for theta, Z, _, _ in runs]
-    mu_nevnex = dos_quantile(nodes, target, sig)
-    # The quantile must lie strictly inside (mu_1, b_sup) for the filter
-    # interval to make sense; Sec. 4.2 leaves the safeguards unpublished.
-    # Reading: halve the width until it does, else take the quantile of a
-    # uniform density on [mu_1, b_sup].
-    margin = 1e-6 * (b_sup - mu1)
-    for _ in range(40):
-        if mu1 + margin < mu_nevnex < b_sup - margin:
-            break
-        sig *= 0.5
-        mu_nevnex = dos_quantile(nodes, target, sig)
-    if not (mu1 + margin < mu_nevnex < b_sup - margin):
-        mu_nevnex = mu1 + (b_sup - mu1) * min(max(target, 1e-3), 0.5)
+    mu_nevnex = dos_estimate(nodes, target, mu1, b_sup, sigma)["mu"]
     Vout = None
     if V is not None:                                        # line 13
         Vout = np.array(V, dtype=np.complex128, copy=True)

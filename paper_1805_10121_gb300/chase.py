@@ -20,7 +20,7 @@ import torch
 __all__ = [
     "ChaseError", "ChaseOpts", "ChaseStats", "lib", "lib_path", "declared_symbols",
     "chase_opts_default", "chase_last_error", "chase_kernel_launches", "chase_filter", "chase_lanczos",
-    "chase_degrees", "chase_lock", "chase_tridiag_eigh", "chase_orthonormalize",
+    "chase_degrees", "chase_lock", "chase_tridiag_eigh", "chase_dos_estimate", "chase_orthonormalize",
     "chase_rayleigh_ritz", "chase_residuals", "chase_residuals_noalloc", "chase_solve",
     "CHASE_OK", "CHASE_INVALID_ARG", "CHASE_NOT_CONVERGED", "CHASE_QR_BREAKDOWN",
     "CHASE_BOUND_VIOLATION", "CHASE_CUDA_ERROR", "CHASE_OUT_OF_MEMORY", "CHASE_TIMEOUT",
@@ -126,6 +126,7 @@ _SIGNATURES = {
     "chase_degrees": (_int, [_int, _dp, _dp, _dbl, _dbl, _dbl, _int, _int, _ip]),
     "chase_lock": (_int, [_int, _dp, _dp, _dbl, _ip, _ip]),
     "chase_tridiag_eigh": (_int, [_int, _dp, _dp, _dp, _dp]),
+    "chase_dos_estimate": (_int, [_int, _ip, _dp, _dp, _dbl, _dbl, _dbl, _dbl, _dp, _ip]),
     "chase_orthonormalize": (_int, [_c_p, _i64, _i64, _int, _c_p, _i64, _int, _c_p]),
     "chase_rayleigh_ritz": (_int, [_c_p, _i64, _i64, _c_p, _i64, _int, _dp, _dp, _c_p]),
     "chase_residuals": (_int, [_c_p, _i64, _i64, _c_p, _i64, _int, _dp, _dp, _c_p]),
@@ -426,6 +427,22 @@ def chase_tridiag_eigh(diag, off):
     _check(lib().chase_tridiag_eigh(k, _dptr(dg), _dptr(of), _dptr(w), _dptr(z)),
            "chase_tridiag_eigh")
     return w, z.reshape(k, k).T.copy()
+
+
+def chase_dos_estimate(nodes, target, mu1, b_sup, dos_sigma=0.25):
+    """mu_nev+nex of Alg. 6 line 11 from per-run (theta, weights) pairs.
+    Returns ``(mu, halvings)``; ``halvings`` is -1 for the uniform fallback."""
+    steps = np.array([len(th) for th, _ in nodes], dtype=np.int32)
+    theta = _f64(np.concatenate([np.asarray(th, dtype=np.float64) for th, _ in nodes]))
+    w = _f64(np.concatenate([np.asarray(x, dtype=np.float64) for _, x in nodes]))
+    if w.shape != theta.shape:
+        raise ValueError("one weight per Ritz value")
+    mu = np.zeros(1)
+    h = np.zeros(1, dtype=np.int32)
+    _check(lib().chase_dos_estimate(len(nodes), _iptr(steps), _dptr(theta), _dptr(w),
+                                    float(target), float(mu1), float(b_sup), float(dos_sigma),
+                                    _dptr(mu), _iptr(h)), "chase_dos_estimate")
+    return float(mu[0]), int(h[0])
 
 
 def chase_orthonormalize(Y, V, stream=None):

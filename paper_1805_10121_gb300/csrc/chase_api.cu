@@ -343,8 +343,6 @@ struct LanczosOut {
   long long matvecs = 0;
 };
 
-double normal_cdf(double x) { return 0.5 * (1.0 + std::erf(x / std::sqrt(2.0))); }
-
 // starts: N x r device (ld N), r = 1 (approx) or 1 + nvec.  V: N x ncolv
 // device or NULL.
 template <class T>
@@ -416,47 +414,19 @@ int lanczos_core(Dev& d, const T* H, int64_t N, int64_t ldh, int k, int nvec, bo
   // density runs are c = 1 .. nvec
   double mu1 = theta[1][0];
   for (int c = 2; c < r; ++c) mu1 = std::min(mu1, theta[c][0]);  // Alg. 6 line 12
-  const double half = 0.5 * (bsup - mu1);
-  double sig = half > 1e-12 * std::max(1.0, std::max(std::fabs(bsup), std::fabs(mu1)))
-                   ? dos_sigma * half
-                   : dos_sigma;
-  double tmin = theta[1][0], tmax = theta[1].back();
-  for (int c = 2; c < r; ++c) {
-    tmin = std::min(tmin, theta[c][0]);
-    tmax = std::max(tmax, theta[c].back());
-  }
-  auto cdf = [&](double t, double s) {  // integral of Eq. 10 up to t
-    double total = 0.0;
-    for (int c = 1; c < r; ++c)
-      for (int i = 0; i < steps[c]; ++i) {
-        const double z0 = Z[c][static_cast<size_t>(i) * steps[c]];
-        total += z0 * z0 * normal_cdf((t - theta[c][i]) / s);
-      }
-    return total / nvec;
-  };
-  const double target = static_cast<double>(nev + nex) / static_cast<double>(N);  // line 11
-  auto quantile = [&](double s) {
-    double lo = tmin - 10.0 * s, hi = tmax + 10.0 * s;
-    for (int it = 0; it < 200; ++it) {
-      const double mid = 0.5 * (lo + hi);
-      if (cdf(mid, s) < target)
-        lo = mid;
-      else
-        hi = mid;
+  // Eq. 10 over the density runs, quantile of line 11 with its safeguard
+  std::vector<int> dsteps(steps.begin() + 1, steps.end());
+  std::vector<double> dtheta, dw;
+  for (int c = 1; c < r; ++c)
+    for (int i = 0; i < steps[c]; ++i) {
+      const double z0 = Z[c][static_cast<size_t>(i) * steps[c]];
+      dtheta.push_back(theta[c][i]);
+      dw.push_back(z0 * z0);
     }
-    return 0.5 * (lo + hi);
-  };
-  // Keep the estimate strictly inside (mu1, b_sup): halve the width, else
-  // fall back to the quantile of a uniform density on [mu1, b_sup].
-  double mu_nn = quantile(sig);
-  const double margin = 1e-6 * (bsup - mu1);
-  for (int h = 0; h < 40; ++h) {
-    if (mu1 + margin < mu_nn && mu_nn < bsup - margin) break;
-    sig *= 0.5;
-    mu_nn = quantile(sig);
-  }
-  if (!(mu1 + margin < mu_nn && mu_nn < bsup - margin))
-    mu_nn = mu1 + (bsup - mu1) * std::min(std::max(target, 1e-3), 0.5);
+  const double target = static_cast<double>(nev + nex) / static_cast<double>(N);  // line 11
+  const double mu_nn =
+      dos_estimate(nvec, dsteps.data(), dtheta.data(), dw.data(), target, mu1, bsup, dos_sigma,
+                   nullptr, nullptr);
   out.mu1 = mu1;
   out.mu_nn = mu_nn;
 

@@ -290,5 +290,10 @@ void release_thread_solver();
 // diag[k], off[k-1] -> eigenvalues ascending in w, eigenvectors (k x k,
 // column-major) in z.  Returns false if it fails to converge.
 bool tridiag_eigh(int k, const double* diag, const double* off, double* w, double* z);
+// Alg. 6 line 11 (Eq. 10 quantile with its width safeguard); see
+// chase_dos_estimate in chase.h.  halvings / fallback may be NULL.
+double dos_estimate(int nruns, const int* steps, const double* theta, const double* w,
+                    double target, double mu1, double b_sup, double dos_sigma, int* halvings,
+                    bool* fallback);
 
 }  // namespace chase

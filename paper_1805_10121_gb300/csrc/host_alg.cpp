@@ -111,7 +111,81 @@ bool tridiag_eigh(int k, const double* diag, const double* off, double* w, doubl
   return true;
 }
 
+// Alg. 6 line 11: the target quantile of the Eq. 10 density estimate, kept
+// strictly inside (mu1, b_sup).  Run c contributes the nodes
+// theta[off_c .. off_c + steps[c]) with weights w (|Z_1i|^2); the estimate
+// is the average of the runs' Gaussian sums.  Sec. 4.2 leaves its
+// safeguards unpublished; the width is halved (at most 40 times) until the
+// quantile lies inside the interval by 1e-6 of its width, failing which the
+// quantile of a uniform density on [mu1, b_sup] is taken (target clamped to
+// [1e-3, 0.5]).
+double dos_estimate(int nruns, const int* steps, const double* theta, const double* w,
+                    double target, double mu1, double b_sup, double dos_sigma, int* halvings,
+                    bool* fallback) {
+  const double half = 0.5 * (b_sup - mu1);
+  double sig = half > 1e-12 * std::max(1.0, std::max(std::fabs(b_sup), std::fabs(mu1)))
+                   ? dos_sigma * half
+                   : dos_sigma;
+  double tmin = HUGE_VAL, tmax = -HUGE_VAL;
+  int total = 0;
+  for (int c = 0; c < nruns; ++c) total += steps[c];
+  for (int i = 0; i < total; ++i) {
+    tmin = std::min(tmin, theta[i]);
+    tmax = std::max(tmax, theta[i]);
+  }
+  auto normal_cdf = [](double x) { return 0.5 * (1.0 + std::erf(x / std::sqrt(2.0))); };
+  auto cdf = [&](double t, double s) {  // integral of Eq. 10 up to t
+    double acc = 0.0;
+    for (int i = 0; i < total; ++i) acc += w[i] * normal_cdf((t - theta[i]) / s);
+    return acc / nruns;
+  };
+  auto quantile = [&](double s) {  // bisection on the monotone cdf
+    double lo = tmin - 10.0 * s, hi = tmax + 10.0 * s;
+    for (int it = 0; it < 200; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (cdf(mid, s) < target)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    return 0.5 * (lo + hi);
+  };
+  const double margin = 1e-6 * (b_sup - mu1);
+  auto inside = [&](double m) { return mu1 + margin < m && m < b_sup - margin; };
+  double mu = quantile(sig);
+  int h = 0;
+  while (!inside(mu) && h < 40) {
+    sig *= 0.5;
+    ++h;
+    mu = quantile(sig);
+  }
+  if (halvings) *halvings = h;
+  if (fallback) *fallback = !inside(mu);
+  if (inside(mu)) return mu;
+  return mu1 + (b_sup - mu1) * std::min(std::max(target, 1e-3), 0.5);
+}
+
 }  // namespace chase
+
+extern "C" int chase_dos_estimate(int nruns, const int* steps, const double* theta,
+                                  const double* weights, double target, double mu1, double b_sup,
+                                  double dos_sigma, double* mu_out, int* halvings_out) {
+  bool ok = nruns > 0 && steps && theta && weights && mu_out && std::isfinite(target) &&
+            target > 0.0 && target < 1.0 && std::isfinite(mu1) && std::isfinite(b_sup) &&
+            mu1 <= b_sup && dos_sigma > 0.0 && std::isfinite(dos_sigma);
+  for (int c = 0; ok && c < nruns; ++c) ok = steps[c] > 0;
+  if (!ok) {
+    chase::set_error("chase_dos_estimate: invalid argument");
+    return CHASE_INVALID_ARG;
+  }
+  int h = 0;
+  bool fb = false;
+  *mu_out = chase::dos_estimate(nruns, steps, theta, weights, target, mu1, b_sup, dos_sigma, &h,
+                                &fb);
+  // halvings_out: the number of halvings, or -1 when the uniform fallback was taken
+  if (halvings_out) *halvings_out = fb ? -1 : h;
+  return CHASE_OK;
+}
 
 extern "C" int chase_degrees(int b, const double* resid, const double* ritz, double c, double e,
                              double tol, int deg_extra, int deg_max, int* degrees_out) {

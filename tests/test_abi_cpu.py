@@ -99,3 +99,43 @@ def test_invalid_arguments_return_status(lib):
         chase.chase_degrees([1.0], [0.0], 0.0, -1.0, 1e-10)
     assert ei.value.status == chase.CHASE_INVALID_ARG
     assert "chase_degrees" in chase.chase_last_error()
+
+
+def _dos_golden():
+    from tests.test_oracle_pins import load_dos_golden
+    return load_dos_golden()
+
+
+def test_dos_estimate_golden(lib):
+    # the library's Alg. 6 line 11 (the host step of chase_lanczos) against the
+    # hand-worked cases, safeguard branches included
+    for name, target, mu1, b_sup, mu, halv, nodes in _dos_golden():
+        got, h = chase.chase_dos_estimate(nodes, target, mu1, b_sup, 0.25)
+        assert got == pytest.approx(mu, abs=1e-9), name
+        assert h == halv, name
+
+
+def test_dos_estimate_matches_oracle_on_lanczos_runs(lib):
+    n, nev, nex = 400, 16, 8
+    rng = np.random.default_rng(41)
+    lam = np.sort(np.concatenate([rng.uniform(-1, -0.95, 25), rng.uniform(-0.95, 1, n - 25)]))
+    q, _ = np.linalg.qr(rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n)))
+    H = (q * lam) @ q.conj().T
+    H = 0.5 * (H + H.conj().T)
+    starts = (rng.normal(size=(n, 4)) + 1j * rng.normal(size=(n, 4))) / np.sqrt(2)
+    runs = [oracle.lanczos_run(H, starts[:, j], 25) for j in range(4)]
+    nodes = [(th, np.abs(Z[0, :]) ** 2) for th, Z, _, _ in runs]
+    mu1 = min(float(th.min()) for th, _ in nodes)
+    b_sup = max(f + float(th.max()) for th, _, f, _ in runs)
+    ref = oracle.dos_estimate(nodes, (nev + nex) / n, mu1, b_sup, 0.25)
+    got, h = chase.chase_dos_estimate(nodes, (nev + nex) / n, mu1, b_sup, 0.25)
+    assert got == pytest.approx(ref["mu"], abs=1e-12 * max(1.0, abs(b_sup)))
+    assert h == (-1 if ref["fallback"] else ref["halvings"])
+
+
+def test_dos_estimate_invalid_arguments(lib):
+    with pytest.raises(chase.ChaseError) as ei:
+        chase.chase_dos_estimate([([0.0], [1.0])], 1.5, 0.0, 1.0)
+    assert ei.value.status == chase.CHASE_INVALID_ARG
+    with pytest.raises(chase.ChaseError):
+        chase.chase_dos_estimate([([0.0], [1.0])], 0.5, 2.0, 1.0)

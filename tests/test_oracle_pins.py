@@ -340,6 +340,43 @@ def test_dos_estimate_kept_inside_interval():
     assert lam[0] <= est["mu_nevnex"] <= lam[nev + nex + 40]
 
 
+def load_dos_golden():
+    """Cases of tests/golden/dos_safeguard.txt: (name, target, mu1, b_sup,
+    expected mu, expected halvings, nodes)."""
+    cases = []
+    with open(os.path.join(GOLDEN, "dos_safeguard.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            name, target, mu1, b_sup, mu, halv, runs = line.split()
+            nodes = []
+            for run in runs.split("|"):
+                th, w = run.split(":")
+                nodes.append((np.array([float(x) for x in th.split(",")]),
+                              np.array([float(x) for x in w.split(",")])))
+            cases.append((name, float(target), float(mu1), float(b_sup), float(mu), int(halv),
+                          nodes))
+    return cases
+
+
+@pytest.mark.parametrize("case", load_dos_golden(), ids=lambda c: c[0])
+def test_dos_safeguard_golden(case):
+    # hand-worked values of Alg. 6 line 11 with the width safeguard (Sec. 4.2)
+    name, target, mu1, b_sup, mu, halv, nodes = case
+    got = oracle.dos_estimate(nodes, target, mu1, b_sup, sigma=0.25)
+    assert got["mu"] == pytest.approx(mu, abs=1e-9), name
+    if halv < 0:
+        assert got["fallback"] and got["halvings"] == 40
+    else:
+        assert not got["fallback"] and got["halvings"] == halv
+
+
+def test_dos_safeguard_golden_file_covers_each_branch():
+    halvings = sorted({c[5] for c in load_dos_golden()})
+    assert halvings == [-1, 0, 1, 2]
+
+
 def test_dos_two_clusters_quantile():
     # two eigenvalues with multiplicity: the Krylov space is 2-dimensional,
     # theta = {a, b}, weights = the start vector's mass on each eigenspace.
