@@ -1,11 +1,20 @@
-"""Benchmark: ChASE solves over a correlated sequence of Hermitian problems.
+"""Benchmark: the Chebyshev filter of ChASE (Alg. 4) in mixed precision on
+one GB300, against the FP64 filter on the same GPU.
 
-Workload (default): N = 8000 complex128, DFT-like spectrum (N/4 eigenvalues
-in [-2, 0], the rest 50 u^2 up to 50), H_{k+1} = H_k + 1e-3 ||H_1|| E_k,
-nev = 400, nex = 80, tol = 1e-10 (relative to ||H||), warm start from the
-previous problem.  One step = one full solve (Alg. 1: Lanczos bounds,
-filter, QR, Rayleigh-Ritz, residuals, locking) of the next problem of the
-sequence.  Problem 1 is solved cold during the warm-up.
+Workload (default, ``--workload filter``): N = 30000 complex128 Hermitian H
+with a DFT-like spectrum (N/4 eigenvalues in [-2, 0], the rest 50 u^2 up to
+50; FFT construction of Q diag(lambda) Q^H), block of nev + nex = 1200 + 300
+columns.  One step = one ``chase_filter`` call of degree 20 on the whole
+block with the split-BF16 tensor-core product (Eq. 7 recurrence, FP64
+epilogue).  Beside the timed steps the line carries: the FP64 filter of the
+same block (degree 2, timed, and extrapolated by FLOPs), one cold solve of
+the same problem to residual <= 1e-10 ||H|| with the split filter and FP64
+QR, Rayleigh-Ritz and residuals, the end-to-end rate through host buffers,
+the roofline of the product kernel and the CPU oracle on a column subset.
+
+``--workload sequence`` gives the correlated-sequence solves (N = 8000,
+nev 400, nex 80, warm starts) with the FP64 solve of the same problem; the
+other workloads are listed under ``--workload``.
 
 Prints one JSON line.  ``--impl reference`` times the CPU oracle instead (a
 bounded sample of the same workload on the host cores).
@@ -45,20 +54,22 @@ def parse():
     p.add_argument("--steps", type=int, default=1)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    p.add_argument("--n", type=int, default=8000)
-    p.add_argument("--nev", type=int, default=400)
-    p.add_argument("--nex", type=int, default=80)
+    p.add_argument("--n", type=int, default=None,
+                   help="matrix order (default 30000 for filter/solve, 8000 otherwise)")
+    p.add_argument("--nev", type=int, default=None)
+    p.add_argument("--nex", type=int, default=None)
     p.add_argument("--tol", type=float, default=1e-10)
     p.add_argument("--seed", type=int, default=2024)
     p.add_argument("--precision", default="split",
                    choices=["split", "split_rr", "split_adapt", "fp64"],
                    help="split: split-BF16 filter; split_rr: also Rayleigh-Ritz's H Q on the "
                         "split product; fp64: FP64 throughout")
-    p.add_argument("--workload", default="sequence",
-                   choices=["sequence", "filter", "serve", "batched", "batched-solve",
+    p.add_argument("--workload", default="filter",
+                   choices=["filter", "sequence", "serve", "batched", "batched-solve",
                             "degree-sweep", "side", "variants", "solve"],
-                   help="sequence: timed solves of the correlated sequence (default); "
-                        "filter: timed degree-m filter calls on one problem, split vs FP64")
+                   help="filter: timed degree-m filter calls on one N = 30000 problem, split "
+                        "vs FP64, plus one cold solve (default); sequence: timed solves of the "
+                        "correlated N = 8000 sequence")
     p.add_argument("--filter-degree", type=int, default=20)
     p.add_argument("--deg-extra", type=int, default=None,
                    help="DEGEXTRA of Alg. 5 for the sequence workload (default: 6 with a "
@@ -78,7 +89,19 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-seconds", type=float, default=20.0)
-    return p.parse_args()
+    p.add_argument("--no-solve", action="store_true",
+                   help="filter workload: skip the cold solve")
+    p.add_argument("--solve-deg-extra", type=int, default=None,
+                   help="filter workload: DEGEXTRA of the cold solve")
+    args = p.parse_args()
+    big = args.workload in ("filter", "solve")
+    if args.n is None:
+        args.n = 30000 if big else 8000
+    if args.nev is None:
+        args.nev = 1200 if big else 400
+    if args.nex is None:
+        args.nex = 300 if big else 80
+    return args
 
 
 def combine_over_ranks(elapsed, flops, device):
@@ -194,7 +217,7 @@ def prec_code(name):
 SPLIT_PAIRS = 28
 
 
-# DRAM traffic of single launches measured with ncu (profiles/*_n4000_full.md):
+# DRAM traffic of single launches measured with ncu (the N = 4000 captures):
 # the bench's own N = 8000 launches are larger than the capture size rule
 # allows, so "traffic" stays null and the small-case figures ride along.
 NCU_TRAFFIC = {
@@ -390,19 +413,34 @@ def cpu_baseline_sample(n, nev, nex, seed, budget_s):
 
 def run_reference(args, rank, world):
     """The reference arm: the CPU oracle as it stands, W untimed and K timed
-    bounded samples of the workload (rank 0 only)."""
+    bounded samples of the workload (rank 0 only).  Filter workload: each
+    step is the oracle's Alg. 4 of the workload's degree on 8 columns of the
+    N x (nev + nex) block (inputs from the same seeded generators on the
+    host).  Sequence workload: a degree-2 filter of the whole block, its
+    Householder QR and the Rayleigh quotient."""
     if rank != 0:
         return
-    smp = OracleSample(args.n, args.nev, args.nex, args.seed)
+    if args.workload == "filter":
+        from paper_1805_10121_gb300 import synth
+        lam = synth.spectrum_dft(args.n, args.seed)
+        H = synth.hermitian_dft(lam, args.seed + 1).numpy()
+        V = synth.gaussian_block(args.n, 8, args.seed + 7).numpy()
+        smp = OracleFilterSample(H, V, lam.numpy(), args.nev + args.nex, args.filter_degree)
+        step, flops, describe = smp.step, smp.flops(), smp.describe
+        cfg = filter_workload_config(args, world)
+        cfg["precision"] = "fp64 (CPU oracle)"
+    else:
+        smp = OracleSample(args.n, args.nev, args.nex, args.seed)
+        step, flops, describe = smp.step, smp.flops, smp.describe
+        cfg = workload_config(args, world)
+        cfg["precision"] = "fp64 (CPU oracle)"
     for _ in range(args.warmup):
-        smp.step()
+        step()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        smp.step()
+        step()
     dt = time.perf_counter() - t0
-    value = smp.flops * args.steps / dt / 1e12
-    cfg = workload_config(args, world)
-    cfg["precision"] = "fp64 (CPU oracle)"
+    value = flops * args.steps / dt / 1e12
     line = {
         "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "TFLOP/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -410,79 +448,349 @@ def run_reference(args, rank, world):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": cfg,
         "cpu_baseline": {"value": round(value, 6), "unit": "TFLOP/s", "cores": os.cpu_count(),
-                         "kind": "oracle", "sample": smp.describe(args.steps)},
+                         "kind": "oracle", "sample": describe(args.steps)},
         "e2e": {"value": round(value, 6), "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
+class BlasThreads:
+    """Set the BLAS thread count of NumPy's bundled OpenBLAS for a region
+    (for the one-thread oracle figure).  ``ok`` is False when the library or
+    its thread call cannot be found; the region then runs unchanged."""
+
+    def __init__(self, n):
+        self.n = n
+        self.ok = False
+        self.prev = None
+        self.set_fn = self.get_fn = None
+        import ctypes
+        try:
+            with open("/proc/self/maps") as f:
+                paths = sorted({ln.split()[-1] for ln in f
+                                if "openblas" in ln.lower() and ".so" in ln})
+        except OSError:
+            paths = []
+        for path in paths:
+            try:
+                lib = ctypes.CDLL(path)
+            except OSError:
+                continue
+            for suffix in ("scipy_openblas_set_num_threads64_", "openblas_set_num_threads64_",
+                           "openblas_set_num_threads"):
+                if hasattr(lib, suffix):
+                    self.set_fn = getattr(lib, suffix)
+                    get = suffix.replace("set_num", "get_num")
+                    self.get_fn = getattr(lib, get) if hasattr(lib, get) else None
+                    self.ok = True
+                    return
+
+    def __enter__(self):
+        if self.ok:
+            self.prev = int(self.get_fn()) if self.get_fn else os.cpu_count()
+            self.set_fn(int(self.n))
+        return self
+
+    def __exit__(self, *exc):
+        if self.ok:
+            self.set_fn(int(self.prev))
+        return False
+
+
+class OracleFilterSample:
+    """A bounded sample of the filter workload for the CPU oracle: Alg. 4 of
+    the given degree on a subset of the block's columns (the oracle's
+    ``cheb_filter``, NumPy BLAS products with H).  ``H`` is a host array
+    (column-major complex128) of the workload's matrix."""
+
+    def __init__(self, H, V, l, nx, degree):
+        import oracle
+        self.oracle = oracle
+        self.H, self.V = H, V
+        self.n = H.shape[0]
+        self.cols = V.shape[1]
+        self.degree = degree
+        self.b_sup, self.mu1, self.mu_nn = 1.01 * float(l[-1]), float(l[0]), float(l[nx])
+
+    def flops(self, degree=None):
+        return 8.0 * self.n * self.n * self.cols * (degree or self.degree)
+
+    def step(self, degree=None):
+        d = degree or self.degree
+        return self.oracle.cheb_filter(self.H, self.V, [d] * self.cols, self.b_sup, self.mu1,
+                                       self.mu_nn)
+
+    def describe(self, reps, threads="all host cores", degree=None):
+        return (f"{reps} x oracle Alg. 4 filter of degree {degree or self.degree} on {self.cols} "
+                f"of the columns of the N={self.n} block (NumPy, BLAS threads = {threads})")
+
+
+def filter_cpu_baseline(smp, budget_s):
+    """The oracle sample timed on the host cores: repeated until budget_s is
+    spent (at least once), then a short one-thread figure."""
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        smp.step()
+        reps += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    out = {"value": round(smp.flops() * reps / dt / 1e12, 6), "unit": "TFLOP/s",
+           "cores": os.cpu_count(), "kind": "oracle", "sample": smp.describe(reps),
+           "seconds": round(dt, 2)}
+    one = {"value": None, "note": "BLAS thread control not found"}
+    bt = BlasThreads(1)
+    if bt.ok:
+        with bt:
+            t1 = time.perf_counter()
+            smp.step(degree=2)
+            d1 = time.perf_counter() - t1
+        one = {"value": round(smp.flops(degree=2) / d1 / 1e12, 6), "unit": "TFLOP/s",
+               "cores": 1, "sample": smp.describe(1, threads="1", degree=2),
+               "seconds": round(d1, 2)}
+    out["one_thread"] = one
+    return out
+
+
+def filter_workload_config(args, world):
+    n, nx, m = args.n, args.nev + args.nex, args.filter_degree
+    return {
+        "workload": (f"mixed-precision Chebyshev filter, N={n} complex128 (FFT construction of "
+                     f"Q diag(lambda) Q^H, DFT-like spectrum), block of nev+nex={args.nev}+"
+                     f"{args.nex} columns, degree {m} for every column; step = one chase_filter "
+                     f"call (Alg. 4) with the split-BF16 tensor-core product"),
+        "n": n, "nev": args.nev, "nex": args.nex, "degree": m, "precision": "split",
+        "l2": (f"inputs larger than L2 (H {16 * n * n / 1e9:.1f} GB, its BF16 slices "
+               f"{28 * n * n / 1e9:.1f} GB, block {16 * n * nx / 1e9:.2f} GB)"),
+        "parallelism": "replicas" if world > 1 else "single GPU",
+    }
+
+
+# DRAM traffic of one zgemm_split_kernel launch of the default filter
+# workload (one of its two K segments: 30000 rows of H, 1500 complex
+# columns, K = 30000), measured with ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum, one pass, --clock-control none) on the committed
+# kernel; None until a capture of the current kernel exists.
+SPLIT_N30000_TRAFFIC = None
+
+
+def split_algorithmic_bytes(n, ncols, k_per_launch):
+    """Bytes one split product launch must move at least: the 7 slice planes
+    of H and of the block over its K range, once, and the FP64 result
+    (a K-segment partial product, N x ncols complex)."""
+    return 7 * 2.0 * (n + 2 * ncols) * k_per_launch + 16.0 * n * ncols
+
+
 def run_filter_workload(args, rank, world, local):
-    """One problem (N, nev + nex columns, same spectrum law): time the filter
-    of constant degree m on the whole block with the split-BF16 product, and
-    one FP64 degree-2 filter for comparison (FP64 is ~30x slower per column
-    product, so a full FP64 filter at this size is extrapolated by FLOPs)."""
+    """The mixed-precision filter configuration (default)."""
     from paper_1805_10121_gb300 import build, chase, synth
     build.build()
     chase.lib()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    n, nx, m = args.n, args.nev + args.nex, args.filter_degree
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    n, nev, nex, m = args.n, args.nev, args.nex, args.filter_degree
+    nx = nev + nex
+    W, K = args.warmup, args.steps
     seed = args.seed + 1000 * rank
     lam = synth.spectrum_dft(n, seed, device=dev)
     H = synth.hermitian_dft(lam, seed + 1)
     V0 = synth.gaussian_block(n, nx, seed + 7, device=dev)
     l = lam.cpu().numpy()
-    b_sup, mu1, mu_nn = float(l[-1]) * 1.01, float(l[0]), float(l[nx])
+    hnorm = float(np.abs(l).max())
+    b_sup, mu1, mu_nn = 1.01 * float(l[-1]), float(l[0]), float(l[nx])
+    degs = torch.full((nx,), m, dtype=torch.int32)
     stream = torch.cuda.current_stream(dev)
+    split = chase.CHASE_SPLIT_BF16
 
-    def timed(prec, deg, reps):
-        V = V0.clone()
-        for _ in range(args.warmup if reps > 1 else 1):
-            chase.chase_filter(H, V, [deg] * nx, b_sup, mu1, mu_nn, precision=prec)
-        torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        clocks = ClockSampler(local)
-        clocks.start()
-        a.record(stream)
-        for _ in range(reps):
-            chase.chase_filter(H, V, [deg] * nx, b_sup, mu1, mu_nn, precision=prec)
-        b.record(stream)
-        torch.cuda.synchronize()
-        clk = clocks.stop()
-        return a.elapsed_time(b) / 1e3 / reps, clk
-
+    V = V0.clone()
+    for _ in range(W):
+        chase.chase_filter(H, V, degs, b_sup, mu1, mu_nn, precision=split)
+    torch.cuda.synchronize()
+    # ---------------- timed region ----------------
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
     launches0 = chase.chase_kernel_launches()
-    t_split, clk = timed(chase.CHASE_SPLIT_BF16, m, args.steps)
+    chase.chase_kernel_timing(True)
+    clocks.start()
+    e0.record(stream)
+    for _ in range(K):
+        chase.chase_filter(H, V, degs, b_sup, mu1, mu_nn, precision=split)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    chase.chase_kernel_timing(False)
+    if world > 1:
+        torch.distributed.barrier()
     launches = chase.chase_kernel_launches() - launches0
-    fl = 8.0 * n * n * nx * m
-    t_fp64, _ = timed(chase.CHASE_FP64, 2, 1)
-    fl64 = 8.0 * n * n * nx * 2
+    kt = chase.chase_kernel_timing_read(chase.CHASE_TIMED_SPLIT_PRODUCT)
+    elapsed = e0.elapsed_time(e1) / 1e3
+    flops_step = 8.0 * n * n * nx * m
+    t_max, total_flops = combine_over_ranks(elapsed, flops_step * K, dev)
+    value = total_flops / t_max / 1e12
     pk, src = peaks()
-    split_tf = fl / t_split / 1e12
-    fp64_tf = fl64 / t_fp64 / 1e12
-    cfg = workload_config(args, world)
-    cfg["workload"] = (f"filter of degree {m} on N={n} x {nx} (nev={args.nev}, nex={args.nex}), "
-                       f"spectrum of the sequence workload; step = one filter call")
+
+    # roofline of the product kernel, from its own launches in the timed region
+    peak = pk.get("bf16_tflops_sustained", 1700.0)
+    per_launch_s = kt["seconds"] / max(kt["launches"], 1)
+    tensor_per_launch = kt["tensor_flops"] / max(kt["launches"], 1)
+    achieved = tensor_per_launch / per_launch_s / 1e12 if per_launch_s > 0 else 0.0
+    launches_per_product = kt["launches"] / max(K * m, 1)
+    k_per_launch = 2.0 * n / launches_per_product
+    alg_bytes = split_algorithmic_bytes(n, nx, k_per_launch)
+    roof = {
+        "bound": "tensor",
+        "kernel": "zgemm_split_kernel (tcgen05 BF16 slice products, exact int32 level sums, "
+                  "FP64 recurrence epilogue)",
+        "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
+        "frac": round(achieved / peak, 4),
+        "traffic": SPLIT_N30000_TRAFFIC,
+        "peak_source": f"{src} bf16_tflops_sustained (a kernel inside a multi-second loop)",
+        "achieved_counts": "BF16 tensor FLOPs the kernel executes: 28 slice-pair products of "
+                           "8 N^2 per complex column",
+        "fp64_equivalent_tflops": round(kt["flops"] / kt["seconds"] / 1e12, 3)
+        if kt["seconds"] > 0 else None,
+        "launches": kt["launches"], "avg_launch_ms": round(1e3 * per_launch_s, 3),
+        "algorithmic_bytes_per_launch": alg_bytes,
+        "timing": "CUDA events recorded by the library on the launching stream around the "
+                  "product launches of the timed steps (chase_kernel_timing)",
+    }
+
+    # ---------------- FP64 filter of the same block ----------------
+    fp64 = None
+    if not args.no_fp64_compare:
+        V64 = V0.clone()
+        chase.chase_filter(H, V64, torch.full((nx,), 2, dtype=torch.int32), b_sup, mu1, mu_nn,
+                           precision=chase.CHASE_FP64)  # warm-up: tile setup
+        V64.copy_(V0)
+        torch.cuda.synchronize()
+        chase.chase_kernel_timing(True)
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        chase.chase_filter(H, V64, torch.full((nx,), 2, dtype=torch.int32), b_sup, mu1, mu_nn,
+                           precision=chase.CHASE_FP64)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        chase.chase_kernel_timing(False)
+        k64 = chase.chase_kernel_timing_read(chase.CHASE_TIMED_FP64_PRODUCT)
+        t64 = c0.elapsed_time(c1) / 1e3
+        fl64 = 8.0 * n * n * nx * 2
+        fp64_peak = pk.get("bf16_tflops", 1900.0) * NOMINAL_FP64_OVER_BF16
+        ex = k64["tensor_flops"] / k64["seconds"] / 1e12 if k64["seconds"] > 0 else 0.0
+        fp64 = {"filter_tflops": round(fl64 / t64 / 1e12, 4),
+                "seconds_degree2": round(t64, 3),
+                "seconds_same_filter_extrapolated": round(t64 * m / 2.0, 1),
+                "speedup_split_vs_fp64_filter": round((flops_step * K / elapsed) / (fl64 / t64), 2),
+                "roofline": {"bound": "tensor",
+                             "kernel": "zgemm_tma_kernel (FP64 DMMA, 3M complex form)",
+                             "achieved": round(ex, 4), "peak": round(fp64_peak, 4),
+                             "unit": "TFLOP/s", "frac": round(ex / fp64_peak, 4),
+                             "achieved_counts": "executed DMMA FLOPs (6 of 8 algorithmic)",
+                             "peak_source": f"{src} bf16_tflops (burst) x nominal FP64/BF16 "
+                                            "ratio (1.25/2250)"}}
+        del V64
+
+    # ---------------- end to end through host buffers ----------------
+    e2e = None
+    Hh = None
+    if not args.no_e2e:
+        Hh = torch.empty((n, n), dtype=torch.complex128, pin_memory=True).t()
+        Hh.copy_(H)
+        Vh = torch.empty((nx, n), dtype=torch.complex128, pin_memory=True).t()
+        reps = max(1, min(K, 3))
+        chase.chase_filter(Hh, Vh.copy_(V0), degs, b_sup, mu1, mu_nn, precision=split)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            chase.chase_filter(Hh, Vh, degs, b_sup, mu1, mu_nn, precision=split)
+        torch.cuda.synchronize()
+        te = (time.perf_counter() - t0) / reps
+        e2e = {"value": round(flops_step / te / 1e12, 4), "unit": "TFLOP/s",
+               "h2d_bytes_per_step": int(16 * n * n + 16 * n * nx),
+               "d2h_bytes_per_step": int(16 * n * nx), "seconds": round(te, 3),
+               "steps": reps,
+               "how": "chase_filter with pinned host H and V: the library copies both in, "
+                      "filters, and copies V out, all inside the timed call"}
+        del Vh
+
+    # ---------------- one cold solve of the same problem ----------------
+    solve = None
+    if not args.no_solve:
+        de = args.solve_deg_extra if args.solve_deg_extra is not None else SPLIT_DEG_EXTRA
+        Vs = synth.gaussian_block(n, nx, seed + 11, device=dev)
+        S = synth.gaussian_block(n, 5, seed + 8, device=dev)
+        o = chase.chase_opts_default(precision=split, deg_extra=de)
+        chase.chase_kernel_timing(True)
+        torch.cuda.synchronize()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        st, ritz, res, ss = chase.chase_solve(H, nev, nex, args.tol, Vs, S, opts=o)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        chase.chase_kernel_timing(False)
+        ts = s0.elapsed_time(s1) / 1e3
+        k64s = chase.chase_kernel_timing_read(chase.CHASE_TIMED_FP64_PRODUCT)
+        # The FP64 solve takes the same iterations (every step but the filter
+        # product is the same FP64 code); its time is this solve's time with
+        # the filter replaced by the same FLOPs at the measured FP64 filter rate.
+        fp64_model = None
+        if fp64 is not None:
+            t_f64 = ss["flops_filter"] / (fp64["filter_tflops"] * 1e12)
+            fp64_model = {"seconds": round(ts - ss["t_filter"] + t_f64, 1),
+                          "speedup_split_vs_fp64": round((ts - ss["t_filter"] + t_f64) / ts, 2),
+                          "how": "split solve time - its filter time + its filter FLOPs at the "
+                                 "FP64 filter rate measured above (same iterations: every other "
+                                 "step is the same FP64 code)"}
+        solve = {"status": st, "seconds": round(ts, 2), "iterations": ss["iterations"],
+                 "deg_extra": de,
+                 "resid_max_over_norm": float(np.max(res[:nev])) / hnorm,
+                 "eig_err_max_over_norm": float(np.max(np.abs(ritz[:nev] - l[:nev]))) / hnorm,
+                 "phase_seconds": {k2: round(ss[k2], 2) for k2 in
+                                   ("t_lanczos", "t_filter", "t_qr", "t_rr", "t_eigh",
+                                    "t_rr_product")},
+                 "filter_tflops": round(ss["flops_filter"] / max(ss["t_filter"], 1e-12) / 1e12, 2),
+                 "rr_columns_total": int(round(ss["flops_rr_product"] / (8.0 * n * n))),
+                 "rr_fp64_product_tflops": round(k64s["flops"] / k64s["seconds"] / 1e12, 4)
+                 if k64s["seconds"] > 0 else None,
+                 "fp64_solve_modelled": fp64_model}
+        del Vs, S
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    cb = None
+    if not args.no_cpu_baseline and world == 1:
+        if Hh is None:
+            Hh = H.cpu()
+        smp = OracleFilterSample(Hh.numpy(), V0[:, :8].cpu().numpy(), l, nx, m)
+        cb = filter_cpu_baseline(smp, args.cpu_sample_seconds)
     line = {
-        "metric": METRIC, "value": round(split_tf, 3), "unit": "TFLOP/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t_split, 1),
+        "metric": METRIC, "value": round(value, 3), "unit": "TFLOP/s", "n_gpus": world,
+        "steps": K, "warmup": W, "ms_per_step": round(1e3 * t_max / K, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16-split+f64", "data": "synthetic", "config": cfg,
-        "fp64": {"filter_tflops": round(fp64_tf, 4), "seconds_degree2": round(t_fp64, 3),
-                 "seconds_same_filter_extrapolated": round(t_fp64 * m / 2.0, 1)},
-        "speedup_split_vs_fp64_filter": round(split_tf / fp64_tf, 1),
-        "roofline": {"bound": "tensor", "kernel": "zgemm_split_kernel",
-                     "achieved": round(SPLIT_PAIRS * split_tf, 2),
-                     "peak": pk.get("bf16_tflops_sustained", 1700.0), "unit": "TFLOP/s",
-                     "frac": round(SPLIT_PAIRS * split_tf / pk.get("bf16_tflops_sustained", 1700.0), 4),
-                     "traffic": None, "peak_source": f"{src} bf16_tflops_sustained",
-                     "fp64_equivalent_tflops": round(split_tf, 3)},
+        "dtype": "bf16-split+f64", "data": "synthetic",
+        "config": filter_workload_config(args, world),
+        "roofline": roof,
+        "fp64_filter": fp64,
+        "solve": solve,
+        "cpu_baseline": cb,
+        "e2e": e2e,
         "gpu_launches": int(launches), "clocks": clk,
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
 
 
 def run_batched_workload(args, rank, world, local):

@@ -171,6 +171,42 @@ const char* chase_last_error(void);
  * (all entry points, all threads).  Instrumentation; never fails. */
 long long chase_kernel_launches(void);
 
+/* Kernel timing, for benchmarks (the paper has no counterpart).  While
+ * timing is on, the library records a pair of CUDA events on the launching
+ * stream around the launches of its products with H:
+ *   CHASE_TIMED_SPLIT_PRODUCT  the split-BF16 tensor-core product kernel
+ *                              (zgemm_split_kernel; the slicing of the block
+ *                              and the K-segment combine are outside);
+ *   CHASE_TIMED_FP64_PRODUCT   the FP64 product with H of the filter and of
+ *                              Rayleigh-Ritz (DMMA tile kernel, or the
+ *                              few-column kernel for at most 6 columns).
+ * chase_kernel_timing(1) clears the record and starts; (0) stops.
+ * chase_kernel_timing_read waits for the recorded events of one kind and
+ * returns their summed duration (seconds), the kernel launches they cover,
+ * the algorithmic FLOPs (8 N^2 per complex column, 2 N^2 per real column)
+ * and the executed tensor FLOPs (split: slice pairs x algorithmic; FP64: 6
+ * of every 8 algorithmic complex FLOPs, the 3M form).  flops and
+ * tensor_flops are nullable.  Recording adds two event records per product
+ * call and no synchronisation.  Errors: CHASE_INVALID_ARG, CHASE_CUDA_ERROR. */
+/* Failure detection (the paper has no counterpart): every wait of the
+ * library's pipelined kernels on an mbarrier (TMA stages, MMA completion,
+ * flush handshakes) gives up after a cycle budget (about one second), sets
+ * a device error flag and lets the kernel return, so that a stuck pipeline
+ * ends as CHASE_TIMEOUT with a usable context instead of a hung GPU.  This
+ * call runs that wait alone: one thread waits on an mbarrier that nothing
+ * arrives at, for budget_cycles SM cycles (0 .. 2e9), with no copy or MMA
+ * in flight, and the call returns the status the host derives from the
+ * flag: CHASE_TIMEOUT.  Errors: CHASE_INVALID_ARG (budget out of range),
+ * CHASE_CUDA_ERROR. */
+int chase_wait_selftest(long long budget_cycles, void* stream);
+
+#define CHASE_TIMED_SPLIT_PRODUCT 0
+#define CHASE_TIMED_FP64_PRODUCT 1
+#define CHASE_TIMED_KINDS 2
+int chase_kernel_timing(int enable);
+int chase_kernel_timing_read(int kind, double* seconds, long long* launches, double* flops,
+                             double* tensor_flops);
+
 /* Chebyshev filter with per-column degrees: Alg. 4 with the three-term
  * recurrence of Eq. 7, c = (b_sup + mu_nevnex)/2, e = (b_sup - mu_nevnex)/2,
  * sigma_1 = e / (mu1 - c).  Column a of V is replaced by p_{m_a}(H) v_a with

@@ -19,7 +19,8 @@ import torch
 
 __all__ = [
     "ChaseError", "ChaseOpts", "ChaseStats", "lib", "lib_path", "declared_symbols",
-    "chase_opts_default", "chase_last_error", "chase_kernel_launches", "chase_filter", "chase_lanczos",
+    "chase_opts_default", "chase_last_error", "chase_kernel_launches", "chase_kernel_timing",
+    "chase_kernel_timing_read", "chase_wait_selftest", "CHASE_TIMED_SPLIT_PRODUCT", "CHASE_TIMED_FP64_PRODUCT", "chase_filter", "chase_lanczos",
     "chase_degrees", "chase_lock", "chase_tridiag_eigh", "chase_dos_estimate", "chase_orthonormalize",
     "chase_rayleigh_ritz", "chase_residuals", "chase_residuals_noalloc", "chase_solve",
     "CHASE_OK", "CHASE_INVALID_ARG", "CHASE_NOT_CONVERGED", "CHASE_QR_BREAKDOWN",
@@ -114,6 +115,9 @@ _SIGNATURES = {
     "chase_opts_default": (_int, [ctypes.POINTER(ChaseOpts)]),
     "chase_last_error": (ctypes.c_char_p, []),
     "chase_kernel_launches": (ctypes.c_longlong, []),
+    "chase_kernel_timing": (_int, [_int]),
+    "chase_wait_selftest": (_int, [ctypes.c_longlong, _c_p]),
+    "chase_kernel_timing_read": (_int, [_int, _dp, ctypes.POINTER(ctypes.c_longlong), _dp, _dp]),
     "chase_filter": (_int, [_c_p, _i64, _i64, _c_p, _i64, _int, _c_p, _dbl, _dbl, _dbl, _int, _c_p,
                             _c_p]),
     "chase_filter_batched": (_int, [_int, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p,
@@ -182,6 +186,35 @@ def declared_symbols(header: str = _HEADER) -> list[str]:
 
 def chase_kernel_launches() -> int:
     return int(lib().chase_kernel_launches())
+
+
+CHASE_TIMED_SPLIT_PRODUCT = 0
+CHASE_TIMED_FP64_PRODUCT = 1
+
+
+def chase_kernel_timing(enable: bool) -> None:
+    """Start (clearing the record) or stop the library's product-kernel timing."""
+    _check(lib().chase_kernel_timing(1 if enable else 0), "chase_kernel_timing")
+
+
+def chase_kernel_timing_read(kind: int) -> dict:
+    """Summed CUDA-event time, launches and FLOPs of the recorded product
+    launches of one kind (CHASE_TIMED_SPLIT_PRODUCT or _FP64_PRODUCT)."""
+    s, f, tf = np.zeros(1), np.zeros(1), np.zeros(1)
+    n = ctypes.c_longlong(0)
+    _check(lib().chase_kernel_timing_read(int(kind), _dptr(s), ctypes.byref(n), _dptr(f), _dptr(tf)),
+           "chase_kernel_timing_read")
+    return {"seconds": float(s[0]), "launches": int(n.value), "flops": float(f[0]),
+            "tensor_flops": float(tf[0])}
+
+
+def chase_wait_selftest(budget_cycles: int, stream=None) -> int:
+    """Run the kernels' bounded mbarrier wait on a barrier nothing arrives
+    at; returns the status (CHASE_TIMEOUT when the wait gave up)."""
+    s = ctypes.c_void_p(0 if stream is None else int(stream))
+    if stream is None and torch.cuda.is_available():
+        s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return int(lib().chase_wait_selftest(int(budget_cycles), s))
 
 
 def chase_last_error() -> str:

@@ -111,6 +111,22 @@ struct PhaseTimer {
   }
 };
 
+// A product with H on the FP64 path, recorded for
+// chase_kernel_timing as one launch.  Executed FLOPs: the DMMA tile kernel
+// forms complex products in the 3M form (6 of 8 real FLOPs); the few-column
+// kernel and real products execute all of them.
+template <class T>
+int timed_h_product(Dev& d, const T* H, int64_t N, int64_t ldh, const T* X, int64_t ldx, int b,
+                    T* Y, int64_t ldy, int j0, double alpha, double beta, double shift) {
+  if constexpr (is_single<T>) return gemm(d, N, N, H, ldh, X, ldx, b, Y, ldy, j0, b, alpha, beta, shift);
+  KernelTimer kt(d.st, CHASE_TIMED_FP64_PRODUCT);
+  CHASE_TRY(gemm(d, N, N, H, ldh, X, ldx, b, Y, ldy, j0, b, alpha, beta, shift));
+  const int w = b - j0;
+  const double alg = (is_cplx<T> ? 8.0 : 2.0) * static_cast<double>(N) * static_cast<double>(N) * w;
+  kt.end(w > 0 ? 1 : 0, alg, is_cplx<T> && w > kFewColMax ? 0.75 * alg : alg);
+  return CHASE_OK;
+}
+
 // Alg. 4 on a block whose columns are sorted by ascending degree.
 // X (N x b, ldx) holds the input and receives the output; Wk (N x b, ldw)
 // is the second buffer of the double buffering.  start[i] = number of
@@ -125,7 +141,7 @@ int filter_product(Dev& d, const T* H, int64_t N, int64_t ldh, const SplitH* sh,
   if constexpr (!is_single<T>) {
     if (sh) return zgemm_split(d, *sh, *sx, X, ldx, j0, b, Y, ldy, alpha, beta, shift, nslices);
   }
-  return gemm(d, N, N, H, ldh, X, ldx, b, Y, ldy, j0, b, alpha, beta, shift);
+  return timed_h_product(d, H, N, ldh, X, ldx, b, Y, ldy, j0, alpha, beta, shift);
 }
 
 template <class T>
@@ -314,7 +330,7 @@ int rr_core(Dev& d, const T* H, int64_t N, int64_t ldh, T* Q, int64_t ldq, int b
       on_split = true;
     }
   }
-  if (!on_split) CHASE_TRY(gemm(d, N, N, H, ldh, Q, ldq, b, w.HQ, lN, 0, b, 1.0, 0.0, 0.0));
+  if (!on_split) CHASE_TRY(timed_h_product(d, H, N, ldh, Q, ldq, b, w.HQ, lN, 0, 1.0, 0.0, 0.0));
   if (t_hq) tq.end();
   // G = Q^H H Q is Hermitian up to rounding: form its lower triangle (the one
   // the eigensolver reads) and take the upper one from it
@@ -485,6 +501,30 @@ bool ld_ok(int64_t ld, int64_t n) { return ld >= std::max<int64_t>(1, n); }
 // line 1-2), then per iteration begin_iteration (line 3 and the bound
 // check), the filter (line 4), after_filter (lines 5-15), and finally
 // finish (ascending output).
+// Inputs must be finite: a NaN or Inf in H or a block would otherwise run
+// through every step and surface, if at all, as a breakdown far from its
+// cause.  One pass of the column-norm kernel per array (a norm that
+// overflows, |entries| above about 1e154, is rejected too); `what` names
+// the array in the message.
+template <class T>
+int check_finite(Dev& d, const T* X, int64_t ld, int64_t rows, int64_t cols, const char* where,
+                 const char* what) {
+  if (rows == 0 || cols == 0) return CHASE_OK;
+  double* nrm = nullptr;
+  CHASE_TRY(d.alloc(&nrm, static_cast<size_t>(cols)));
+  CHASE_TRY(launch_col_norms(d, X, ld, rows, static_cast<int>(cols), nrm));
+  std::vector<double> h(static_cast<size_t>(cols));
+  CHASE_CUDA(cudaMemcpyAsync(h.data(), nrm, sizeof(double) * cols, cudaMemcpyDeviceToHost, d.st));
+  CHASE_TRY(d.sync_check(where));
+  for (int64_t j = 0; j < cols; ++j)
+    if (!std::isfinite(h[static_cast<size_t>(j)])) {
+      set_error("%s: %s holds a non-finite entry (or one beyond 1e154) in column %lld", where,
+                what, static_cast<long long>(j));
+      return CHASE_INVALID_ARG;
+    }
+  return CHASE_OK;
+}
+
 template <class T>
 struct Solver {
   // arguments
@@ -550,6 +590,9 @@ struct Solver {
     }
     CHASE_TRY(stage_in(d, dev, V, ldv, N, nx, &dV, &lv));
     CHASE_TRY(stage_in(d, dev, starts, N, N, r, &dS, &ls));
+    CHASE_TRY(check_finite(d, dH, lh, N, N, "chase_solve", "H"));
+    CHASE_TRY(check_finite(d, dV, lv, N, nx, "chase_solve", "V"));
+    CHASE_TRY(check_finite(d, dS, ls, N, r, "chase_solve", "lanczos_starts"));
     lw = ld_pad<T>(N);
     CHASE_TRY(d.alloc(&Wk, static_cast<size_t>(lw) * nx));  // filter double buffer / permutation scratch
     CHASE_TRY(orth_alloc(d, N, nx, nx, ow));
@@ -590,7 +633,16 @@ struct Solver {
     S.lanczos_matvecs += lz.matvecs;
     S.flops_total += kMv * N2 * lz.matvecs;
     b_sup = lz.b_sup;
+    if (!std::isfinite(lz.b_sup) || (!o.approx && !(std::isfinite(lz.mu1) && std::isfinite(lz.mu_nn)))) {
+      set_error("chase_solve: the Lanczos bounds are not finite (b_sup=%g)", lz.b_sup);
+      return CHASE_BOUND_VIOLATION;
+    }
     if (o.approx) {
+      for (int a = 0; a < nx; ++a)
+        if (!std::isfinite(Lambda[a])) {
+          set_error("chase_solve: Lambda[%d] is not finite (approx = 1 reads it)", a);
+          return CHASE_INVALID_ARG;
+        }
       mu1 = *std::min_element(Lambda, Lambda + nx);
       mu_nn = *std::max_element(Lambda, Lambda + nx);
     } else {
@@ -978,6 +1030,8 @@ int filter_impl(const T* H, int64_t N, int64_t ldh, T* V, int64_t ldv, int b, co
   int64_t lh = 0, lv = 0;
   CHASE_TRY(stage_in(d, dev, H, ldh, N, N, &dH, &lh));
   CHASE_TRY(stage_in(d, dev, V, ldv, N, b, &dV, &lv));
+  CHASE_TRY(check_finite(d, dH, lh, N, N, "chase_filter", "H"));
+  CHASE_TRY(check_finite(d, dV, lv, N, b, "chase_filter", "V"));
   // the workspace (leading dimension ld_pad(N)) must suit the TMA products
   const int64_t lw = ld_pad<T>(N);
   T* wk = dev && lw == N ? work : nullptr;

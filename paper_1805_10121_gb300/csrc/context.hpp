@@ -34,6 +34,25 @@ struct Dev {
 
 bool is_device_ptr(const void* p);
 
+// Records a CUDA event pair on stream `s` around product launches while
+// chase_kernel_timing is on (a no-op otherwise).  end() gives the launches
+// the range covered and their algorithmic (FP64-equivalent) and executed
+// tensor FLOPs; a timer destroyed without end() records nothing.
+class KernelTimer {
+ public:
+  KernelTimer(cudaStream_t s, int kind);
+  ~KernelTimer();
+  KernelTimer(const KernelTimer&) = delete;
+  KernelTimer& operator=(const KernelTimer&) = delete;
+  void end(long long launches, double flops, double tensor_flops);
+
+ private:
+  cudaStream_t st_;
+  int kind_;
+  cudaEvent_t a_ = nullptr, b_ = nullptr;
+  bool active_ = false;
+};
+
 // 2-D copies of column-major complex128 blocks (rows x cols).
 int copy_block(Dev& d, chase_c64* dst, int64_t ldd, const chase_c64* src, int64_t lds, int64_t rows,
                int64_t cols, cudaMemcpyKind kind);

@@ -1185,3 +1185,35 @@ int eigh_device(Dev& d, chase_c64* G, int64_t ldg, int p, double* w_dev) {
 }
 
 }  // namespace chase
+
+// ---------------------------------------------------------------------------
+// Failure detection: the bounded wait of the pipelined kernels, on its own
+// ---------------------------------------------------------------------------
+namespace chase {
+namespace {
+// One thread waits on an mbarrier that nothing ever arrives at, for at most
+// `budget` cycles, then records the timeout flag exactly as the product
+// kernels' producers and consumers do.  No copy or MMA is in flight.
+__global__ void wait_selftest_kernel(long long budget, int* __restrict__ err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  fence_barrier_init();
+  if (!mbar_wait_bounded(&bar, 0, budget)) atomicOr(err, KERR_TIMEOUT_FULL);
+}
+}  // namespace
+}  // namespace chase
+
+extern "C" int chase_wait_selftest(long long budget_cycles, void* stream) {
+  if (budget_cycles < 0 || budget_cycles > chase::kWaitBudgetCycles) {
+    chase::set_error("chase_wait_selftest: budget must be in [0, %lld] cycles",
+                     chase::kWaitBudgetCycles);
+    return CHASE_INVALID_ARG;
+  }
+  chase::Dev d(stream);
+  CHASE_TRY(d.init());
+  chase::wait_selftest_kernel<<<1, 32, 0, d.st>>>(budget_cycles, d.err);
+  chase::note_launch();
+  CHASE_CUDA(cudaGetLastError());
+  return d.sync_check("chase_wait_selftest");
+}

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 #include "context.hpp"
@@ -224,7 +225,94 @@ int copy_block(Dev& d, float* dst, int64_t ldd, const float* src, int64_t lds, i
   return copy_block_bytes(d, dst, ldd, src, lds, rows, cols, sizeof(float), kind);
 }
 
+// ---------------------------------------------------------------------------
+// Kernel timing for benchmarks: event pairs on the launching stream around
+// the product launches, read back (and destroyed) by chase_kernel_timing_read
+// ---------------------------------------------------------------------------
+namespace {
+struct TimedRange {
+  int kind;
+  cudaEvent_t a, b;
+  long long launches;
+  double flops, tensor_flops;
+};
+std::mutex g_timing_mu;
+std::atomic<bool> g_timing_on{false};
+std::vector<TimedRange> g_timed;
+
+void clear_timed_locked() {
+  for (auto& r : g_timed) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  g_timed.clear();
+}
+}  // namespace
+
+KernelTimer::KernelTimer(cudaStream_t s, int kind) : st_(s), kind_(kind) {
+  if (!g_timing_on.load(std::memory_order_relaxed)) return;
+  if (cudaEventCreate(&a_) != cudaSuccess || cudaEventCreate(&b_) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  active_ = cudaEventRecord(a_, st_) == cudaSuccess;
+}
+
+void KernelTimer::end(long long launches, double flops, double tensor_flops) {
+  if (!active_) return;
+  active_ = false;
+  if (cudaEventRecord(b_, st_) != cudaSuccess) {
+    cudaGetLastError();
+    cudaEventDestroy(a_);
+    cudaEventDestroy(b_);
+    return;
+  }
+  std::lock_guard<std::mutex> lk(g_timing_mu);
+  g_timed.push_back({kind_, a_, b_, launches, flops, tensor_flops});
+}
+
+KernelTimer::~KernelTimer() {
+  if (active_) {  // left by an error path: discard
+    cudaEventDestroy(a_);
+    cudaEventDestroy(b_);
+  }
+}
+
 }  // namespace chase
+
+extern "C" int chase_kernel_timing(int enable) {
+  std::lock_guard<std::mutex> lk(chase::g_timing_mu);
+  if (enable) chase::clear_timed_locked();
+  chase::g_timing_on.store(enable != 0, std::memory_order_relaxed);
+  return CHASE_OK;
+}
+
+extern "C" int chase_kernel_timing_read(int kind, double* seconds, long long* launches,
+                                        double* flops, double* tensor_flops) {
+  if (kind < 0 || kind >= CHASE_TIMED_KINDS || !seconds || !launches) {
+    chase::set_error("chase_kernel_timing_read: invalid argument");
+    return CHASE_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lk(chase::g_timing_mu);
+  double s = 0.0, f = 0.0, tf = 0.0;
+  long long n = 0;
+  for (auto& r : chase::g_timed) {
+    if (r.kind != kind) continue;
+    if (cudaEventSynchronize(r.b) != cudaSuccess) return chase::cuda_status(cudaGetLastError(), "chase_kernel_timing_read");
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess)
+      return chase::cuda_status(cudaGetLastError(), "chase_kernel_timing_read");
+    s += 1e-3 * ms;
+    n += r.launches;
+    f += r.flops;
+    tf += r.tensor_flops;
+  }
+  *seconds = s;
+  *launches = n;
+  if (flops) *flops = f;
+  if (tensor_flops) *tensor_flops = tf;
+  return CHASE_OK;
+}
 
 extern "C" const char* chase_last_error(void) { return chase::g_err; }
 

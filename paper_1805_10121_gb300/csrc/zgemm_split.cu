@@ -969,12 +969,18 @@ int split_product_ns(Dev& d, const SplitH& h, SplitX& x, const E* X, int64_t ldx
   const int nseg = segments_for(nkb, ctiles * rtiles);
   const double2* Xd = reinterpret_cast<const double2*>(X);
   double2* Cd = reinterpret_cast<double2*>(C);
+  // algorithmic FLOPs (8 N^2 per complex column, 2 N^2 per real one) and the
+  // BF16 tensor FLOPs of the NS (NS + 1) / 2 slice pairs
+  const double alg = (cplx ? 8.0 : 2.0) * static_cast<double>(N) * static_cast<double>(N) * ncols;
+  const double pairs = NS * (NS + 1) / 2.0;
   if (nseg == 1) {
+    KernelTimer kt(d.st, CHASE_TIMED_SPLIT_PRODUCT);
     split::zgemm_split_kernel<NS><<<grid, split::kThreads, SC::SMEM, d.st>>>(
         tmA, tmB, h.E, x.F, h.Dg, static_cast<int>(N), 0, nkb, ncols, j0, Xd, ldx, Cd, ldc, alpha,
         beta, shift, nullptr, 0, cplx ? 1 : 0, d.err);
     note_launch();
     CHASE_CUDA(cudaGetLastError());
+    kt.end(1, alg, pairs * alg);
     return CHASE_OK;
   }
   // K segments write raw partial products; the combine kernel sums them and
@@ -990,6 +996,8 @@ int split_product_ns(Dev& d, const SplitH& h, SplitX& x, const E* X, int64_t ldx
   E* P = static_cast<E*>(x.P);
   int per = (nkb + nseg - 1) / nseg;
   per = (per + split::KPS - 1) / split::KPS * split::KPS;  // segments start on stage boundaries
+  KernelTimer kt(d.st, CHASE_TIMED_SPLIT_PRODUCT);
+  int launched = 0;
   for (int g = 0; g < nseg; ++g) {
     const int kb0 = g * per;
     const int cnt = std::min(per, nkb - kb0);
@@ -999,7 +1007,9 @@ int split_product_ns(Dev& d, const SplitH& h, SplitX& x, const E* X, int64_t ldx
         alpha, beta, shift, reinterpret_cast<double2*>(P + g * pstride), N, cplx ? 1 : 0, d.err);
     note_launch();
     CHASE_CUDA(cudaGetLastError());
+    ++launched;
   }
+  kt.end(launched, alg, pairs * alg);
   const long long total = pstride;
   const unsigned blocks = static_cast<unsigned>(std::min<long long>((total + 255) / 256, 152 * 16));
   split::split_combine_kernel<E><<<blocks, 256, 0, d.st>>>(P, nseg, pstride, N, h.Dg, X, ldx, j0,

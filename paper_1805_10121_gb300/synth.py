@@ -111,29 +111,47 @@ def hermitian_from(q: torch.Tensor, lam: torch.Tensor) -> torch.Tensor:
     return h.t().contiguous().t()
 
 
-def hermitian_dft(lam: torch.Tensor, seed: int) -> torch.Tensor:
+def hermitian_dft(lam: torch.Tensor, seed: int, chunk: int = 2048) -> torch.Tensor:
     """``Q diag(lam) Q^H`` for the unitary ``Q = D1 F D2 F D3`` of
     ``unitary_dft(n, seed)`` without forming Q: ``D3 diag(lam) D3^H`` is
     ``diag(lam)``, ``F diag(lam) F^H`` is circulant with first column
     ``fft(lam) / n``, and the remaining factors are FFTs along the two axes
-    and phase scalings.  O(n^2 log n); column-major full storage."""
+    and phase scalings.  O(n^2 log n); column-major full storage.  Works in
+    place on one n x n buffer, ``chunk`` columns or rows at a time, so that
+    n = 30000 (14.4 GB) also builds in host memory."""
     n = lam.numel()
     device = lam.device
     g = generator(seed, device)
     ph = torch.rand(3, n, dtype=torch.float64, device=device, generator=g) * (2.0 * math.pi)
     d = torch.polar(torch.ones_like(ph), ph)
     c = torch.fft.fft(lam.to(torch.complex128)) / n           # circulant column
-    idx = (torch.arange(n, device=device)[:, None] - torch.arange(n, device=device)[None, :]) % n
-    t = c[idx]                                                 # F diag(lam) F^H
-    del idx
-    t.mul_(d[1][:, None]).mul_(d[1].conj()[None, :])           # D2 . D2^H
-    t = torch.fft.fft(t, dim=0, norm="ortho")                  # F .
-    t = torch.fft.ifft(t, dim=1, norm="ortho")                 # . F^H
-    t.mul_(d[0][:, None]).mul_(d[0].conj()[None, :])           # D1 . D1^H
-    h = t.t().conj()
-    h = 0.5 * (t + h)
-    del t
-    return h.t().contiguous().t()
+    t = torch.empty((n, n), dtype=torch.complex128, device=device)
+    rows = torch.arange(n, device=device)
+    for j0 in range(0, n, chunk):                              # F diag(lam) F^H, D2 . D2^H, F .
+        j1 = min(n, j0 + chunk)
+        blk = c[(rows[:, None] - rows[None, j0:j1]) % n]
+        blk.mul_(d[1][:, None]).mul_(d[1][j0:j1].conj()[None, :])
+        t[:, j0:j1] = torch.fft.fft(blk, dim=0, norm="ortho")
+        del blk
+    for i0 in range(0, n, chunk):                              # . F^H, D1 . D1^H
+        i1 = min(n, i0 + chunk)
+        blk = torch.fft.ifft(t[i0:i1, :], dim=1, norm="ortho")
+        blk.mul_(d[0][i0:i1, None]).mul_(d[0].conj()[None, :])
+        t[i0:i1, :] = blk
+        del blk
+    # Hermitian part, tile pair by tile pair: t <- (t + t^H) / 2
+    for i0 in range(0, n, chunk):
+        i1 = min(n, i0 + chunk)
+        for j0 in range(i0, n, chunk):
+            j1 = min(n, j0 + chunk)
+            a = t[i0:i1, j0:j1].clone()
+            b = t[j0:j1, i0:i1].clone()
+            t[i0:i1, j0:j1] = 0.5 * (a + b.conj().t())
+            t[j0:j1, i0:i1] = 0.5 * (b + a.conj().t())
+            del a, b
+    # column-major storage of a Hermitian h is the row-major storage of conj(h)
+    t.conj_physical_()
+    return t.t()
 
 
 def hermitian_noise(n: int, seed: int, device="cpu") -> torch.Tensor:

@@ -139,3 +139,9 @@ def test_dos_estimate_invalid_arguments(lib):
     assert ei.value.status == chase.CHASE_INVALID_ARG
     with pytest.raises(chase.ChaseError):
         chase.chase_dos_estimate([([0.0], [1.0])], 0.5, 2.0, 1.0)
+
+
+def test_wait_selftest_rejects_a_budget_out_of_range(lib):
+    # validated before any device work, so this runs without a GPU
+    assert chase.chase_wait_selftest(-1) == chase.CHASE_INVALID_ARG
+    assert chase.chase_wait_selftest(3_000_000_000) == chase.CHASE_INVALID_ARG

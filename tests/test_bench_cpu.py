@@ -9,9 +9,13 @@ import sys
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def test_reference_arm_prints_one_contract_line():
+import pytest
+
+
+@pytest.mark.parametrize("workload", ["filter", "sequence"])
+def test_reference_arm_prints_one_contract_line(workload):
     cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--n", "300",
-           "--nev", "20", "--nex", "10", "--steps", "1", "--warmup", "3"]
+           "--nev", "20", "--nex", "10", "--steps", "1", "--warmup", "3", "--workload", workload]
     out = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=300, check=True)
     lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1
@@ -27,3 +31,4 @@ def test_reference_arm_prints_one_contract_line():
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
     assert "workload" in d["config"]
+    assert ("8 of the columns" in cb["sample"]) == (workload == "filter")

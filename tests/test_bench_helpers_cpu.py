@@ -65,3 +65,26 @@ def test_deg_extra_defaults():
     assert bench.deg_extra_for(args, chase.CHASE_FP64) == 2
     assert bench.deg_extra_for(args, chase.CHASE_SPLIT_BF16) == bench.SPLIT_DEG_EXTRA
     assert bench.deg_extra_for(types.SimpleNamespace(deg_extra=4), chase.CHASE_FP64) == 4
+
+
+def test_split_algorithmic_bytes_per_launch():
+    # one K segment of the N = 30000 filter: 7 slice planes of H (30000 rows)
+    # and of the block (3000 real rows) over K = 30000, and the FP64 result
+    n, b, k = 30000, 1500, 30000
+    got = bench.split_algorithmic_bytes(n, b, k)
+    assert got == pytest.approx(7 * 2 * (30000 + 3000) * 30000 + 16 * 30000 * 1500)
+
+
+def test_blas_threads_round_trip():
+    import numpy as np
+    a = np.ones((64, 64))
+    a @ a  # load the BLAS
+    bt = bench.BlasThreads(1)
+    if not bt.ok:
+        pytest.skip("no OpenBLAS thread control in this NumPy")
+    before = int(bt.get_fn()) if bt.get_fn else None
+    with bt:
+        if bt.get_fn:
+            assert int(bt.get_fn()) == 1
+    if bt.get_fn:
+        assert int(bt.get_fn()) == before
