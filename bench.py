@@ -104,6 +104,27 @@ def parse():
     return args
 
 
+def build_library():
+    """Build (or find current) libchase.so; returns what the build did, for
+    the JSON line: whether nvcc compiled anything in this process and the
+    digest of the sources the library was built from."""
+    from paper_1805_10121_gb300 import build
+    build.build()
+    info = dict(build.last_build)
+    return {"nvcc_ran": bool(info["compiled"]) or bool(info["linked"]),
+            "compiled": len(info["compiled"]), "sources_sha256": info["sources_sha256"][:16]}
+
+
+BUILD_INFO = None
+
+
+def emit(line):
+    """Print the JSON line (with the build record of this process)."""
+    if BUILD_INFO is not None:
+        line["build"] = BUILD_INFO
+    print(json.dumps(line), flush=True)
+
+
 def combine_over_ranks(elapsed, flops, device):
     """Whole-job figures of replicas: the slowest rank's time and the FLOPs of
     all ranks (the identity without a process group)."""
@@ -788,7 +809,7 @@ def run_filter_workload(args, rank, world, local):
         "e2e": e2e,
         "gpu_launches": int(launches), "clocks": clk,
     }
-    print(json.dumps(line), flush=True)
+    emit(line)
     if world > 1:
         torch.distributed.destroy_process_group()
 
@@ -939,7 +960,7 @@ def run_batched_workload(args, rank, world, local):
         "gpu_launches": int(launches), "clocks": clk,
     }
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        emit(line)
 
 
 def run_batched_solve_workload(args, rank, world, local):
@@ -1036,7 +1057,7 @@ def run_batched_solve_workload(args, rank, world, local):
         "gpu_launches": int(launches), "clocks": clk,
     }
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        emit(line)
 
 
 def batched_cpu_baseline(shapes, degs, seed, budget_s):
@@ -1126,7 +1147,7 @@ def run_degree_sweep(args, rank, world, local):
         "gpu_launches": int(chase.chase_kernel_launches() - launches0), "clocks": clk,
     }
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        emit(line)
 
 
 def run_side_workload(args, rank, world, local):
@@ -1212,7 +1233,7 @@ def run_side_workload(args, rank, world, local):
         "gpu_launches": int(launches), "clocks": clk,
     }
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        emit(line)
 
 
 def run_variants_workload(args, rank, world, local):
@@ -1314,7 +1335,7 @@ def run_variants_workload(args, rank, world, local):
         "gpu_launches": int(chase.chase_kernel_launches() - launches0), "clocks": clk,
     }
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        emit(line)
 
 
 def run_solve_workload(args, rank, world, local):
@@ -1393,7 +1414,7 @@ def run_solve_workload(args, rank, world, local):
         "gpu_launches": int(chase.chase_kernel_launches() - launches0), "clocks": clk,
     }
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        emit(line)
 
 
 def run_serve_workload(args, rank, world, local):
@@ -1455,15 +1476,17 @@ def run_serve_workload(args, rank, world, local):
         "gpu_launches": int(chase.chase_kernel_launches() - launches0), "clocks": clk,
     }
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        emit(line)
 
 
 def main():
+    global BUILD_INFO
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
+    BUILD_INFO = build_library()
     if args.workload == "filter":
         run_filter_workload(args, rank, world, local)
         return
@@ -1664,7 +1687,7 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clk,
     }
-    print(json.dumps(line), flush=True)
+    emit(line)
     if world > 1:
         torch.distributed.destroy_process_group()
 

@@ -171,6 +171,11 @@ const char* chase_last_error(void);
  * (all entry points, all threads).  Instrumentation; never fails. */
 long long chase_kernel_launches(void);
 
+/* Number of device memory allocations (stream-ordered workspace and error
+ * flags) this library has requested in the process so far, all threads.
+ * Instrumentation (the paper has no counterpart); never fails. */
+long long chase_device_allocations(void);
+
 /* Kernel timing, for benchmarks (the paper has no counterpart).  While
  * timing is on, the library records a pair of CUDA events on the launching
  * stream around the launches of its products with H:
@@ -344,10 +349,13 @@ int chase_residuals(const chase_c64* H, int64_t N, int64_t ldh, const chase_c64*
  * until the process exits: requires N * b <= 2097152, else
  * CHASE_INVALID_ARG.  Calls no cudaMalloc / cudaFree.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress); make
- * that first call before any stream capture.  All calls share the array:
- * calls whose work overlaps on the GPU race.
- * Errors: CHASE_INVALID_ARG (sizes, non-device arrays), CHASE_CUDA_ERROR,
- * CHASE_TIMEOUT. */
+ * that first call before any stream capture.  The address is cached for the
+ * life of the process: after a cudaDeviceReset by the application it is
+ * stale, and this entry point must not be called again on that device.  All
+ * calls share the array: calls whose work overlaps on the GPU race.  H, V,
+ * lambda and resid must live on the current device.
+ * Errors: CHASE_INVALID_ARG (sizes, non-device arrays, arrays on another
+ * device than the current one), CHASE_CUDA_ERROR, CHASE_TIMEOUT. */
 int chase_residuals_noalloc(const chase_c64* H, int64_t N, int64_t ldh, const chase_c64* V,
                             int64_t ldv, int b, const double* lambda, double* resid, void* stream);
 

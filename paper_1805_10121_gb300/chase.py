@@ -9,6 +9,7 @@ library has not been built.
 
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import re
@@ -19,7 +20,8 @@ import torch
 
 __all__ = [
     "ChaseError", "ChaseOpts", "ChaseStats", "lib", "lib_path", "declared_symbols",
-    "chase_opts_default", "chase_last_error", "chase_kernel_launches", "chase_kernel_timing",
+    "chase_opts_default", "chase_last_error", "chase_kernel_launches", "chase_device_allocations",
+    "chase_kernel_timing",
     "chase_kernel_timing_read", "chase_wait_selftest", "CHASE_TIMED_SPLIT_PRODUCT", "CHASE_TIMED_FP64_PRODUCT", "chase_filter", "chase_lanczos",
     "chase_degrees", "chase_lock", "chase_tridiag_eigh", "chase_dos_estimate", "chase_orthonormalize",
     "chase_rayleigh_ritz", "chase_residuals", "chase_residuals_noalloc", "chase_solve",
@@ -115,6 +117,7 @@ _SIGNATURES = {
     "chase_opts_default": (_int, [ctypes.POINTER(ChaseOpts)]),
     "chase_last_error": (ctypes.c_char_p, []),
     "chase_kernel_launches": (ctypes.c_longlong, []),
+    "chase_device_allocations": (ctypes.c_longlong, []),
     "chase_kernel_timing": (_int, [_int]),
     "chase_wait_selftest": (_int, [ctypes.c_longlong, _c_p]),
     "chase_kernel_timing_read": (_int, [_int, _dp, ctypes.POINTER(ctypes.c_longlong), _dp, _dp]),
@@ -186,6 +189,10 @@ def declared_symbols(header: str = _HEADER) -> list[str]:
 
 def chase_kernel_launches() -> int:
     return int(lib().chase_kernel_launches())
+
+
+def chase_device_allocations() -> int:
+    return int(lib().chase_device_allocations())
 
 
 CHASE_TIMED_SPLIT_PRODUCT = 0
@@ -542,9 +549,14 @@ def chase_residuals_noalloc(H, V, lam, resid, stream=None):
     for t, name in ((lam, "lam"), (resid, "resid")):
         if t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != b:
             raise ValueError(f"{name} must be a contiguous float64 tensor of {b} values")
-    _check(lib().chase_residuals_noalloc(hp, n, ldh, vp, ldv, b, ctypes.c_void_p(lam.data_ptr()),
-                                         ctypes.c_void_p(resid.data_ptr()), _stream(V, stream)),
-           "chase_residuals_noalloc")
+    if any(t.device != V.device for t in (H, lam, resid)):
+        raise ValueError("H, V, lam and resid must be on one device")
+    ctx = torch.cuda.device(V.device) if V.is_cuda else contextlib.nullcontext()
+    with ctx:
+        _check(lib().chase_residuals_noalloc(hp, n, ldh, vp, ldv, b,
+                                             ctypes.c_void_p(lam.data_ptr()),
+                                             ctypes.c_void_p(resid.data_ptr()), _stream(V, stream)),
+               "chase_residuals_noalloc")
     return resid
 
 

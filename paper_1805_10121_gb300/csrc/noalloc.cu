@@ -18,7 +18,10 @@
 // keeps the last call's contents: the error flag is cleared on every call,
 // and the H V staging area is fully overwritten before it is read.  Calls
 // whose work overlaps on the GPU (different streams, or different host
-// threads on one device) race on the array.
+// threads on one device) race on the array.  The cached address assumes the
+// device's context lives as long as the process: after a cudaDeviceReset by
+// the application it is stale, so this entry point must not be used again
+// on that device in that process.
 #include <mutex>
 
 #include "common.cuh"
@@ -77,15 +80,32 @@ extern "C" int chase_residuals_noalloc(const chase_c64* H, int64_t N, int64_t ld
     return CHASE_INVALID_ARG;
   }
   if (N == 0 || b == 0) return CHASE_OK;
-  if (static_cast<size_t>(N) * static_cast<size_t>(b) > kNoAllocMaxElems) {
-    set_error("chase_residuals_noalloc: N*b = %lld exceeds the fixed scratch of %zu entries",
-              static_cast<long long>(N) * b, kNoAllocMaxElems);
+  // N b <= max without forming the product (which could wrap for a huge N)
+  if (static_cast<size_t>(N) > kNoAllocMaxElems / static_cast<size_t>(b)) {
+    set_error("chase_residuals_noalloc: N*b exceeds the fixed scratch of %zu entries (N = %lld, "
+              "b = %d)", kNoAllocMaxElems, static_cast<long long>(N), b);
     return CHASE_INVALID_ARG;
   }
   if (!H || !V || !lambda || !resid || !is_device_ptr(H) || !is_device_ptr(V) ||
       !is_device_ptr(lambda) || !is_device_ptr(resid)) {
     set_error("chase_residuals_noalloc: H, V, lambda and resid must be device arrays");
     return CHASE_INVALID_ARG;
+  }
+  // the scratch looked up below belongs to the current device: every array
+  // must live there too
+  {
+    int cur = 0;
+    CHASE_CUDA(cudaGetDevice(&cur));
+    for (const void* p : {static_cast<const void*>(H), static_cast<const void*>(V),
+                          static_cast<const void*>(lambda), static_cast<const void*>(resid)}) {
+      cudaPointerAttributes a;
+      CHASE_CUDA(cudaPointerGetAttributes(&a, p));
+      if (a.device != cur) {
+        set_error("chase_residuals_noalloc: an array lives on device %d, the current device is "
+                  "%d", a.device, cur);
+        return CHASE_INVALID_ARG;
+      }
+    }
   }
   void* base = nullptr;
   CHASE_TRY(scratch_address(&base));

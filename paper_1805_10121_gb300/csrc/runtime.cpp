@@ -18,6 +18,7 @@ namespace chase {
 namespace {
 thread_local char g_err[512] = "";
 std::atomic<long long> g_launches{0};
+std::atomic<long long> g_allocs{0};
 }
 
 void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -143,6 +144,7 @@ Dev::~Dev() {
 
 int Dev::init() {
   void* p = nullptr;
+  g_allocs.fetch_add(1, std::memory_order_relaxed);
   CHASE_CUDA(cudaMallocAsync(&p, sizeof(int), st));
   err = static_cast<int*>(p);
   CHASE_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
@@ -152,6 +154,7 @@ int Dev::init() {
 int Dev::alloc_bytes(void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) return CHASE_OK;
+  g_allocs.fetch_add(1, std::memory_order_relaxed);
   cudaError_t e = cudaMallocAsync(p, bytes, st);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -315,6 +318,10 @@ extern "C" int chase_kernel_timing_read(int kind, double* seconds, long long* la
 }
 
 extern "C" const char* chase_last_error(void) { return chase::g_err; }
+
+extern "C" long long chase_device_allocations(void) {
+  return chase::g_allocs.load(std::memory_order_relaxed);
+}
 
 extern "C" long long chase_kernel_launches(void) {
   return chase::g_launches.load(std::memory_order_relaxed);

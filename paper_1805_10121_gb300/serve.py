@@ -56,6 +56,7 @@ class Result:
     ritz: List[np.ndarray]
     resid_max_over_norm: List[float]
     flops: float
+    last_h: Optional[np.ndarray] = None  # the last problem's H (host), when kept for checks
 
     @property
     def latency(self) -> float:
@@ -205,9 +206,12 @@ class Server:
         return sorted(self._results, key=lambda x: x.rid)
 
 
-def gpu_sequence_solver(device, precision: int, tol: float = 1e-10, seq_scale: float = 1e-3):
+def gpu_sequence_solver(device, precision: int, tol: float = 1e-10, seq_scale: float = 1e-3,
+                        keep_last_h: bool = False):
     """solve_fn for Server: builds the request's sequence on the slot's
-    stream and solves it problem after problem with warm starts."""
+    stream and solves it problem after problem with warm starts.  With
+    ``keep_last_h`` the result also carries the last problem's H on the host
+    (for checks against its exact spectrum)."""
     import torch
 
     from . import chase, synth
@@ -243,8 +247,9 @@ def gpu_sequence_solver(device, precision: int, tol: float = 1e-10, seq_scale: f
                 rmax.append(float(np.max(res[:req.nev])) / hnorm)
                 flops += float(stats["flops_total"])
             s.synchronize()
+            last = H.cpu().numpy() if keep_last_h else None
             del H, V, S
         return {"statuses": statuses, "iterations": iters, "ritz": ritz,
-                "resid_max_over_norm": rmax, "flops": flops}
+                "resid_max_over_norm": rmax, "flops": flops, "last_h": last}
 
     return solve

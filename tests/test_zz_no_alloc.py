@@ -33,13 +33,20 @@ def _problem(n, b, seed):
 
 
 def test_noalloc_matches_allocating_entry_point_twice():
-    # two calls in a row, different shapes: the second must not see the first's scratch
-    for n, b, seed in ((1000, 70, 11), (333, 13, 21)):
+    # calls in a row, different shapes: none may see an earlier call's scratch.
+    # b <= 6 takes the few-column product, larger b the tiled FP64 product.
+    for n, b, seed in ((1000, 70, 11), (333, 13, 21), (1000, 1, 41), (2000, 4, 51)):
         H, V, w = _problem(n, b, seed)
         lam_d = torch.from_numpy(w).to(DEV)
         out_d = torch.full((b,), -1.0, dtype=torch.float64, device=DEV)
+        torch.cuda.synchronize()
+        allocs = chase.chase_device_allocations()
         chase.chase_residuals_noalloc(H, V, lam_d, out_d)
+        torch.cuda.synchronize()
+        # the property this entry point exists for: the library allocated nothing
+        assert chase.chase_device_allocations() == allocs
         ref = chase.chase_residuals(H, V, w)
+        assert chase.chase_device_allocations() > allocs  # the counter does count
         got = out_d.cpu().numpy()
         assert np.max(np.abs(got - ref) / ref) < 1e-13
 
