@@ -75,13 +75,18 @@ typedef struct {
  * FP64.  chase_solve and chase_solve_batched only (the filter entry points
  * take CHASE_FP64 or CHASE_SPLIT_BF16). */
 #define CHASE_SPLIT_BF16_RR 2
-/* Split-BF16 filter whose accuracy follows the residuals (chase_solve only):
- * while every active residual exceeds 1e-3 h (h = largest |Ritz value|) the
- * filter products keep the leading 3 slices of each operand (about 2^-21
- * relative), above 1e-6 h 4 slices (2^-28), then all 7 (2^-49).  Rayleigh-
- * Ritz, QR and residuals stay FP64, so the converged pairs meet the same
- * tolerance; a low-precision iteration only limits how far that iteration
- * can reduce the residuals. */
+/* Split-BF16 filter whose accuracy follows each column's residual
+ * (chase_solve only; the batched solve treats it as CHASE_SPLIT_BF16).  By
+ * the model behind Alg. 5 a degree-m filter divides a column's residual by
+ * |rho|^m; while that expected residual exceeds 1e-3 h (h = largest |Ritz
+ * value|) the column's products keep the leading 3 slices of each operand
+ * (about 2^-21 relative), above 1e-6 h 4 slices (2^-28), else all 7
+ * (2^-49).  The first filter, before any residual is known, uses 3.  The
+ * active block is ordered by (slices, degree), and each run of equal slices
+ * is filtered as its own suffix-retiring block.  Rayleigh-Ritz, QR and
+ * residuals stay FP64, so the converged pairs meet the same tolerance; a
+ * low-precision column only limits how far this filter can reduce its
+ * residual, which it could not reduce to the tolerance anyway. */
 #define CHASE_SPLIT_BF16_ADAPT 3
 /* chase_filter only: split-BF16 products with the leading 4 or 3 slices of
  * each operand (about 2^-28 or 2^-21 relative per product), the reduced
@@ -129,9 +134,11 @@ typedef struct {
   double t_total, t_lanczos, t_filter, t_qr, t_rr, t_eigh, t_resid, t_host; /* seconds */
   double t_rr_product;     /* seconds of Rayleigh-Ritz's H Q products (inside t_rr) */
   double flops_rr_product; /* their algorithmic FLOPs (8 N^2 b complex, 2 N^2 b real) */
-  int filter_slices_low;   /* iterations whose split filter kept fewer than 7 slices
-                              (CHASE_SPLIT_BF16_ADAPT; single precision) */
+  int filter_slices_low;   /* iterations in which some column products of the split
+                              filter kept fewer than 7 slices (CHASE_SPLIT_BF16_ADAPT;
+                              single precision) */
   long long lanczos_matvecs; /* column products with H inside Alg. 6 (k per run) */
+  long long filter_matvecs_low; /* filter column products made with fewer than 7 slices */
 } chase_stats;
 
 /* Tile choice of the grouped FP64 filter: time the candidates on the first
@@ -234,6 +241,23 @@ int chase_kernel_timing_read(int kind, double* seconds, long long* launches, dou
 int chase_filter(const chase_c64* H, int64_t N, int64_t ldh, chase_c64* V, int64_t ldv, int b,
                  const int* degrees, double b_sup, double mu1, double mu_nevnex, int precision,
                  chase_c64* work, void* stream);
+
+/* Alg. 4 with a precision per column (Sec. 3.2: the filter only needs to be
+ * as accurate as the residual it can reach; the paper filters every column
+ * in one precision): column a is filtered with its degree degrees[a] on the
+ * split-BF16 product that keeps the leading slices[a] slices of each
+ * operand, slices[a] in {3, 4, 7} (about 2^-21, 2^-28 and 2^-49 relative
+ * per product).  The columns are ordered by (slices, degree) inside the
+ * call and each run of equal slices is filtered as its own suffix-retiring
+ * block of the same recurrence; V returns in the caller's column order.
+ * H, V, work: as chase_filter (complex128, column-major, host or device).
+ * degrees, slices: b ints each, host or device.
+ * Errors: CHASE_INVALID_ARG (sizes, NULL arrays, bounds out of order, an odd
+ * or out-of-range degree, slices outside {3, 4, 7}, non-finite H or V),
+ * CHASE_OUT_OF_MEMORY, CHASE_CUDA_ERROR, CHASE_TIMEOUT. */
+int chase_filter_mixed(const chase_c64* H, int64_t N, int64_t ldh, chase_c64* V, int64_t ldv,
+                       int b, const int* degrees, const int* slices, double b_sup, double mu1,
+                       double mu_nevnex, chase_c64* work, void* stream);
 
 /* Spectral estimates by Lanczos (Alg. 6, Sec. 4.2).
  * starts   N x (1 + nvec) start vectors, leading dimension N (host or device);

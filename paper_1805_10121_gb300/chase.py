@@ -20,7 +20,7 @@ import torch
 
 __all__ = [
     "ChaseError", "ChaseOpts", "ChaseStats", "lib", "lib_path", "declared_symbols",
-    "chase_opts_default", "chase_last_error", "chase_kernel_launches", "chase_device_allocations",
+    "chase_opts_default", "chase_last_error", "chase_filter_mixed", "chase_kernel_launches", "chase_device_allocations",
     "chase_kernel_timing",
     "chase_kernel_timing_read", "chase_wait_selftest", "CHASE_TIMED_SPLIT_PRODUCT", "CHASE_TIMED_FP64_PRODUCT", "chase_filter", "chase_lanczos",
     "chase_degrees", "chase_lock", "chase_tridiag_eigh", "chase_dos_estimate", "chase_orthonormalize",
@@ -87,7 +87,7 @@ class ChaseStats(ctypes.Structure):
         ("t_rr", ctypes.c_double), ("t_eigh", ctypes.c_double), ("t_resid", ctypes.c_double),
         ("t_host", ctypes.c_double), ("t_rr_product", ctypes.c_double),
         ("flops_rr_product", ctypes.c_double), ("filter_slices_low", ctypes.c_int),
-        ("lanczos_matvecs", ctypes.c_longlong),
+        ("lanczos_matvecs", ctypes.c_longlong), ("filter_matvecs_low", ctypes.c_longlong),
     ]
 
     def as_dict(self):
@@ -123,6 +123,8 @@ _SIGNATURES = {
     "chase_kernel_timing_read": (_int, [_int, _dp, ctypes.POINTER(ctypes.c_longlong), _dp, _dp]),
     "chase_filter": (_int, [_c_p, _i64, _i64, _c_p, _i64, _int, _c_p, _dbl, _dbl, _dbl, _int, _c_p,
                             _c_p]),
+    "chase_filter_mixed": (_int, [_c_p, _i64, _i64, _c_p, _i64, _int, _c_p, _c_p, _dbl, _dbl,
+                                  _dbl, _c_p, _c_p]),
     "chase_filter_batched": (_int, [_int, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p,
                                     _c_p, _int, _int, ctypes.POINTER(ChaseBatchStats), _c_p]),
     "chase_solve_batched": (_int, [_int, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p,
@@ -312,6 +314,25 @@ def chase_filter(H, V, degrees, b_sup, mu1, mu_nevnex, work=None, stream=None,
     (host or device) or a sequence of ints."""
     return _filter("chase_filter", torch.complex128, H, V, degrees, b_sup, mu1, mu_nevnex, work,
                    stream, precision)
+
+
+def chase_filter_mixed(H, V, degrees, slices, b_sup, mu1, mu_nevnex, work=None, stream=None):
+    """Alg. 4 with a precision per column: ``slices[a]`` in {3, 4, 7} slices of
+    the split-BF16 product for column a (complex128 tensors, V in place)."""
+    n = H.shape[0]
+    hp, ldh = _mat(H, n, "H")
+    vp, ldv = _mat(V, n, "V")
+    b = V.shape[1]
+    deg = np.ascontiguousarray(np.asarray(degrees, dtype=np.int32))
+    ns = np.ascontiguousarray(np.asarray(slices, dtype=np.int32))
+    if deg.shape != (b,) or ns.shape != (b,):
+        raise ValueError("one degree and one slice count per column")
+    wp = ctypes.c_void_p(work.data_ptr()) if work is not None else None
+    _check(lib().chase_filter_mixed(hp, n, ldh, vp, ldv, b, ctypes.c_void_p(deg.ctypes.data),
+                                    ctypes.c_void_p(ns.ctypes.data), float(b_sup), float(mu1),
+                                    float(mu_nevnex), wp, _stream(V, stream)),
+           "chase_filter_mixed")
+    return V
 
 
 def chase_filter_c32(H, V, degrees, b_sup, mu1, mu_nevnex, work=None, stream=None):

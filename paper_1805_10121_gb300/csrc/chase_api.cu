@@ -144,29 +144,53 @@ int filter_product(Dev& d, const T* H, int64_t N, int64_t ldh, const SplitH* sh,
   return timed_h_product(d, H, N, ldh, X, ldx, b, Y, ldy, j0, alpha, beta, shift);
 }
 
+// A run of columns [col0, col0 + ncols) of the filter block that share one
+// precision (nslices of the split product; 7 = full) and are sorted by
+// ascending degree: start[i] (i = 0 .. maxdeg + 1) counts the run's columns
+// of degree < i, which have retired before step i (Alg. 4 lines 12-14).
+struct FilterGroup {
+  int col0 = 0, ncols = 0, nslices = 7;
+  std::vector<int> start;
+};
+
+// Alg. 4 on a block made of runs of columns, each sorted by degree.  X (N x
+// b, ldx) holds the input and receives the output; Wk (N x b, ldw) is the
+// second buffer of the double buffering.  Every run is an independent set of
+// columns of the same three-term recurrence (the coefficients of Eq. 7 do
+// not depend on the column), filtered with its own precision and retiring
+// its own finished columns.  Adds the column products to *matvecs and those
+// made with fewer than 7 slices to *matvecs_low.
 template <class T>
-int filter_sorted(Dev& d, const T* H, int64_t N, int64_t ldh, T* X, int64_t ldx,
-                  T* Wk, int64_t ldw, int b, const int* start, int maxdeg, double b_sup,
+int filter_groups(Dev& d, const T* H, int64_t N, int64_t ldh, T* X, int64_t ldx, T* Wk,
+                  int64_t ldw, const std::vector<FilterGroup>& groups, int maxdeg, double b_sup,
                   double mu1, double mu_nn, long long* matvecs, const SplitH* sh = nullptr,
-                  SplitX* sx = nullptr, int nslices = 7) {
+                  SplitX* sx = nullptr, long long* matvecs_low = nullptr) {
   const double c = 0.5 * (b_sup + mu_nn);  // Alg. 4 line 2
   const double e = 0.5 * (b_sup - mu_nn);
   const double sigma1 = e / (mu1 - c);     // line 3
+  long long mv = 0, low = 0;
+  auto product = [&](const FilterGroup& g, int s, const T* src, int64_t lds, T* dst, int64_t ldd,
+                     double alpha, double beta) -> int {
+    const int j0 = g.col0 + s, j1 = g.col0 + g.ncols;
+    if (j0 >= j1) return CHASE_OK;
+    CHASE_TRY(filter_product(d, H, N, ldh, sh, sx, src, lds, j1, dst, ldd, j0, alpha, beta, c,
+                             g.nslices));
+    mv += j1 - j0;
+    if (sh && g.nslices < 7) low += j1 - j0;
+    return CHASE_OK;
+  };
   // line 4: W = (sigma_1 / e) (H - c I) V
-  CHASE_TRY(filter_product(d, H, N, ldh, sh, sx, X, ldx, b, Wk, ldw, 0, sigma1 / e, 0.0, c,
-                           nslices));
-  long long mv = b;
+  for (const FilterGroup& g : groups) CHASE_TRY(product(g, 0, X, ldx, Wk, ldw, sigma1 / e, 0.0));
   double sigma = sigma1;  // line 5
   T* Vb = X;
   T* Wb = Wk;
   int64_t ldV = ldx, ldW = ldw;
   for (int i = 2; i <= maxdeg; ++i) {  // line 7
     const double tau = 1.0 / (2.0 / sigma1 - sigma);  // line 8
-    const int s = start[i];  // lines 12-14: columns with degree < i are done
-    // line 9: V[:, s:] = 2 (tau / e) (H - c I) W[:, s:] - tau sigma V[:, s:]
-    CHASE_TRY(filter_product(d, H, N, ldh, sh, sx, Wb, ldW, b, Vb, ldV, s, 2.0 * tau / e,
-                             -tau * sigma, c, nslices));
-    mv += b - s;
+    // line 9: V[:, s:] = 2 (tau / e) (H - c I) W[:, s:] - tau sigma V[:, s:],
+    // s = the first column of each run with degree >= i (lines 12-14)
+    for (const FilterGroup& g : groups)
+      CHASE_TRY(product(g, g.start[i], Wb, ldW, Vb, ldV, 2.0 * tau / e, -tau * sigma));
     std::swap(Vb, Wb);  // line 10
     std::swap(ldV, ldW);
     sigma = tau;  // line 11
@@ -177,7 +201,23 @@ int filter_sorted(Dev& d, const T* H, int64_t N, int64_t ldh, T* X, int64_t ldx,
     return CHASE_INVALID_ARG;
   }
   if (matvecs) *matvecs += mv;
+  if (matvecs_low) *matvecs_low += low;
   return CHASE_OK;
+}
+
+// Alg. 4 on a block whose columns are all sorted by ascending degree and
+// filtered with one precision (start as in FilterGroup).
+template <class T>
+int filter_sorted(Dev& d, const T* H, int64_t N, int64_t ldh, T* X, int64_t ldx,
+                  T* Wk, int64_t ldw, int b, const int* start, int maxdeg, double b_sup,
+                  double mu1, double mu_nn, long long* matvecs, const SplitH* sh = nullptr,
+                  SplitX* sx = nullptr, int nslices = 7) {
+  std::vector<FilterGroup> one(1);
+  one[0].ncols = b;
+  one[0].nslices = nslices;
+  one[0].start.assign(start, start + maxdeg + 2);
+  return filter_groups(d, H, N, ldh, X, ldx, Wk, ldw, one, maxdeg, b_sup, mu1, mu_nn, matvecs,
+                       sh, sx);
 }
 
 void starts_from_sorted(const int* m, int b, int maxdeg, std::vector<int>& start) {
@@ -560,7 +600,12 @@ struct Solver {
   // host state
   double N2 = 0, b_sup = 0, mu1 = 0, mu_nn = 0, h = 0, tol_eff = 0;
   int d0 = 0, nconv = 0, iter = 0, status = CHASE_OK, maxdeg = 0;
+  bool grouped = false;  // the batched solve filters through the grouped kernels
   std::vector<int> m, order, perm, start;
+  // slices of the split product per column (7 = full precision; the FP64
+  // filter ignores it), and the runs of equal precision the filter works on
+  std::vector<int> cls;
+  std::vector<FilterGroup> groups;
   std::vector<double> ritz, res, ra, rr;
   chase_stats S{};
 
@@ -622,6 +667,8 @@ struct Solver {
     // Alg. 1 line 1: constant initial degree, rounded up to even
     d0 = std::min(o.deg + o.deg % 2, kMaxDegAllowed);
     m.assign(nx, d0);
+    grouped = grouped_split;
+    cls.assign(nx, initial_slices());
     // line 2: bounds (and start vectors when approx == 0)
     LanczosOut lz;
     tm.begin(&S.t_lanczos);
@@ -669,49 +716,77 @@ struct Solver {
       status = CHASE_BOUND_VIOLATION;
       return false;
     }
-    // line 4: the active columns are sorted by degree (line 15)
-    maxdeg = m[nx - 1];
-    starts_from_sorted(m.data() + nconv, b(), maxdeg, start);
+    // line 4: the active columns form runs of equal precision, each sorted
+    // by degree (line 15)
+    maxdeg = *std::max_element(m.begin() + nconv, m.end());
+    groups.clear();
+    for (int r0 = nconv; r0 < nx;) {
+      int r1 = r0 + 1;
+      while (r1 < nx && cls[r1] == cls[r0]) ++r1;
+      FilterGroup g;
+      g.col0 = r0 - nconv;
+      g.ncols = r1 - r0;
+      g.nslices = cls[r0];
+      starts_from_sorted(m.data() + r0, r1 - r0, maxdeg, g.start);
+      groups.push_back(std::move(g));
+      r0 = r1;
+    }
+    start = groups.size() == 1 ? groups[0].start : std::vector<int>(maxdeg + 2, 0);
     return true;
   }
 
-  // Slices of the split product for this iteration's filter.  With
-  // CHASE_SPLIT_BF16_ADAPT the precision follows the residuals (Sec. 3.2:
-  // the filter only has to beat the residuals it is asked to reduce): while
-  // every active residual is above 1e-3 h the product keeps 3 slices (about
-  // 2^-21 relative), above 1e-6 h 4 slices (2^-28), else all 7.
-  int slices_for_iteration() const {
+  // Slices of the split product before any residual is known: 3 with
+  // CHASE_SPLIT_BF16_ADAPT (the first filter starts from random vectors),
+  // 4 for single precision, else 7.  The batched solve's grouped filter
+  // takes one precision for all columns (7).
+  int initial_slices() const {
     if constexpr (is_single<T>) return 4;
-    if (o.precision != CHASE_SPLIT_BF16_ADAPT) return 7;
-    double rmin = HUGE_VAL;
-    for (int a = nconv; a < nx; ++a) rmin = std::min(rmin, res[a]);
-    if (rmin > 1e-3 * h) return 3;
-    if (rmin > 1e-6 * h) return 4;
+    if (o.precision == CHASE_SPLIT_BF16_ADAPT && !grouped) return 3;
+    return 7;
+  }
+
+  // CHASE_SPLIT_BF16_ADAPT: slices of the split product for one column in the
+  // next filter (Sec. 3.2: the filter only has to beat the residual it can
+  // reach).  By the model behind Alg. 5 a degree-m filter divides the
+  // residual by |rho|^m; while that expected residual stays above 1e-3 h the
+  // column's products keep 3 slices (about 2^-21 relative), above 1e-6 h 4
+  // slices (2^-28), else all 7 (2^-49).  Columns whose degree was chosen to
+  // reach the tolerance therefore run in full precision, and only those
+  // that cannot converge in this filter (degree capped at DEGMAX, or a Ritz
+  // value inside the damped interval) run on fewer slices.
+  int column_slices(double res_a, double ritz_a, int m_a, double c, double e) const {
+    if constexpr (is_single<T>) return 4;
+    if (o.precision != CHASE_SPLIT_BF16_ADAPT || grouped || !(e > 0.0)) return 7;
+    const double t = (ritz_a - c) / e;
+    const double rho = std::fabs(t) > 1.0 ? std::fabs(t) + std::sqrt(t * t - 1.0) : 1.0;
+    const double expect = res_a * std::pow(rho, -static_cast<double>(m_a));
+    if (!(expect <= 1e-3 * h)) return 3;
+    if (!(expect <= 1e-6 * h)) return 4;
     return 7;
   }
 
   // The filter of this solve alone (line 4).
   int filter(Dev& d) {
     PhaseTimer tm(d.st);
-    long long fm = 0;
-    const int ns = slices_for_iteration();
-    S.filter_slices_low += split && ns < 7 ? 1 : 0;
+    long long fm = 0, low = 0;
     tm.begin(&S.t_filter);
     if constexpr (is_single<T>) {
       if (split) {  // widen, filter on the split product, round back
         CHASE_TRY(launch_convert(d, Va(), lv, Dv, lD, N, b()));
-        CHASE_TRY(filter_sorted(d, static_cast<const Wide*>(nullptr), N, lD, Dv, lD, Dw, lD, b(),
-                                start.data(), maxdeg, b_sup, mu1, mu_nn, &fm, &sh, &sx, ns));
+        CHASE_TRY(filter_groups(d, static_cast<const Wide*>(nullptr), N, lD, Dv, lD, Dw, lD,
+                                groups, maxdeg, b_sup, mu1, mu_nn, &fm, &sh, &sx, &low));
         CHASE_TRY(launch_convert(d, Dv, lD, Va(), lv, N, b()));
       } else {
-        CHASE_TRY(filter_sorted(d, dH, N, lh, Va(), lv, Wk, lw, b(), start.data(), maxdeg, b_sup,
-                                mu1, mu_nn, &fm, nullptr, &sx, ns));
+        CHASE_TRY(filter_groups(d, dH, N, lh, Va(), lv, Wk, lw, groups, maxdeg, b_sup, mu1, mu_nn,
+                                &fm, nullptr, &sx));
       }
     } else {
-      CHASE_TRY(filter_sorted(d, dH, N, lh, Va(), lv, Wk, lw, b(), start.data(), maxdeg, b_sup,
-                              mu1, mu_nn, &fm, split ? &sh : nullptr, &sx, ns));
+      CHASE_TRY(filter_groups(d, dH, N, lh, Va(), lv, Wk, lw, groups, maxdeg, b_sup, mu1, mu_nn,
+                              &fm, split ? &sh : nullptr, &sx, &low));
     }
     tm.end();
+    S.filter_slices_low += low > 0 ? 1 : 0;
+    S.filter_matvecs_low += low;
     count_filter(fm);
     return CHASE_OK;
   }
@@ -795,8 +870,16 @@ struct Solver {
                       o.deg_extra, std::min(o.deg_max, kMaxDegAllowed), m.data() + nconv_new);
       else
         std::fill(m.begin() + nconv_new, m.end(), d0);
+      // precision of each column in the next filter (7 unless ADAPT)
+      for (int a = 0; a < nrest; ++a)
+        cls[nconv_new + a] = column_slices(res[nconv_new + a], ritz[nconv_new + a],
+                                           m[nconv_new + a], c, e);
       std::iota(ord2.begin(), ord2.end(), 0);  // line 15: stable sort by degree
+      // (within runs of equal precision, so that each run is one suffix-
+      // retiring block of Alg. 4)
       std::stable_sort(ord2.begin(), ord2.end(), [&](int x, int y) {
+        const int cx = cls[nconv_new + x], cy = cls[nconv_new + y];
+        if (cx != cy) return cx < cy;
         return m[nconv_new + x] < m[nconv_new + y];
       });
     }
@@ -805,16 +888,18 @@ struct Solver {
     for (int a = 0; a < n_new; ++a) perm[a] = order[a];
     for (int a = 0; a < nrest; ++a) perm[n_new + a] = order[n_new + ord2[a]];
     std::vector<double> r2(nrest), s2(nrest);
-    std::vector<int> m2(nrest);
+    std::vector<int> m2(nrest), c2(nrest);
     for (int a = 0; a < nrest; ++a) {
       r2[a] = ritz[nconv_new + ord2[a]];
       s2[a] = res[nconv_new + ord2[a]];
       m2[a] = m[nconv_new + ord2[a]];
+      c2[a] = cls[nconv_new + ord2[a]];
     }
     for (int a = 0; a < nrest; ++a) {
       ritz[nconv_new + a] = r2[a];
       res[nconv_new + a] = s2[a];
       m[nconv_new + a] = m2[a];
+      cls[nconv_new + a] = c2[a];
     }
     S.t_host += std::chrono::duration<double>(std::chrono::steady_clock::now() - t_host0).count();
     CHASE_CUDA(cudaMemcpyAsync(dperm, perm.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, d.st));
@@ -1100,6 +1185,97 @@ extern "C" int chase_filter_f32(const float* H, int64_t N, int64_t ldh, float* V
   return filter_impl(H, N, ldh, V, ldv, b, degrees, b_sup, mu1, mu_nevnex, CHASE_FP64, work, stream);
 }
 
+
+extern "C" int chase_filter_mixed(const chase_c64* H, int64_t N, int64_t ldh, chase_c64* V,
+                                  int64_t ldv, int b, const int* degrees, const int* slices,
+                                  double b_sup, double mu1, double mu_nevnex, chase_c64* work,
+                                  void* stream) {
+  using namespace chase;
+  if (N < 0 || b < 0 || !ld_ok(ldh, N) || !ld_ok(ldv, N) || N > (1LL << 30)) {
+    set_error("chase_filter_mixed: invalid size or leading dimension");
+    return CHASE_INVALID_ARG;
+  }
+  if (N == 0 || b == 0) return CHASE_OK;
+  if (!H || !V || !degrees || !slices) {
+    set_error("chase_filter_mixed: NULL array");
+    return CHASE_INVALID_ARG;
+  }
+  if (!(mu1 < mu_nevnex && mu_nevnex < b_sup) || !std::isfinite(b_sup) || !std::isfinite(mu1)) {
+    set_error("chase_filter_mixed: need mu1 < mu_nevnex < b_sup");
+    return CHASE_INVALID_ARG;
+  }
+  Dev d(stream);
+  CHASE_TRY(d.init());
+  const bool dev = is_device_ptr(H);
+  if (is_device_ptr(V) != dev) {
+    set_error("chase_filter_mixed: H and V must both be host or both be device arrays");
+    return CHASE_INVALID_ARG;
+  }
+  // the plan is made on the host: degrees and slices there
+  std::vector<int> deg(b), ns(b);
+  for (auto [src, dst] : {std::pair<const int*, int*>{degrees, deg.data()},
+                          std::pair<const int*, int*>{slices, ns.data()}}) {
+    if (is_device_ptr(src))
+      CHASE_CUDA(cudaMemcpyAsync(dst, src, sizeof(int) * b, cudaMemcpyDeviceToHost, d.st));
+    else
+      std::copy(src, src + b, dst);
+  }
+  CHASE_TRY(d.sync_check("chase_filter_mixed"));
+  for (int a = 0; a < b; ++a)
+    if (deg[a] < 2 || deg[a] > kMaxDegAllowed || deg[a] % 2 != 0 ||
+        (ns[a] != 3 && ns[a] != 4 && ns[a] != 7)) {
+      set_error("chase_filter_mixed: column %d: degree %d (even, 2..%d) or slices %d (3, 4, 7)", a,
+                deg[a], kMaxDegAllowed, ns[a]);
+      return CHASE_INVALID_ARG;
+    }
+  chase_c64 *dH = nullptr, *dV = nullptr;
+  int64_t lh = 0, lv = 0;
+  CHASE_TRY(stage_in(d, dev, H, ldh, N, N, &dH, &lh));
+  CHASE_TRY(stage_in(d, dev, V, ldv, N, b, &dV, &lv));
+  CHASE_TRY(check_finite(d, dH, lh, N, N, "chase_filter_mixed", "H"));
+  CHASE_TRY(check_finite(d, dV, lv, N, b, "chase_filter_mixed", "V"));
+  const int64_t lw = ld_pad<chase_c64>(N);
+  chase_c64* wk = dev && lw == N ? work : nullptr;
+  if (!wk) CHASE_TRY(d.alloc(&wk, static_cast<size_t>(lw) * b));
+  // columns ordered by (slices, degree): runs of equal precision, each sorted
+  // by degree, each filtered as its own suffix-retiring block
+  std::vector<int> order(b);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    if (ns[x] != ns[y]) return ns[x] < ns[y];
+    return deg[x] < deg[y];
+  });
+  const int maxdeg = *std::max_element(deg.begin(), deg.end());
+  std::vector<int> msorted(b);
+  for (int a = 0; a < b; ++a) msorted[a] = deg[order[a]];
+  std::vector<FilterGroup> groups;
+  for (int r0 = 0; r0 < b;) {
+    int r1 = r0 + 1;
+    while (r1 < b && ns[order[r1]] == ns[order[r0]]) ++r1;
+    FilterGroup g;
+    g.col0 = r0;
+    g.ncols = r1 - r0;
+    g.nslices = ns[order[r0]];
+    starts_from_sorted(msorted.data() + r0, r1 - r0, maxdeg, g.start);
+    groups.push_back(std::move(g));
+    r0 = r1;
+  }
+  int* dperm = nullptr;
+  CHASE_TRY(d.alloc(&dperm, b));
+  CHASE_CUDA(cudaMemcpyAsync(dperm, order.data(), sizeof(int) * b, cudaMemcpyHostToDevice, d.st));
+  SplitH sh;
+  SplitX sx;
+  CHASE_TRY(split_prepare_h(d, dH, N, lh, sh));
+  CHASE_TRY(split_alloc_x(d, N, b, sx, true));
+  CHASE_TRY(launch_permute_cols(d, dV, lv, wk, lw, N, b, dperm, false));
+  CHASE_TRY(filter_groups(d, dH, N, lh, wk, lw, dV, lv, groups, maxdeg, b_sup, mu1, mu_nevnex,
+                          nullptr, &sh, &sx));
+  CHASE_TRY(launch_permute_cols(d, wk, lw, dV, lv, N, b, dperm, true));
+  if (dV != V)
+    CHASE_TRY(copy_block(d, V, ldv, dV, lv, N, b,
+                         dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
+  return d.sync_check("chase_filter_mixed");
+}
 
 extern "C" int chase_lanczos(const chase_c64* H, int64_t N, int64_t ldh, int k, int nvec, int approx,
                              int nev, int nex, double dos_sigma, const chase_c64* starts,

@@ -171,7 +171,7 @@ def test_lanczos_matches_oracle():
     hn = float(lam.abs().max())
     assert abs(got["b_sup"] - ref["b_sup"]) <= 1e-10 * hn
     assert abs(got["mu1"] - ref["mu1"]) <= 1e-10 * hn
-    assert abs(got["mu_nevnex"] - ref["mu_nevnex"]) <= 1e-8 * hn
+    assert abs(got["mu_nevnex"] - ref["mu_nevnex"]) <= 1e-10 * hn
     assert got["b_sup"] >= float(lam.max())
     # replaced leading columns equal the oracle's Ritz vectors up to sign
     Vg, Vr = Vd.cpu().numpy(), ref["V"]

@@ -3,10 +3,10 @@ use it, against the CPU oracle and known spectra.
 
 Tolerance of the filter: each split-BF16 product carries an error of about
 2^-49 max|off-diagonal row of H| max|column| per term (7 slices of 7 bits);
-six slices measured 1.1e-11 to 1.4e-11 of a column's norm on Gaussian
-operands, seven are 128 times finer.  The diagonal of H and the shift are
-applied exactly in FP64.  A degree-m filter chains m such products whose
-errors add, so m <= 36 stays far below the 1e-9 per column used here.  Full solves
+the diagonal of H and the shift are applied exactly in FP64.  The K terms'
+errors add like sqrt(K) and a degree-m filter chains m products, so each
+column is held to 4 m sqrt(K) 2^-49 (``tolerances.split_filter_rtol``:
+about 1e-11 at N = 1000, 5e-11 at N = 22500, both with m = 36).  Full solves
 must meet the same eigenvalue (1e-10 ||H||) and residual (tol ||H||) bars as
 the FP64 path, because Rayleigh-Ritz, QR and residuals stay FP64."""
 
@@ -16,11 +16,11 @@ import torch
 
 import oracle
 from paper_1805_10121_gb300 import chase, synth
+from tests.tolerances import reduced_slice_rtol, split_filter_rtol
 
 pytestmark = pytest.mark.gpu
 
 DEV = torch.device("cuda:0")
-SPLIT_FILTER_RTOL = 1e-9
 EIG_RTOL = 1e-10
 
 
@@ -63,7 +63,7 @@ def test_split_filter_matches_oracle(n, b):
     ref = oracle_filter_any_order(H.numpy(), V.numpy(), deg, b_sup, mu1, mu_nn)
     Vd = dcol(V)
     chase.chase_filter(dcol(H), Vd, deg, b_sup, mu1, mu_nn, precision=chase.CHASE_SPLIT_BF16)
-    assert col_rel_err(Vd.cpu().numpy(), ref) <= SPLIT_FILTER_RTOL
+    assert col_rel_err(Vd.cpu().numpy(), ref) <= split_filter_rtol(n, int(deg.max()))
 
 
 def test_split_filter_full_size_sampled_columns():
@@ -82,7 +82,7 @@ def test_split_filter_full_size_sampled_columns():
     cols = [0, 7, 200, 333, 478, 479]
     ref = oracle_filter_any_order(H.cpu().numpy(), Vin[:, cols].cpu().numpy(), deg[cols], b_sup,
                                   mu1, mu_nn)
-    assert col_rel_err(V[:, cols].cpu().numpy(), ref) <= SPLIT_FILTER_RTOL
+    assert col_rel_err(V[:, cols].cpu().numpy(), ref) <= split_filter_rtol(n, int(deg.max()))
 
 
 def test_split_filter_narrow_block_uses_k_segments():
@@ -101,7 +101,7 @@ def test_split_filter_narrow_block_uses_k_segments():
                        precision=chase.CHASE_SPLIT_BF16)
     ref = oracle_filter_any_order(H.cpu().numpy(), Vin.cpu().numpy(), deg, 50.5, float(l[0]),
                                   float(l[240]))
-    assert col_rel_err(V.cpu().numpy(), ref) <= SPLIT_FILTER_RTOL
+    assert col_rel_err(V.cpu().numpy(), ref) <= split_filter_rtol(n, int(deg.max()))
 
 
 def test_split_filter_beyond_one_launch_exact_range():
@@ -119,7 +119,7 @@ def test_split_filter_beyond_one_launch_exact_range():
     cols = [0, 9, 17, 31]
     ref = oracle_filter_any_order(H.cpu().numpy(), Vin[:, cols].cpu().numpy(), deg[cols], 50.5,
                                   float(l[0]), float(l[1350]))
-    assert col_rel_err(V[:, cols].cpu().numpy(), ref) <= SPLIT_FILTER_RTOL
+    assert col_rel_err(V[:, cols].cpu().numpy(), ref) <= split_filter_rtol(n, int(deg.max()))
     del H, V, Vin
     torch.cuda.empty_cache()
 
@@ -218,8 +218,8 @@ def test_split_rr_batched_solve():
 # Per filtered column the error is a few hundred times the per-product
 # truncation 2^-(7 S) over degrees up to 20 (measured: 2e-6 with 4 slices,
 # 2e-4 with 3, 1e-12 with 7); the bound allows 4000 x 2^-(7 S).
-@pytest.mark.parametrize("precision,rtol", [(chase.CHASE_SPLIT_BF16_4, 4000 * 2.0 ** -28),
-                                            (chase.CHASE_SPLIT_BF16_3, 4000 * 2.0 ** -21)])
+@pytest.mark.parametrize("precision,rtol", [(chase.CHASE_SPLIT_BF16_4, reduced_slice_rtol(4)),
+                                            (chase.CHASE_SPLIT_BF16_3, reduced_slice_rtol(3))])
 @pytest.mark.parametrize("n,b", [(300, 37), (1000, 33)])
 def test_reduced_slice_filter_accuracy(precision, rtol, n, b):
     # the leading 4 (3) slices: about 2^-28 (2^-21) relative per product;
@@ -253,7 +253,45 @@ def test_adaptive_slices_solve_matches_fp64(n, nev, nex):
         assert st == chase.CHASE_OK
         check_solution(H.numpy(), lam.numpy(), ritz, resid, Vd.cpu().numpy(), nev, tol)
         out[prec] = (ritz, stats)
-    assert out[chase.CHASE_SPLIT_BF16_ADAPT][1]["filter_slices_low"] >= 1
+    st_ad = out[chase.CHASE_SPLIT_BF16_ADAPT][1]
+    assert st_ad["filter_slices_low"] >= 1
+    # per column: some products ran on fewer slices, not all of them
+    assert 0 < st_ad["filter_matvecs_low"] < st_ad["filter_matvecs"]
     hn = float(lam.abs().max())
     assert np.max(np.abs(out[chase.CHASE_SPLIT_BF16][0][:nev] -
                          out[chase.CHASE_SPLIT_BF16_ADAPT][0][:nev])) <= EIG_RTOL * hn
+
+
+@pytest.mark.parametrize("n,b", [(1000, 61), (517, 9)])
+def test_filter_with_a_precision_per_column(n, b):
+    H, lam = known_h(n, 401 + n)
+    V = synth.gaussian_block(n, b, 402 + b)
+    rng = np.random.default_rng(403 + n)
+    deg = (2 * rng.integers(1, 19, size=b)).astype(np.int32)
+    ns = rng.choice([3, 4, 7], size=b).astype(np.int32)
+    l = lam.numpy()
+    b_sup, mu1, mu_nn = 1.02, float(l[0]), float(l[n // 8])
+    ref = oracle_filter_any_order(H.numpy(), V.numpy(), deg, b_sup, mu1, mu_nn)
+    Vd = dcol(V)
+    chase.chase_filter_mixed(dcol(H), Vd, deg, ns, b_sup, mu1, mu_nn)
+    got = Vd.cpu().numpy()
+    err = np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    for a in range(b):
+        bound = (split_filter_rtol(n, int(deg.max())) if ns[a] == 7
+                 else reduced_slice_rtol(int(ns[a])))
+        assert err[a] <= bound, (a, int(ns[a]), float(err[a]))
+    # all columns at 7 slices: the uniform split filter's result
+    Vm = dcol(V)
+    chase.chase_filter_mixed(dcol(H), Vm, deg, np.full(b, 7, np.int32), b_sup, mu1, mu_nn)
+    Vu = dcol(V)
+    chase.chase_filter(dcol(H), Vu, deg, b_sup, mu1, mu_nn, precision=chase.CHASE_SPLIT_BF16)
+    assert col_rel_err(Vm.cpu().numpy(), Vu.cpu().numpy()) <= 1e-12
+
+
+def test_filter_mixed_rejects_bad_slices():
+    H, lam = known_h(64, 411)
+    V = dcol(synth.gaussian_block(64, 3, 412))
+    l = lam.numpy()
+    with pytest.raises(chase.ChaseError) as ei:
+        chase.chase_filter_mixed(dcol(H), V, [2, 4, 6], [3, 5, 7], 1.02, float(l[0]), float(l[8]))
+    assert ei.value.status == chase.CHASE_INVALID_ARG
