@@ -111,8 +111,11 @@ def build_library():
     from paper_1805_10121_gb300 import build
     build.build()
     info = dict(build.last_build)
-    return {"nvcc_ran": bool(info["compiled"]) or bool(info["linked"]),
-            "compiled": len(info["compiled"]), "sources_sha256": info["sources_sha256"][:16]}
+    prov = build.library_provenance()
+    return {"nvcc_ran_in_this_process": bool(info["compiled"]) or bool(info["linked"]),
+            "sources_sha256": info["sources_sha256"][:16],
+            "library_built_on": prov.get("machine"), "library_built_at": prov.get("built_at"),
+            "library_matches_sources": bool(prov.get("matches_tree"))}
 
 
 BUILD_INFO = None

@@ -13,10 +13,13 @@ from __future__ import annotations
 import concurrent.futures as cf
 import glob
 import hashlib
+import json
 import os
+import platform
 import shutil
 import subprocess
 import sys
+import time
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
@@ -59,6 +62,31 @@ def _stale(out: str, digest: str) -> bool:
 def _record(out: str, digest: str) -> None:
     with open(out + ".sha256", "w") as f:
         f.write(digest + "\n")
+
+
+def _record_library(digest: str) -> None:
+    """Provenance of the linked library: source digest, machine, time."""
+    with open(LIB + ".built", "w") as f:
+        json.dump({"sources_sha256": digest, "machine": platform.machine(),
+                   "built_at": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime())}, f)
+
+
+def library_provenance() -> dict:
+    """Where and from which sources the current libchase.so was built, and
+    whether it matches the sources in the tree now."""
+    try:
+        with open(LIB + ".built") as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        rec = {}
+    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
+    headers = sorted(glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.hpp"))
+                     + glob.glob(os.path.join(ROOT, "include", "*.h"))) + [os.path.abspath(__file__)]
+    flags = " ".join(_flags())
+    objs = "".join(_digest([s] + headers, flags) for s in srcs)
+    now = hashlib.sha256(objs.encode()).hexdigest()
+    rec["matches_tree"] = rec.get("sources_sha256") == now and os.path.exists(LIB)
+    return rec
 
 
 # What the last build() of this process did: the translation units nvcc
@@ -108,6 +136,7 @@ def build(verbose: bool = False) -> str:
             sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
             raise RuntimeError("link of libchase.so failed")
         _record(LIB, lib_digest)
+        _record_library(lib_digest)
         linked = True
     last_build.update(compiled=compiled, linked=linked, sources_sha256=lib_digest)
     if compiled or linked:

@@ -1,9 +1,9 @@
 """GPU parity of the grouped (batched) filter: every problem of a ragged
 batch must match the oracle's Alg. 4 on that problem alone, with the same
 tolerances as the single-problem filter (FP64: 1e-11 per column; split-BF16:
-4 m sqrt(2N) 2^-49 per column, its 2^-49 per-term truncation error added
-over the K = 2N terms of a product and the m products of a degree-m
-filter; ``tests/tolerances.py``)."""
+1e-11, or 4 m sqrt(2N) 2^-49 per column where that is larger: its 2^-49
+per-term truncation error added over the K = 2N terms of a product and the
+m products of a degree-m filter; ``tests/tolerances.py``)."""
 
 import numpy as np
 import pytest

@@ -1,8 +1,8 @@
 """GPU parity of the real-symmetric path (float64 H and blocks) against the
 oracle, which treats a real symmetric matrix as a Hermitian one (its results
 are then real).  Same bars as the complex path: filter 1e-11 (FP64) and
-4 m sqrt(N) 2^-49 (split-BF16, K = N terms per product; ``tests/tolerances.py``)
-relative per column; eigenvalues 1e-10 ||H||; residuals
+max(1e-11, 4 m sqrt(N) 2^-49) (split-BF16, K = N terms per product;
+``tests/tolerances.py``) relative per column; eigenvalues 1e-10 ||H||; residuals
 tol ||H||.  Odd orders and odd leading dimensions exercise the staging of
 real arrays into the even leading dimensions the TMA products need."""
 

@@ -5,8 +5,9 @@ Tolerance of the filter: each split-BF16 product carries an error of about
 2^-49 max|off-diagonal row of H| max|column| per term (7 slices of 7 bits);
 the diagonal of H and the shift are applied exactly in FP64.  The K terms'
 errors add like sqrt(K) and a degree-m filter chains m products, so each
-column is held to 4 m sqrt(K) 2^-49 (``tolerances.split_filter_rtol``:
-about 1e-11 at N = 1000, 5e-11 at N = 22500, both with m = 36).  Full solves
+column is held to the FP64 filter's bar of 1e-11, or to 4 m sqrt(K) 2^-49
+where that is larger (``tolerances.split_filter_rtol``: 1e-11 up to
+N = 1000, 3.2e-11 at N = 8000, 5.4e-11 at N = 22500 with m = 36).  Full solves
 must meet the same eigenvalue (1e-10 ||H||) and residual (tol ||H||) bars as
 the FP64 path, because Rayleigh-Ritz, QR and residuals stay FP64."""
 

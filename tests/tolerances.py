@@ -13,15 +13,18 @@ SPLIT_UNIT = 2.0 ** -49
 
 
 def split_filter_rtol(n, max_degree, real=False):
-    """Bound on the relative error per column of a degree <= max_degree
-    filter on the 7-slice split product: the K per-term truncation errors
-    (K = 2n complex, n real) have no common sign and add like sqrt(K), and
-    the m products of the recurrence add theirs, so the column error is
-    about m sqrt(K) 2^-49; the factor 4 covers the constants of this model
-    (measured errors on the test cases sit 1.3x to 4x below the bound, from
-    2.8e-12 at n = 300 to 1.04e-11 at n = 22500 with degrees up to 36)."""
+    """Bar for the relative error per column of a degree <= max_degree filter
+    on the 7-slice split product: the FP64 filter's bar (1e-11), raised where
+    the split product's error model exceeds it.  Model: the K per-term
+    truncation errors of a product (K = 2n complex, n real) have no common
+    sign and add like sqrt(K), and the m products of the recurrence add
+    theirs, so a column's error is about m sqrt(K) 2^-49; the factor 4
+    covers the model's constants at large K.  Measured: 1.7e-12 to 5.1e-12
+    for n <= 1000 (where the model is not the binding term), 7.3e-12 at
+    n = 8000 and 1.04e-11 at n = 22500 (bars 3.2e-11 and 5.4e-11), all with
+    degrees up to 36."""
     k = n if real else 2 * n
-    return 4.0 * max_degree * math.sqrt(k) * SPLIT_UNIT
+    return max(FP64_FILTER_RTOL, 4.0 * max_degree * math.sqrt(k) * SPLIT_UNIT)
 
 
 def reduced_slice_rtol(nslices):
