@@ -160,6 +160,11 @@ typedef struct {
   double t_steps;          /* device seconds of the step graph (every degree step) */
   double t_product;        /* device seconds of the grouped product launches alone */
   double t_total;          /* host seconds of the whole call */
+  /* chase_solve_batched: device seconds of Alg. 1's other phases, all
+   * problems together (Cholesky QR; Rayleigh-Ritz with residuals, the
+   * batched projected eigensolves included; locking, degrees and the
+   * reordering of the blocks) */
+  double t_qr, t_rr, t_eigh, t_lock;
 } chase_batch_stats;
 
 /* Fill `opts` with the defaults of Table 1 (double precision column):

@@ -100,6 +100,8 @@ class ChaseBatchStats(ctypes.Structure):
         ("launches", ctypes.c_int), ("matvecs", ctypes.c_longlong), ("flops", ctypes.c_double),
         ("t_autotune", ctypes.c_double), ("t_graph_build", ctypes.c_double),
         ("t_steps", ctypes.c_double), ("t_product", ctypes.c_double), ("t_total", ctypes.c_double),
+        ("t_qr", ctypes.c_double), ("t_rr", ctypes.c_double), ("t_eigh", ctypes.c_double),
+        ("t_lock", ctypes.c_double),
     ]
 
     def as_dict(self):

@@ -90,19 +90,21 @@ struct PhaseTimer {
   cudaStream_t st;
   cudaEvent_t a = nullptr, b = nullptr;
   double* acc = nullptr;
-  explicit PhaseTimer(cudaStream_t s) : st(s) {
-    cudaEventCreate(&a);
-    cudaEventCreate(&b);
-  }
+  explicit PhaseTimer(cudaStream_t s) : st(s) {}
   ~PhaseTimer() {
     if (a) cudaEventDestroy(a);
     if (b) cudaEventDestroy(b);
   }
   void begin(double* target) {
+    if (!a && (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)) {
+      cudaGetLastError();
+      return;
+    }
     acc = target;
     cudaEventRecord(a, st);
   }
   void end() {
+    if (!a || !b) return;
     cudaEventRecord(b, st);
     cudaEventSynchronize(b);
     float ms = 0.f;
@@ -252,9 +254,13 @@ int orth_alloc(Dev& d, int64_t N, int nconv, int b, OrthWork<T>& w) {
   return CHASE_OK;
 }
 
+// One Cholesky QR pass in two halves: cholqr_launch projects V against Y
+// and factors its Gram matrix (a breakdown sets KERR_CHOL_BREAKDOWN in d.err,
+// read at the caller's next synchronisation); cholqr_finish applies the
+// factor, V <- V L^-H.
 template <class T>
-int cholqr_pass(Dev& d, int64_t N, const T* Y, int64_t ldy, int nconv, T* V,
-                int64_t ldv, int b, OrthWork<T>& w, double shift, double* flops) {
+int cholqr_launch(Dev& d, int64_t N, const T* Y, int64_t ldy, int nconv, T* V, int64_t ldv,
+                  int b, OrthWork<T>& w, double shift, double* flops) {
   const int64_t ldp = ld_pad<T>(nconv), ldg = ld_pad<T>(b);
   if (nconv > 0) {  // V <- V - Y (Y^H V)
     CHASE_TRY(gram(d, N, Y, ldy, nconv, V, ldv, b, w.P, ldp));
@@ -262,17 +268,28 @@ int cholqr_pass(Dev& d, int64_t N, const T* Y, int64_t ldy, int nconv, T* V,
     *flops += (is_cplx<T> ? 16.0 : 4.0) * N * nconv * b;
   }
   CHASE_TRY(gram(d, N, V, ldv, b, V, ldv, b, w.G, ldg, /*lower=*/true));  // the factor reads only it
-  CHASE_TRY(cholesky_blocked(d, w.G, ldg, b, Prec<T>::chol_tol, shift, w.nrm, w.Rinv));
+  return cholesky_blocked(d, w.G, ldg, b, Prec<T>::chol_tol, shift, w.nrm, w.Rinv);
+}
+
+template <class T>
+int cholqr_finish(Dev& d, int64_t N, T* V, int64_t ldv, int b, OrthWork<T>& w, double* flops) {
+  // V <- V L^-H (= V R^-1 with R = L^H), in place
+  CHASE_TRY(trsm_right_lh(d, V, ldv, N, w.G, ld_pad<T>(b), b, w.Rinv));
+  *flops += (is_cplx<T> ? 1.0 : 0.25) *
+            (8.0 * N * b * b + 4.0 * N * b * b + 8.0 * b * b * b / 3.0);
+  return CHASE_OK;
+}
+
+template <class T>
+int cholqr_pass(Dev& d, int64_t N, const T* Y, int64_t ldy, int nconv, T* V,
+                int64_t ldv, int b, OrthWork<T>& w, double shift, double* flops) {
+  CHASE_TRY(cholqr_launch(d, N, Y, ldy, nconv, V, ldv, b, w, shift, flops));
   int st = d.sync_check("cholesky");
   if (st != CHASE_OK) {
     cudaMemsetAsync(d.err, 0, sizeof(int), d.st);
     return st;
   }
-  // V <- V L^-H (= V R^-1 with R = L^H), in place
-  CHASE_TRY(trsm_right_lh(d, V, ldv, N, w.G, ldg, b, w.Rinv));
-  *flops += (is_cplx<T> ? 1.0 : 0.25) *
-            (8.0 * N * b * b + 4.0 * N * b * b + 8.0 * b * b * b / 3.0);
-  return CHASE_OK;
+  return cholqr_finish(d, N, V, ldv, b, w, flops);
 }
 
 template <class T>
@@ -355,13 +372,17 @@ int rr_alloc(Dev& d, int64_t N, int b, RRWork<T>& w) {
   return CHASE_OK;
 }
 
+// Alg. 2 in three parts: rr_pre forms H Q (FP64, or the split product for
+// CHASE_SPLIT_BF16_RR) and the lower triangle of G = Q^H (H Q) mirrored to
+// the upper one; the eigensolve of G follows (one problem: eigh_device, a
+// batch: eigh_batched); rr_post forms Q W, the residuals from (H Q) W, and
+// copies Q W into Q.
 template <class T>
-int rr_core(Dev& d, const T* H, int64_t N, int64_t ldh, T* Q, int64_t ldq, int b,
-            double* w_dev, double* res_dev, RRWork<T>& w, double* t_eigh, double* flops,
-            const SplitH* sh = nullptr, SplitX* sx = nullptr, double* t_hq = nullptr) {
-  if (b == 0) return CHASE_OK;
+int rr_pre(Dev& d, const T* H, int64_t N, int64_t ldh, const T* Q, int64_t ldq, int b,
+           RRWork<T>& w, const SplitH* sh = nullptr, SplitX* sx = nullptr,
+           double* t_hq = nullptr) {
   const int64_t lN = ld_pad<T>(N), lg = ld_pad<T>(b);
-  PhaseTimer tq(d.st);
+  PhaseTimer tq(d.st);  // the product alone (synchronises only when timed)
   if (t_hq) tq.begin(t_hq);
   bool on_split = false;
   if constexpr (!is_single<T>) {
@@ -375,11 +396,13 @@ int rr_core(Dev& d, const T* H, int64_t N, int64_t ldh, T* Q, int64_t ldq, int b
   // G = Q^H H Q is Hermitian up to rounding: form its lower triangle (the one
   // the eigensolver reads) and take the upper one from it
   CHASE_TRY(gram(d, N, Q, ldq, b, w.HQ, lN, b, w.G, lg, /*lower=*/true));
-  CHASE_TRY(launch_fill_upper_hermitian(d, w.G, lg, b));
-  PhaseTimer tm(d.st);
-  tm.begin(t_eigh);
-  CHASE_TRY(eigh_device(d, w.G, lg, b, w_dev));  // (W, Lambda) = TSOLVE(G)
-  tm.end();
+  return launch_fill_upper_hermitian(d, w.G, lg, b);
+}
+
+template <class T>
+int rr_post(Dev& d, int64_t N, T* Q, int64_t ldq, int b, const double* w_dev, double* res_dev,
+            RRWork<T>& w, double* flops) {
+  const int64_t lN = ld_pad<T>(N), lg = ld_pad<T>(b);
   CHASE_TRY(gemm(d, N, b, Q, ldq, w.G, lg, b, w.T2, lN, 0, b, 1.0, 0.0, 0.0));  // Q W
   if (res_dev) {
     // H (Q W) = (H Q) W: the residual reuses the product with H
@@ -389,6 +412,20 @@ int rr_core(Dev& d, const T* H, int64_t N, int64_t ldh, T* Q, int64_t ldq, int b
   CHASE_TRY(copy_block(d, Q, ldq, w.T2, lN, N, b, cudaMemcpyDeviceToDevice));
   *flops += (is_cplx<T> ? 1.0 : 0.25) * (8.0 * N * N * b + 8.0 * N * b * b * (res_dev ? 3.0 : 2.0));
   return CHASE_OK;
+}
+
+template <class T>
+int rr_core(Dev& d, const T* H, int64_t N, int64_t ldh, T* Q, int64_t ldq, int b,
+            double* w_dev, double* res_dev, RRWork<T>& w, double* t_eigh, double* flops,
+            const SplitH* sh = nullptr, SplitX* sx = nullptr, double* t_hq = nullptr) {
+  if (b == 0) return CHASE_OK;
+  const int64_t lg = ld_pad<T>(b);
+  CHASE_TRY(rr_pre(d, H, N, ldh, Q, ldq, b, w, sh, sx, t_hq));
+  PhaseTimer tm(d.st);
+  tm.begin(t_eigh);
+  CHASE_TRY(eigh_device(d, w.G, lg, b, w_dev));  // (W, Lambda) = TSOLVE(G)
+  tm.end();
+  return rr_post(d, N, Q, ldq, b, w_dev, res_dev, w, flops);
 }
 
 // ---------------------------------------------------------------------------
@@ -843,7 +880,21 @@ struct Solver {
     tm.end();
     CHASE_TRY(d.sync_check("chase_solve iteration"));
     S.matvecs += nb;
-    // host decisions
+    const int nconv_new = decide(nb);
+    CHASE_CUDA(cudaMemcpyAsync(dperm, perm.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, d.st));
+    CHASE_TRY(apply_perm(d, dperm));
+    // the host arrays read by the copies above change in the next iteration
+    CHASE_TRY(d.sync_check("chase_solve permutation"));
+    nconv = nconv_new;
+    return CHASE_OK;
+  }
+
+  // Lines 9-15 on the host, from this iteration's Ritz values and residuals
+  // of the nb active columns (ra, rr): locking, the new bounds, degrees,
+  // precision classes, and in perm the column order of the next iteration
+  // (locked first in Ritz order, then the rest by precision and degree).
+  // Returns the new number of locked columns.
+  int decide(int nb) {
     const auto t_host0 = std::chrono::steady_clock::now();
     for (int a = 0; a < nb; ++a) h = std::max(h, std::fabs(ra[a]));
     tol_eff = o.conv_mode == CHASE_CONV_REL ? tol * h : tol;
@@ -902,13 +953,14 @@ struct Solver {
       cls[nconv_new + a] = c2[a];
     }
     S.t_host += std::chrono::duration<double>(std::chrono::steady_clock::now() - t_host0).count();
-    CHASE_CUDA(cudaMemcpyAsync(dperm, perm.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, d.st));
-    CHASE_TRY(launch_permute_cols(d, va, lv, Wk, lw, N, nb, dperm, false));
-    CHASE_TRY(copy_block(d, va, lv, Wk, lw, N, nb, cudaMemcpyDeviceToDevice));
-    // the host arrays read by the copies above change in the next iteration
-    CHASE_TRY(d.sync_check("chase_solve permutation"));
-    nconv = nconv_new;
-    return CHASE_OK;
+    return nconv_new;
+  }
+
+  // Gather of the active block into the order of perm (device copy dp).
+  int apply_perm(Dev& d, const int* dp) {
+    const int nb = b();
+    CHASE_TRY(launch_permute_cols(d, Va(), lv, Wk, lw, N, nb, dp, false));
+    return copy_block(d, Va(), lv, Wk, lw, N, nb, cudaMemcpyDeviceToDevice);
   }
 
   // Output: all pairs ascending by Ritz value; returns the solve's status.
@@ -1521,6 +1573,144 @@ extern "C" int chase_solve_f32(const float* H, int64_t N, int64_t ldh, int nev, 
                     stream);
 }
 
+namespace chase {
+namespace {
+// Lines 5-15 of Alg. 1 for every problem of a batch at once.  The steps are
+// those of Solver::after_filter, launched for all problems on one stream
+// with one synchronisation per phase instead of several per problem, and
+// the projected eigenproblems of Alg. 2 solved together (eigh_batched).
+// A problem whose first Cholesky QR pass breaks down takes the single-
+// problem orthogonalisation (shifted retry, its own synchronisations).
+// Adds the phases' times (events on the batch's stream) to t[0] (QR),
+// t[1] (Rayleigh-Ritz and residuals), t[2] (the eigensolves) and t[3]
+// (locking, degrees and the reordering).
+int batched_after_filter(Dev& d, std::vector<Solver<chase_c64>*>& act, double* t) {
+  using T = chase_c64;
+  const int P = static_cast<int>(act.size());
+  if (P == 0) return CHASE_OK;
+  int* flags = nullptr;  // per problem: KERR_* bits of its launches
+  CHASE_TRY(d.alloc(&flags, P));
+  CHASE_CUDA(cudaMemsetAsync(flags, 0, sizeof(int) * P, d.st));
+  std::vector<std::unique_ptr<Dev>> view(P);
+  for (int i = 0; i < P; ++i) {
+    view[i].reset(new Dev(d.st));
+    view[i]->err = flags + i;
+    view[i]->own_err = false;
+    view[i]->sync_on_exit = false;
+  }
+  std::vector<int> hf(P);
+  auto read_flags = [&](const char* where) -> int {
+    CHASE_CUDA(cudaMemcpyAsync(hf.data(), flags, sizeof(int) * P, cudaMemcpyDeviceToHost, d.st));
+    CHASE_CUDA(cudaStreamSynchronize(d.st));
+    for (int i = 0; i < P; ++i)
+      if (hf[i] & (KERR_TIMEOUT_FULL | KERR_TIMEOUT_EMPTY)) {
+        set_error("%s: a bounded wait in a kernel gave up (problem %d)", where, i);
+        return CHASE_TIMEOUT;
+      }
+    return CHASE_OK;
+  };
+  PhaseTimer tm(d.st);
+  // ---- lines 5-6: Cholesky QR, twice ----
+  tm.begin(&t[0]);
+  for (int i = 0; i < P; ++i) {
+    Solver<T>& s = *act[i];
+    Dev& v = *view[i];
+    const int nb = s.b();
+    CHASE_TRY(launch_col_norms(v, s.Va(), s.lv, s.N, nb, s.ow.nrm));
+    CHASE_TRY(launch_col_inv_scale(v, s.Va(), s.lv, s.N, nb, s.ow.nrm));
+    CHASE_TRY(cholqr_launch(v, s.N, s.dV, s.lv, s.nconv, s.Va(), s.lv, nb, s.ow, 0.0,
+                            &s.S.flops_total));
+  }
+  CHASE_TRY(read_flags("chase_solve_batched QR"));
+  std::vector<char> second(P, 0);
+  for (int i = 0; i < P; ++i) {
+    Solver<T>& s = *act[i];
+    Dev& v = *view[i];
+    if (hf[i] & KERR_CHOL_BREAKDOWN) {  // the single-problem path, with its retry
+      CHASE_CUDA(cudaMemsetAsync(flags + i, 0, sizeof(int), d.st));
+      CHASE_TRY(orth_core(v, s.N, s.dV, s.lv, s.nconv, s.Va(), s.lv, s.b(), s.ow,
+                          &s.S.flops_total));
+      continue;
+    }
+    CHASE_TRY(cholqr_finish(v, s.N, s.Va(), s.lv, s.b(), s.ow, &s.S.flops_total));
+    CHASE_TRY(cholqr_launch(v, s.N, s.dV, s.lv, s.nconv, s.Va(), s.lv, s.b(), s.ow, 0.0,
+                            &s.S.flops_total));
+    second[i] = 1;
+  }
+  CHASE_TRY(read_flags("chase_solve_batched QR"));
+  for (int i = 0; i < P; ++i) {
+    if (!second[i]) continue;
+    Solver<T>& s = *act[i];
+    if (hf[i] & KERR_CHOL_BREAKDOWN) {
+      set_error("orthonormalisation: Cholesky QR broke down (problem %d of the batch)", i);
+      return CHASE_QR_BREAKDOWN;
+    }
+    CHASE_TRY(cholqr_finish(*view[i], s.N, s.Va(), s.lv, s.b(), s.ow, &s.S.flops_total));
+  }
+  tm.end();
+  // ---- lines 7-8: Rayleigh-Ritz and residuals ----
+  tm.begin(&t[1]);
+  std::vector<int> off(P + 1, 0);
+  for (int i = 0; i < P; ++i) off[i + 1] = off[i] + act[i]->b();
+  double* wres = nullptr;  // Ritz values, then residuals, of every problem
+  CHASE_TRY(d.alloc(&wres, static_cast<size_t>(2) * off[P]));
+  std::vector<EighItem> items(P);
+  for (int i = 0; i < P; ++i) {
+    Solver<T>& s = *act[i];
+    const int nb = s.b();
+    CHASE_TRY(rr_pre(*view[i], s.dH, s.N, s.lh, s.Va(), s.lv, nb, s.rw,
+                     s.split_rr ? s.rr_slices : nullptr, s.split_rr ? s.rr_sx : nullptr));
+    items[i] = EighItem{s.rw.G, ld_pad<T>(nb), nb, wres + off[i]};
+  }
+  PhaseTimer te(d.st);
+  te.begin(&t[2]);
+  int* info = nullptr;
+  CHASE_TRY(eigh_batched(d, items, &info));  // (W, Lambda) = TSOLVE(G), every problem
+  te.end();
+  for (int i = 0; i < P; ++i) {
+    Solver<T>& s = *act[i];
+    const int nb = s.b();
+    CHASE_TRY(rr_post(*view[i], s.N, s.Va(), s.lv, nb, wres + off[i], wres + off[P] + off[i], s.rw,
+                      &s.S.flops_total));
+    s.S.flops_rr_product += s.kMv * s.N2 * nb;
+    s.S.matvecs += nb;
+  }
+  std::vector<double> hw(static_cast<size_t>(2) * off[P]);
+  std::vector<int> hinfo(P);
+  CHASE_CUDA(cudaMemcpyAsync(hinfo.data(), info, sizeof(int) * P, cudaMemcpyDeviceToHost, d.st));
+  CHASE_CUDA(cudaMemcpyAsync(hw.data(), wres, sizeof(double) * hw.size(), cudaMemcpyDeviceToHost,
+                             d.st));
+  CHASE_TRY(read_flags("chase_solve_batched Rayleigh-Ritz"));
+  tm.end();
+  for (int i = 0; i < P; ++i)
+    if (hinfo[i] != 0) {
+      set_error("batched projected eigensolve returned info = %d", hinfo[i]);
+      return CHASE_EIGENSOLVER_ERROR;
+    }
+  // ---- lines 9-15: locking, bounds, degrees on the host; one reordering ----
+  tm.begin(&t[3]);
+  std::vector<int> nconv_new(P), hperm(off[P]);
+  for (int i = 0; i < P; ++i) {
+    Solver<T>& s = *act[i];
+    const int nb = s.b();
+    std::copy(hw.begin() + off[i], hw.begin() + off[i] + nb, s.ra.begin());
+    std::copy(hw.begin() + off[P] + off[i], hw.begin() + off[P] + off[i] + nb, s.rr.begin());
+    nconv_new[i] = s.decide(nb);
+    std::copy(s.perm.begin(), s.perm.begin() + nb, hperm.begin() + off[i]);
+  }
+  int* dperm = nullptr;
+  CHASE_TRY(d.alloc(&dperm, std::max(off[P], 1)));
+  CHASE_CUDA(cudaMemcpyAsync(dperm, hperm.data(), sizeof(int) * off[P], cudaMemcpyHostToDevice,
+                             d.st));
+  for (int i = 0; i < P; ++i) CHASE_TRY(act[i]->apply_perm(*view[i], dperm + off[i]));
+  CHASE_TRY(read_flags("chase_solve_batched reordering"));
+  tm.end();
+  for (int i = 0; i < P; ++i) act[i]->nconv = nconv_new[i];
+  return CHASE_OK;
+}
+}  // namespace
+}  // namespace chase
+
 extern "C" int chase_solve_batched(int P, const chase_c64* const* H, const int64_t* N,
                                    const int64_t* ldh, const int* nev, const int* nex,
                                    const double* tol, chase_c64* const* V, const int64_t* ldv,
@@ -1646,11 +1836,15 @@ extern "C" int chase_solve_batched(int P, const chase_c64* const* H, const int64
       // the grouped filter's time, shared out by each problem's FLOPs
       if (tt.flops > 0) s.S.t_filter += tt.t_steps * 8.0 * s.N2 * fm / tt.flops;
     }
-    // lines 5-15 per problem, largest first so that the workers finish together
-    std::stable_sort(act.begin(), act.end(), [&](int a, int b) {  // cost ~ N^2 (active columns)
-      return sv[a].N2 * sv[a].b() > sv[b].N2 * sv[b].b();
-    });
-    CHASE_TRY(pool.run(act, [&](Dev& w, int p) { return sv[p].after_filter(w); }));
+    // lines 5-15 of every problem at once
+    std::vector<Solver<chase_c64>*> ap;
+    for (int p : act) ap.push_back(&sv[p]);
+    double tph[4] = {0.0, 0.0, 0.0, 0.0};
+    CHASE_TRY(batched_after_filter(d, ap, tph));
+    bs.t_qr += tph[0];
+    bs.t_rr += tph[1];
+    bs.t_eigh += tph[2];
+    bs.t_lock += tph[3];
   }
   int worst = CHASE_OK;
   const double t_total =

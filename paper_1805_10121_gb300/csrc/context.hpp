@@ -16,6 +16,10 @@ struct Dev {
   cudaStream_t st = nullptr;
   int* err = nullptr;  // device int, bit field of KERR_* codes
   std::vector<void*> bufs;
+  // A view on another context's stream with a flag slot of its own (the
+  // per-problem flags of a batch): err is borrowed, and leaving the view
+  // does not synchronise (its workspace is released stream-ordered).
+  bool own_err = true, sync_on_exit = true;
 
   explicit Dev(void* stream) : st(static_cast<cudaStream_t>(stream)) {}
   Dev(const Dev&) = delete;
@@ -301,6 +305,20 @@ int eigh_device(Dev& d, double* G, int64_t ldg, int p, double* w_dev);
 // Single precision (cheevd / ssyevd); eigenvalues returned in double.
 int eigh_device(Dev& d, chase_c32* G, int64_t ldg, int p, double* w_dev);
 int eigh_device(Dev& d, float* G, int64_t ldg, int p, double* w_dev);
+// Many small projected eigenproblems at once (cuSOLVER's batched Hermitian
+// eigensolver on buckets of sizes rounded up to 16, each matrix padded as
+// diag(G, pad I)): item q's G (p x p, ldg, Hermitian, both triangles) is
+// overwritten by its eigenvectors and w (p doubles, device) receives its
+// eigenvalues ascending.  *info_dev (device, one int per item in bucket
+// order) is nonzero where the eigensolver failed; the caller reads it after
+// its next synchronisation.
+struct EighItem {
+  chase_c64* G;
+  long long ldg;
+  int p;
+  double* w;
+};
+int eigh_batched(Dev& d, const std::vector<EighItem>& items, int** info_dev);
 // Destroy the calling thread's cuSOLVER handle (worker threads, before they end).
 void release_thread_solver();
 

@@ -8,6 +8,7 @@
 #include <cusolverDn.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
 
 #include "common.cuh"
@@ -1181,6 +1182,122 @@ int eigh_device(Dev& d, chase_c64* G, int64_t ldg, int p, double* w_dev) {
     set_error("zheevd returned info = %d", h_info);
     return CHASE_EIGENSOLVER_ERROR;
   }
+  return CHASE_OK;
+}
+
+}  // namespace chase
+
+// ---------------------------------------------------------------------------
+// Projected eigenproblems of a batch (Alg. 2 line 3), many at once
+// ---------------------------------------------------------------------------
+namespace chase {
+namespace {
+// Item q of a bucket: G (p x p, ld), padded into slot q of the bucket
+// (n x n, column-major) as diag(G, pad I) with pad = 1 + 2 ||G||_F, above
+// every eigenvalue of G, so that the p lowest eigenpairs of the slot are
+// those of G with eigenvectors [w; 0].
+__global__ void eigh_pack_kernel(const EighItem* __restrict__ items, int n,
+                                 double2* __restrict__ A) {
+  __shared__ double scratch[33];
+  const EighItem it = items[blockIdx.x];
+  const double2* G = reinterpret_cast<const double2*>(it.G);
+  double s = 0.0;
+  for (long long e = threadIdx.x; e < (long long)it.p * it.p; e += blockDim.x) {
+    const double2 v = G[(e / it.p) * it.ldg + e % it.p];
+    s += v.x * v.x + v.y * v.y;
+  }
+  s = block_sum(s, scratch);
+  const double pad = 1.0 + 2.0 * sqrt(s);
+  double2* slot = A + (long long)blockIdx.x * n * n;
+  for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) {
+    const int i = static_cast<int>(e % n), j = static_cast<int>(e / n);
+    double2 v = make_double2(0.0, 0.0);
+    if (i < it.p && j < it.p)
+      v = G[(long long)j * it.ldg + i];
+    else if (i == j)
+      v = make_double2(pad, 0.0);
+    slot[e] = v;
+  }
+}
+
+// The p lowest eigenpairs of slot q back to item q: eigenvectors into G
+// (columns, first p rows), eigenvalues into w.
+__global__ void eigh_unpack_kernel(const EighItem* __restrict__ items, int n,
+                                   const double2* __restrict__ A, const double* __restrict__ W) {
+  const EighItem it = items[blockIdx.x];
+  double2* G = reinterpret_cast<double2*>(it.G);
+  const double2* slot = A + (long long)blockIdx.x * n * n;
+  for (long long e = threadIdx.x; e < (long long)it.p * it.p; e += blockDim.x) {
+    const int i = static_cast<int>(e % it.p), j = static_cast<int>(e / it.p);
+    G[(long long)j * it.ldg + i] = slot[(long long)j * n + i];
+  }
+  for (int j = threadIdx.x; j < it.p; j += blockDim.x) it.w[j] = W[(long long)blockIdx.x * n + j];
+}
+}  // namespace
+
+int eigh_batched(Dev& d, const std::vector<EighItem>& items, int** info_dev) {
+  if (items.empty()) return CHASE_OK;
+  CHASE_TRY(solver_handle(d));
+  cusolverDnParams_t prm = nullptr;
+  if (cusolverDnCreateParams(&prm) != CUSOLVER_STATUS_SUCCESS) {
+    set_error("cusolverDnCreateParams failed");
+    return CHASE_EIGENSOLVER_ERROR;
+  }
+  struct ParamsGuard {
+    cusolverDnParams_t p;
+    ~ParamsGuard() { cusolverDnDestroyParams(p); }
+  } guard{prm};
+  // buckets of matrix sizes rounded up to a multiple of 16; matrices above
+  // kBatchedEighMax take the one-matrix solver
+  constexpr int kBatchedEighMax = 256;
+  std::map<int, std::vector<int>> buckets;
+  int* info = nullptr;
+  CHASE_TRY(d.alloc(&info, items.size()));
+  CHASE_CUDA(cudaMemsetAsync(info, 0, sizeof(int) * items.size(), d.st));
+  int off = 0;
+  for (size_t q = 0; q < items.size(); ++q) {
+    if (items[q].p > kBatchedEighMax)
+      CHASE_TRY(eigh_device(d, items[q].G, items[q].ldg, items[q].p, items[q].w));
+    else if (items[q].p > 0)
+      buckets[(items[q].p + 15) / 16 * 16].push_back(static_cast<int>(q));
+  }
+  for (auto& [n, idx] : buckets) {
+    const int c = static_cast<int>(idx.size());
+    std::vector<EighItem> sub(c);
+    for (int k = 0; k < c; ++k) sub[k] = items[idx[k]];
+    EighItem* dsub = nullptr;
+    double2* A = nullptr;
+    double* W = nullptr;
+    CHASE_TRY(d.alloc(&dsub, c));
+    CHASE_TRY(d.alloc(&A, static_cast<size_t>(c) * n * n));
+    CHASE_TRY(d.alloc(&W, static_cast<size_t>(c) * n));
+    CHASE_CUDA(cudaMemcpyAsync(dsub, sub.data(), sizeof(EighItem) * c, cudaMemcpyHostToDevice, d.st));
+    eigh_pack_kernel<<<c, 256, 0, d.st>>>(dsub, n, A);
+    note_launch();
+    CHASE_CUDA(cudaGetLastError());
+    size_t wd = 0, wh = 0;
+    if (cusolverDnXsyevBatched_bufferSize(t_solver, prm, CUSOLVER_EIG_MODE_VECTOR,
+                                          CUBLAS_FILL_MODE_LOWER, n, CUDA_C_64F, A, n, CUDA_R_64F, W,
+                                          CUDA_C_64F, &wd, &wh, c) != CUSOLVER_STATUS_SUCCESS) {
+      set_error("cusolverDnXsyevBatched_bufferSize failed (n = %d, batch = %d)", n, c);
+      return CHASE_EIGENSOLVER_ERROR;
+    }
+    void* work = nullptr;
+    CHASE_TRY(d.alloc_bytes(&work, std::max<size_t>(wd, 16)));
+    std::vector<char> hwork(std::max<size_t>(wh, 16));
+    if (cusolverDnXsyevBatched(t_solver, prm, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n,
+                               CUDA_C_64F, A, n, CUDA_R_64F, W, CUDA_C_64F, work, wd, hwork.data(),
+                               wh, info + off, c) != CUSOLVER_STATUS_SUCCESS) {
+      set_error("cusolverDnXsyevBatched failed to launch (n = %d, batch = %d)", n, c);
+      return CHASE_EIGENSOLVER_ERROR;
+    }
+    eigh_unpack_kernel<<<c, 256, 0, d.st>>>(dsub, n, A, W);
+    note_launch();
+    CHASE_CUDA(cudaGetLastError());
+    if (wh > 0) CHASE_CUDA(cudaStreamSynchronize(d.st));  // the host workspace is in use until here
+    off += c;
+  }
+  if (info_dev) *info_dev = info;
   return CHASE_OK;
 }
 

@@ -138,8 +138,8 @@ int make_tmap_bf16_3d(CUtensorMap* map, const void* base, int64_t d0, int64_t d1
 // ---------------------------------------------------------------------------
 Dev::~Dev() {
   for (void* p : bufs) cudaFreeAsync(p, st);
-  if (err) cudaFreeAsync(err, st);
-  cudaStreamSynchronize(st);
+  if (err && own_err) cudaFreeAsync(err, st);
+  if (sync_on_exit) cudaStreamSynchronize(st);
 }
 
 int Dev::init() {
