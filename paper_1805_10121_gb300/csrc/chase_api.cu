@@ -31,6 +31,7 @@ namespace {
 
 constexpr int kMaxDegAllowed = 1024;
 constexpr int kBatchWorkers = 8;  // host threads for the per-problem phases of a batched solve
+constexpr int kBatchStreams = 16;  // streams the batched QR / Rayleigh-Ritz launches spread over
 
 // Scalar types of the solver: complex128 and float64 (the default), complex64
 // and float32 (the single-precision entry points; Sec. 5.1 templates the
@@ -1584,22 +1585,48 @@ namespace {
 // Adds the phases' times (events on the batch's stream) to t[0] (QR),
 // t[1] (Rayleigh-Ritz and residuals), t[2] (the eigensolves) and t[3]
 // (locking, degrees and the reordering).
-int batched_after_filter(Dev& d, std::vector<Solver<chase_c64>*>& act, double* t) {
+// Problem i's launches go to stream fan[i % fan.size()] (the small kernels
+// of different problems then run side by side); the batch's stream d.st
+// forks to and joins the fan around each phase.
+int batched_after_filter(Dev& d, std::vector<Solver<chase_c64>*>& act,
+                         const std::vector<cudaStream_t>& fan, double* t) {
   using T = chase_c64;
   const int P = static_cast<int>(act.size());
   if (P == 0) return CHASE_OK;
+  const int S = static_cast<int>(fan.size());
+  struct Events {
+    std::vector<cudaEvent_t> e;
+    ~Events() {
+      for (auto x : e) cudaEventDestroy(x);
+    }
+  } ev;
+  ev.e.assign(S + 1, nullptr);
+  for (auto& x : ev.e) CHASE_CUDA(cudaEventCreateWithFlags(&x, cudaEventDisableTiming));
+  auto fork = [&]() -> int {
+    CHASE_CUDA(cudaEventRecord(ev.e[S], d.st));
+    for (int k = 0; k < S; ++k) CHASE_CUDA(cudaStreamWaitEvent(fan[k], ev.e[S], 0));
+    return CHASE_OK;
+  };
+  auto join = [&]() -> int {
+    for (int k = 0; k < S; ++k) {
+      CHASE_CUDA(cudaEventRecord(ev.e[k], fan[k]));
+      CHASE_CUDA(cudaStreamWaitEvent(d.st, ev.e[k], 0));
+    }
+    return CHASE_OK;
+  };
   int* flags = nullptr;  // per problem: KERR_* bits of its launches
   CHASE_TRY(d.alloc(&flags, P));
   CHASE_CUDA(cudaMemsetAsync(flags, 0, sizeof(int) * P, d.st));
   std::vector<std::unique_ptr<Dev>> view(P);
   for (int i = 0; i < P; ++i) {
-    view[i].reset(new Dev(d.st));
+    view[i].reset(new Dev(S > 0 ? fan[i % S] : d.st));
     view[i]->err = flags + i;
     view[i]->own_err = false;
     view[i]->sync_on_exit = false;
   }
   std::vector<int> hf(P);
   auto read_flags = [&](const char* where) -> int {
+    CHASE_TRY(join());
     CHASE_CUDA(cudaMemcpyAsync(hf.data(), flags, sizeof(int) * P, cudaMemcpyDeviceToHost, d.st));
     CHASE_CUDA(cudaStreamSynchronize(d.st));
     for (int i = 0; i < P; ++i)
@@ -1612,6 +1639,7 @@ int batched_after_filter(Dev& d, std::vector<Solver<chase_c64>*>& act, double* t
   PhaseTimer tm(d.st);
   // ---- lines 5-6: Cholesky QR, twice ----
   tm.begin(&t[0]);
+  CHASE_TRY(fork());
   for (int i = 0; i < P; ++i) {
     Solver<T>& s = *act[i];
     Dev& v = *view[i];
@@ -1623,6 +1651,7 @@ int batched_after_filter(Dev& d, std::vector<Solver<chase_c64>*>& act, double* t
   }
   CHASE_TRY(read_flags("chase_solve_batched QR"));
   std::vector<char> second(P, 0);
+  CHASE_TRY(fork());
   for (int i = 0; i < P; ++i) {
     Solver<T>& s = *act[i];
     Dev& v = *view[i];
@@ -1638,6 +1667,7 @@ int batched_after_filter(Dev& d, std::vector<Solver<chase_c64>*>& act, double* t
     second[i] = 1;
   }
   CHASE_TRY(read_flags("chase_solve_batched QR"));
+  CHASE_TRY(fork());
   for (int i = 0; i < P; ++i) {
     if (!second[i]) continue;
     Solver<T>& s = *act[i];
@@ -1662,11 +1692,13 @@ int batched_after_filter(Dev& d, std::vector<Solver<chase_c64>*>& act, double* t
                      s.split_rr ? s.rr_slices : nullptr, s.split_rr ? s.rr_sx : nullptr));
     items[i] = EighItem{s.rw.G, ld_pad<T>(nb), nb, wres + off[i]};
   }
+  CHASE_TRY(join());
   PhaseTimer te(d.st);
   te.begin(&t[2]);
   int* info = nullptr;
   CHASE_TRY(eigh_batched(d, items, &info));  // (W, Lambda) = TSOLVE(G), every problem
   te.end();
+  CHASE_TRY(fork());
   for (int i = 0; i < P; ++i) {
     Solver<T>& s = *act[i];
     const int nb = s.b();
@@ -1677,6 +1709,7 @@ int batched_after_filter(Dev& d, std::vector<Solver<chase_c64>*>& act, double* t
   }
   std::vector<double> hw(static_cast<size_t>(2) * off[P]);
   std::vector<int> hinfo(P);
+  CHASE_TRY(join());
   CHASE_CUDA(cudaMemcpyAsync(hinfo.data(), info, sizeof(int) * P, cudaMemcpyDeviceToHost, d.st));
   CHASE_CUDA(cudaMemcpyAsync(hw.data(), wres, sizeof(double) * hw.size(), cudaMemcpyDeviceToHost,
                              d.st));
@@ -1702,6 +1735,7 @@ int batched_after_filter(Dev& d, std::vector<Solver<chase_c64>*>& act, double* t
   CHASE_TRY(d.alloc(&dperm, std::max(off[P], 1)));
   CHASE_CUDA(cudaMemcpyAsync(dperm, hperm.data(), sizeof(int) * off[P], cudaMemcpyHostToDevice,
                              d.st));
+  CHASE_TRY(fork());
   for (int i = 0; i < P; ++i) CHASE_TRY(act[i]->apply_perm(*view[i], dperm + off[i]));
   CHASE_TRY(read_flags("chase_solve_batched reordering"));
   tm.end();
@@ -1765,6 +1799,22 @@ extern "C" int chase_solve_batched(int P, const chase_c64* const* H, const int64
   }
   WorkerPool pool(d.st);
   CHASE_TRY(pool.init(std::min(P, kBatchWorkers)));
+  // streams for the batched phases (the workspace the workers allocated is
+  // released after these finish: the pool synchronises the main stream)
+  struct Fan {
+    std::vector<cudaStream_t> s;
+    ~Fan() {
+      for (auto x : s) {
+        cudaStreamSynchronize(x);
+        cudaStreamDestroy(x);
+      }
+    }
+  } fan;
+  for (int k = 0; k < std::min(P, kBatchStreams); ++k) {
+    cudaStream_t x = nullptr;
+    CHASE_CUDA(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+    fan.s.push_back(x);
+  }
   std::vector<int> all(P);  // largest problems first (see WorkerPool::run)
   std::iota(all.begin(), all.end(), 0);
   std::stable_sort(all.begin(), all.end(),
@@ -1840,7 +1890,7 @@ extern "C" int chase_solve_batched(int P, const chase_c64* const* H, const int64
     std::vector<Solver<chase_c64>*> ap;
     for (int p : act) ap.push_back(&sv[p]);
     double tph[4] = {0.0, 0.0, 0.0, 0.0};
-    CHASE_TRY(batched_after_filter(d, ap, tph));
+    CHASE_TRY(batched_after_filter(d, ap, fan.s, tph));
     bs.t_qr += tph[0];
     bs.t_rr += tph[1];
     bs.t_eigh += tph[2];
