@@ -995,7 +995,7 @@ def run_batched_solve_workload(args, rank, world, local):
     nevs = [s[1] for s in shapes]
     nexs = [s[2] for s in shapes]
     prec = prec_code(args.precision)
-    o = chase.chase_opts_default(precision=prec)
+    o = chase.chase_opts_default(precision=prec, deg_extra=deg_extra_for(args, prec))
 
     def batched(idx):
         Vs = [V0s[i].clone() for i in idx]
@@ -1036,7 +1036,7 @@ def run_batched_solve_workload(args, rank, world, local):
         "workload": (f"batched solve of {P} independent problems, N uniform in [256, 2048], "
                      f"nev = 5% N, nex = 2% N, eigenvalues uniform in [-1, 1], tol {args.tol}; "
                      f"step = one chase_solve_batched call"),
-        "problems": P, "precision": args.precision,
+        "problems": P, "precision": args.precision, "deg_extra": o.deg_extra,
         "l2": "inputs larger than L2",
         "parallelism": "replicas" if world > 1 else "single GPU",
     }
@@ -1443,7 +1443,7 @@ def run_serve_workload(args, rank, world, local):
     trace = serve.poisson_trace(args.serve_requests, args.serve_rate, args.seed + 1000 * rank,
                                 sizes=sizes, weights=weights)
     fp = lambda r: serve.footprint_bytes(r.n, r.nev, r.nex, split)
-    solver = serve.gpu_sequence_solver(dev, prec, tol=args.tol)
+    solver = serve.gpu_sequence_solver(dev, prec, tol=args.tol, deg_extra=deg_extra_for(args, prec))
     # warm-up: one small request (library load, handles, kernels)
     small = serve.Request(-1, min(sizes), int(np.ceil(0.04 * min(sizes))),
                           int(np.ceil(0.008 * min(sizes))), 2, 99, 0.0)
@@ -1466,6 +1466,7 @@ def run_serve_workload(args, rank, world, local):
                        f"N in {sizes} weighted {weights}, 5-10 problems each, nev = 4% N, "
                        f"nex = 20% nev, admission cap {args.serve_cap_gb} GB, "
                        f"{args.serve_slots} slots; step = the whole trace")
+    cfg["deg_extra"] = deg_extra_for(args, prec)
     line = {
         "metric": METRIC, "value": round(flops / wall / 1e12, 3), "unit": "TFLOP/s",
         "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": round(1e3 * wall, 1),

@@ -194,8 +194,122 @@ __device__ __forceinline__ void acquire_tmap(const CUtensorMap* map) {
                : "memory");
 }
 
+// The FP64 epilogue of one output tile: combine the exact int32 level sums
+// of this thread's row (32 columns, half hf of the tile) with the FP32 tail
+// levels read from TMEM, scale, and apply the diagonal, shift, scale and
+// axpby of Eq. 7 (or store the raw K-segment partial product).
 template <int NS>
-__device__ __forceinline__ void split_tile_body(const SplitTile& T, int* __restrict__ err) {
+__device__ __forceinline__ void split_epilogue(const SplitTile& T, uint32_t tbase,
+                                               const int (&sums)[Slices<NS>::NEXACT][32], int row,
+                                               int hf) {
+  constexpr int S = Slices<NS>::S;
+  constexpr int NEXACT = Slices<NS>::NEXACT;
+  const int row0 = T.arow, colr0 = T.brow, M = T.M;
+  {
+    const int grow = row0 + row;
+    const bool in_rows = grow < M;
+    const int er = in_rows ? T.E[grow] : 0;
+    const bool raw = T.P != nullptr;  // one K segment: the combine kernel finishes
+    const double alpha = raw ? 1.0 : T.alpha;
+    const double adsh = raw ? 0.0 : T.alpha * ((T.Dg && in_rows ? T.Dg[grow] : 0.0) - T.shift);
+#pragma unroll
+    for (int c0 = 0; c0 < 32; c0 += 8) {
+      float t[8];
+      if constexpr (S > NEXACT) {
+        uint32_t r[8];
+        TMEM_LD8(tbase + (S - 1) * BN + c0, r);
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 8; ++j) t[j] = __uint_as_float(r[j]);
+#pragma unroll 1
+        for (int d = S - 2; d >= NEXACT; --d) {
+          TMEM_LD8(tbase + d * BN + c0, r);
+          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+          for (int j = 0; j < 8; ++j) t[j] = fmaf(t[j], 0.0078125f, __uint_as_float(r[j]));
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) t[j] = 0.f;  // no tail levels
+      }
+      if (in_rows && T.cplx) {
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) {
+          const int cc = (colr0 + hf * 32 + c0 + j) >> 1;  // complex column (B map)
+          if (cc >= T.cend) continue;
+          const int ex = er + T.F[cc] - 28;
+          const bool normal = ex >= -1022 && ex <= 1023;
+          const double sc = normal ? pow2_normal(ex) * alpha : alpha;
+          double v[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const long long Sx = (static_cast<long long>(sums[0][c0 + j + h]) << 14) +
+                                 (static_cast<long long>(sums[1][c0 + j + h]) << 7) +
+                                 static_cast<long long>(sums[2][c0 + j + h]);
+            v[h] = (static_cast<double>(Sx) + static_cast<double>(t[j + h] * 0.0078125f)) * sc;
+            if (!normal) v[h] = ldexp(v[h], ex);  // subnormal or overflowing scale
+          }
+          if (raw) {
+            T.P[static_cast<long long>(cc) * T.ldp + grow] = make_double2(v[0], v[1]);
+            continue;
+          }
+          const long long jc = cc + T.joff;
+          if (adsh != 0.0) {
+            const double2 xv = T.X[jc * T.ldx + grow];
+            v[0] = fma(adsh, xv.x, v[0]);
+            v[1] = fma(adsh, xv.y, v[1]);
+          }
+          double2* yp = T.Y + jc * T.ldy + grow;
+          if (T.beta != 0.0) {
+            const double2 yv = *yp;
+            v[0] = fma(T.beta, yv.x, v[0]);
+            v[1] = fma(T.beta, yv.y, v[1]);
+          }
+          *yp = make_double2(v[0], v[1]);
+        }
+      } else if (in_rows) {  // real operands: one B-map row per column
+        const double* Xr = reinterpret_cast<const double*>(T.X);
+        double* Yr = reinterpret_cast<double*>(T.Y);
+        double* Pr = reinterpret_cast<double*>(T.P);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int cc = colr0 + hf * 32 + c0 + j;
+          if (cc >= T.cend) continue;
+          const int ex = er + T.F[cc] - 28;
+          const bool normal = ex >= -1022 && ex <= 1023;
+          const double sc = normal ? pow2_normal(ex) * alpha : alpha;
+          const long long Sx = (static_cast<long long>(sums[0][c0 + j]) << 14) +
+                               (static_cast<long long>(sums[1][c0 + j]) << 7) +
+                               static_cast<long long>(sums[2][c0 + j]);
+          double v = (static_cast<double>(Sx) + static_cast<double>(t[j] * 0.0078125f)) * sc;
+          if (!normal) v = ldexp(v, ex);
+          if (raw) {
+            Pr[static_cast<long long>(cc) * T.ldp + grow] = v;
+            continue;
+          }
+          const long long jc = cc + T.joff;
+          if (adsh != 0.0) v = fma(adsh, Xr[jc * T.ldx + grow], v);
+          double* yp = Yr + jc * T.ldy + grow;
+          if (T.beta != 0.0) v = fma(T.beta, *yp, v);
+          *yp = v;
+        }
+      }
+    }
+  }
+}
+
+// The split product over a list of output tiles, persistent: each CTA
+// allocates its TMEM and initialises its barriers once, then takes tiles
+// t = blockIdx.x, blockIdx.x + gridDim.x, ... (tile(t, T) describes tile t).
+// Barrier phases run on across tiles (global stage and chunk counters).
+// While the flush warps run a tile's epilogue, the producer already loads
+// the next tile's first stages; the MMA issuer starts the next tile once
+// the epilogue has read TMEM (tmem_free).  CTAs that start their k-th tile
+// together stream the same K ranges of neighbouring tiles, so the L2 serves
+// each slab once to all of them.
+template <int NS, class TileFn>
+__device__ __forceinline__ void split_tiles_body(const TileFn& tile, int ntiles,
+                                                 int* __restrict__ err) {
   static_assert(NS >= 3 && NS <= 7, "3 to 7 slices");
   using C = Slices<NS>;
   constexpr int S = C::S;
@@ -216,16 +330,10 @@ __device__ __forceinline__ void split_tile_body(const SplitTile& T, int* __restr
   uint64_t* chunk_full = bars + 2 * NSTAGE;
   uint64_t* chunk_empty = chunk_full + 1;
   uint64_t* done = chunk_full + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(chunk_full + 3);
+  uint64_t* tmem_free = chunk_full + 3;  // the epilogue has read the tile's TMEM
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(chunk_full + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row0 = T.arow;
-  const int colr0 = T.brow;
-  const int nkb = T.nkb;
-  const int kb0 = T.kb0;
-  const int M = T.M;
-  const int nchunks = (nkb + CHUNK - 1) / CHUNK;
-  const int nst = (nkb + KPS - 1) / KPS;  // stages (the last may hold one K block)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NSTAGE; ++s) {
@@ -235,6 +343,7 @@ __device__ __forceinline__ void split_tile_body(const SplitTile& T, int* __restr
     mbar_init(chunk_full, 1);
     mbar_init(chunk_empty, kFlushWarps);
     mbar_init(done, 1);
+    mbar_init(tmem_free, kFlushWarps);
     fence_barrier_init();
   }
   if (warp == 1) {
@@ -250,79 +359,115 @@ __device__ __forceinline__ void split_tile_body(const SplitTile& T, int* __restr
 
   if (warp == 0) {
     if (lane == 0) {  // ---------------- TMA producer
-      if (T.maps_in_global) {
-        acquire_tmap(T.mapA);
-        acquire_tmap(T.mapB);
-      }
-      prefetch_tmap(T.mapA);
-      prefetch_tmap(T.mapB);
-      int issued = 0;
-      for (int ks = 0; ks < nst; ++ks) {
-        const int st = ks % NSTAGE;
-        if (ks >= NSTAGE && !mbar_wait_bounded(&empty[st], ((ks / NSTAGE) & 1) ^ 1)) {
-          atomicOr(err, KERR_TIMEOUT_EMPTY);
-          break;
+      long long g = 0;  // stages issued by this CTA so far
+      bool ok = true;
+      const CUtensorMap* last_a = nullptr;
+      const CUtensorMap* last_b = nullptr;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        SplitTile T;
+        tile(t, T);
+        if (T.mapA != last_a || T.mapB != last_b) {
+          if (T.maps_in_global) {
+            acquire_tmap(T.mapA);
+            acquire_tmap(T.mapB);
+          }
+          prefetch_tmap(T.mapA);
+          prefetch_tmap(T.mapB);
+          last_a = T.mapA;
+          last_b = T.mapB;
         }
-        mbar_arrive_expect_tx(&full[st], STAGE_BYTES);
-        tma_load_3d(smem_u32(sA + st * STAGE_A), T.mapA, (kb0 + ks * KPS) * BK, row0, 0, smem_u32(&full[st]));
-        tma_load_3d(smem_u32(sB + st * STAGE_B), T.mapB, (kb0 + ks * KPS) * BK, colr0, 0, smem_u32(&full[st]));
-        ++issued;
+        const int nst = (T.nkb + KPS - 1) / KPS;  // stages (the last may hold one K block)
+        for (int ks = 0; ks < nst; ++ks, ++g) {
+          const int st = static_cast<int>(g % NSTAGE);
+          if (g >= NSTAGE &&
+              !mbar_wait_bounded(&empty[st], static_cast<uint32_t>((g / NSTAGE) & 1) ^ 1u)) {
+            atomicOr(err, KERR_TIMEOUT_EMPTY);
+            ok = false;
+            break;
+          }
+          mbar_arrive_expect_tx(&full[st], STAGE_BYTES);
+          tma_load_3d(smem_u32(sA + st * STAGE_A), T.mapA, (T.kb0 + ks * KPS) * BK, T.arow, 0,
+                      smem_u32(&full[st]));
+          tma_load_3d(smem_u32(sB + st * STAGE_B), T.mapB, (T.kb0 + ks * KPS) * BK, T.brow, 0,
+                      smem_u32(&full[st]));
+        }
       }
-      for (int ks = (issued > NSTAGE ? issued - NSTAGE : 0); ks < issued; ++ks)
-        if (!mbar_wait_bounded(&full[ks % NSTAGE], (ks / NSTAGE) & 1)) atomicOr(err, KERR_TIMEOUT_FULL);
+      // no copy may be in flight when the CTA ends
+      for (long long k = (g > NSTAGE ? g - NSTAGE : 0); k < g; ++k)
+        if (!mbar_wait_bounded(&full[k % NSTAGE], static_cast<uint32_t>((k / NSTAGE) & 1)))
+          atomicOr(err, KERR_TIMEOUT_FULL);
     }
   } else if (warp == 1) {
     if (lane == 0) {  // ---------------- MMA issuer
       // kind::f16 instruction descriptor without N: FP32 D, BF16 A and B, K-major, M = 128
       const uint32_t idesc_base = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BM >> 4) << 24);
       bool ok = true;
-      for (int ks = 0; ks < nst && ok; ++ks) {
-        const int st = ks % NSTAGE;
-        if (!mbar_wait_bounded(&full[st], (ks / NSTAGE) & 1)) {
+      long long g = 0, gc = 0;  // stages and exact chunks consumed so far
+      int tk = 0;               // tiles started
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tk) {
+        SplitTile T;
+        tile(t, T);
+        const int nkb = T.nkb;
+        const int nst = (nkb + KPS - 1) / KPS;
+        const int nchunks = (nkb + CHUNK - 1) / CHUNK;
+        // the previous tile's epilogue must have read TMEM before it is overwritten
+        if (tk > 0 && !mbar_wait_bounded(tmem_free, static_cast<uint32_t>((tk - 1) & 1))) {
           atomicOr(err, KERR_TIMEOUT_FULL);
           ok = false;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        for (int kh = 0; kh < KPS && ok; ++kh) {
-          const int kb = ks * KPS + kh;
-          if (kb >= nkb) break;
-          const int ch = kb / CHUNK, kin = kb % CHUNK;
-          const uint32_t a0 = smem_u32(sA + st * STAGE_A) + kh * (BK * 2);
-          const uint32_t b0 = smem_u32(sB + st * STAGE_B) + kh * (BK * 2);
-          // At a chunk boundary the tail levels (3-6) go first: they do not touch
-          // the exact levels that the flush warps are still reading, so the
-          // tensor pipe works while the flush runs.
-          const bool boundary = (kin == 0 && ch > 0);
+        for (int ks = 0; ks < nst && ok; ++ks, ++g) {
+          const int st = static_cast<int>(g % NSTAGE);
+          if (!mbar_wait_bounded(&full[st], static_cast<uint32_t>((g / NSTAGE) & 1))) {
+            atomicOr(err, KERR_TIMEOUT_FULL);
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+          for (int kh = 0; kh < KPS && ok; ++kh) {
+            const int kb = ks * KPS + kh;
+            if (kb >= nkb) break;
+            const int ch = kb / CHUNK, kin = kb % CHUNK;
+            const uint32_t a0 = smem_u32(sA + st * STAGE_A) + kh * (BK * 2);
+            const uint32_t b0 = smem_u32(sB + st * STAGE_B) + kh * (BK * 2);
+            // At a chunk boundary the tail levels (3-6) go first: they do not touch
+            // the exact levels that the flush warps are still reading, so the
+            // tensor pipe works while the flush runs.
+            const bool boundary = (kin == 0 && ch > 0);
 #pragma unroll
-          for (int pass = 0; pass < 2; ++pass) {
-            const bool exact_pass = (pass == 1);
-            if (boundary && exact_pass && !mbar_wait_bounded(chunk_empty, (ch - 1) & 1)) {
-              atomicOr(err, KERR_TIMEOUT_FULL);
-              ok = false;
-              break;
-            }
+            for (int pass = 0; pass < 2; ++pass) {
+              const bool exact_pass = (pass == 1);
+              if (boundary && exact_pass &&
+                  !mbar_wait_bounded(chunk_empty, static_cast<uint32_t>((gc + ch - 1) & 1))) {
+                atomicOr(err, KERR_TIMEOUT_FULL);
+                ok = false;
+                break;
+              }
 #pragma unroll
-            for (int s = 0; s < S; ++s) {
-              // Slice s of H against the slices t of the block that feed the levels
-              // d = s + t of this pass, as one MMA: the B planes t are consecutive
-              // rows of the B tile and the levels consecutive TMEM columns, so
-              // N = 64 x (number of levels).
-              const uint64_t da = desc_sw64(a0 + s * A_TILE);
-              const int d0 = exact_pass ? s : (s < NEXACT ? NEXACT : s);
-              const int nlev = exact_pass ? NEXACT - s : S - d0;
-              if (nlev <= 0) continue;
-              // first contribution to these levels in this accumulation window?
-              const bool first = (s == 0) && (exact_pass ? kin == 0 : kb == 0);
-              const uint32_t idn = idesc_base | ((uint32_t)((nlev * BN) >> 3) << 17);
-              umma_bf16(tmem + d0 * BN, da, desc_sw64(b0 + (d0 - s) * B_TILE), idn, first ? 0u : 1u);
+              for (int s = 0; s < S; ++s) {
+                // Slice s of H against the slices t of the block that feed the levels
+                // d = s + t of this pass, as one MMA: the B planes t are consecutive
+                // rows of the B tile and the levels consecutive TMEM columns, so
+                // N = 64 x (number of levels).
+                const uint64_t da = desc_sw64(a0 + s * A_TILE);
+                const int d0 = exact_pass ? s : (s < NEXACT ? NEXACT : s);
+                const int nlev = exact_pass ? NEXACT - s : S - d0;
+                if (nlev <= 0) continue;
+                // first contribution to these levels in this accumulation window?
+                const bool first = (s == 0) && (exact_pass ? kin == 0 : kb == 0);
+                const uint32_t idn = idesc_base | ((uint32_t)((nlev * BN) >> 3) << 17);
+                umma_bf16(tmem + d0 * BN, da, desc_sw64(b0 + (d0 - s) * B_TILE), idn,
+                          first ? 0u : 1u);
+              }
             }
+            if (!ok) break;
+            if (kin == CHUNK - 1 || kb == nkb - 1) umma_commit(smem_u32(chunk_full));
           }
           if (!ok) break;
-          if (kin == CHUNK - 1 || kb == nkb - 1) umma_commit(smem_u32(chunk_full));
+          umma_commit(smem_u32(&empty[st]));
         }
-        if (!ok) break;
-        umma_commit(smem_u32(&empty[st]));
+        gc += nchunks;
       }
       umma_commit(smem_u32(done));  // every MMA of this CTA has completed when this fires
       if (!mbar_wait_bounded(done, 0)) atomicOr(err, KERR_TIMEOUT_FULL);
@@ -336,124 +481,40 @@ __device__ __forceinline__ void split_tile_body(const SplitTile& T, int* __restr
     const uint32_t tbase = tmem + (static_cast<uint32_t>(q * 32) << 16) + hf * 32;
     int sums[NEXACT][32];  // exact level sums of this row, 32 columns
     bool ok = true;
-    for (int ch = 0; ch < nchunks; ++ch) {
-      if (!mbar_wait_bounded(chunk_full, ch & 1)) {
-        if (lane == 0) atomicOr(err, KERR_TIMEOUT_FULL);
-        ok = false;
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-#pragma unroll
-      for (int d = 0; d < NEXACT; ++d) {
-        uint32_t r[32];
-        TMEM_LD32(tbase + d * BN, r);
-        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int v = __float2int_rn(__uint_as_float(r[j]));
-          sums[d][j] = (ch == 0) ? v : sums[d][j] + v;
+    long long gc = 0;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      SplitTile T;
+      tile(t, T);
+      const int nchunks = (T.nkb + CHUNK - 1) / CHUNK;
+      for (int ch = 0; ch < nchunks; ++ch) {
+        if (!mbar_wait_bounded(chunk_full, static_cast<uint32_t>((gc + ch) & 1))) {
+          if (lane == 0) atomicOr(err, KERR_TIMEOUT_FULL);
+          ok = false;
+          break;
         }
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-      __syncwarp();
-      if (lane == 0) mbar_arrive(chunk_empty);
-    }
-    if (ok) {
-      // The last chunk_full covers every MMA, tail levels included.  With
-      // S = 2^14 L0 + 2^7 L1 + L2 (exact in int64) and the tail
-      // T = L3 + 2^-7 L4 + 2^-14 L5 + 2^-21 L6 (FP32, Horner), an entry is
-      // 2^(E_r + F_c - 28) (S + 2^-7 T); the FP64 work per entry is one add,
-      // one scale and the two fused multiply-adds of the recurrence (the
-      // FP64 pipe is narrow on this GPU, so the epilogue keeps it short).
-      const int grow = row0 + row;
-      const bool in_rows = grow < M;
-      const int er = in_rows ? T.E[grow] : 0;
-      const bool raw = T.P != nullptr;  // one K segment: the combine kernel finishes
-      const double alpha = raw ? 1.0 : T.alpha;
-      const double adsh = raw ? 0.0 : T.alpha * ((T.Dg && in_rows ? T.Dg[grow] : 0.0) - T.shift);
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll
-      for (int c0 = 0; c0 < 32; c0 += 8) {
-        float t[8];
-        if constexpr (S > NEXACT) {
-          uint32_t r[8];
-          TMEM_LD8(tbase + (S - 1) * BN + c0, r);
+        for (int d = 0; d < NEXACT; ++d) {
+          uint32_t r[32];
+          TMEM_LD32(tbase + d * BN, r);
           asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-          for (int j = 0; j < 8; ++j) t[j] = __uint_as_float(r[j]);
-#pragma unroll 1
-          for (int d = S - 2; d >= NEXACT; --d) {
-            TMEM_LD8(tbase + d * BN + c0, r);
-            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-            for (int j = 0; j < 8; ++j) t[j] = fmaf(t[j], 0.0078125f, __uint_as_float(r[j]));
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < 8; ++j) t[j] = 0.f;  // no tail levels
-        }
-        if (in_rows && T.cplx) {
-#pragma unroll
-          for (int j = 0; j < 8; j += 2) {
-            const int cc = (colr0 + hf * 32 + c0 + j) >> 1;  // complex column (B map)
-            if (cc >= T.cend) continue;
-            const int ex = er + T.F[cc] - 28;
-            const bool normal = ex >= -1022 && ex <= 1023;
-            const double sc = normal ? pow2_normal(ex) * alpha : alpha;
-            double v[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const long long Sx = (static_cast<long long>(sums[0][c0 + j + h]) << 14) +
-                                   (static_cast<long long>(sums[1][c0 + j + h]) << 7) +
-                                   static_cast<long long>(sums[2][c0 + j + h]);
-              v[h] = (static_cast<double>(Sx) + static_cast<double>(t[j + h] * 0.0078125f)) * sc;
-              if (!normal) v[h] = ldexp(v[h], ex);  // subnormal or overflowing scale
-            }
-            if (raw) {
-              T.P[static_cast<long long>(cc) * T.ldp + grow] = make_double2(v[0], v[1]);
-              continue;
-            }
-            const long long jc = cc + T.joff;
-            if (adsh != 0.0) {
-              const double2 xv = T.X[jc * T.ldx + grow];
-              v[0] = fma(adsh, xv.x, v[0]);
-              v[1] = fma(adsh, xv.y, v[1]);
-            }
-            double2* yp = T.Y + jc * T.ldy + grow;
-            if (T.beta != 0.0) {
-              const double2 yv = *yp;
-              v[0] = fma(T.beta, yv.x, v[0]);
-              v[1] = fma(T.beta, yv.y, v[1]);
-            }
-            *yp = make_double2(v[0], v[1]);
-          }
-        } else if (in_rows) {  // real operands: one B-map row per column
-          const double* Xr = reinterpret_cast<const double*>(T.X);
-          double* Yr = reinterpret_cast<double*>(T.Y);
-          double* Pr = reinterpret_cast<double*>(T.P);
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int cc = colr0 + hf * 32 + c0 + j;
-            if (cc >= T.cend) continue;
-            const int ex = er + T.F[cc] - 28;
-            const bool normal = ex >= -1022 && ex <= 1023;
-            const double sc = normal ? pow2_normal(ex) * alpha : alpha;
-            const long long Sx = (static_cast<long long>(sums[0][c0 + j]) << 14) +
-                                 (static_cast<long long>(sums[1][c0 + j]) << 7) +
-                                 static_cast<long long>(sums[2][c0 + j]);
-            double v = (static_cast<double>(Sx) + static_cast<double>(t[j] * 0.0078125f)) * sc;
-            if (!normal) v = ldexp(v, ex);
-            if (raw) {
-              Pr[static_cast<long long>(cc) * T.ldp + grow] = v;
-              continue;
-            }
-            const long long jc = cc + T.joff;
-            if (adsh != 0.0) v = fma(adsh, Xr[jc * T.ldx + grow], v);
-            double* yp = Yr + jc * T.ldy + grow;
-            if (T.beta != 0.0) v = fma(T.beta, *yp, v);
-            *yp = v;
+          for (int j = 0; j < 32; ++j) {
+            const int v = __float2int_rn(__uint_as_float(r[j]));
+            sums[d][j] = (ch == 0) ? v : sums[d][j] + v;
           }
         }
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(chunk_empty);
       }
+      if (!ok) break;
+      // The last chunk_full covers every MMA of the tile, tail levels included.
+      split_epilogue<NS>(T, tbase, sums, row, hf);
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tmem_free);
+      gc += nchunks;
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -481,8 +542,21 @@ __device__ __forceinline__ void raster_tile(int bid, int rtiles, int ctiles, int
   *ct = in / gr;
 }
 
-// One problem: a 1-D grid over the output tiles (raster_tile), B map over
-// the active block.
+// The tiles of one problem: a base tile description and the raster order.
+struct OneProblemTiles {
+  SplitTile base;
+  int rtiles, ctiles;
+  __device__ __forceinline__ void operator()(int t, SplitTile& T) const {
+    T = base;
+    int rt, ct;
+    raster_tile(t, rtiles, ctiles, &rt, &ct);
+    T.arow = rt * BM;
+    T.brow = ct * BN;
+  }
+};
+
+// One problem, persistent CTAs over its output tiles (raster_tile order); B
+// map over the active block.
 template <int NS>
 __global__ void __launch_bounds__(kThreads, 1)
     zgemm_split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -491,17 +565,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                        const double2* __restrict__ Xsh, long long ldx, double2* __restrict__ Y,
                        long long ldy, double alpha, double beta, double shift,
                        double2* __restrict__ P, long long ldp, int cplx, int* __restrict__ err) {
-  SplitTile T;
+  OneProblemTiles src;
+  SplitTile& T = src.base;
   T.mapA = &tmA;
   T.mapB = &tmB;
   T.maps_in_global = 0;
   T.cplx = cplx;
-  const int ctiles = ((cplx ? 2 : 1) * ncols + BN - 1) / BN;
-  const int rtiles = (M + BM - 1) / BM;
-  int rt, ct;
-  raster_tile(blockIdx.x, rtiles, ctiles, &rt, &ct);
-  T.arow = rt * BM;
-  T.brow = ct * BN;
+  T.arow = 0;
+  T.brow = 0;
   T.cend = ncols;
   T.joff = j0;
   T.kb0 = kb0;
@@ -519,7 +590,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   T.shift = shift;
   T.P = P;
   T.ldp = ldp;
-  split_tile_body<NS>(T, err);
+  src.ctiles = ((cplx ? 2 : 1) * ncols + BN - 1) / BN;
+  src.rtiles = (M + BM - 1) / BM;
+  split_tiles_body<NS>(src, src.rtiles * src.ctiles, err);
 }
 
 // Problem of CTA `bid` in a grouped step list: the last entry with
@@ -535,44 +608,54 @@ __device__ __forceinline__ int grouped_find(const GroupedStep* __restrict__ step
   return lo;
 }
 
-// Many problems in one launch: one CTA per output tile of every active
-// problem of one degree step.  Within a problem the column tile runs
-// fastest, so CTAs that run together share rows of H in L2.
+// The tiles of every active problem of one degree step of a grouped filter
+// (tile t: the problem whose tile range holds t, found by binary search;
+// within a problem the column tile runs fastest).
+struct GroupedStepTiles {
+  const GroupedProblem* probs;
+  const GroupedStep* steps;
+  int nact, parity;
+  __device__ __forceinline__ void operator()(int t, SplitTile& T) const {
+    const int e = grouped_find(steps, nact, t, true);
+    const GroupedStep stp = steps[e];
+    const GroupedProblem& pr = probs[stp.prob];
+    const int local = t - stp.tile0;
+    const int ncol_tiles = (2 * (pr.b - stp.s) + BN - 1) / BN;
+    T.mapA = pr.mapA;
+    T.mapB = pr.mapB0;
+    T.maps_in_global = 1;
+    T.cplx = 1;
+    T.arow = (local / ncol_tiles) * BM;
+    T.brow = 2 * stp.s + (local % ncol_tiles) * BN;
+    T.cend = pr.b;
+    T.joff = 0;
+    T.kb0 = 0;
+    T.nkb = static_cast<int>(pr.Kp / BK);
+    T.M = pr.n;
+    T.E = pr.E;
+    T.F = pr.F;
+    T.Dg = pr.Dg;
+    T.X = parity ? pr.buf1 : pr.buf0;
+    T.ldx = parity ? pr.ld1 : pr.ld0;
+    T.Y = parity ? pr.buf0 : pr.buf1;
+    T.ldy = parity ? pr.ld0 : pr.ld1;
+    T.alpha = stp.alpha;
+    T.beta = stp.beta;
+    T.shift = stp.shift;
+    T.P = nullptr;
+    T.ldp = 0;
+  }
+};
+
+// Many problems in one launch: persistent CTAs over the output tiles of
+// every active problem of one degree step (problems ordered by decreasing
+// N, so the longest tiles go first).
 __global__ void __launch_bounds__(kThreads, 1)
     zgemm_split_grouped_kernel(const GroupedProblem* __restrict__ probs,
                                const GroupedStep* __restrict__ steps, int nact, int parity,
-                               int* __restrict__ err) {
-  const int bid = blockIdx.x;
-  const int e = grouped_find(steps, nact, bid, true);
-  const GroupedStep stp = steps[e];
-  const GroupedProblem& pr = probs[stp.prob];
-  const int local = bid - stp.tile0;
-  const int ncol_tiles = (2 * (pr.b - stp.s) + BN - 1) / BN;
-  SplitTile T;
-  T.mapA = pr.mapA;
-  T.mapB = pr.mapB0;
-  T.maps_in_global = 1;
-  T.cplx = 1;
-  T.arow = (local / ncol_tiles) * BM;
-  T.brow = 2 * stp.s + (local % ncol_tiles) * BN;
-  T.cend = pr.b;
-  T.joff = 0;
-  T.kb0 = 0;
-  T.nkb = static_cast<int>(pr.Kp / BK);
-  T.M = pr.n;
-  T.E = pr.E;
-  T.F = pr.F;
-  T.Dg = pr.Dg;
-  T.X = parity ? pr.buf1 : pr.buf0;
-  T.ldx = parity ? pr.ld1 : pr.ld0;
-  T.Y = parity ? pr.buf0 : pr.buf1;
-  T.ldy = parity ? pr.ld0 : pr.ld1;
-  T.alpha = stp.alpha;
-  T.beta = stp.beta;
-  T.shift = stp.shift;
-  T.P = nullptr;
-  T.ldp = 0;
-  split_tile_body<S>(T, err);
+                               int ntiles, int* __restrict__ err) {
+  GroupedStepTiles src{probs, steps, nact, parity};
+  split_tiles_body<S>(src, ntiles, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -865,6 +948,19 @@ __global__ void split_combine_kernel(const E* __restrict__ P, int nseg, long lon
 // ---------------------------------------------------------------------------
 namespace {
 int64_t k_padded(int64_t N) { return ((2 * N + split::BK - 1) / split::BK) * split::BK; }
+
+// SMs of the current device (persistent grids: one CTA per SM)
+int split_sm_count() {
+  static const int v = [] {  // thread-safe one-time initialisation
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+      n = 152;
+    cudaGetLastError();
+    return n;
+  }();
+  return v;
+}
 static_assert(kSplitTileRows == split::BM && kSplitTileRealCols == split::BN &&
                   kSplitSlices == split::S && kSplitStageK == split::BX,
               "grouped tile constants");
@@ -988,7 +1084,8 @@ int split_product_ns(Dev& d, const SplitH& h, SplitX& x, const E* X, int64_t ldx
   CHASE_CUDA(attr_rc);
   const int64_t ctiles = (brows + split::BN - 1) / split::BN;
   const int64_t rtiles = (N + split::BM - 1) / split::BM;
-  dim3 grid(static_cast<unsigned>(ctiles * rtiles));  // raster_tile maps it to (row, column)
+  // persistent CTAs, one per SM at most (raster_tile orders the tiles)
+  dim3 grid(static_cast<unsigned>(std::min<int64_t>(ctiles * rtiles, split_sm_count())));
   const int nkb = static_cast<int>(Kp / split::BK);
   const int nseg = segments_for(nkb, ctiles * rtiles);
   const double2* Xd = reinterpret_cast<const double2*>(X);
@@ -1102,8 +1199,9 @@ int zgemm_split_grouped(Dev& d, const GroupedProblem* probs, const GroupedStep* 
                         int ntiles, int parity) {
   if (ntiles <= 0) return CHASE_OK;
   CHASE_TRY(zgemm_split_grouped_prepare());
-  split::zgemm_split_grouped_kernel<<<static_cast<unsigned>(ntiles), split::kThreads, split::SMEM,
-                                      d.st>>>(probs, steps, nact, parity, d.err);
+  split::zgemm_split_grouped_kernel<<<static_cast<unsigned>(std::min(ntiles, split_sm_count())),
+                                      split::kThreads, split::SMEM, d.st>>>(probs, steps, nact,
+                                                                          parity, ntiles, d.err);
   note_launch();
   CHASE_CUDA(cudaGetLastError());
   return CHASE_OK;

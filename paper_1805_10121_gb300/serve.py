@@ -207,11 +207,12 @@ class Server:
 
 
 def gpu_sequence_solver(device, precision: int, tol: float = 1e-10, seq_scale: float = 1e-3,
-                        keep_last_h: bool = False):
+                        keep_last_h: bool = False, deg_extra: Optional[int] = None):
     """solve_fn for Server: builds the request's sequence on the slot's
     stream and solves it problem after problem with warm starts.  With
     ``keep_last_h`` the result also carries the last problem's H on the host
-    (for checks against its exact spectrum)."""
+    (for checks against its exact spectrum).  ``deg_extra`` overrides
+    DEGEXTRA of Alg. 5 (Table 1: 2)."""
     import torch
 
     from . import chase, synth
@@ -238,6 +239,8 @@ def gpu_sequence_solver(device, precision: int, tol: float = 1e-10, seq_scale: f
                     H = (H + (seq_scale * hnorm) * E).t().contiguous().t()
                     del E
                 o = chase.chase_opts_default(approx=0 if k == 0 else 1, precision=precision)
+                if deg_extra is not None:
+                    o.deg_extra = int(deg_extra)
                 st, Lam, res, stats = chase.chase_solve(
                     H, req.nev, req.nex, tol, V, S if k == 0 else S[:, :1].contiguous(),
                     Lambda=Lam, opts=o, stream=s.cuda_stream)
