@@ -599,10 +599,11 @@ def filter_workload_config(args, world):
 
 # DRAM traffic of one zgemm_split_kernel launch of the default filter
 # workload (one of its two K segments: 30000 rows of H, 1500 complex
-# columns, K = 30000), measured with ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum, one pass, --clock-control none) on the committed
-# kernel; None until a capture of the current kernel exists.
-SPLIT_N30000_TRAFFIC = None
+# columns, K = 30000), measured with ncu on the persistent-CTA kernel
+# (dram__bytes_read.sum 265.45 GB + dram__bytes_write.sum 0.72 GB, one
+# pass, --clock-control none; the command is in the profile of this
+# kernel).  Set back to None whenever the kernel changes.
+SPLIT_N30000_TRAFFIC = 265.45e9 + 0.72461e9
 
 
 def split_algorithmic_bytes(n, ncols, k_per_launch):
@@ -681,7 +682,7 @@ def run_filter_workload(args, rank, world, local):
                   "FP64 recurrence epilogue)",
         "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
         "frac": round(achieved / peak, 4),
-        "traffic": SPLIT_N30000_TRAFFIC,
+        "traffic": SPLIT_N30000_TRAFFIC if (n == 30000 and nx == 1500) else None,
         "peak_source": f"{src} bf16_tflops_sustained (a kernel inside a multi-second loop)",
         "achieved_counts": "BF16 tensor FLOPs the kernel executes: 28 slice-pair products of "
                            "8 N^2 per complex column",
@@ -689,6 +690,8 @@ def run_filter_workload(args, rank, world, local):
         if kt["seconds"] > 0 else None,
         "launches": kt["launches"], "avg_launch_ms": round(1e3 * per_launch_s, 3),
         "algorithmic_bytes_per_launch": alg_bytes,
+        "traffic_over_algorithmic": round(SPLIT_N30000_TRAFFIC / alg_bytes, 2)
+        if SPLIT_N30000_TRAFFIC and n == 30000 and nx == 1500 else None,
         "timing": "CUDA events recorded by the library on the launching stream around the "
                   "product launches of the timed steps (chase_kernel_timing)",
     }
@@ -1367,6 +1370,8 @@ def run_solve_workload(args, rank, world, local):
     nx = nev + nex
     seed = args.seed + 1000 * rank
     prec = prec_code(args.precision)
+    de = args.deg_extra if args.deg_extra is not None else (
+        2 if prec == chase.CHASE_FP64 else COLD_SOLVE_DEG_EXTRA)
     stream = torch.cuda.current_stream(dev)
 
     def problem(nn, sd):
@@ -1380,7 +1385,7 @@ def run_solve_workload(args, rank, world, local):
         nxw = max(ns + 1, nw * nx // n)
         chase.chase_solve(Hw, ns, nxw - ns, tol, synth.gaussian_block(nw, nxw, seed + 51, device=dev),
                           synth.gaussian_block(nw, 5, seed + 52, device=dev),
-                          opts=chase.chase_opts_default(precision=prec))
+                          opts=chase.chase_opts_default(precision=prec, deg_extra=de))
     del Hw
     H, lam = problem(n, seed)
     hnorm = float(np.abs(lam).max())
@@ -1397,7 +1402,8 @@ def run_solve_workload(args, rank, world, local):
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
         st, ritz, res, s = chase.chase_solve(H, nev, nex, tol, V, S,
-                                             opts=chase.chase_opts_default(precision=prec))
+                                             opts=chase.chase_opts_default(precision=prec,
+                                                                           deg_extra=de))
         b.record(stream)
         torch.cuda.synchronize()
         t = a.elapsed_time(b) / 1e3
@@ -1408,10 +1414,13 @@ def run_solve_workload(args, rank, world, local):
                      "eig_err_max_over_norm": float(np.max(np.abs(ritz[:nev] - lam[:nev]))) / hnorm,
                      "phase_seconds": {k2: round(s[k2], 2) for k2 in
                                        ("t_lanczos", "t_filter", "t_qr", "t_rr", "t_eigh")},
+                     "filter_matvecs": s["filter_matvecs"],
+                     "filter_matvecs_low_precision": s["filter_matvecs_low"],
                      "filter_tflops": round(s["flops_filter"] / max(s["t_filter"], 1e-12) / 1e12, 2)})
         del V
     clk = clocks.stop()
     cfg = workload_config(args, world)
+    cfg["deg_extra"] = de
     cfg["workload"] = (f"cold solve of one problem, N={n} complex128 (FFT construction of "
                        f"Q diag(lambda) Q^H, the sequence law's spectrum), nev={nev}, nex={nex}, "
                        f"tol={tol} x ||H||; step = one solve")
@@ -1684,6 +1693,7 @@ def main():
         "filter_share_of_time": round(filt_t / max(elapsed, 1e-12), 4),
         "iterations": [s["iterations"] for s in stats_t],
         "matvecs": [s["matvecs"] for s in stats_t],
+        "filter_matvecs_low_precision": [s["filter_matvecs_low"] for s in stats_t],
         "status": statuses,
         "resid_max_over_norm": resid_max,
         "phase_seconds": {k2: round(sum(s[k2] for s in stats_t), 3)

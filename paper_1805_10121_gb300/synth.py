@@ -14,8 +14,21 @@ consecutive problems differ by a small Hermitian perturbation.
 from __future__ import annotations
 
 import math
+import threading
 
 import torch
+
+# torch.fft executes cached cuFFT plans whose stream and work area are set
+# on the shared plan just before each execution; generators running in
+# several threads at once (the serving loop builds each request's matrices
+# in its own thread) take this lock around every FFT call so that a plan is
+# never re-pointed by one thread while another enqueues it.
+_FFT_LOCK = threading.Lock()
+
+
+def _fft(x, dim, inverse=False):
+    with _FFT_LOCK:
+        return (torch.fft.ifft if inverse else torch.fft.fft)(x, dim=dim, norm="ortho")
 
 __all__ = [
     "generator",
@@ -70,9 +83,9 @@ def unitary_dft(n: int, seed: int, device="cpu") -> torch.Tensor:
     ph = torch.rand(3, n, dtype=torch.float64, device=device, generator=g) * (2.0 * math.pi)
     d = torch.polar(torch.ones_like(ph), ph)
     x = torch.diag(d[2])
-    x = torch.fft.fft(x, dim=0, norm="ortho")
+    x = _fft(x, 0)
     x = x * d[1][:, None]
-    x = torch.fft.fft(x, dim=0, norm="ortho")
+    x = _fft(x, 0)
     return x * d[0][:, None]
 
 
@@ -124,18 +137,19 @@ def hermitian_dft(lam: torch.Tensor, seed: int, chunk: int = 2048) -> torch.Tens
     g = generator(seed, device)
     ph = torch.rand(3, n, dtype=torch.float64, device=device, generator=g) * (2.0 * math.pi)
     d = torch.polar(torch.ones_like(ph), ph)
-    c = torch.fft.fft(lam.to(torch.complex128)) / n           # circulant column
+    with _FFT_LOCK:
+        c = torch.fft.fft(lam.to(torch.complex128)) / n       # circulant column
     t = torch.empty((n, n), dtype=torch.complex128, device=device)
     rows = torch.arange(n, device=device)
     for j0 in range(0, n, chunk):                              # F diag(lam) F^H, D2 . D2^H, F .
         j1 = min(n, j0 + chunk)
         blk = c[(rows[:, None] - rows[None, j0:j1]) % n]
         blk.mul_(d[1][:, None]).mul_(d[1][j0:j1].conj()[None, :])
-        t[:, j0:j1] = torch.fft.fft(blk, dim=0, norm="ortho")
+        t[:, j0:j1] = _fft(blk, 0)
         del blk
     for i0 in range(0, n, chunk):                              # . F^H, D1 . D1^H
         i1 = min(n, i0 + chunk)
-        blk = torch.fft.ifft(t[i0:i1, :], dim=1, norm="ortho")
+        blk = _fft(t[i0:i1, :], 1, inverse=True)
         blk.mul_(d[0][i0:i1, None]).mul_(d[0].conj()[None, :])
         t[i0:i1, :] = blk
         del blk
