@@ -241,12 +241,14 @@ def prec_code(name):
 SPLIT_PAIRS = 28
 
 
-# DRAM traffic of single launches measured with ncu (the N = 4000 captures):
-# the bench's own N = 8000 launches are larger than the capture size rule
-# allows, so "traffic" stays null and the small-case figures ride along.
+# DRAM traffic of single launches of other shapes, measured with ncu: the
+# sequence workload's own launches (N = 8000, 480 columns; the FP64 H Q on
+# its 64 x 16 tile) have no capture, so its "traffic" stays null and these
+# figures ride along as context.
 NCU_TRAFFIC = {
-    "zgemm_split_kernel": {"case": "N=4000, 480 real columns, full-width degree step",
-                           "dram_bytes": 588.6e6 + 41.9e6, "algorithmic_bytes": 548e6},
+    "zgemm_split_kernel": {"case": "N=8000, 1500 complex columns, full-width degree step of the "
+                                   "persistent kernel (the sequence workload's blocks are narrower)",
+                           "dram_bytes": 12.25e9 + 0.191e9, "algorithmic_bytes": 2.656e9},
     "zgemm_tma_kernel": {"case": "N=4000, 240 columns, FP64 filter step on the 64 x 8 tile that "
                                  "the host picks there (the N=8000 Rayleigh-Ritz H Q of 480 "
                                  "columns takes 64 x 16)",
