@@ -600,12 +600,13 @@ def filter_workload_config(args, world):
 
 
 # DRAM traffic of one zgemm_split_kernel launch of the default filter
-# workload (one of its two K segments: 30000 rows of H, 1500 complex
-# columns, K = 30000), measured with ncu on the persistent-CTA kernel
-# (dram__bytes_read.sum 265.45 GB + dram__bytes_write.sum 0.72 GB, one
+# workload (one of its four K segments: 30000 rows of H, 1500 complex
+# columns, K = 15000), measured with ncu on the persistent-CTA kernel
+# (dram__bytes_read.sum 58.80 GB + dram__bytes_write.sum 0.72 GB, one
 # pass, --clock-control none; the command is in the profile of this
-# kernel).  Set back to None whenever the kernel changes.
-SPLIT_N30000_TRAFFIC = 265.45e9 + 0.72461e9
+# kernel).  Set back to None whenever the kernel or its launch shape
+# changes.
+SPLIT_N30000_TRAFFIC = 58.80e9 + 0.72087e9
 
 
 def split_algorithmic_bytes(n, ncols, k_per_launch):

@@ -1035,9 +1035,19 @@ namespace {
 // 3 pairs, 3 * K * 127^2 < 2^31 gives K < 44380.
 constexpr int kMaxKBlocksPerSegment = 44000 / split::BK;
 
+// K blocks one launch streams at most (K = 16000).  Resident CTAs share
+// operand slabs in L2 only while their K positions stay close, and they
+// drift apart over a tile's K range: at K = 30000 per launch (N = 30000,
+// 1500 columns) a launch read 18x its algorithmic bytes from DRAM, at
+// K = 16000 (N = 8000) 4.6x.  Longer products therefore run as K segments
+// of at most this length, their FP64 partial products summed by the
+// combine kernel.
+constexpr int kStreamKBlocks = 1000;
+
 // nkb K blocks, `tiles` output tiles per segment
 int segments_for(int64_t nkb, int64_t tiles) {
-  int nseg = static_cast<int>((nkb + kMaxKBlocksPerSegment - 1) / kMaxKBlocksPerSegment);
+  const int64_t cap = std::min<int64_t>(kMaxKBlocksPerSegment, kStreamKBlocks);
+  int nseg = static_cast<int>((nkb + cap - 1) / cap);
   // Narrow blocks leave SMs idle: split K until the grid covers the SMs,
   // keeping every segment at least 64 K blocks long.  (Splitting wider
   // grids to trim the last wave costs more in the combine pass and the
