@@ -1040,6 +1040,15 @@ int solver_handle(Dev& d) {
       set_error("cusolverDnCreate failed");
       return CHASE_EIGENSOLVER_ERROR;
     }
+    // Deterministic results are cuSOLVER's default; stated here so that a
+    // change of that default cannot make two identical solves diverge.
+    if (cusolverDnSetDeterministicMode(t_solver, CUSOLVER_DETERMINISTIC_RESULTS) !=
+        CUSOLVER_STATUS_SUCCESS) {
+      cusolverDnDestroy(t_solver);
+      t_solver = nullptr;
+      set_error("cusolverDnSetDeterministicMode failed");
+      return CHASE_EIGENSOLVER_ERROR;
+    }
   }
   if (cusolverDnSetStream(t_solver, d.st) != CUSOLVER_STATUS_SUCCESS) {
     set_error("cusolverDnSetStream failed");
@@ -1147,17 +1156,7 @@ int eigh_device(Dev& d, float* G, int64_t ldg, int p, double* w_dev) {
 
 int eigh_device(Dev& d, chase_c64* G, int64_t ldg, int p, double* w_dev) {
   if (p == 0) return CHASE_OK;
-  if (!t_solver) {
-    if (cusolverDnCreate(&t_solver) != CUSOLVER_STATUS_SUCCESS) {
-      t_solver = nullptr;
-      set_error("cusolverDnCreate failed");
-      return CHASE_EIGENSOLVER_ERROR;
-    }
-  }
-  if (cusolverDnSetStream(t_solver, d.st) != CUSOLVER_STATUS_SUCCESS) {
-    set_error("cusolverDnSetStream failed");
-    return CHASE_EIGENSOLVER_ERROR;
-  }
+  CHASE_TRY(solver_handle(d));
   int lwork = 0;
   if (cusolverDnZheevd_bufferSize(t_solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, p,
                                   reinterpret_cast<cuDoubleComplex*>(G), static_cast<int>(ldg),
@@ -1175,14 +1174,7 @@ int eigh_device(Dev& d, chase_c64* G, int64_t ldg, int p, double* w_dev) {
     set_error("cusolverDnZheevd failed to launch");
     return CHASE_EIGENSOLVER_ERROR;
   }
-  int h_info = 0;
-  CHASE_CUDA(cudaMemcpyAsync(&h_info, info, sizeof(int), cudaMemcpyDeviceToHost, d.st));
-  CHASE_CUDA(cudaStreamSynchronize(d.st));
-  if (h_info != 0) {
-    set_error("zheevd returned info = %d", h_info);
-    return CHASE_EIGENSOLVER_ERROR;
-  }
-  return CHASE_OK;
+  return eigh_info(d, info, "zheevd");
 }
 
 }  // namespace chase

@@ -191,6 +191,12 @@ __device__ __forceinline__ void zgemm_tile_body(const Fp64Tile& T, int* __restri
           dmma_8x8x4(t3[mi][ni][0], t3[mi][ni][1], as[mi], bs[ni]);
         }
     }
+    // The stage was read through the generic proxy and the producer's next
+    // TMA copy overwrites it through the async proxy: order the reads first.
+    // Without this fence a copy could land before the last loads of a warp
+    // had returned whenever the SM's load pipe was busy (other kernels on the
+    // device), corrupting 8 x 8 fragments of the product.
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
   }
@@ -318,6 +324,12 @@ __device__ __forceinline__ void dgemm_tile_body(const Fp64Tile& T, int* __restri
 #pragma unroll
         for (int ni = 0; ni < C::NI; ++ni) dmma_8x8x4(acc[mi][ni][0], acc[mi][ni][1], af[mi], bf[ni]);
     }
+    // The stage was read through the generic proxy and the producer's next
+    // TMA copy overwrites it through the async proxy: order the reads first.
+    // Without this fence a copy could land before the last loads of a warp
+    // had returned whenever the SM's load pipe was busy (other kernels on the
+    // device), corrupting 8 x 8 fragments of the product.
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
   }
