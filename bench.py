@@ -249,10 +249,10 @@ NCU_TRAFFIC = {
     "zgemm_split_kernel": {"case": "N=8000, 1500 complex columns, full-width degree step of the "
                                    "persistent kernel (the sequence workload's blocks are narrower)",
                            "dram_bytes": 12.25e9 + 0.191e9, "algorithmic_bytes": 2.656e9},
-    "zgemm_tma_kernel": {"case": "N=4000, 240 columns, FP64 filter step on the 64 x 8 tile that "
-                                 "the host picks there (the N=8000 Rayleigh-Ritz H Q of 480 "
-                                 "columns takes 64 x 16)",
-                         "dram_bytes": 2989.5e6 + 18.1e6, "algorithmic_bytes": 301e6},
+    "zgemm_tma_kernel": {"case": "N=4000, 64 columns, first product of a degree-2 FP64 filter on "
+                                 "the 64 x 32 tile that the host picks there (the N=8000 "
+                                 "Rayleigh-Ritz H Q of 480 columns takes 64 x 16)",
+                         "dram_bytes": 263.4e6 + 3.4e6, "algorithmic_bytes": 264e6},
 }
 
 
