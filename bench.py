@@ -93,6 +93,11 @@ def parse():
                    help="filter workload: skip the cold solve")
     p.add_argument("--solve-deg-extra", type=int, default=None,
                    help="filter workload: DEGEXTRA of the cold solve")
+    p.add_argument("--deg-max", type=int, default=None,
+                   help="DEGMAX of Alg. 5 for the sequence, serve and batched-solve workloads "
+                        "(default: 64 with a split filter, Table 1's 36 with FP64)")
+    p.add_argument("--solve-deg-max", type=int, default=None,
+                   help="filter workload: DEGMAX of the cold solve (default 64)")
     args = p.parse_args()
     big = args.workload in ("filter", "solve")
     if args.n is None:
@@ -368,6 +373,29 @@ SPLIT_DEG_EXTRA = 6
 # (measured; Rayleigh-Ritz's FP64 H Q, about 5.6 s per iteration there,
 # is what fewer iterations save).
 COLD_SOLVE_DEG_EXTRA = 10
+# DEGMAX of Alg. 5 (Table 1: 36) for solves with the split filter.  Higher
+# caps let far-from-converged columns take the degree that converges them in
+# one more iteration; each saved iteration saves an FP64 Rayleigh-Ritz and QR
+# (measured: N = 8000 sequence 2.47 s / 9 iterations per warm solve with 36,
+# 1.94 s / 6 with 64, 1.71 s / 4-5 with 96; cold N = 30000 solve 160 s / 13
+# with 36, 139 s / 10 with 48, 135 s / 9 with 64, 129 s / 7 with 96; the
+# 512-problem batched solve 10.1 s with 36, 9.9 s with 64).  The cap also
+# guards rank deficiency of the filtered block (Sec. 4.1.3): at 96 the
+# batched solve's Cholesky QR needed its shifted retries (QR 6.5 s against
+# 1.1 s) and at 128 it broke down, so the split path takes 64 and the FP64
+# path keeps Table 1's 36.
+SPLIT_DEG_MAX = 64
+
+
+def deg_max_for(args, precision_code):
+    """DEGMAX of Alg. 5 for a workload's solves: --deg-max, else SPLIT_DEG_MAX
+    with a split filter and the library's default (Table 1) with FP64."""
+    from paper_1805_10121_gb300 import chase
+    if getattr(args, "deg_max", None) is not None:
+        return int(args.deg_max)
+    if precision_code == chase.CHASE_FP64:
+        return int(chase.chase_opts_default().deg_max)
+    return SPLIT_DEG_MAX
 
 
 def deg_extra_for(args, precision_code):
@@ -765,6 +793,7 @@ def run_filter_workload(args, rank, world, local):
         Vs = synth.gaussian_block(n, nx, seed + 11, device=dev)
         S = synth.gaussian_block(n, 5, seed + 8, device=dev)
         o = chase.chase_opts_default(precision=split, deg_extra=de)
+        o.deg_max = int(args.solve_deg_max) if args.solve_deg_max is not None else SPLIT_DEG_MAX
         chase.chase_kernel_timing(True)
         torch.cuda.synchronize()
         s0 = torch.cuda.Event(enable_timing=True)
@@ -788,7 +817,7 @@ def run_filter_workload(args, rank, world, local):
                                  "FP64 filter rate measured above (same iterations: every other "
                                  "step is the same FP64 code)"}
         solve = {"status": st, "seconds": round(ts, 2), "iterations": ss["iterations"],
-                 "deg_extra": de,
+                 "deg_extra": de, "deg_max": int(o.deg_max),
                  "resid_max_over_norm": float(np.max(res[:nev])) / hnorm,
                  "eig_err_max_over_norm": float(np.max(np.abs(ritz[:nev] - l[:nev]))) / hnorm,
                  "phase_seconds": {k2: round(ss[k2], 2) for k2 in
@@ -1001,7 +1030,8 @@ def run_batched_solve_workload(args, rank, world, local):
     nevs = [s[1] for s in shapes]
     nexs = [s[2] for s in shapes]
     prec = prec_code(args.precision)
-    o = chase.chase_opts_default(precision=prec, deg_extra=deg_extra_for(args, prec))
+    o = chase.chase_opts_default(precision=prec, deg_extra=deg_extra_for(args, prec),
+                                 deg_max=deg_max_for(args, prec))
 
     def batched(idx):
         Vs = [V0s[i].clone() for i in idx]
@@ -1388,7 +1418,8 @@ def run_solve_workload(args, rank, world, local):
         nxw = max(ns + 1, nw * nx // n)
         chase.chase_solve(Hw, ns, nxw - ns, tol, synth.gaussian_block(nw, nxw, seed + 51, device=dev),
                           synth.gaussian_block(nw, 5, seed + 52, device=dev),
-                          opts=chase.chase_opts_default(precision=prec, deg_extra=de))
+                          opts=chase.chase_opts_default(precision=prec, deg_extra=de,
+                                                        deg_max=deg_max_for(args, prec)))
     del Hw
     H, lam = problem(n, seed)
     hnorm = float(np.abs(lam).max())
@@ -1405,8 +1436,9 @@ def run_solve_workload(args, rank, world, local):
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
         st, ritz, res, s = chase.chase_solve(H, nev, nex, tol, V, S,
-                                             opts=chase.chase_opts_default(precision=prec,
-                                                                           deg_extra=de))
+                                             opts=chase.chase_opts_default(
+                                                 precision=prec, deg_extra=de,
+                                                 deg_max=deg_max_for(args, prec)))
         b.record(stream)
         torch.cuda.synchronize()
         t = a.elapsed_time(b) / 1e3
@@ -1455,7 +1487,8 @@ def run_serve_workload(args, rank, world, local):
     trace = serve.poisson_trace(args.serve_requests, args.serve_rate, args.seed + 1000 * rank,
                                 sizes=sizes, weights=weights)
     fp = lambda r: serve.footprint_bytes(r.n, r.nev, r.nex, split)
-    solver = serve.gpu_sequence_solver(dev, prec, tol=args.tol, deg_extra=deg_extra_for(args, prec))
+    solver = serve.gpu_sequence_solver(dev, prec, tol=args.tol, deg_extra=deg_extra_for(args, prec),
+                                       deg_max=deg_max_for(args, prec))
     # warm-up: one small request (library load, handles, kernels)
     small = serve.Request(-1, min(sizes), int(np.ceil(0.04 * min(sizes))),
                           int(np.ceil(0.008 * min(sizes))), 2, 99, 0.0)
@@ -1479,6 +1512,7 @@ def run_serve_workload(args, rank, world, local):
                        f"nex = 20% nev, admission cap {args.serve_cap_gb} GB, "
                        f"{args.serve_slots} slots; step = the whole trace")
     cfg["deg_extra"] = deg_extra_for(args, prec)
+    cfg["deg_max"] = deg_max_for(args, prec)
     line = {
         "metric": METRIC, "value": round(flops / wall / 1e12, 3), "unit": "TFLOP/s",
         "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": round(1e3 * wall, 1),
@@ -1557,7 +1591,7 @@ def main():
     def solve(k, Vb, Lamb, precision=None):
         p = prec if precision is None else precision
         o = chase.chase_opts_default(approx=0 if k == 0 else 1, precision=p,
-                                     deg_extra=deg_extra_for(args, p))
+                                     deg_extra=deg_extra_for(args, p), deg_max=deg_max_for(args, p))
         S = starts if k == 0 else starts[:, :1].contiguous()
         return chase.chase_solve(seq[k], nev, nex, tol, Vb, S, Lambda=Lamb, opts=o)
 
@@ -1655,7 +1689,8 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         o = chase.chase_opts_default(approx=1, precision=prec,
-                                     deg_extra=deg_extra_for(args, prec))
+                                     deg_extra=deg_extra_for(args, prec),
+                                     deg_max=deg_max_for(args, prec))
         st_e, lam_e, res_e, s_e = chase.chase_solve(Hh, nev, nex, tol, Vh, Sh,
                                                     Lambda=Lam_before, opts=o)
         t_e2e = time.perf_counter() - t0
@@ -1690,7 +1725,8 @@ def main():
         "vs_baseline": None,
         "dtype": "bf16-split+f64" if args.precision != "fp64" else "f64",
         "data": "synthetic",
-        "config": dict(workload_config(args, world), deg_extra=deg_extra_for(args, prec)),
+        "config": dict(workload_config(args, world), deg_extra=deg_extra_for(args, prec),
+                       deg_max=deg_max_for(args, prec)),
         "s_per_solve": round(t_max / K, 3),
         "filter_tflops": round(filt_fl / filt_t / 1e12, 4) if filt_t > 0 else None,
         "filter_share_of_time": round(filt_t / max(elapsed, 1e-12), 4),

@@ -207,12 +207,13 @@ class Server:
 
 
 def gpu_sequence_solver(device, precision: int, tol: float = 1e-10, seq_scale: float = 1e-3,
-                        keep_last_h: bool = False, deg_extra: Optional[int] = None):
+                        keep_last_h: bool = False, deg_extra: Optional[int] = None,
+                        deg_max: Optional[int] = None):
     """solve_fn for Server: builds the request's sequence on the slot's
     stream and solves it problem after problem with warm starts.  With
     ``keep_last_h`` the result also carries the last problem's H on the host
-    (for checks against its exact spectrum).  ``deg_extra`` overrides
-    DEGEXTRA of Alg. 5 (Table 1: 2)."""
+    (for checks against its exact spectrum).  ``deg_extra`` and ``deg_max``
+    override DEGEXTRA and DEGMAX of Alg. 5 (Table 1: 2 and 36)."""
     import torch
 
     from . import chase, synth
@@ -241,6 +242,8 @@ def gpu_sequence_solver(device, precision: int, tol: float = 1e-10, seq_scale: f
                 o = chase.chase_opts_default(approx=0 if k == 0 else 1, precision=precision)
                 if deg_extra is not None:
                     o.deg_extra = int(deg_extra)
+                if deg_max is not None:
+                    o.deg_max = int(deg_max)
                 st, Lam, res, stats = chase.chase_solve(
                     H, req.nev, req.nex, tol, V, S if k == 0 else S[:, :1].contiguous(),
                     Lambda=Lam, opts=o, stream=s.cuda_stream)
