@@ -60,6 +60,22 @@ def test_degrees_match_oracle_random(lib):
     assert list(ed) == [36, 36, 36, 36]
 
 
+@pytest.mark.parametrize("deg_extra,deg_max", [(6, 64), (10, 64), (6, 63), (10, 96)])
+def test_degrees_match_oracle_raised_caps(lib, deg_extra, deg_max):
+    # the split-filter solves raise DEGEXTRA and DEGMAX above Table 1's 2 and
+    # 36; an odd cap exercises the even rounding after the clamp (Alg. 5)
+    rng = np.random.default_rng(deg_extra * 1000 + deg_max)
+    n = 3000
+    ritz = rng.uniform(-3.0, 2.0, n)
+    res = 10 ** rng.uniform(-14, 1, n)
+    c, e, tol = 0.4, 0.8, 1e-10
+    got = chase.chase_degrees(res, ritz, c, e, tol, deg_extra, deg_max)
+    ref = oracle.degrees(res, ritz, c, e, tol, deg_extra, deg_max)
+    assert np.array_equal(got, ref)
+    assert np.all(got % 2 == 0) and got.max() <= deg_max
+    assert np.any(got > 36)  # the raised cap is reached by some columns
+
+
 def test_lock_matches_oracle(lib):
     rng = np.random.default_rng(9)
     for _ in range(200):

@@ -304,6 +304,27 @@ def test_solve_single_problem_1000():
     assert stats["filter_matvecs"] > 0 and stats["iterations"] >= 1
 
 
+@pytest.mark.parametrize("precision", [chase.CHASE_FP64, chase.CHASE_SPLIT_BF16])
+def test_solve_raised_degree_caps_match_oracle(precision):
+    # DEGEXTRA 6 and DEGMAX 64, the caps of the benchmarked split-filter
+    # solves: the same eigenpairs as the oracle's solve with the same caps,
+    # in the same number of iterations (the degrees follow Alg. 5 exactly)
+    n, nev, nex, tol = 1000, 50, 20, 1e-10
+    H, lam, _ = known_h(n, 145, n_cluster=60)
+    V0 = synth.gaussian_block(n, nev + nex, 146)
+    S = synth.gaussian_block(n, 5, 147)
+    Vd = dcol(V0)
+    o = chase.chase_opts_default(precision=precision, deg_extra=6, deg_max=64)
+    st, ritz, resid, stats = chase.chase_solve(dcol(H), nev, nex, tol, Vd, dcol(S), opts=o)
+    assert st == chase.CHASE_OK
+    Hn = H.numpy()
+    check_solution(Hn, lam.numpy(), ritz, resid, Vd.cpu().numpy(), nev, tol)
+    ref = oracle.solve(Hn, nev, nex, V0.numpy(), S.numpy(), tol=tol, deg_extra=6, deg_max=64)
+    assert ref["converged"]
+    assert np.max(np.abs(ritz[:nev] - ref["ritz"][:nev])) <= EIG_RTOL
+    assert abs(stats["iterations"] - ref["iterations"]) <= 1
+
+
 def test_solve_host_arrays_equal_device():
     n, nev, nex, tol = 300, 12, 6, 1e-10
     H, lam, _ = known_h(n, 151)
