@@ -161,29 +161,9 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def warm_eigensolver(dev, widths, seed=77):
-    """Run Rayleigh-Ritz (its projected eigensolve) once at each width and at
-    widths below it down to 16 (factor sqrt 2), outside any timed region.
-    On a fresh machine the first eigensolve of a size class costs seconds
-    (measured: 9.5 s for the first 1500 x 1500 solve of a process, 0.32 s
-    for every later one) while the toolkit's solver prepares its kernels for
-    the device; a timed solve should not pay that."""
-    from paper_1805_10121_gb300 import chase, synth
-    ws = set()
-    for w in widths:
-        w = float(w)
-        while w >= 16:
-            ws.add(int(w))
-            w /= 1.4142
-    for w in sorted(ws, reverse=True):
-        n = max(2 * w, 64)
-        lam = synth.spectrum_uniform(n, seed, device=dev)
-        H = synth.hermitian_dft(lam, seed + 1)
-        Q = synth.gaussian_block(n, w, seed + 2, device=dev).t().contiguous().t()
-        chase.chase_orthonormalize(None, Q)
-        chase.chase_rayleigh_ritz(H, Q)
-        del H, Q
-    torch.cuda.synchronize()
+def warm_eigensolver(dev, widths):
+    from paper_1805_10121_gb300 import serve
+    serve.warm_eigensolver(dev, widths)
 
 
 class ClockSampler:

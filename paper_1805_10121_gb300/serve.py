@@ -28,7 +28,7 @@ from typing import Callable, List, Optional
 import numpy as np
 
 __all__ = ["Request", "Result", "poisson_trace", "footprint_bytes", "Server", "gpu_sequence_solver",
-           "percentile"]
+           "percentile", "warm_eigensolver"]
 
 
 @dataclasses.dataclass(frozen=True)
@@ -259,3 +259,32 @@ def gpu_sequence_solver(device, precision: int, tol: float = 1e-10, seq_scale: f
                 "resid_max_over_norm": rmax, "flops": flops, "last_h": last}
 
     return solve
+
+
+def warm_eigensolver(device, widths, seed: int = 77):
+    """Run Rayleigh-Ritz (and so its projected eigensolve) once at each width
+    and at the widths below it down to 16 (factor sqrt 2).  On a fresh
+    machine the first eigensolve of a size class in a process costs seconds
+    (measured on GB300: 9.5 s for the first 1500 x 1500 solve, 0.32 s for
+    every later one) while the solver prepares its kernels for the device;
+    a server calls this once at start-up with the widths (nev + nex) it
+    expects, so that no request pays that cost."""
+    import torch
+
+    from . import chase, synth
+
+    ws = set()
+    for w in widths:
+        w = float(w)
+        while w >= 16:
+            ws.add(int(w))
+            w /= 1.4142
+    for w in sorted(ws, reverse=True):
+        n = max(2 * w, 64)
+        lam = synth.spectrum_uniform(n, seed, device=device)
+        H = synth.hermitian_dft(lam, seed + 1)
+        Q = synth.gaussian_block(n, w, seed + 2, device=device).t().contiguous().t()
+        chase.chase_orthonormalize(None, Q)
+        chase.chase_rayleigh_ritz(H, Q)
+        del H, Q
+    torch.cuda.synchronize(device)

@@ -62,3 +62,12 @@ def test_served_request_matches_the_oracle():
     ref = oracle.solve(H, req.nev, req.nex, V, S, tol=1e-10)
     hn = float(np.abs(np.linalg.eigvalsh(H)).max())
     assert np.max(np.abs(res.ritz[-1] - ref["ritz"][:req.nev])) <= EIG_RTOL * hn
+
+
+def test_warm_eigensolver_runs_every_size_class():
+    # the start-up warm-up: one Rayleigh-Ritz per width from 100 down to 16
+    dev = torch.device("cuda:0")
+    n0 = chase.chase_kernel_launches()
+    serve.warm_eigensolver(dev, [100])
+    # widths 100, 70, 50, 35, 25, 17: six Rayleigh-Ritz calls, each several launches
+    assert chase.chase_kernel_launches() - n0 >= 6
