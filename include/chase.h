@@ -26,6 +26,11 @@
  * - Every entry point returns a CHASE_* status; none aborts or throws.  On a
  *   status other than CHASE_OK or CHASE_NOT_CONVERGED, chase_last_error()
  *   returns a message for the calling thread.
+ * - Calls may run at the same time from several host threads on different
+ *   streams (each thread keeps its own eigensolver handle); their results
+ *   are bit-identical to the same calls run one at a time, whatever else
+ *   runs on the device.  Calls that share an output array must be ordered
+ *   by the caller.
  */
 #ifndef CHASE_H_
 #define CHASE_H_
@@ -110,7 +115,10 @@ typedef struct {
   int deg;          /* initial / constant degree (Table 1: 20); rounded up to even */
   int optim;        /* 1: per-column optimised degrees (Alg. 5); 0: constant deg (Table 1: false) */
   int deg_extra;    /* DEGEXTRA of Alg. 5 line 5 (Table 1: 2) */
-  int deg_max;      /* DEGMAX of Alg. 5 line 5 (Table 1: 36) */
+  int deg_max;      /* DEGMAX of Alg. 5 line 5 (Table 1: 36; with a split-BF16 filter
+                       higher caps, e.g. 64, trade cheap filter steps for FP64
+                       iterations; the cap also guards rank deficiency of the
+                       filtered block, Sec. 4.1.3) */
   int max_iter;     /* cap on the while loop of Alg. 1 (Table 1: 25) */
   int lanczos_iter; /* k, steps of each Lanczos run (Table 1: 25) */
   int num_lanczos;  /* n_vec, density runs of Alg. 6 (Table 1: 4) */
