@@ -85,6 +85,10 @@ def parse():
     p.add_argument("--serve-slots", type=int, default=4)
     p.add_argument("--serve-cap-gb", type=float, default=150.0)
     p.add_argument("--serve-sizes", default="2048,4096,8192,16384")
+    p.add_argument("--serve-policy", default="fifo", choices=["fifo", "sjf"],
+                   help="admission order of waiting requests: arrival, or shortest job first")
+    p.add_argument("--serve-max-wait", type=float, default=None,
+                   help="sjf: seconds after which a waiting request goes ahead of newer ones")
     p.add_argument("--no-fp64-compare", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -1512,7 +1516,8 @@ def run_serve_workload(args, rank, world, local):
     launches0 = chase.chase_kernel_launches()
     clocks.start()
     t0 = time.perf_counter()
-    srv = serve.Server(solver, args.serve_cap_gb * 1e9, args.serve_slots, fp)
+    srv = serve.Server(solver, args.serve_cap_gb * 1e9, args.serve_slots, fp,
+                       policy=args.serve_policy, max_wait_s=args.serve_max_wait)
     res = srv.run(trace)
     wall = time.perf_counter() - t0
     clk = clocks.stop()
@@ -1524,7 +1529,8 @@ def run_serve_workload(args, rank, world, local):
     cfg["workload"] = (f"serving: {len(trace)} sequence-solve requests, Poisson {args.serve_rate}/s, "
                        f"N in {sizes} weighted {weights}, 5-10 problems each, nev = 4% N, "
                        f"nex = 20% nev, admission cap {args.serve_cap_gb} GB, "
-                       f"{args.serve_slots} slots; step = the whole trace")
+                       f"{args.serve_slots} slots, admission {args.serve_policy}; "
+                       f"step = the whole trace")
     cfg["deg_extra"] = deg_extra_for(args, prec)
     cfg["deg_max"] = deg_max_for(args, prec)
     line = {

@@ -8,9 +8,10 @@ stay resident on the device for the request's lifetime.
 
 Continuous batching: requests arrive over time (a seeded Poisson trace);
 the dispatcher admits a waiting request as soon as a slot is free and its
-estimated device footprint fits under the memory cap (first fit in arrival
-order, so a large request at the head does not block smaller ones behind
-it).  Every slot owns a CUDA stream and a host thread; the solves of
+estimated device footprint fits under the memory cap (first fit, so a
+large request at the head does not block smaller ones behind it; waiting
+requests are taken in arrival order, or shortest job first with an aging
+limit).  Every slot owns a CUDA stream and a host thread; the solves of
 admitted requests run concurrently and overlap on the device.  Every step
 of every solve runs in libchase's kernels through the C ABI; this module
 only schedules, generates inputs and records latencies.
@@ -106,19 +107,37 @@ def percentile(xs, q):
     return float(np.percentile(np.asarray(xs, dtype=float), q))
 
 
+def work_estimate(r: Request) -> float:
+    """Relative cost of a request for shortest-job-first admission: its
+    problems times the N^2 (nev + nex) of one filter product."""
+    return float(r.nprob) * float(r.n) ** 2 * float(r.nev + r.nex)
+
+
 class Server:
     """Admission by device footprint, slots with their own streams and threads.
 
     ``solve_fn(request, slot) -> Result-like dict`` runs one whole request
     (all its problems) on the slot's stream; it is injected so that the
-    scheduling logic can be exercised without a GPU."""
+    scheduling logic can be exercised without a GPU.
+
+    ``policy`` orders the waiting requests for first-fit admission:
+    ``"fifo"`` by arrival, ``"sjf"`` by ``cost_fn`` (shortest job first),
+    except that a request that has waited ``max_wait_s`` seconds or more
+    goes ahead of every request that has not (no request starves)."""
 
     def __init__(self, solve_fn: Callable, mem_cap_bytes: float, max_slots: int,
-                 footprint_fn: Callable[[Request], int]):
+                 footprint_fn: Callable[[Request], int], policy: str = "fifo",
+                 cost_fn: Callable[[Request], float] = work_estimate,
+                 max_wait_s: Optional[float] = None):
+        if policy not in ("fifo", "sjf"):
+            raise ValueError(f"unknown admission policy {policy!r}")
         self.solve_fn = solve_fn
         self.mem_cap = float(mem_cap_bytes)
         self.max_slots = int(max_slots)
         self.footprint_fn = footprint_fn
+        self.policy = policy
+        self.cost_fn = cost_fn
+        self.max_wait_s = max_wait_s
         self._cv = threading.Condition()
         self._waiting: List[Request] = []
         self._mem_used = 0.0
@@ -133,11 +152,27 @@ class Server:
     def _now(self) -> float:
         return time.perf_counter() - self._t0
 
+    def _order_locked(self):
+        """Indices into the waiting list in admission order."""
+        idx = list(range(len(self._waiting)))
+        if self.policy == "fifo":
+            return idx
+        now = self._now()
+
+        def key(i):
+            r = self._waiting[i]
+            aged = self.max_wait_s is not None and now - r.arrival >= self.max_wait_s
+            # aged requests first (oldest first), then the cheapest
+            return (0, r.arrival, 0.0) if aged else (1, 0.0, self.cost_fn(r))
+
+        return sorted(idx, key=key)
+
     def _admit_locked(self):
-        """First fit in arrival order; returns (request, slot) or None."""
+        """First fit in the policy's order; returns (request, slot) or None."""
         if not self._free_slots:
             return None
-        for i, r in enumerate(self._waiting):
+        for i in self._order_locked():
+            r = self._waiting[i]
             fp = self.footprint_fn(r)
             if fp > self.mem_cap:
                 raise ValueError(f"request {r.rid} needs {fp} bytes, above the cap")

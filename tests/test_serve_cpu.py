@@ -96,3 +96,32 @@ def test_footprint_grows_with_n_and_split():
     b = serve.footprint_bytes(2048, 82, 17, split=True)
     c = serve.footprint_bytes(4096, 164, 33, split=True)
     assert b > a and c > 3 * b
+
+
+def _start_order(policy, max_wait_s=None):
+    log = []
+    dur = {0: 0.25, 1: 0.02, 2: 0.02}
+    srv = serve.Server(fake_solver(lambda r: dur[r.rid], log), 1e12, 1,
+                       lambda r: 1, policy=policy, max_wait_s=max_wait_s)
+    # request 0 holds the only slot while 1 (large) and 2 (small) queue up
+    trace = [mk(0, 64, 0.0), mk(1, 4096, 0.02), mk(2, 256, 0.04)]
+    srv.run(trace)
+    return [rid for ev, rid, _, _ in sorted(log, key=lambda e: e[3]) if ev == "start"]
+
+
+def test_sjf_admits_the_cheapest_waiting_request_first():
+    assert _start_order("fifo") == [0, 1, 2]
+    assert _start_order("sjf") == [0, 2, 1]
+    c = [serve.work_estimate(mk(i, n, 0.0)) for i, n in enumerate((256, 4096))]
+    assert c[0] < c[1]
+
+
+def test_sjf_aging_lets_a_long_waiter_go_first():
+    # both queued requests have waited past max_wait_s when the slot frees:
+    # the older one (the large request) goes first
+    assert _start_order("sjf", max_wait_s=0.05) == [0, 1, 2]
+
+
+def test_unknown_policy_is_rejected():
+    with pytest.raises(ValueError):
+        serve.Server(lambda r, s: {}, 1e9, 1, lambda r: 1, policy="lifo")
