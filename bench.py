@@ -313,7 +313,7 @@ def _fp64_roofline(flops, secs, pk, src, what):
         "frac": round(executed / peak, 4),
         "traffic": None,
         "peak_source": f"{src} bf16_tflops (burst) x nominal FP64/BF16 ratio (1.25/2250); "
-                       "a DMMA-only probe kernel measured 1.05 TFLOP/s on this pool",
+                       "a DMMA-only probe kernel measured 1.05 TFLOP/s on GB300",
         "achieved_counts": "executed DMMA FLOPs (3M form: 6 per 8 algorithmic)",
         "algorithmic_tflops": round(alg, 4),
         "traffic_ncu_small_case": NCU_TRAFFIC["zgemm_tma_kernel"],
