@@ -88,3 +88,16 @@ def test_blas_threads_round_trip():
             assert int(bt.get_fn()) == 1
     if bt.get_fn:
         assert int(bt.get_fn()) == before
+
+
+def test_degree_caps_by_precision():
+    # DEGMAX 64 with a split filter, Table 1's 36 with FP64; --deg-max wins
+    from paper_1805_10121_gb300 import chase
+    args = types.SimpleNamespace(deg_max=None, deg_extra=None)
+    assert bench.deg_max_for(args, chase.CHASE_SPLIT_BF16) == bench.SPLIT_DEG_MAX == 64
+    assert bench.deg_max_for(args, chase.CHASE_FP64) == chase.chase_opts_default().deg_max == 36
+    assert bench.deg_extra_for(args, chase.CHASE_FP64) == 2
+    assert bench.deg_extra_for(args, chase.CHASE_SPLIT_BF16) == bench.SPLIT_DEG_EXTRA
+    args = types.SimpleNamespace(deg_max=48, deg_extra=4)
+    assert bench.deg_max_for(args, chase.CHASE_FP64) == 48
+    assert bench.deg_extra_for(args, chase.CHASE_SPLIT_BF16) == 4
