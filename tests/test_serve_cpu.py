@@ -125,3 +125,25 @@ def test_sjf_aging_lets_a_long_waiter_go_first():
 def test_unknown_policy_is_rejected():
     with pytest.raises(ValueError):
         serve.Server(lambda r, s: {}, 1e9, 1, lambda r: 1, policy="lifo")
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_sjf_on_random_traces(seed):
+    rng = np.random.default_rng(seed)
+    trace = [mk(i, int(rng.choice([64, 256, 1024, 4096])), 0.0, nprob=int(rng.integers(1, 6)))
+             for i in range(12)]
+    # one slot, everything waiting from the start: starts in order of cost
+    log = []
+    serve.Server(fake_solver(lambda r: 0.002, log), 1e12, 1, lambda r: 1,
+                 policy="sjf").run(trace, realtime=False)
+    starts = [rid for ev, rid, _, _ in sorted(log, key=lambda e: e[3]) if ev == "start"]
+    costs = [serve.work_estimate(trace[rid]) for rid in starts]
+    assert sorted(starts) == list(range(12))
+    assert costs == sorted(costs)
+    # three slots under a memory cap: caps hold and every request finishes
+    log = []
+    srv = serve.Server(fake_solver(lambda r: 0.002 * r.nprob, log), 10.0, 3,
+                       lambda r: 1 + (r.n >= 1024) * 3, policy="sjf")
+    res = srv.run(trace, realtime=False)
+    assert [r.rid for r in res] == list(range(12))
+    assert srv.peak_concurrency <= 3 and srv.peak_mem <= 10.0
